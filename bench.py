@@ -1,0 +1,413 @@
+"""Benchmark of the GE solver on the single large 1D solve:
+N = 2^24 interior points, r = 2, 10000 GE steps, zero walls, u0 = eight seeded
+sine modes.  One benchmark step = one full solve (reset the state, advance
+10000 steps) through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision f64|f32|f32c] [--kernel temporal|onestep|canonical]
+                    [--depth D] [--no-variants] [--no-cpu]
+
+Prints one JSON line (rank 0).  Under torchrun every rank solves its own
+independent problem of the same size (weak scaling, no collective on the
+data path); `value` is the updates of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GE grid-point updates/s & HBM-roofline fraction; surrogate speedup at 1e-3 err"
+UNIT = "grid-point updates/s"
+N_POINTS = 1 << 24
+R = 2.0
+GE_STEPS = 10000
+WORKLOAD = ("single large 1D GE solve: N=2^24 interior points, r=2.0, 10000 steps, Dirichlet zero "
+            "walls, u0 = sum of 8 seeded sine modes k in [1,64], amplitudes U(-1,1)")
+CPU_SAMPLE_STEPS = 100     # oracle baseline: 100 GE steps over the full grid
+REF_SAMPLE_STEPS = 10      # --impl reference: 10 GE steps over the full grid per step
+N_SAMPLES = 12             # oracle-checked sample points
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), float(pk.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+# FP64 / FP32 FMA lanes per SM per clock on GB300 (152 SMs): FP64 1.25 TFLOP/s
+# nominal at 2.07 GHz is 2 FMA/clk/SM; FP32 is 128 FMA/clk/SM.
+SMS = 152
+FMA_PER_CLK = {"f64": 2.0, "f32": 128.0, "f32c": 128.0}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def sample_indices(n):
+    rng = np.random.default_rng(20240613)
+    return sorted(set([0, 1, n // 2, n - 2, n - 1] + [int(i) for i in rng.integers(0, n, N_SAMPLES - 5)]))
+
+
+def oracle_reference(u0, idx):
+    import oracle
+    return oracle.sample(u0, R, 0.0, 0.0, GE_STEPS, idx)
+
+
+def errors(got, want, scale):
+    d = np.asarray(got, dtype=np.float64) - want
+    return {"max_rel_err": float(np.max(np.abs(d)) / scale),
+            "l2_rel_err": float(np.linalg.norm(d) / max(1e-300, np.linalg.norm(want))),
+            "samples": int(len(want)), "reference": "CPU FP64 oracle on dependency-cone windows"}
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the oracle as it stands on the host cores."""
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1310_3422_gb300 import inputs
+    u0 = inputs.sine_modes_state(N_POINTS)
+    oracle.default()
+    u = u0.copy()
+    for _ in range(args.warmup):
+        u = oracle.run(u, R, 0.0, 0.0, REF_SAMPLE_STEPS)
+    t0 = time.perf_counter()
+    step0 = 0
+    for _ in range(args.steps):
+        u = oracle.run(u, R, 0.0, 0.0, REF_SAMPLE_STEPS, step0=step0)
+        step0 += REF_SAMPLE_STEPS
+    dt = time.perf_counter() - t0
+    value = N_POINTS * REF_SAMPLE_STEPS * args.steps / dt
+    sample = f"{REF_SAMPLE_STEPS} GE steps over the full N=2^24 grid per benchmark step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_POINTS, "r": R,
+                                            "ge_steps_per_sample": REF_SAMPLE_STEPS},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_solver(B, torch, ctx, u0_dev, steps, warmup, stream, flush=None):
+    """Per-solve CUDA-event timing on the solver's stream; returns ms per solve."""
+    def one():
+        B.ge_write_state(ctx, u0_dev, 0)
+        B.ge_step_n(ctx, GE_STEPS)
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one()
+        e1.record(stream)
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    return total / steps
+
+
+def measure_e2e(B, torch, u0, prec, kern, depth, steps, world):
+    """The metric through ge_solve with pinned host buffers: every solve
+    copies u0 host->device, advances GE_STEPS and copies the result back."""
+    pin_in = torch.from_numpy(u0.astype(np.float64 if prec == B.GE_F64 else np.float32)).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    hin, hout = pin_in.numpy(), pin_out.numpy()
+    B.ge_solve(N_POINTS, R, 0.0, 0.0, prec, kern, depth, GE_STEPS, hin, hout)
+    k_e2e = max(1, min(steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        B.ge_solve(N_POINTS, R, 0.0, 0.0, prec, kern, depth, GE_STEPS, hin, hout)
+    t_e2e = (time.perf_counter() - t0) / k_e2e
+    return {"value": float(N_POINTS) * GE_STEPS * world / t_e2e, "unit": UNIT,
+            "h2d_bytes_per_step": int(hin.nbytes), "d2h_bytes_per_step": int(hout.nbytes),
+            "ms_per_step": t_e2e * 1e3, "timer": "host wall clock around ge_solve (synchronous)"}
+
+
+def launches_per_solve(kernel, depth):
+    if kernel == "canonical":
+        return GE_STEPS
+    d = 1 if kernel == "onestep" else depth
+    return (GE_STEPS + d - 1) // d
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32", "f32c"])
+    ap.add_argument("--kernel", default="temporal", choices=["temporal", "onestep", "canonical"])
+    ap.add_argument("--depth", type=int, default=0)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    args = ap.parse_args()
+
+    world, rank, local, dist = dist_setup(args)
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+        if dist is not None:
+            dist.destroy_process_group()
+        return rc
+
+    import torch
+    from paper_1310_3422_gb300 import binding as B
+    from paper_1310_3422_gb300 import inputs
+
+    B.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = {"f64": B.GE_F64, "f32": B.GE_F32, "f32c": B.GE_F32_COMP}[args.precision]
+    kern = {"temporal": B.GE_KERNEL_TEMPORAL, "onestep": B.GE_KERNEL_ONESTEP,
+            "canonical": B.GE_KERNEL_CANONICAL}[args.kernel]
+    depth = args.depth or (32 if args.precision == "f64" else 64)
+    hbm_gbs, sm_max_mhz, peak_src = load_peaks()
+
+    u0 = inputs.sine_modes_state(N_POINTS, seed=inputs.SEED_BASE + 1 + rank)
+    dt = B.dtype_of(prec)
+    u0_dev = torch.from_numpy(u0).to(dev, dtype=dt)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        ctx = B.ge_create(N_POINTS, R, 0.0, 0.0, prec, u0_dev, stream=stream)
+        B.ge_set_kernel(ctx, kern, depth)
+
+        # ---- timed region: K full solves --------------------------------
+        for _ in range(args.warmup):
+            B.ge_write_state(ctx, u0_dev, 0)
+            B.ge_step_n(ctx, GE_STEPS)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        with sampler:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                B.ge_write_state(ctx, u0_dev, 0)
+                B.ge_step_n(ctx, GE_STEPS)
+            e1.record(stream)
+            e1.synchronize()
+        torch.cuda.synchronize()
+        elapsed_ms = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([elapsed_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            elapsed_ms = float(t.item())
+            dist.barrier()
+        torch.cuda.synchronize()
+        out = torch.empty_like(u0_dev)
+        B.ge_read_state(ctx, out)
+        B.ge_sync(ctx)
+    got = out.cpu().numpy()
+
+    ms_per_step = elapsed_ms / args.steps
+    updates = float(N_POINTS) * GE_STEPS
+    value = updates * world / (ms_per_step / 1e3)
+    n_launch = launches_per_solve(args.kernel, depth)
+    launch_ms = ms_per_step / n_launch
+
+    if rank != 0:
+        B.ge_destroy(ctx)
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    bytes_per_update = 8 if prec == B.GE_F64 else 4
+    if args.kernel == "canonical":
+        flops_per_update = 8.0    # four multiply-adds, Eqs. (cc)/(dd)
+    elif prec == B.GE_F32_COMP:
+        flops_per_update = 6.0    # normalised block map + Kahan sum, FP32
+    else:
+        flops_per_update = 2.0    # one multiply-add per point and step (right-hand-side form)
+    alu_peak = 2.0 * FMA_PER_CLK[args.precision] * SMS * sm_max_mhz * 1e6  # flop/s
+    if args.kernel == "temporal":
+        achieved = flops_per_update * N_POINTS * (GE_STEPS / n_launch) / (launch_ms / 1e3)
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
+                    "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                    "traffic": None, "peak_source": "derived: %g FMA/clk/SM x %d SMs x %.0f MHz"
+                    % (FMA_PER_CLK[args.precision], SMS, sm_max_mhz),
+                    "kernel": "tb_kernel<%s>" % ("double" if prec == B.GE_F64 else "float")}
+    else:
+        byt = 2.0 * bytes_per_update * N_POINTS
+        achieved = byt / (launch_ms / 1e3)
+        roofline = {"bound": "hbm", "achieved": achieved / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                    "frac": achieved / (hbm_gbs * 1e9), "traffic": None,
+                    "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                    "kernel": "canon_kernel" if args.kernel == "canonical" else "tb_kernel (1 step/launch)"}
+    hbm_roof_updates = hbm_gbs * 1e9 / (2.0 * bytes_per_update)
+
+    # ---- accuracy against the oracle (sampled) ----------------------------
+    idx = sample_indices(N_POINTS)
+    scale = float(np.max(np.abs(u0)))
+    acc, want = None, None
+    if not args.no_accuracy or not args.no_variants:
+        want = oracle_reference(u0, idx)
+        acc = errors(got[idx], want, scale)
+
+    # ---- end to end through the public API with host buffers --------------
+    e2e = {"value": None, "unit": UNIT, "skipped": "--no-e2e"}
+    if not args.no_e2e:
+        try:
+            e2e = measure_e2e(B, torch, u0, prec, kern, depth, args.steps, world)
+        except Exception as exc:  # report, never hide
+            e2e = {"value": None, "unit": UNIT, "error": str(exc)}
+
+    # ---- variants: one-step kernels and FP32 paths -------------------------
+    variants = {}
+    if not args.no_variants:
+        flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+        def flush():
+            flush_buf.fill_(1)
+        for vp, vk, vd in (("f64", "onestep", 1), ("f64", "canonical", 1), ("f32", "temporal", 64),
+                           ("f32c", "temporal", 64), ("f32", "onestep", 1)):
+            if (vp, vk) == (args.precision, args.kernel):
+                continue
+            p2 = {"f64": B.GE_F64, "f32": B.GE_F32, "f32c": B.GE_F32_COMP}[vp]
+            k2 = {"temporal": B.GE_KERNEL_TEMPORAL, "onestep": B.GE_KERNEL_ONESTEP,
+                  "canonical": B.GE_KERNEL_CANONICAL}[vk]
+            x2 = torch.from_numpy(u0).to(dev, dtype=B.dtype_of(p2))
+            with torch.cuda.stream(stream):
+                c2 = B.ge_create(N_POINTS, R, 0.0, 0.0, p2, x2, stream=stream)
+                B.ge_set_kernel(c2, k2, vd)
+                ms = time_solver(B, torch, c2, x2, 2, 1, stream, flush=flush)
+                o2 = torch.empty_like(x2)
+                B.ge_read_state(c2, o2)
+                B.ge_sync(c2)
+                B.ge_destroy(c2)
+            bpu = 8 if p2 == B.GE_F64 else 4
+            upd_s = updates / (ms / 1e3)
+            ent = {"updates_per_s": upd_s, "ms_per_step": ms,
+                   "hbm_roofline_frac_1step": upd_s / (hbm_gbs * 1e9 / (2.0 * bpu)),
+                   "launches_per_step": launches_per_solve(vk, vd)}
+            ent.update(errors(o2.cpu().numpy().astype(np.float64)[idx], want, scale))
+            variants[f"{vp}_{vk}" + (f"_d{vd}" if vk == "temporal" else "")] = ent
+            del x2, o2
+        del flush_buf
+
+    # ---- CPU baseline: the oracle on a bounded sample -----------------------
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.run(u0, R, 0.0, 0.0, CPU_SAMPLE_STEPS)
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": N_POINTS * CPU_SAMPLE_STEPS / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{CPU_SAMPLE_STEPS} GE steps over the full N=2^24 grid (serial FP64 C)",
+               "seconds": t_cpu}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision if args.precision != "f32c" else "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_POINTS, "r": R, "ge_steps": GE_STEPS,
+                   "precision": args.precision, "kernel": args.kernel, "depth": depth,
+                   "parallelism": f"independent problem per GPU x{world}",
+                   "l2": "inputs larger than L2 (two %d MB state buffers); no flush"
+                         % (N_POINTS * bytes_per_update >> 20)},
+        "roofline": roofline,
+        "hbm_roofline_frac_effective": value / world / hbm_roof_updates,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": n_launch * args.steps,
+        "kernel_ms_per_launch": launch_ms,
+        "clocks": sampler.summary(),
+        "accuracy": acc,
+        "variants": variants,
+    }
+    B.ge_destroy(ctx)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,149 @@
+/*
+ * ge.h -- C ABI of the GB300 group explicit (GE) solver for the transient
+ * diffusion equation u_t = u_xx on [0, 1] (Parand, Zafarvahedian, Hossayni,
+ * arXiv:1310.3422, Sec. 2; Tavakoli's unconditionally stable alternating
+ * Saul'yev scheme, sub-domain width 1).
+ *
+ * Problem (Sec. 2, problem statement):
+ *   u_t = u_xx,  u(x, 0) = phi(x),  u(0, t) = beta_l,  u(1, t) = beta_r.
+ *   The paper has one wall value beta; two independent values are a superset.
+ * Mesh (Sec. 2): n interior points, h = 1/(n+1), x_i = (i+1) h for the 0-based
+ *   array index i = 0..n-1, tau = r h^2, r = tau / h^2 the mesh ratio.
+ * Step (Sec. 2, Eqs. (aa), (bb), (cc), (dd)): with parity p = s mod 2 of the
+ *   global step counter s, p = 0 couples the points in groups (0,1),(2,3),...
+ *   and p = 1 in groups (1,2),(3,4),...; a point without a partner at either
+ *   end is a singleton.  Each group's 2x2 system (Saul'yev B at its left
+ *   member, A at its right member) is solved by Eqs. (cc)/(dd) with the
+ *   prefactor 1/(1+2r); a singleton uses Saul'yev A at the left wall and B at
+ *   the right wall, the wall value standing in for the new-level neighbour.
+ *
+ * Conventions for every entry point:
+ *   - Element type: double for GE_F64, float for GE_F32 and GE_F32_COMP.
+ *   - "_dev" pointers are CUDA device pointers (or managed memory) on the
+ *     current device; "_host" pointers are host memory.  The caller owns
+ *     every buffer it passes; the library never frees or retains them past
+ *     the call (asynchronous calls read/write them in stream order).
+ *   - `stream` is a cudaStream_t passed as void*; NULL selects the legacy
+ *     default stream.  Work is enqueued asynchronously on that stream unless
+ *     stated otherwise.
+ *   - Every call returns a ge_status and never throws; a thread-local text
+ *     for the last failure is available from ge_last_error().
+ *   - Device-side failures (a bounded wait that ran out) are recorded in a
+ *     device word and reported by ge_sync() or the next synchronising call.
+ */
+#ifndef GE_H
+#define GE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GE_OK = 0,
+    GE_EINVAL = 1,      /* invalid argument (see each entry point)           */
+    GE_ENOMEM = 2,      /* a device or pinned-host allocation failed         */
+    GE_ECUDA = 3,       /* a CUDA runtime or driver call failed              */
+    GE_ETIMEOUT = 4,    /* a bounded device-side wait gave up                */
+    GE_ENONFINITE = 5   /* the checked state holds NaN or Inf                */
+} ge_status;
+
+typedef enum {
+    GE_F64 = 0,         /* FP64 storage and arithmetic                        */
+    GE_F32 = 1,         /* FP32 storage and arithmetic                        */
+    GE_F32_COMP = 2     /* FP32 storage; each point's updates are summed with
+                           a compensation word (Kahan) kept on chip within a
+                           launch                                            */
+} ge_precision;
+
+typedef enum {
+    GE_KERNEL_AUTO = 0,      /* GE_KERNEL_TEMPORAL with the built-in depth    */
+    GE_KERNEL_CANONICAL = 1, /* one launch per step; Eqs. (cc)/(dd), (aa)/(bb)
+                                evaluated literally with fused multiply-adds
+                                in the order the equations print their terms
+                                (GE_F64: bit-identical to a serial FP64
+                                evaluation in that order); GE_F64/GE_F32 only */
+    GE_KERNEL_ONESTEP = 2,   /* one launch per step on the group systems'
+                                right-hand sides (see GE_KERNEL_TEMPORAL)     */
+    GE_KERNEL_TEMPORAL = 3   /* `depth` steps per launch: a tile plus a halo
+                                of depth+1 points per side is staged in shared
+                                memory by TMA and advanced on chip.  Between
+                                steps it carries the right-hand side of each
+                                group's 2x2 system, w = (I - r G') u + wall
+                                terms, so one step is the block map
+                                (I - r G)(I + r G)^{-1} = [[1,2r],[2r,1]]/(1+2r)
+                                on each group: the same scheme, reassociated */
+} ge_kernel;
+
+typedef struct ge_ctx ge_ctx;  /* opaque; owned by the library */
+
+/* Create a solver for one problem.
+ *   out        receives the new context (set to NULL on failure).
+ *   n          number of interior points, n >= 1.
+ *   r          mesh ratio tau/h^2, finite and > 0.
+ *   beta_l/r   wall values u(0,t), u(1,t), finite.
+ *   prec       GE_F64, GE_F32 or GE_F32_COMP.
+ *   u0_dev     n elements of phi(x_i) (device memory, caller-owned, copied
+ *              before the call returns); NULL starts from zeros.
+ *   stream     stream all later work of this context is enqueued on.
+ * The context owns two device buffers of n elements (padded to whole
+ * 128-byte rows).  The step counter starts at 0 (next step has parity 0).
+ * Errors: GE_EINVAL (bad n, r, beta, prec, out == NULL), GE_ENOMEM, GE_ECUDA. */
+ge_status ge_create(ge_ctx **out, int64_t n, double r, double beta_l, double beta_r,
+                    ge_precision prec, const void *u0_dev, void *stream);
+
+/* Select the kernel used by later ge_step_n calls.  depth: steps per launch
+ * for GE_KERNEL_TEMPORAL, 1..1023 (0 = built-in default); ignored otherwise.
+ * Errors: GE_EINVAL (NULL ctx, unknown kernel, depth out of range,
+ * GE_KERNEL_CANONICAL with GE_F32_COMP). */
+ge_status ge_set_kernel(ge_ctx *ctx, ge_kernel kernel, int32_t depth);
+
+/* Advance the state by `steps` GE time steps (steps >= 0), continuing the
+ * parity of the step counter, which increases by `steps`.  Asynchronous on
+ * the context's stream; may be captured in a CUDA graph once the context
+ * exists.  Errors: GE_EINVAL (NULL ctx, steps < 0), GE_ECUDA (launch). */
+ge_status ge_step_n(ge_ctx *ctx, int64_t steps);
+
+/* Copy the current n values into out_dev (device, n elements of the
+ * context's type).  Asynchronous.  Errors: GE_EINVAL, GE_ECUDA. */
+ge_status ge_read_state(ge_ctx *ctx, void *out_dev);
+
+/* Replace the state by in_dev (n elements) and set the step counter to
+ * step_count >= 0 (resume from a checkpoint).  Asynchronous.
+ * Errors: GE_EINVAL, GE_ECUDA. */
+ge_status ge_write_state(ge_ctx *ctx, const void *in_dev, int64_t step_count);
+
+/* Query the step counter.  Errors: GE_EINVAL. */
+ge_status ge_get_step(const ge_ctx *ctx, int64_t *step_count);
+
+/* Wait for the context's stream and report deferred device errors
+ * (GE_ETIMEOUT) and launch errors (GE_ECUDA). */
+ge_status ge_sync(ge_ctx *ctx);
+
+/* Release the context and its buffers (after finishing its stream's work).
+ * NULL is a no-op. */
+void ge_destroy(ge_ctx *ctx);
+
+/* One-shot solve from HOST memory (the end-to-end path): copies u0_host
+ * (n elements) to the device, advances `steps` steps from step counter 0
+ * with the given kernel/depth, and copies the result to u_out_host.
+ * Synchronous.  Both host buffers may be pageable or pinned, and may alias.
+ * Errors: as ge_create / ge_set_kernel / ge_step_n, plus GE_EINVAL for NULL
+ * host buffers. */
+ge_status ge_solve(int64_t n, double r, double beta_l, double beta_r, ge_precision prec,
+                   ge_kernel kernel, int32_t depth, int64_t steps, const void *u0_host,
+                   void *u_out_host, void *stream);
+
+/* Name of a status code (static string). */
+const char *ge_status_str(ge_status status);
+
+/* Text describing the last failure on the calling thread (static storage,
+ * valid until the next failing call on this thread); "" if none. */
+const char *ge_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GE_H */

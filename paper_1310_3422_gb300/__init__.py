@@ -5,13 +5,6 @@ The compute path is the CUDA library ``libge.so`` (sm_103a) behind the C ABI in
 front end with the same entry-point names.  The library is loaded on first use
 and a missing or unbuilt library raises immediately: there is no CPU fallback.
 """
-from . import inputs  # noqa: F401  (seeded generators; no method arithmetic)
+from . import binding, inputs  # noqa: F401  (binding loads libge.so lazily)
 
-__all__ = ["inputs", "binding"]
-
-
-def __getattr__(name):
-    if name == "binding":
-        from . import binding
-        return binding
-    raise AttributeError(name)
+__all__ = ["binding", "inputs"]

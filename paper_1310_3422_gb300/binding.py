@@ -1,0 +1,189 @@
+"""ctypes binding of ``libge.so`` (the C ABI of ``include/ge.h``).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Entry points keep the C names; device buffers are torch CUDA
+tensors (or raw integer device pointers), host buffers numpy arrays.  A
+failing call raises :class:`GeError` with the library's status and message.
+Loading fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libge.so")
+
+GE_OK, GE_EINVAL, GE_ENOMEM, GE_ECUDA, GE_ETIMEOUT, GE_ENONFINITE = range(6)
+GE_F64, GE_F32, GE_F32_COMP = 0, 1, 2
+GE_KERNEL_AUTO, GE_KERNEL_CANONICAL, GE_KERNEL_ONESTEP, GE_KERNEL_TEMPORAL = 0, 1, 2, 3
+
+# Every symbol include/ge.h declares.
+EXPORTS = ("ge_create", "ge_set_kernel", "ge_step_n", "ge_read_state", "ge_write_state",
+           "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_status_str", "ge_last_error")
+
+_lock = threading.Lock()
+_lib = None
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_I32 = ctypes.c_int32
+
+
+class GeError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {message} (status {status})")
+
+
+def load(path: str | None = None):
+    """Load libge.so and declare the C signatures (idempotent)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libge.so not built at {p}: run __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(p)
+        lib.ge_create.argtypes = [ctypes.POINTER(_VP), _I64, _D, _D, _D, ctypes.c_int, _VP, _VP]
+        lib.ge_create.restype = ctypes.c_int
+        lib.ge_set_kernel.argtypes = [_VP, ctypes.c_int, _I32]
+        lib.ge_set_kernel.restype = ctypes.c_int
+        lib.ge_step_n.argtypes = [_VP, _I64]
+        lib.ge_step_n.restype = ctypes.c_int
+        lib.ge_read_state.argtypes = [_VP, _VP]
+        lib.ge_read_state.restype = ctypes.c_int
+        lib.ge_write_state.argtypes = [_VP, _VP, _I64]
+        lib.ge_write_state.restype = ctypes.c_int
+        lib.ge_get_step.argtypes = [_VP, ctypes.POINTER(_I64)]
+        lib.ge_get_step.restype = ctypes.c_int
+        lib.ge_sync.argtypes = [_VP]
+        lib.ge_sync.restype = ctypes.c_int
+        lib.ge_destroy.argtypes = [_VP]
+        lib.ge_destroy.restype = None
+        lib.ge_solve.argtypes = [_I64, _D, _D, _D, ctypes.c_int, ctypes.c_int, _I32, _I64, _VP, _VP, _VP]
+        lib.ge_solve.restype = ctypes.c_int
+        lib.ge_status_str.argtypes = [ctypes.c_int]
+        lib.ge_status_str.restype = ctypes.c_char_p
+        lib.ge_last_error.argtypes = []
+        lib.ge_last_error.restype = ctypes.c_char_p
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(st: int, where: str):
+    if st != GE_OK:
+        lib = load()
+        raise GeError(st, where, lib.ge_last_error().decode(errors="replace"))
+
+
+def _dptr(x) -> int | None:
+    """Device pointer of a CUDA tensor (or an int), None for None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return x.data_ptr()
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def dtype_of(prec: int):
+    import torch
+    return torch.float64 if prec == GE_F64 else torch.float32
+
+
+class Ctx:
+    """Owner of a ``ge_ctx*``; destroyed explicitly or when collected."""
+
+    def __init__(self, handle: int, n: int, prec: int):
+        self.handle = handle
+        self.n = n
+        self.prec = prec
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                ge_destroy(self)
+            except Exception:
+                pass
+
+
+def ge_create(n: int, r: float, beta_l: float, beta_r: float, prec: int, u0=None, stream=None) -> Ctx:
+    lib = load()
+    h = _VP()
+    if u0 is not None and (u0.numel() != n or u0.dtype != dtype_of(prec)):
+        raise ValueError("u0 must hold n elements of the precision's dtype")
+    _check(lib.ge_create(ctypes.byref(h), int(n), float(r), float(beta_l), float(beta_r), int(prec),
+                         _dptr(u0), _stream_handle(stream)), "ge_create")
+    return Ctx(h.value, int(n), int(prec))
+
+
+def ge_set_kernel(ctx: Ctx, kernel: int, depth: int = 0):
+    _check(load().ge_set_kernel(ctx.handle, int(kernel), int(depth)), "ge_set_kernel")
+
+
+def ge_step_n(ctx: Ctx, steps: int):
+    _check(load().ge_step_n(ctx.handle, int(steps)), "ge_step_n")
+
+
+def ge_read_state(ctx: Ctx, out):
+    if out.numel() < ctx.n or out.dtype != dtype_of(ctx.prec):
+        raise ValueError("output tensor too small or of the wrong dtype")
+    _check(load().ge_read_state(ctx.handle, _dptr(out)), "ge_read_state")
+
+
+def ge_write_state(ctx: Ctx, src, step_count: int):
+    if src.numel() < ctx.n or src.dtype != dtype_of(ctx.prec):
+        raise ValueError("state tensor too small or of the wrong dtype")
+    _check(load().ge_write_state(ctx.handle, _dptr(src), int(step_count)), "ge_write_state")
+
+
+def ge_get_step(ctx: Ctx) -> int:
+    v = _I64()
+    _check(load().ge_get_step(ctx.handle, ctypes.byref(v)), "ge_get_step")
+    return int(v.value)
+
+
+def ge_sync(ctx: Ctx):
+    _check(load().ge_sync(ctx.handle), "ge_sync")
+
+
+def ge_destroy(ctx: Ctx):
+    if ctx.handle:
+        load().ge_destroy(ctx.handle)
+        ctx.handle = None
+
+
+def ge_solve(n: int, r: float, beta_l: float, beta_r: float, prec: int, kernel: int, depth: int,
+             steps: int, u0_host: np.ndarray, u_out_host: np.ndarray, stream=None):
+    """One-shot solve from host memory (numpy arrays of n float64/float32)."""
+    dt = np.float64 if prec == GE_F64 else np.float32
+    for a in (u0_host, u_out_host):
+        if a.dtype != dt or a.size < n or not a.flags.c_contiguous:
+            raise ValueError("host buffers must be contiguous arrays of n elements of the precision's dtype")
+    _check(load().ge_solve(int(n), float(r), float(beta_l), float(beta_r), int(prec), int(kernel),
+                           int(depth), int(steps), u0_host.ctypes.data, u_out_host.ctypes.data,
+                           _stream_handle(stream)), "ge_solve")
+
+
+def ge_status_str(status: int) -> str:
+    return load().ge_status_str(int(status)).decode()
+
+
+def ge_last_error() -> str:
+    return load().ge_last_error().decode(errors="replace")

@@ -1,0 +1,446 @@
+// ge_api.cpp -- the C ABI declared in include/ge.h: argument checking,
+// contexts and their device buffers, coefficients, kernel selection and
+// launch sequencing.  Host code only; built with -ffp-contract=off so the
+// coefficients are rounded exactly as written.
+#include "ge.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime_api.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "ge_internal.h"
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+ge_status fail(ge_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+ge_status cuda_fail(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return fail(GE_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(GE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr int kDefaultDepthF64 = 32;
+constexpr int kDefaultDepthF32 = 64;
+constexpr int kMaxDepth = 1023;
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+size_t elem_size(ge_precision p) { return p == GE_F64 ? sizeof(double) : sizeof(float); }
+int elems_per_row(ge_precision p) { return ge::kRowBytes / (int)elem_size(p); }
+
+}  // namespace
+
+struct ge_ctx {
+    CUtensorMap tmap[2];  // one per buffer (source of a tiled launch)
+    int64_t n = 0;
+    double r = 0, beta_l = 0, beta_r = 0;
+    ge_precision prec = GE_F64;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int64_t n_rows = 0;  // 128-byte rows per buffer
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;         // buffer holding the state
+    int64_t step = 0;    // global step counter
+    ge_kernel kernel = GE_KERNEL_AUTO;
+    int depth = 0;
+    int *err_dev = nullptr;
+    int num_sms = 0;
+    int tb_blocks_per_sm = 0;
+    ge::CanonCoef canon{};
+    ge::TbParams tb{};   // launch-independent fields filled at creation
+};
+
+namespace {
+
+void fill_coefficients(ge_ctx *c)
+{
+    const double r = c->r;
+    const double r2 = r * r;
+    const double det = 1.0 + 2.0 * r;
+    // Eqs. (cc)/(dd): numerator coefficients over the determinant 1 + 2r
+    c->canon.c1 = (r + r2) / det;
+    c->canon.c2 = (1.0 - r2) / det;
+    c->canon.c3 = (r - r2) / det;
+    c->canon.c4 = r2 / det;
+    // Eqs. (aa)/(bb): r/(1+r) and (1-r)/(1+r)
+    c->canon.s0 = r / (1.0 + r);
+    c->canon.s1 = (1.0 - r) / (1.0 + r);
+    c->canon.beta_l = c->beta_l;
+    c->canon.beta_r = c->beta_r;
+
+    ge::TbParams &p = c->tb;
+    p.g = 2.0 * r;
+    p.r = r;
+    p.omr = 1.0 - r;
+    p.d = 2.0 * r / det;
+    p.f_l = r * c->beta_l;
+    p.f_r = r * c->beta_r;
+    p.x1 = (1.0 + r) / det;
+    p.x2 = r / det;
+    p.xs = 1.0 / (1.0 + r);
+    if (c->prec == GE_F32_COMP) {
+        p.kappa = (1.0 - r) / (1.0 + r);
+        p.rescale_every = 0;
+    } else {
+        p.kappa = det * (1.0 - r) / (1.0 + r);
+        // block steps between rescalings: (1+2r)^R <= 2^headroom
+        const double headroom = (c->prec == GE_F64) ? 128.0 : 16.0;
+        int every = (int)std::floor(headroom / std::log2(1.0 + 2.0 * r));
+        p.rescale_every = every < 1 ? 1 : every;
+    }
+    p.rescale = 1.0;
+}
+
+ge_status make_tensor_maps(ge_ctx *c)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc)
+        return fail(GE_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const int K = elems_per_row(c->prec);
+    for (int b = 0; b < 2; ++b) {
+        cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)c->n_rows};
+        cuuint64_t strides[1] = {(cuuint64_t)ge::kRowBytes};
+        cuuint32_t box[2] = {(cuuint32_t)K, (cuuint32_t)ge::kTileThreads};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = enc(&c->tmap[b],
+                         c->prec == GE_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                         2, c->buf[b], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return fail(GE_ECUDA, "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+    }
+    return GE_OK;
+}
+
+bool valid_prec(int p) { return p == GE_F64 || p == GE_F32 || p == GE_F32_COMP; }
+bool valid_kernel(int k)
+{
+    return k == GE_KERNEL_AUTO || k == GE_KERNEL_CANONICAL || k == GE_KERNEL_ONESTEP ||
+           k == GE_KERNEL_TEMPORAL;
+}
+
+// Steps advanced by one launch of the tiled kernel.
+ge_status run_tiled(ge_ctx *c, int64_t steps, int depth)
+{
+    const int K = elems_per_row(c->prec);
+    const int span = ge::kTileThreads * K;
+    int64_t n0 = 0;
+    while (n0 < steps) {
+        const int64_t L = (steps - n0 < depth) ? steps - n0 : depth;
+        ge::TbParams p = c->tb;
+        const bool last = (n0 + L == steps);
+        p.do_entry = (n0 == 0) ? 1 : 0;
+        p.n_mid = (int)(last ? L - 1 : L);
+        p.do_exit = last ? 1 : 0;
+        p.p_first = (int)((c->step + n0) & 1);
+        const int reach = p.do_entry + p.n_mid + p.do_exit;
+        p.H = K * ((reach + K - 1) / K);
+        p.U = span - 2 * p.H;
+        p.n = c->n;
+        p.n_rows = c->n_rows;
+        p.n_tiles = (c->n + p.U - 1) / p.U;
+        p.out = c->buf[c->cur ^ 1];
+        p.err = c->err_dev;
+        long long grid = (long long)c->num_sms * c->tb_blocks_per_sm;
+        if (grid > p.n_tiles)
+            grid = p.n_tiles;
+        if (grid < 1)
+            grid = 1;
+        const int prec = c->prec == GE_F64 ? 0 : (c->prec == GE_F32 ? 1 : 2);
+        cudaError_t e = ge::launch_tb(prec, &c->tmap[c->cur], p, (int)grid, c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "tiled GE kernel launch");
+        c->cur ^= 1;
+        n0 += L;
+    }
+    return GE_OK;
+}
+
+ge_status run_canonical(ge_ctx *c, int64_t steps)
+{
+    for (int64_t s = 0; s < steps; ++s) {
+        const int parity = (int)((c->step + s) & 1);
+        cudaError_t e;
+        if (c->prec == GE_F64)
+            e = ge::launch_canon_f64(static_cast<const double *>(c->buf[c->cur]),
+                                     static_cast<double *>(c->buf[c->cur ^ 1]), c->n, parity, c->canon,
+                                     c->stream);
+        else
+            e = ge::launch_canon_f32(static_cast<const float *>(c->buf[c->cur]),
+                                     static_cast<float *>(c->buf[c->cur ^ 1]), c->n, parity, c->canon,
+                                     c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "canonical GE kernel launch");
+        c->cur ^= 1;
+    }
+    return GE_OK;
+}
+
+void release(ge_ctx *c)
+{
+    if (!c)
+        return;
+    for (int b = 0; b < 2; ++b)
+        if (c->buf[b])
+            cudaFree(c->buf[b]);
+    if (c->err_dev)
+        cudaFree(c->err_dev);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ge_status_str(ge_status s)
+{
+    switch (s) {
+    case GE_OK: return "GE_OK";
+    case GE_EINVAL: return "GE_EINVAL";
+    case GE_ENOMEM: return "GE_ENOMEM";
+    case GE_ECUDA: return "GE_ECUDA";
+    case GE_ETIMEOUT: return "GE_ETIMEOUT";
+    case GE_ENONFINITE: return "GE_ENONFINITE";
+    }
+    return "GE_UNKNOWN";
+}
+
+const char *ge_last_error(void) { return g_last_error; }
+
+ge_status ge_create(ge_ctx **out, int64_t n, double r, double beta_l, double beta_r, ge_precision prec,
+                    const void *u0_dev, void *stream)
+{
+    if (out == nullptr)
+        return fail(GE_EINVAL, "ge_create: out is NULL");
+    *out = nullptr;
+    if (n < 1)
+        return fail(GE_EINVAL, "ge_create: n = %lld, need n >= 1", (long long)n);
+    if (!(r > 0.0) || !std::isfinite(r))
+        return fail(GE_EINVAL, "ge_create: r = %g, need a finite r > 0", r);
+    if (!std::isfinite(beta_l) || !std::isfinite(beta_r))
+        return fail(GE_EINVAL, "ge_create: wall values must be finite");
+    if (!valid_prec(prec))
+        return fail(GE_EINVAL, "ge_create: unknown precision %d", (int)prec);
+    const int K = elems_per_row(prec);
+    const int64_t n_rows = (n + K - 1) / K;
+    if (n_rows >= (1LL << 31) - 2 * ge::kTileThreads)
+        return fail(GE_EINVAL, "ge_create: n = %lld is too large", (long long)n);
+
+    ge_ctx *c = new (std::nothrow) ge_ctx();
+    if (!c)
+        return fail(GE_ENOMEM, "ge_create: host allocation failed");
+    c->n = n;
+    c->r = r;
+    c->beta_l = beta_l;
+    c->beta_r = beta_r;
+    c->prec = prec;
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->n_rows = n_rows;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        release(c);
+        return cuda_fail(e, "ge_create: device query");
+    }
+    const size_t bytes = (size_t)n_rows * ge::kRowBytes;
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+        e = cudaMalloc(&c->buf[b], bytes);
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void **>(&c->err_dev), 256);
+    if (e != cudaSuccess) {
+        release(c);
+        return cuda_fail(e, "ge_create: device allocation");
+    }
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b)
+        e = cudaMemsetAsync(c->buf[b], 0, bytes, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->err_dev, 0, 256, c->stream);
+    if (e == cudaSuccess && u0_dev)
+        e = cudaMemcpyAsync(c->buf[0], u0_dev, (size_t)n * elem_size(prec), cudaMemcpyDeviceToDevice,
+                            c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        release(c);
+        return cuda_fail(e, "ge_create: initialising buffers");
+    }
+    fill_coefficients(c);
+    ge_status st = make_tensor_maps(c);
+    if (st != GE_OK) {
+        release(c);
+        return st;
+    }
+    const int prec_idx = prec == GE_F64 ? 0 : (prec == GE_F32 ? 1 : 2);
+    e = ge::tb_occupancy(prec_idx, &c->tb_blocks_per_sm);
+    if (e != cudaSuccess || c->tb_blocks_per_sm < 1) {
+        release(c);
+        return cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e,
+                         "ge_create: tiled kernel occupancy");
+    }
+    *out = c;
+    return GE_OK;
+}
+
+ge_status ge_set_kernel(ge_ctx *c, ge_kernel kernel, int32_t depth)
+{
+    if (!c)
+        return fail(GE_EINVAL, "ge_set_kernel: ctx is NULL");
+    if (!valid_kernel(kernel))
+        return fail(GE_EINVAL, "ge_set_kernel: unknown kernel %d", (int)kernel);
+    if (depth < 0 || depth > kMaxDepth)
+        return fail(GE_EINVAL, "ge_set_kernel: depth %d outside 0..%d", (int)depth, kMaxDepth);
+    if (kernel == GE_KERNEL_CANONICAL && c->prec == GE_F32_COMP)
+        return fail(GE_EINVAL, "ge_set_kernel: the canonical kernel has no compensated variant");
+    c->kernel = kernel;
+    c->depth = depth;
+    return GE_OK;
+}
+
+ge_status ge_step_n(ge_ctx *c, int64_t steps)
+{
+    if (!c)
+        return fail(GE_EINVAL, "ge_step_n: ctx is NULL");
+    if (steps < 0)
+        return fail(GE_EINVAL, "ge_step_n: steps = %lld < 0", (long long)steps);
+    if (steps == 0)
+        return GE_OK;
+    ge_status st;
+    switch (c->kernel) {
+    case GE_KERNEL_CANONICAL:
+        st = run_canonical(c, steps);
+        break;
+    case GE_KERNEL_ONESTEP:
+        st = run_tiled(c, steps, 1);
+        break;
+    default: {
+        int depth = c->depth;
+        if (depth == 0)
+            depth = (c->prec == GE_F64) ? kDefaultDepthF64 : kDefaultDepthF32;
+        st = run_tiled(c, steps, depth);
+    }
+    }
+    if (st == GE_OK)
+        c->step += steps;
+    return st;
+}
+
+ge_status ge_read_state(ge_ctx *c, void *out_dev)
+{
+    if (!c || !out_dev)
+        return fail(GE_EINVAL, "ge_read_state: NULL argument");
+    cudaError_t e = cudaMemcpyAsync(out_dev, c->buf[c->cur], (size_t)c->n * elem_size(c->prec),
+                                    cudaMemcpyDeviceToDevice, c->stream);
+    return e == cudaSuccess ? GE_OK : cuda_fail(e, "ge_read_state");
+}
+
+ge_status ge_write_state(ge_ctx *c, const void *in_dev, int64_t step_count)
+{
+    if (!c || !in_dev)
+        return fail(GE_EINVAL, "ge_write_state: NULL argument");
+    if (step_count < 0)
+        return fail(GE_EINVAL, "ge_write_state: step_count < 0");
+    cudaError_t e = cudaMemcpyAsync(c->buf[c->cur], in_dev, (size_t)c->n * elem_size(c->prec),
+                                    cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "ge_write_state");
+    c->step = step_count;
+    return GE_OK;
+}
+
+ge_status ge_get_step(const ge_ctx *c, int64_t *step_count)
+{
+    if (!c || !step_count)
+        return fail(GE_EINVAL, "ge_get_step: NULL argument");
+    *step_count = c->step;
+    return GE_OK;
+}
+
+ge_status ge_sync(ge_ctx *c)
+{
+    if (!c)
+        return fail(GE_EINVAL, "ge_sync: ctx is NULL");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "ge_sync");
+    int word = 0;
+    e = cudaMemcpy(&word, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "ge_sync: reading the device error word");
+    if (word == ge::kDevTimeout)
+        return fail(GE_ETIMEOUT, "a tile load did not complete within the wait limit");
+    return GE_OK;
+}
+
+void ge_destroy(ge_ctx *c)
+{
+    if (!c)
+        return;
+    cudaStreamSynchronize(c->stream);
+    release(c);
+}
+
+ge_status ge_solve(int64_t n, double r, double beta_l, double beta_r, ge_precision prec, ge_kernel kernel,
+                   int32_t depth, int64_t steps, const void *u0_host, void *u_out_host, void *stream)
+{
+    if (!u0_host || !u_out_host)
+        return fail(GE_EINVAL, "ge_solve: NULL host buffer");
+    if (steps < 0)
+        return fail(GE_EINVAL, "ge_solve: steps < 0");
+    ge_ctx *c = nullptr;
+    ge_status st = ge_create(&c, n, r, beta_l, beta_r, prec, nullptr, stream);
+    if (st != GE_OK)
+        return st;
+    const size_t bytes = (size_t)n * elem_size(prec);
+    cudaError_t e = cudaMemcpyAsync(c->buf[c->cur], u0_host, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) {
+        ge_destroy(c);
+        return cuda_fail(e, "ge_solve: host to device copy");
+    }
+    st = ge_set_kernel(c, kernel, depth);
+    if (st == GE_OK)
+        st = ge_step_n(c, steps);
+    if (st == GE_OK) {
+        e = cudaMemcpyAsync(u_out_host, c->buf[c->cur], bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess)
+            st = cuda_fail(e, "ge_solve: device to host copy");
+    }
+    if (st == GE_OK)
+        st = ge_sync(c);
+    ge_destroy(c);
+    return st;
+}
+
+}  // extern "C"

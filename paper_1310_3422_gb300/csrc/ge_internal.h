@@ -1,0 +1,67 @@
+// ge_internal.h -- parameter blocks and launcher prototypes shared by the C ABI
+// (ge_api.cpp, host compiler) and the kernel translation units (*.cu, nvcc).
+// Plain C++: no device code, no CUDA headers beyond the runtime API.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime_api.h>
+
+namespace ge {
+
+// Bytes of one shared-memory / tensor-map row; a thread of the tiled kernels
+// owns exactly one row: 32 floats or 16 doubles.
+constexpr int kRowBytes = 128;
+// Threads per CTA of the tiled kernels (one row each: 8192 floats or 4096
+// doubles per tile).
+constexpr int kTileThreads = 256;
+
+// Device error codes written to the context's error word.
+enum DevErr : int { kDevOk = 0, kDevTimeout = 1 };
+
+// Coefficients of the literal step (Eqs. (cc)/(dd), (aa)/(bb)), FP64 on the
+// host; the FP32 kernels round them once.
+struct CanonCoef {
+    double c1, c2, c3, c4;  // (r+r^2, 1-r^2, r-r^2, r^2) / (1+2r)
+    double s0, s1;          // r/(1+r), (1-r)/(1+r)
+    double beta_l, beta_r;
+};
+
+// One launch of the tiled right-hand-side kernel (GE_KERNEL_TEMPORAL and
+// GE_KERNEL_ONESTEP).  See ge_tb.cu for the stage definitions.
+struct TbParams {
+    void *out;            // destination buffer (element 0 = interior point 0)
+    int *err;             // device error word
+    long long n;          // interior points
+    long long n_rows;     // 128-byte rows in each buffer (n_rows * K >= n)
+    long long n_tiles;    // tiles of U output elements
+    int U;                // output elements per tile (multiple of K)
+    int H;                // halo elements per side (multiple of K, >= reach)
+    int p_first;          // parity of the first step of this launch
+    int do_entry;         // convert u -> w at the start
+    int n_mid;            // block steps w_n -> w_{n+1} in this launch
+    int do_exit;          // convert w -> u at the end
+    int rescale_every;    // apply `rescale` every this many block steps (0: never)
+    double rescale;       // exact power of two 2^-E
+    double g;             // 2r  (scaled block: (x, y) -> (x + 2r y, 2r x + y))
+    double r, omr;        // r, 1 - r  (entry: w = (1-r) u + r u_partner)
+    double kappa;         // singleton block factor: scaled (1+2r)(1-r)/(1+r);
+                          // compensated kernel: (1-r)/(1+r)
+    double d;             // compensated kernel: 2r/(1+2r)
+    double f_l, f_r;      // wall terms r*beta_l, r*beta_r
+    double x1, x2, xs;    // exit: (1+r)/(1+2r), r/(1+2r), 1/(1+r)
+};
+
+// Launchers (return the cudaError_t of the launch).
+cudaError_t launch_canon_f64(const double *in, double *out, long long n, int parity,
+                             const CanonCoef &c, cudaStream_t s);
+cudaError_t launch_canon_f32(const float *in, float *out, long long n, int parity,
+                             const CanonCoef &c, cudaStream_t s);
+
+// prec: 0 = FP64, 1 = FP32, 2 = FP32 compensated.  tmap: 128-byte-aligned
+// CUtensorMap (opaque here) describing the source buffer.
+cudaError_t launch_tb(int prec, const void *tmap, const TbParams &p, int grid, cudaStream_t s);
+// Largest co-resident CTAs per SM for the tiled kernel of this precision.
+cudaError_t tb_occupancy(int prec, int *blocks_per_sm);
+int tb_smem_bytes();
+
+}  // namespace ge

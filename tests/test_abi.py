@@ -1,0 +1,85 @@
+"""The C-ABI library loads and exports every entry point include/*.h declares;
+argument checks that fail before any device work (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1310_3422_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(ge_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(B.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return B.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ge_create", "ge_step_n", "ge_destroy", "ge_read_state", "ge_write_state",
+                     "ge_sync", "ge_solve"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert names, "no declarations found"
+    for name in sorted(names):
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported by libge.so"
+    assert set(B.EXPORTS) <= names
+
+
+def test_status_strings(lib):
+    assert B.ge_status_str(B.GE_OK) == "GE_OK"
+    assert B.ge_status_str(B.GE_EINVAL) == "GE_EINVAL"
+    assert B.ge_status_str(B.GE_ETIMEOUT) == "GE_ETIMEOUT"
+    assert B.ge_status_str(99) == "GE_UNKNOWN"
+
+
+@pytest.mark.parametrize("n,r,bl,br,prec", [
+    (0, 1.0, 0.0, 0.0, B.GE_F64),
+    (-5, 1.0, 0.0, 0.0, B.GE_F64),
+    (8, 0.0, 0.0, 0.0, B.GE_F64),
+    (8, -1.0, 0.0, 0.0, B.GE_F64),
+    (8, float("inf"), 0.0, 0.0, B.GE_F64),
+    (8, float("nan"), 0.0, 0.0, B.GE_F64),
+    (8, 1.0, float("nan"), 0.0, B.GE_F64),
+    (8, 1.0, 0.0, float("inf"), B.GE_F32),
+    (8, 1.0, 0.0, 0.0, 7),
+])
+def test_create_rejects_invalid_arguments(lib, n, r, bl, br, prec):
+    h = ctypes.c_void_p(123)
+    st = lib.ge_create(ctypes.byref(h), n, r, bl, br, prec, None, None)
+    assert st == B.GE_EINVAL
+    assert h.value is None
+    assert B.ge_last_error() != ""
+
+
+def test_null_context_is_rejected(lib):
+    assert lib.ge_step_n(None, 1) == B.GE_EINVAL
+    assert lib.ge_set_kernel(None, 0, 0) == B.GE_EINVAL
+    assert lib.ge_read_state(None, None) == B.GE_EINVAL
+    assert lib.ge_write_state(None, None, 0) == B.GE_EINVAL
+    assert lib.ge_sync(None) == B.GE_EINVAL
+    assert lib.ge_create(None, 8, 1.0, 0.0, 0.0, 0, None, None) == B.GE_EINVAL
+    lib.ge_destroy(None)  # no-op
+
+
+def test_solve_rejects_null_host_buffers(lib):
+    assert lib.ge_solve(8, 1.0, 0.0, 0.0, 0, 0, 0, 1, None, None, None) == B.GE_EINVAL
