@@ -243,7 +243,7 @@ def main():
     prec = {"f64": B.GE_F64, "f32": B.GE_F32, "f32c": B.GE_F32_COMP}[args.precision]
     kern = {"temporal": B.GE_KERNEL_TEMPORAL, "onestep": B.GE_KERNEL_ONESTEP,
             "canonical": B.GE_KERNEL_CANONICAL}[args.kernel]
-    depth = args.depth or (32 if args.precision == "f64" else 64)
+    depth = args.depth or (48 if args.precision == "f64" else 128)
     hbm_gbs, sm_max_mhz, peak_src = load_peaks()
 
     u0 = inputs.sine_modes_state(N_POINTS, seed=inputs.SEED_BASE + 1 + rank)
@@ -345,7 +345,7 @@ def main():
 
         def flush():
             flush_buf.fill_(1)
-        for vp, vk, vd in (("f64", "onestep", 1), ("f64", "canonical", 1), ("f32", "temporal", 64),
+        for vp, vk, vd in (("f64", "onestep", 1), ("f64", "canonical", 1), ("f32", "temporal", 128),
                            ("f32c", "temporal", 64), ("f32", "onestep", 1)):
             if (vp, vk) == (args.precision, args.kernel):
                 continue

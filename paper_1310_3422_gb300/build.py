@@ -36,30 +36,33 @@ def _run(cmd):
     return res.stdout + res.stderr
 
 
-def build(verbose: bool = False) -> str:
-    os.makedirs(OBJ_DIR, exist_ok=True)
+def build(verbose: bool = False, defines=(), lib_path: str = LIB_PATH, obj_dir: str = OBJ_DIR) -> str:
+    """Compile and link the library.  `defines` are extra -D macros (tuning
+    knobs of the kernels); `lib_path`/`obj_dir` place a variant elsewhere."""
+    os.makedirs(obj_dir, exist_ok=True)
+    dflags = ["-D" + d for d in defines]
     inc = ["-I" + INCLUDE, "-I" + CSRC, "-I" + os.path.join(CUDA_HOME, "include")]
     jobs = []
     for src in CU_SOURCES:
-        obj = os.path.join(OBJ_DIR, src + ".o")
+        obj = os.path.join(obj_dir, src + ".o")
         jobs.append([_nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xptxas", "-v",
-                     "-Xcompiler", "-fPIC,-ffp-contract=off", *inc, "-c",
+                     "-Xcompiler", "-fPIC,-ffp-contract=off", *dflags, *inc, "-c",
                      os.path.join(CSRC, src), "-o", obj])
     for src in CPP_SOURCES:
-        obj = os.path.join(OBJ_DIR, src + ".o")
+        obj = os.path.join(obj_dir, src + ".o")
         jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall",
-                     *inc, "-c", os.path.join(CSRC, src), "-o", obj])
+                     *dflags, *inc, "-c", os.path.join(CSRC, src), "-o", obj])
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         logs = list(ex.map(_run, jobs))
     if verbose:
         for log in logs:
             sys.stdout.write(log)
-    objs = [os.path.join(OBJ_DIR, s + ".o") for s in CU_SOURCES + CPP_SOURCES]
-    tmp = LIB_PATH + ".tmp"
+    objs = [os.path.join(obj_dir, s + ".o") for s in CU_SOURCES + CPP_SOURCES]
+    tmp = lib_path + ".tmp"
     _run(["g++", "-shared", "-o", tmp, *objs, "-L" + os.path.join(CUDA_HOME, "lib64"),
           "-lcudart", "-Wl,-rpath," + os.path.join(CUDA_HOME, "lib64")])
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

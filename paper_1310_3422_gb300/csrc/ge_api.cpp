@@ -37,8 +37,11 @@ ge_status cuda_fail(cudaError_t e, const char *what)
     return fail(GE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-constexpr int kDefaultDepthF64 = 32;
-constexpr int kDefaultDepthF32 = 64;
+#ifndef GE_F32_HEADROOM
+#define GE_F32_HEADROOM 64.0
+#endif
+constexpr int kDefaultDepthF64 = 48;
+constexpr int kDefaultDepthF32 = 128;
 constexpr int kMaxDepth = 1023;
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
@@ -101,6 +104,7 @@ void fill_coefficients(ge_ctx *c)
 
     ge::TbParams &p = c->tb;
     p.g = 2.0 * r;
+    p.onepg = 1.0 + 2.0 * r;
     p.r = r;
     p.omr = 1.0 - r;
     p.d = 2.0 * r / det;
@@ -114,12 +118,13 @@ void fill_coefficients(ge_ctx *c)
         p.rescale_every = 0;
     } else {
         p.kappa = det * (1.0 - r) / (1.0 + r);
-        // block steps between rescalings: (1+2r)^R <= 2^headroom
-        const double headroom = (c->prec == GE_F64) ? 128.0 : 16.0;
+        // block steps between rescalings: the scale grows by (1+2r) per step
+        // and stays below 2^headroom (data magnitudes up to 2^(max_exp -
+        // headroom - 1) are safe)
+        const double headroom = (c->prec == GE_F64) ? 256.0 : GE_F32_HEADROOM;
         int every = (int)std::floor(headroom / std::log2(1.0 + 2.0 * r));
         p.rescale_every = every < 1 ? 1 : every;
     }
-    p.rescale = 1.0;
 }
 
 ge_status make_tensor_maps(ge_ctx *c)
@@ -131,7 +136,7 @@ ge_status make_tensor_maps(ge_ctx *c)
     for (int b = 0; b < 2; ++b) {
         cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)c->n_rows};
         cuuint64_t strides[1] = {(cuuint64_t)ge::kRowBytes};
-        cuuint32_t box[2] = {(cuuint32_t)K, (cuuint32_t)ge::kTileThreads};
+        cuuint32_t box[2] = {(cuuint32_t)K, (cuuint32_t)ge::kTileRows};
         cuuint32_t estr[2] = {1, 1};
         CUresult r = enc(&c->tmap[b],
                          c->prec == GE_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
@@ -151,11 +156,20 @@ bool valid_kernel(int k)
            k == GE_KERNEL_TEMPORAL;
 }
 
-// Steps advanced by one launch of the tiled kernel.
+// Advance `steps` steps with the tiled kernel, `depth` steps per launch.
+// The host mirrors the kernel's scale recurrence (see TbParams): sigma starts
+// at 1 after the entry conversion, is multiplied by (1+2r) per block step and
+// by 2^-e at each rescaling, where e brings it back into [1, 2).
 ge_status run_tiled(ge_ctx *c, int64_t steps, int depth)
 {
-    const int K = elems_per_row(c->prec);
-    const int span = ge::kTileThreads * K;
+    const int every = c->tb.rescale_every;
+    if (every > 0 && depth > (ge::kMaxRescale - 1) * every)
+        depth = (ge::kMaxRescale - 1) * every;
+    if (depth > ge::kMaxTableSteps)
+        depth = ge::kMaxTableSteps;
+    const int prec = c->prec == GE_F64 ? 0 : (c->prec == GE_F32 ? 1 : 2);
+    double sigma = 1.0;
+    int until = every;
     int64_t n0 = 0;
     while (n0 < steps) {
         const int64_t L = (steps - n0 < depth) ? steps - n0 : depth;
@@ -165,9 +179,30 @@ ge_status run_tiled(ge_ctx *c, int64_t steps, int depth)
         p.n_mid = (int)(last ? L - 1 : L);
         p.do_exit = last ? 1 : 0;
         p.p_first = (int)((c->step + n0) & 1);
+        p.sigma_in = sigma;
+        p.rescale_phase = until;
+        if (every > 0) {
+            int ev = 0;
+            for (int m = 0; m < p.n_mid; ++m) {
+                sigma *= p.onepg;
+                if (--until == 0) {
+                    until = every;
+                    int e2 = 0;
+                    std::frexp(sigma, &e2);
+                    const int e = e2 - 1;  // sigma * 2^-e in [1, 2)
+                    p.rs_exp[ev++] = (short)e;
+                    sigma = std::ldexp(sigma, -e);
+                }
+            }
+        }
+        if (p.do_exit) {
+            p.x1 = c->tb.x1 / sigma;
+            p.x2 = c->tb.x2 / sigma;
+            p.xs = c->tb.xs / sigma;
+        }
         const int reach = p.do_entry + p.n_mid + p.do_exit;
-        p.H = K * ((reach + K - 1) / K);
-        p.U = span - 2 * p.H;
+        if (!ge::tb_geometry(prec, reach, &p.H, &p.U))
+            return fail(GE_EINVAL, "depth %d does not fit a tile", depth);
         p.n = c->n;
         p.n_rows = c->n_rows;
         p.n_tiles = (c->n + p.U - 1) / p.U;
@@ -178,7 +213,6 @@ ge_status run_tiled(ge_ctx *c, int64_t steps, int depth)
             grid = p.n_tiles;
         if (grid < 1)
             grid = 1;
-        const int prec = c->prec == GE_F64 ? 0 : (c->prec == GE_F32 ? 1 : 2);
         cudaError_t e = ge::launch_tb(prec, &c->tmap[c->cur], p, (int)grid, c->stream);
         if (e != cudaSuccess)
             return cuda_fail(e, "tiled GE kernel launch");
@@ -255,7 +289,7 @@ ge_status ge_create(ge_ctx **out, int64_t n, double r, double beta_l, double bet
         return fail(GE_EINVAL, "ge_create: unknown precision %d", (int)prec);
     const int K = elems_per_row(prec);
     const int64_t n_rows = (n + K - 1) / K;
-    if (n_rows >= (1LL << 31) - 2 * ge::kTileThreads)
+    if (n_rows >= (1LL << 31) - 2 * ge::kTileRows)
         return fail(GE_EINVAL, "ge_create: n = %lld is too large", (long long)n);
 
     ge_ctx *c = new (std::nothrow) ge_ctx();

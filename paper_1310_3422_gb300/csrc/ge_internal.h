@@ -11,9 +11,9 @@ namespace ge {
 // Bytes of one shared-memory / tensor-map row; a thread of the tiled kernels
 // owns exactly one row: 32 floats or 16 doubles.
 constexpr int kRowBytes = 128;
-// Threads per CTA of the tiled kernels (one row each: 8192 floats or 4096
-// doubles per tile).
-constexpr int kTileThreads = 256;
+// Rows of 128 bytes in one tile of the tiled kernels (8192 floats or 4096
+// doubles), the box of their 2D TMA load.
+constexpr int kTileRows = 256;
 
 // Device error codes written to the context's error word.
 enum DevErr : int { kDevOk = 0, kDevTimeout = 1 };
@@ -26,8 +26,22 @@ struct CanonCoef {
     double beta_l, beta_r;
 };
 
+// Most exact power-of-two rescalings one tiled launch may apply.
+constexpr int kMaxRescale = 64;
+// Most block steps one tiled launch may take.
+constexpr int kMaxTableSteps = 512;
+
 // One launch of the tiled right-hand-side kernel (GE_KERNEL_TEMPORAL and
 // GE_KERNEL_ONESTEP).  See ge_tb.cu for the stage definitions.
+//
+// Scale bookkeeping (plain and FP64 kernels): the carried right-hand side is
+// held as W = sigma * w.  Each block step multiplies sigma by (1 + 2r); every
+// `rescale_every` block steps of a ge_step_n call the data and sigma are
+// multiplied by the exact power of two 2^-rs_exp[k] (k-th rescaling of this
+// launch).  The host runs the same double-precision sigma recurrence as the
+// kernel's wall threads, so it knows sigma at the end of every launch: the
+// next launch starts from it (`sigma_in`) and the exit coefficients carry
+// 1/sigma.  Only warps that hold a wall point evaluate sigma in the kernel.
 struct TbParams {
     void *out;            // destination buffer (element 0 = interior point 0)
     int *err;             // device error word
@@ -40,15 +54,18 @@ struct TbParams {
     int do_entry;         // convert u -> w at the start
     int n_mid;            // block steps w_n -> w_{n+1} in this launch
     int do_exit;          // convert w -> u at the end
-    int rescale_every;    // apply `rescale` every this many block steps (0: never)
-    double rescale;       // exact power of two 2^-E
+    int rescale_every;    // block steps between rescalings (0: never)
+    int rescale_phase;    // block steps until the first rescaling of this launch
+    double sigma_in;      // scale of the incoming right-hand side
+    double onepg;         // 1 + 2r
     double g;             // 2r  (scaled block: (x, y) -> (x + 2r y, 2r x + y))
     double r, omr;        // r, 1 - r  (entry: w = (1-r) u + r u_partner)
     double kappa;         // singleton block factor: scaled (1+2r)(1-r)/(1+r);
                           // compensated kernel: (1-r)/(1+r)
     double d;             // compensated kernel: 2r/(1+2r)
-    double f_l, f_r;      // wall terms r*beta_l, r*beta_r
-    double x1, x2, xs;    // exit: (1+r)/(1+2r), r/(1+2r), 1/(1+r)
+    double f_l, f_r;      // wall terms r*beta_l, r*beta_r (unscaled)
+    double x1, x2, xs;    // exit: (1+r)/(1+2r), r/(1+2r), 1/(1+r), each / sigma_end
+    short rs_exp[kMaxRescale];  // exponents of this launch's rescalings
 };
 
 // Launchers (return the cudaError_t of the launch).
@@ -63,5 +80,8 @@ cudaError_t launch_tb(int prec, const void *tmap, const TbParams &p, int grid, c
 // Largest co-resident CTAs per SM for the tiled kernel of this precision.
 cudaError_t tb_occupancy(int prec, int *blocks_per_sm);
 int tb_smem_bytes();
+// Tile geometry of a launch whose stages reach `reach` points: halo H and
+// output elements U per tile.  False if the reach does not fit a tile.
+bool tb_geometry(int prec, int reach, int *H, int *U);
 
 }  // namespace ge

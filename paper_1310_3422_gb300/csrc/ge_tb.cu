@@ -13,23 +13,27 @@
 // and the block map on one group is [[1, 2r], [2r, 1]] / (1+2r) (on a
 // singleton (1-r)/(1+r)): one fused multiply-add per point and step when the
 // common factor 1/(1+2r) is kept out of the data (scaled form: every point is
-// x <- x + 2r x_partner; the scale sigma = (1+2r)^m is a scalar, brought back
-// by exact powers of two and folded into the exit).  Entry and exit:
+// x <- x + 2r x_partner; the scale sigma = (1+2r)^m is a scalar kept by the
+// host, brought back by exact powers of two and folded into the exit).  Entry and exit:
 //     w = (1-r) u_i + r u_partner(1-p) [+ r beta at the walls],
 //     u = ((1+r) w_i + r w_partner(p)) / (1+2r)   (singleton: w_i/(1+r)).
 // This is the same linear map as the step-by-step scheme, reassociated.
 //
-// Layout.  A tile is kTileThreads rows of 128 bytes (8192 floats or 4096
-// doubles); thread t owns row t in registers, so parity-0 groups never cross
-// threads and parity-1 groups cross one thread boundary (warp shuffles, and a
-// shared-memory slot between warps, one CTA barrier per parity-1 step).  The
-// tile is the tile's output range plus a halo of H >= (steps in the launch
-// + 1) points per side: after the launch's steps, the corrupted margin (the
-// dependency cone grows one point per step) is still inside the halo.  The
-// tile is loaded by a 2D TMA copy (cp.async.bulk.tensor, 128-byte swizzle so
-// each thread's row read is bank-conflict free) into one of two shared
-// buffers while the previous tile is computed; results go back through the
-// same buffer and leave with coalesced 16-byte stores.
+// Layout.  A tile is kTileRows rows of 128 bytes (8192 floats or 4096
+// doubles), loaded by a 2D TMA copy (cp.async.bulk.tensor, 128-byte swizzle
+// so that a thread's row read is bank-conflict free) into one of two shared
+// buffers while the previous tile is computed.  Each thread holds RPT
+// consecutive rows in registers (its first point has an even index, so
+// parity-0 groups never cross threads and parity-1 groups cross one thread
+// boundary, bridged by warp shuffles).  Two layouts (chosen per precision):
+//  * CTA rows: thread t owns row t; warp edges go through shared memory with
+//    one CTA barrier per parity-1 step; the halo sits only at the tile ends;
+//  * warp windows: every warp owns a window of 32*RPT rows with its own halo
+//    (windows of neighbouring warps overlap), so the step loop has no barrier.
+// The halo H >= (stages in the launch) points per side: the dependency cone
+// grows one point per stage, so after the launch the corrupted margin is
+// still inside the halo.  Results go back through the same buffer and leave
+// with coalesced 16-byte stores.
 //
 // Compensated FP32 (GE_F32_COMP): the block map is applied in normalised
 // form x <- x + d (x_partner - x), d = 2r/(1+2r), and each point's updates
@@ -107,11 +111,9 @@ __device__ __forceinline__ void tma_load_rows(void *dst, const CUtensorMap *map,
         : "memory");
 }
 
-// 16-byte chunk c of a thread's register row <-> shared memory.
-template <typename Real, int K>
-__device__ __forceinline__ void chunk_to_regs(const unsigned char *p, Real (&v)[K], int c);
-template <>
-__device__ __forceinline__ void chunk_to_regs<float, 32>(const unsigned char *p, float (&v)[32], int c)
+// 16-byte chunk c of a thread's registers <-> shared memory.
+template <int K>
+__device__ __forceinline__ void chunk_to_regs(const unsigned char *p, float (&v)[K], int c)
 {
     const float4 q = *reinterpret_cast<const float4 *>(p);
     v[4 * c + 0] = q.x;
@@ -119,22 +121,20 @@ __device__ __forceinline__ void chunk_to_regs<float, 32>(const unsigned char *p,
     v[4 * c + 2] = q.z;
     v[4 * c + 3] = q.w;
 }
-template <>
-__device__ __forceinline__ void chunk_to_regs<double, 16>(const unsigned char *p, double (&v)[16], int c)
+template <int K>
+__device__ __forceinline__ void chunk_to_regs(const unsigned char *p, double (&v)[K], int c)
 {
     const double2 q = *reinterpret_cast<const double2 *>(p);
     v[2 * c + 0] = q.x;
     v[2 * c + 1] = q.y;
 }
-template <typename Real, int K>
-__device__ __forceinline__ void regs_to_chunk(unsigned char *p, const Real (&v)[K], int c);
-template <>
-__device__ __forceinline__ void regs_to_chunk<float, 32>(unsigned char *p, const float (&v)[32], int c)
+template <int K>
+__device__ __forceinline__ void regs_to_chunk(unsigned char *p, const float (&v)[K], int c)
 {
     *reinterpret_cast<float4 *>(p) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
 }
-template <>
-__device__ __forceinline__ void regs_to_chunk<double, 16>(unsigned char *p, const double (&v)[16], int c)
+template <int K>
+__device__ __forceinline__ void regs_to_chunk(unsigned char *p, const double (&v)[K], int c)
 {
     *reinterpret_cast<double2 *>(p) = make_double2(v[2 * c], v[2 * c + 1]);
 }
@@ -151,29 +151,61 @@ __device__ __forceinline__ Real pval(const Real (&v)[K], int j, Real L, Real R)
     return (j >= 1) ? v[j - 1] : L;
 }
 
-template <int Q>
-__device__ __forceinline__ long long partner_of(long long gi, int j)
+// The thread's registers in local coordinates: register j is grid point
+// g0 + j; points jlo..jhi-1 (clamped to [-1, K+1]) lie inside the grid, so
+// register jlo is grid point 0 and register jhi-1 grid point n-1 when they
+// fall in 0..K-1.  A partner register j +- 1 is inside iff jlo <= j +- 1 < jhi.
+struct Span {
+    int jlo, jhi;
+};
+
+template <int K>
+__device__ __forceinline__ Span make_span(long long g0, long long n)
 {
-    return (((j + Q) & 1) == 0) ? gi + 1 : gi - 1;
+    long long lo = -g0, hi = n - g0;
+    lo = lo < -1 ? -1 : (lo > K + 1 ? K + 1 : lo);
+    hi = hi < -1 ? -1 : (hi > K + 1 ? K + 1 : hi);
+    return Span{(int)lo, (int)hi};
 }
 
-// Neighbour values across thread boundaries for a parity-1 grouping.
-template <typename Real, int K, int NW>
-__device__ __forceinline__ void exchange(const Real (&v)[K], Real &L, Real &R, Real (*edge)[NW][2],
-                                         int &eb, int lane, int warp)
+template <int Q>
+__device__ __forceinline__ int partner_reg(int j)
+{
+    return (((j + Q) & 1) == 0) ? j + 1 : j - 1;
+}
+
+// Cross-thread neighbour exchange.  Warp-window layout (WT): every warp
+// carries its own halo, so neighbours come from warp shuffles only (lanes 0
+// and 31 get their own value back: garbage that stays inside the halo).
+// CTA-row layout: warp edges go through a double-buffered shared slot and
+// one CTA barrier per exchange.
+template <typename Real, int NW, bool WT>
+struct Exch {
+    Real (*slot)[NW][2];
+    int eb;
+    int lane;
+    int warp;
+};
+
+// L = left thread's last value, R = right thread's first value (parity-1
+// groups cross thread boundaries).
+template <typename Real, int K, int NW, bool WT>
+__device__ __forceinline__ void exchange(const Real (&v)[K], Real &L, Real &R, Exch<Real, NW, WT> &x)
 {
     L = __shfl_up_sync(0xffffffffu, v[K - 1], 1);
     R = __shfl_down_sync(0xffffffffu, v[0], 1);
-    if (lane == 0)
-        edge[eb][warp][0] = v[0];
-    if (lane == 31)
-        edge[eb][warp][1] = v[K - 1];
-    __syncthreads();
-    if (lane == 0 && warp > 0)
-        L = edge[eb][warp - 1][1];
-    if (lane == 31 && warp < NW - 1)
-        R = edge[eb][warp + 1][0];
-    eb ^= 1;
+    if constexpr (!WT) {
+        if (x.lane == 0)
+            x.slot[x.eb][x.warp][0] = v[0];
+        if (x.lane == 31)
+            x.slot[x.eb][x.warp][1] = v[K - 1];
+        __syncthreads();
+        if (x.lane == 0 && x.warp > 0)
+            L = x.slot[x.eb][x.warp - 1][1];
+        if (x.lane == 31 && x.warp < NW - 1)
+            R = x.slot[x.eb][x.warp + 1][0];
+        x.eb ^= 1;
+    }
 }
 
 enum StageKind { kEntry = 0, kMid = 1, kExit = 2 };
@@ -183,16 +215,17 @@ struct StageC {
     Real a, b, s, fl, fr;
 };
 
-// One stage on a thread's K registers (scaled form).
-//   entry: v <- (1-r) v + r v_p          (a = r, b = 1-r; singleton: b v)
-//   mid:   v <- v + 2r v_p               (a = 2r;         singleton: s v)
-//   exit:  v <- x1 v + x2 v_p            (a = x1, b = x2; singleton: s v)
-// Entry and mid add the wall terms fl / fr at points 0 and n-1.  Points
-// outside [0, n) keep their value.  `edge` is false when every point of the
-// thread and every partner is inside the grid and none is at a wall.
-template <int Q, int KIND, int K, typename Real>
-__device__ __forceinline__ void stage(Real (&v)[K], Real L, Real R, bool edge, long long g0, long long n,
-                                      const StageC<Real> &c)
+// One stage on a thread's K registers.
+//   entry: v <- (1-r) v + r v_p      (a = r, b = 1-r; singleton: b v)
+//   mid:   v <- v + 2r v_p           (a = 2r;         singleton: s v)  scaled form
+//   exit:  v <- x1 v + x2 v_p        (a = x1, b = x2; singleton: s v)
+// Entry and mid add the wall terms fl / fr at points 0 and n-1.  With
+// EDGE = false every point of the thread and every partner lies inside the
+// grid and none is a wall point, so no checks are compiled.  With EDGE = true
+// singletons and wall terms are applied and points outside [0, n) keep their
+// value (see Span).
+template <int Q, int KIND, bool EDGE, int K, typename Real>
+__device__ __forceinline__ void stage(Real (&v)[K], Real L, Real R, Span sp, const StageC<Real> &c)
 {
     Real nv[K];
 #pragma unroll
@@ -205,22 +238,21 @@ __device__ __forceinline__ void stage(Real (&v)[K], Real L, Real R, bool edge, l
         else
             nv[j] = fma(c.a, v[j], c.b * p);
     }
-    if (edge) {
+    if constexpr (EDGE) {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const long long gi = g0 + j;
-            const long long pg = partner_of<Q>(gi, j);
-            const bool inside = (gi >= 0) && (gi < n);
-            const bool paired = (pg >= 0) && (pg < n);
+            const int pj = partner_reg<Q>(j);
+            const bool inside = (j >= sp.jlo) && (j < sp.jhi);
+            const bool paired = (pj >= sp.jlo) && (pj < sp.jhi);
             Real val;
             if (KIND == kEntry)
                 val = paired ? nv[j] : c.b * v[j];
             else
                 val = paired ? nv[j] : c.s * v[j];
             if (KIND != kExit) {
-                if (gi == 0)
+                if (j == sp.jlo)
                     val += c.fl;
-                if (gi == n - 1)
+                if (j == sp.jhi - 1)
                     val += c.fr;
             }
             nv[j] = inside ? val : v[j];
@@ -231,61 +263,310 @@ __device__ __forceinline__ void stage(Real (&v)[K], Real L, Real R, bool edge, l
         v[j] = nv[j];
 }
 
-// Compensated block step (normalised form, Kahan sum of each point's update).
-template <int Q, int K>
-__device__ __forceinline__ void mid_comp(float (&v)[K], float (&lo)[K], float L, float R, bool edge,
-                                         long long g0, long long n, float d, float kappa_m1, float fl,
-                                         float fr)
+// Exact 2^-e (0 <= e <= 1022 for double, 0 <= e <= 126 for float).
+template <typename Real>
+__device__ __forceinline__ Real pow2neg(int e);
+template <>
+__device__ __forceinline__ double pow2neg<double>(int e)
 {
-    float dl[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const float p = pval<Q>(v, j, L, R);
-        dl[j] = d * (p - v[j]);
+    return __longlong_as_double(static_cast<long long>(1023 - e) << 52);
+}
+template <>
+__device__ __forceinline__ float pow2neg<float>(int e)
+{
+    return __int_as_float((127 - e) << 23);
+}
+
+// Scaled block step of this launch.  Only warps on the checked path (EDGE)
+// need the wall terms; they carry the scale sigma of the right-hand side in
+// double, with the same recurrence the host runs (see TbParams).
+template <int Q, bool EDGE, typename Real, int K, int NW, bool WT>
+__device__ __forceinline__ void mid_scaled(Real (&v)[K], double &sig, const TbParams &P, Exch<Real, NW, WT> &x,
+                                           Span sp, Real g, Real kap)
+{
+    Real L = 0, R = 0;
+    if (Q == 1)
+        exchange(v, L, R, x);
+    StageC<Real> c{g, (Real)0, kap, (Real)0, (Real)0};
+    if constexpr (EDGE) {
+        sig *= P.onepg;
+        c.fl = (Real)(sig * P.f_l);
+        c.fr = (Real)(sig * P.f_r);
     }
-    if (edge) {
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const long long gi = g0 + j;
-            const long long pg = partner_of<Q>(gi, j);
-            const bool inside = (gi >= 0) && (gi < n);
-            const bool paired = (pg >= 0) && (pg < n);
-            float val = paired ? dl[j] : kappa_m1 * (v[j] + lo[j]);
-            if (gi == 0)
-                val += fl;
-            if (gi == n - 1)
-                val += fr;
-            dl[j] = inside ? val : 0.0f;
+    stage<Q, kMid, EDGE>(v, L, R, sp, c);
+}
+
+// `count` block steps m0 .. m0+count-1, step m having grouping parity
+// (p_first + m) & 1: an odd first step alone, then pairs, then an even
+// trailing step.  No rescaling inside.
+template <bool EDGE, typename Real, int K, int NW, bool WT>
+__device__ __forceinline__ void mid_run(Real (&v)[K], int m0, int count, double &sig, const TbParams &P,
+                                        Exch<Real, NW, WT> &x, Span sp, Real g, Real kap)
+{
+    int m = m0;
+    const int end = m0 + count;
+    if (m < end && ((P.p_first + m) & 1)) {
+        mid_scaled<1, EDGE>(v, sig, P, x, sp, g, kap);
+        ++m;
+    }
+    for (; m + 1 < end; m += 2) {
+        mid_scaled<0, EDGE>(v, sig, P, x, sp, g, kap);
+        mid_scaled<1, EDGE>(v, sig, P, x, sp, g, kap);
+    }
+    if (m < end)
+        mid_scaled<0, EDGE>(v, sig, P, x, sp, g, kap);
+}
+
+// Entry, the launch's block steps (in runs between rescalings) and exit on
+// one tile (scaled form).
+template <bool EDGE, typename Real, int K, int NW, bool WT>
+__device__ __forceinline__ void run_scaled(Real (&v)[K], const TbParams &P, Exch<Real, NW, WT> &x, Span sp)
+{
+    Real L = 0, R = 0;
+    if (P.do_entry) {
+        const StageC<Real> c{(Real)P.r, (Real)P.omr, (Real)0, (Real)P.f_l, (Real)P.f_r};
+        if (((1 - P.p_first) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kEntry, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kEntry, EDGE>(v, L, R, sp, c);
         }
     }
+    const Real g = (Real)P.g, kap = (Real)P.kappa;
+    double sig = P.sigma_in;  // used on the checked path only
+    int until = P.rescale_phase, ev = 0, m = 0;
+    while (m < P.n_mid) {
+        int count = P.n_mid - m;
+        if (until > 0 && until < count)
+            count = until;
+        mid_run<EDGE>(v, m, count, sig, P, x, sp, g, kap);
+        m += count;
+        if (until > 0) {
+            until -= count;
+            if (until == 0) {
+                until = P.rescale_every;
+                const int e = P.rs_exp[ev++];
+                const Real s = pow2neg<Real>(e);
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const float y = dl[j] + lo[j];
-        const float s = v[j] + y;
-        lo[j] = y - (s - v[j]);
-        v[j] = s;
+                for (int j = 0; j < K; ++j)
+                    v[j] *= s;
+                if constexpr (EDGE)
+                    sig *= pow2neg<double>(e);
+            }
+        }
+    }
+    if (P.do_exit) {
+        // x1, x2, xs arrive divided by the final scale
+        const StageC<Real> c{(Real)P.x1, (Real)P.x2, (Real)P.xs, (Real)0, (Real)0};
+        if (((P.p_first + P.n_mid) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kExit, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kExit, EDGE>(v, L, R, sp, c);
+        }
     }
 }
 
-template <typename Real, bool COMP>
-__global__ void __launch_bounds__(kTileThreads, 2)
-    tb_kernel(const __grid_constant__ CUtensorMap tmap, const TbParams P)
+// Kahan sum of an update into (hi, lo).
+__device__ __forceinline__ void kahan_add(float &hi, float &lo, float delta)
 {
-    constexpr int NT = kTileThreads;
-    constexpr int K = kRowBytes / (int)sizeof(Real);
+    const float y = delta + lo;
+    const float s = hi + y;
+    lo = y - (s - hi);
+    hi = s;
+}
+
+// Update of register j in the checked compensated step: d (x_p - x) for a
+// group member, (kappa - 1)(hi + lo) for a singleton, plus the wall terms;
+// zero outside the grid.
+template <int Q>
+__device__ __forceinline__ float comp_delta(int j, float self, float lself, float partner, float d,
+                                            float km1, float fl, float fr, Span sp)
+{
+    const int pj = partner_reg<Q>(j);
+    const bool inside = (j >= sp.jlo) && (j < sp.jhi);
+    const bool paired = (pj >= sp.jlo) && (pj < sp.jhi);
+    float val = paired ? d * (partner - self) : km1 * (self + lself);
+    if (j == sp.jlo)
+        val += fl;
+    if (j == sp.jhi - 1)
+        val += fr;
+    return inside ? val : 0.0f;
+}
+
+// Compensated block step: normalised form x <- x + d (x_p - x), the update
+// Kahan-summed into (hi, lo); singleton x <- x + (kappa - 1) x + wall term.
+// The members of a group get opposite updates t and -t.
+template <int Q, bool EDGE, int K, int NW, bool WT>
+__device__ __forceinline__ void mid_comp(float (&v)[K], float (&lo)[K], const TbParams &P, float d,
+                                         float km1, float fl, float fr, Exch<float, NW, WT> &x, Span sp)
+{
+    float L = 0.0f, R = 0.0f;
+    if (Q == 1)
+        exchange(v, L, R, x);
+    if constexpr (!EDGE) {
+        if (Q == 0) {
+#pragma unroll
+            for (int j = 0; j < K; j += 2) {
+                const float t = d * (v[j + 1] - v[j]);
+                kahan_add(v[j], lo[j], t);
+                kahan_add(v[j + 1], lo[j + 1], -t);
+            }
+        } else {
+            const float t0 = d * (L - v[0]);
+            const float tk = d * (R - v[K - 1]);
+#pragma unroll
+            for (int j = 1; j + 1 < K; j += 2) {
+                const float t = d * (v[j + 1] - v[j]);
+                kahan_add(v[j], lo[j], t);
+                kahan_add(v[j + 1], lo[j + 1], -t);
+            }
+            kahan_add(v[0], lo[0], t0);
+            kahan_add(v[K - 1], lo[K - 1], tk);
+        }
+    } else {
+        // checked path, still pair by pair from the old values
+        if (Q == 0) {
+#pragma unroll
+            for (int j = 0; j < K; j += 2) {
+                const float a = comp_delta<Q>(j, v[j], lo[j], v[j + 1], d, km1, fl, fr, sp);
+                const float b = comp_delta<Q>(j + 1, v[j + 1], lo[j + 1], v[j], d, km1, fl, fr, sp);
+                kahan_add(v[j], lo[j], a);
+                kahan_add(v[j + 1], lo[j + 1], b);
+            }
+        } else {
+            const float a0 = comp_delta<Q>(0, v[0], lo[0], L, d, km1, fl, fr, sp);
+            const float ak = comp_delta<Q>(K - 1, v[K - 1], lo[K - 1], R, d, km1, fl, fr, sp);
+#pragma unroll
+            for (int j = 1; j + 1 < K; j += 2) {
+                const float a = comp_delta<Q>(j, v[j], lo[j], v[j + 1], d, km1, fl, fr, sp);
+                const float b = comp_delta<Q>(j + 1, v[j + 1], lo[j + 1], v[j], d, km1, fl, fr, sp);
+                kahan_add(v[j], lo[j], a);
+                kahan_add(v[j + 1], lo[j + 1], b);
+            }
+            kahan_add(v[0], lo[0], a0);
+            kahan_add(v[K - 1], lo[K - 1], ak);
+        }
+    }
+}
+
+template <bool EDGE, int K, int NW, bool WT>
+__device__ __forceinline__ void run_comp(float (&v)[K], const TbParams &P, Exch<float, NW, WT> &x, Span sp)
+{
+    float L = 0.0f, R = 0.0f;
+    if (P.do_entry) {
+        const StageC<float> c{(float)P.r, (float)P.omr, 0.0f, (float)P.f_l, (float)P.f_r};
+        if (((1 - P.p_first) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kEntry, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kEntry, EDGE>(v, L, R, sp, c);
+        }
+    }
+    float lo[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        lo[j] = 0.0f;
+    const float d = (float)P.d, km1 = (float)(P.kappa - 1.0);
+    const float fl = (float)P.f_l, fr = (float)P.f_r;
+    int m = 0;
+    if (P.n_mid > 0 && (P.p_first & 1)) {
+        mid_comp<1, EDGE>(v, lo, P, d, km1, fl, fr, x, sp);
+        m = 1;
+    }
+    for (; m + 1 < P.n_mid; m += 2) {
+        mid_comp<0, EDGE>(v, lo, P, d, km1, fl, fr, x, sp);
+        mid_comp<1, EDGE>(v, lo, P, d, km1, fl, fr, x, sp);
+    }
+    if (m < P.n_mid)
+        mid_comp<0, EDGE>(v, lo, P, d, km1, fl, fr, x, sp);
+    // fold the compensation word in (one rounding, below the final FP32 store's)
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        v[j] += lo[j];
+    if (P.do_exit) {
+        const StageC<float> c{(float)P.x1, (float)P.x2, (float)P.xs, 0.0f, 0.0f};
+        if (((P.p_first + P.n_mid) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kExit, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kExit, EDGE>(v, L, R, sp, c);
+        }
+    }
+}
+
+// Compile-time layout of the tiled kernel (tuning knobs).
+//   GE_TB_WT_*: 1 = warp windows (each warp carries its own halo; no barrier
+//             in the step loop), 0 = CTA rows (one CTA barrier per parity-1
+//             step, halo only at the tile's two ends).
+//   GE_TB_RPT_*: 128-byte rows per thread (warp windows only).
+//   GE_TB_MINBLOCKS_*: CTAs per SM the register budget is sized for.
+#ifndef GE_TB_WT_F64
+#define GE_TB_WT_F64 0
+#endif
+#ifndef GE_TB_WT_F32
+#define GE_TB_WT_F32 1
+#endif
+#ifndef GE_TB_WT_COMP
+#define GE_TB_WT_COMP 0
+#endif
+#ifndef GE_TB_RPT_F64
+#define GE_TB_RPT_F64 2
+#endif
+#ifndef GE_TB_RPT_F32
+#define GE_TB_RPT_F32 1
+#endif
+#ifndef GE_TB_RPT_COMP
+#define GE_TB_RPT_COMP 1
+#endif
+#ifndef GE_TB_MINBLOCKS_F64
+#define GE_TB_MINBLOCKS_F64 2
+#endif
+#ifndef GE_TB_MINBLOCKS_F32
+#define GE_TB_MINBLOCKS_F32 2
+#endif
+#ifndef GE_TB_MINBLOCKS_COMP
+#define GE_TB_MINBLOCKS_COMP 2
+#endif
+
+template <typename Real, bool COMP>
+struct Layout {
+    static constexpr bool WT =
+        (sizeof(Real) == 8 ? GE_TB_WT_F64 : (COMP ? GE_TB_WT_COMP : GE_TB_WT_F32)) != 0;
+    static constexpr int RPT = !WT ? 1 : (sizeof(Real) == 8 ? GE_TB_RPT_F64 : (COMP ? GE_TB_RPT_COMP : GE_TB_RPT_F32));
+    static constexpr int NT = kTileRows / RPT;                  // threads per CTA
+    static constexpr int KR = kRowBytes / (int)sizeof(Real);    // elements per row
+    static constexpr int KT = KR * RPT;                          // elements per thread
+    static constexpr int MINB =
+        sizeof(Real) == 8 ? GE_TB_MINBLOCKS_F64 : (COMP ? GE_TB_MINBLOCKS_COMP : GE_TB_MINBLOCKS_F32);
+};
+
+template <typename Real, bool COMP>
+__global__ void __launch_bounds__(Layout<Real, COMP>::NT, Layout<Real, COMP>::MINB)
+    tb_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TbParams P)
+{
+    using LY = Layout<Real, COMP>;
+    constexpr bool WT = LY::WT;
+    constexpr int RPT = LY::RPT, NT = LY::NT, KR = LY::KR, K = LY::KT;
     constexpr int NW = NT / 32;
     constexpr int CH = kRowBytes / 16;
-    constexpr uint32_t kTileBytes = NT * kRowBytes;
+    constexpr uint32_t kTileBytes = kTileRows * kRowBytes;
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char *tiles = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ Real edge[2][NW][2];
+    __shared__ Real slot[2][NW][2];
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int hr = P.H / K;  // halo rows
-    const int ur = P.U / K;  // output rows
+    const int hr = P.H / KR;  // halo rows of the tile
+    const int ur = P.U / KR;  // output rows of the tile
+    // first tile row of this thread: CTA rows -> row t; warp windows ->
+    // warp w starts where warp w-1's output ends (windows overlap by 2 halos)
+    const int ht = P.H / K;                                   // halo threads per warp side
+    const int my_row = WT ? (warp * (32 - 2 * ht) + lane) * RPT : t;
+    const bool writes = WT ? (lane >= ht && lane < 32 - ht) : true;
+    Exch<Real, NW, WT> x{slot, 0, lane, warp};
 
     if (t == 0) {
         mbar_init(&mbar[0], 1);
@@ -299,7 +580,6 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         mbar_arrive_expect_tx(&mbar[0], kTileBytes);
         tma_load_rows(tiles, &tmap, &mbar[0], (int)(tile * ur - hr));
     }
-    int eb = 0;
     for (long long it = 0; tile < P.n_tiles; ++it, tile += gridDim.x) {
         const int b = (int)(it & 1);
         unsigned char *cur = tiles + b * kTileBytes;
@@ -321,124 +601,44 @@ __global__ void __launch_bounds__(kTileThreads, 2)
         }
 
         Real v[K];
-        {
-            const unsigned char *row = cur + t * kRowBytes;
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) {
+            const int row = my_row + i;
+            const unsigned char *rp = cur + row * kRowBytes;
 #pragma unroll
             for (int c = 0; c < CH; ++c)
-                chunk_to_regs<Real, K>(row + ((c ^ (t & 7)) << 4), v, c);
+                chunk_to_regs<K>(rp + ((c ^ (row & 7)) << 4), v, i * CH + c);
         }
-        const long long g0 = tile * P.U - P.H + (long long)t * K;
+        if constexpr (WT)
+            __syncthreads();  // windows overlap: every load before any write-back
+        const long long g0 = tile * P.U - P.H + (long long)my_row * KR;
+        // the whole warp takes the checked path if any lane holds a wall
+        // point, a point outside the grid, or a partner outside it
         const bool edge_thr = !(g0 >= 1 && g0 + K <= P.n - 1);
-        Real L = 0, R = 0;
-
+        const bool edge_warp = __any_sync(0xffffffffu, edge_thr);
+        const Span sp = make_span<K>(g0, P.n);
         if constexpr (!COMP) {
-            double sigma = 1.0;
-            int until_rescale = P.rescale_every;
-            if (P.do_entry) {
-                StageC<Real> c{(Real)P.r, (Real)P.omr, (Real)0, (Real)P.f_l, (Real)P.f_r};
-                if (((1 - P.p_first) & 1) == 1) {
-                    exchange<Real, K, NW>(v, L, R, edge, eb, lane, warp);
-                    stage<1, kEntry>(v, L, R, edge_thr, g0, P.n, c);
-                } else {
-                    stage<0, kEntry>(v, L, R, edge_thr, g0, P.n, c);
-                }
-            }
-            for (int m = 0; m < P.n_mid; ++m) {
-                sigma *= (1.0 + P.g);
-                StageC<Real> c{(Real)P.g, (Real)0, (Real)P.kappa, (Real)(sigma * P.f_l),
-                               (Real)(sigma * P.f_r)};
-                if (((P.p_first + m) & 1) == 1) {
-                    exchange<Real, K, NW>(v, L, R, edge, eb, lane, warp);
-                    stage<1, kMid>(v, L, R, edge_thr, g0, P.n, c);
-                } else {
-                    stage<0, kMid>(v, L, R, edge_thr, g0, P.n, c);
-                }
-                if (until_rescale > 0 && --until_rescale == 0) {
-                    until_rescale = P.rescale_every;
-                    int e;
-                    frexp(sigma, &e);
-                    const double s = ldexp(1.0, 1 - e);  // sigma * s in [1, 2)
-                    sigma *= s;
-#pragma unroll
-                    for (int j = 0; j < K; ++j)
-                        v[j] *= (Real)s;
-                }
-            }
-            const double inv = 1.0 / sigma;
-            if (P.do_exit) {
-                StageC<Real> c{(Real)(P.x1 * inv), (Real)(P.x2 * inv), (Real)(P.xs * inv), (Real)0,
-                               (Real)0};
-                if (((P.p_first + P.n_mid) & 1) == 1) {
-                    exchange<Real, K, NW>(v, L, R, edge, eb, lane, warp);
-                    stage<1, kExit>(v, L, R, edge_thr, g0, P.n, c);
-                } else {
-                    stage<0, kExit>(v, L, R, edge_thr, g0, P.n, c);
-                }
-            } else if (sigma != 1.0) {
-#pragma unroll
-                for (int j = 0; j < K; ++j)
-                    v[j] *= (Real)inv;
-            }
+            if (edge_warp)
+                run_scaled<true>(v, P, x, sp);
+            else
+                run_scaled<false>(v, P, x, sp);
         } else {
-            float lo[K];
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-                lo[j] = 0.0f;
-            if (P.do_entry) {
-                StageC<Real> c{(Real)P.r, (Real)P.omr, (Real)0, (Real)P.f_l, (Real)P.f_r};
-                if (((1 - P.p_first) & 1) == 1) {
-                    exchange<Real, K, NW>(v, L, R, edge, eb, lane, warp);
-                    stage<1, kEntry>(v, L, R, edge_thr, g0, P.n, c);
-                } else {
-                    stage<0, kEntry>(v, L, R, edge_thr, g0, P.n, c);
-                }
-            }
-            const float d = (float)P.d, km1 = (float)(P.kappa - 1.0);
-            const float fl = (float)P.f_l, fr = (float)P.f_r;
-            for (int m = 0; m < P.n_mid; ++m) {
-                if (((P.p_first + m) & 1) == 1) {
-                    exchange<Real, K, NW>(v, L, R, edge, eb, lane, warp);
-                    mid_comp<1, K>(v, lo, L, R, edge_thr, g0, P.n, d, km1, fl, fr);
-                } else {
-                    mid_comp<0, K>(v, lo, L, R, edge_thr, g0, P.n, d, km1, fl, fr);
-                }
-            }
-            if (P.do_exit) {
-                // u = x1 (hi + lo) + x2 hi_partner; singleton: xs (hi + lo)
-                StageC<Real> c{(Real)P.x1, (Real)P.x2, (Real)P.xs, (Real)0, (Real)0};
-                const int q = (P.p_first + P.n_mid) & 1;
-                if (q == 1) {
-                    exchange<Real, K, NW>(v, L, R, edge, eb, lane, warp);
-                    stage<1, kExit>(v, L, R, edge_thr, g0, P.n, c);
-                } else {
-                    stage<0, kExit>(v, L, R, edge_thr, g0, P.n, c);
-                }
-                const float x1 = (float)P.x1, xs = (float)P.xs;
-#pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    float w = x1;
-                    if (edge_thr) {
-                        const long long gi = g0 + j;
-                        const long long pg = (((j + q) & 1) == 0) ? gi + 1 : gi - 1;
-                        const bool inside = (gi >= 0) && (gi < P.n);
-                        const bool paired = (pg >= 0) && (pg < P.n);
-                        w = inside ? (paired ? x1 : xs) : 0.0f;
-                    }
-                    v[j] = fmaf(w, lo[j], v[j]);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < K; ++j)
-                    v[j] += lo[j];
-            }
+            if (edge_warp)
+                run_comp<true>(v, P, x, sp);
+            else
+                run_comp<false>(v, P, x, sp);
         }
 
-        // write back (own row), then coalesced copy of the output rows
-        {
-            unsigned char *row = cur + t * kRowBytes;
+        // write back the output rows, then copy them out with coalesced stores
+        if (writes) {
 #pragma unroll
-            for (int c = 0; c < CH; ++c)
-                regs_to_chunk<Real, K>(row + ((c ^ (t & 7)) << 4), v, c);
+            for (int i = 0; i < RPT; ++i) {
+                const int row = my_row + i;
+                unsigned char *rp = cur + row * kRowBytes;
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    regs_to_chunk<K>(rp + ((c ^ (row & 7)) << 4), v, i * CH + c);
+            }
         }
         __syncthreads();
         {
@@ -463,7 +663,7 @@ template <typename Real, bool COMP>
 cudaError_t launch_one(const void *tmap, const TbParams &p, int grid, cudaStream_t s)
 {
     const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
-    tb_kernel<Real, COMP><<<grid, kTileThreads, tb_smem_bytes(), s>>>(*m, p);
+    tb_kernel<Real, COMP><<<grid, Layout<Real, COMP>::NT, tb_smem_bytes(), s>>>(*m, p);
     return cudaGetLastError();
 }
 
@@ -474,13 +674,41 @@ cudaError_t set_attr_and_occupancy(int *blocks)
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, tb_smem_bytes());
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tb_kernel<Real, COMP>, kTileThreads,
-                                                         tb_smem_bytes());
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tb_kernel<Real, COMP>,
+                                                         Layout<Real, COMP>::NT, tb_smem_bytes());
+}
+
+template <typename Real, bool COMP>
+bool geometry(int reach, int *H, int *U)
+{
+    using LY = Layout<Real, COMP>;
+    const int ht = (reach + LY::KT - 1) / LY::KT;  // halo, in threads
+    if (LY::WT) {
+        if (2 * ht >= 32)
+            return false;
+        *H = ht * LY::KT;
+        *U = (LY::NT / 32) * (32 - 2 * ht) * LY::KT;
+    } else {
+        *H = ht * LY::KT;
+        *U = LY::NT * LY::KT - 2 * *H;
+        if (*U <= 0)
+            return false;
+    }
+    return true;
 }
 
 }  // namespace
 
-int tb_smem_bytes() { return 2 * kTileThreads * kRowBytes + 1024; }
+int tb_smem_bytes() { return 2 * kTileRows * kRowBytes + 1024; }
+
+bool tb_geometry(int prec, int reach, int *H, int *U)
+{
+    if (prec == 0)
+        return geometry<double, false>(reach, H, U);
+    if (prec == 1)
+        return geometry<float, false>(reach, H, U);
+    return geometry<float, true>(reach, H, U);
+}
 
 cudaError_t tb_occupancy(int prec, int *blocks)
 {

@@ -7,9 +7,10 @@ Tolerances:
     FP64 evaluations of the same steps differ by up to the round-off each one
     carries, which scales with the step's max-norm 2r - 1 (the sum of the
     magnitudes of the coefficients of Eqs. (cc)/(dd)).  For r <= 1 this is the
-    plain 1e-12 target; test_large_r_error_is_conditioning shows that at
-    large r the kernel is as close to an extended-precision evaluation as the
-    oracle is.
+    plain 1e-12 target.  At very large r on rough data (r = 1e4) any FP64
+    evaluation is off by ~1e-6 (the bound grows like steps * kappa^2 * eps);
+    there test_large_r_error_is_conditioning checks that the kernel is as
+    close to an extended-precision evaluation as the oracle is.
   * FP32 / FP32 compensated: 1e-5 relative max-norm against the FP64 oracle
     (the accuracy target for the FP32 path) at the step counts used here.
 """
@@ -101,7 +102,7 @@ def test_tiled_f64_depths_and_parity(depth, step0):
     assert rel_max(got, want) <= tol64(0.8)
 
 
-@pytest.mark.parametrize("r", [0.01, 0.25, 0.5, 1.0, 4.0, 50.0, 1.0e4])
+@pytest.mark.parametrize("r", [0.01, 0.25, 0.5, 1.0, 4.0, 50.0])
 def test_tiled_f64_range_of_r(r):
     n = 5000
     u0 = inputs.random_state(n, seed=7)
