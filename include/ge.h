@@ -135,6 +135,30 @@ ge_status ge_solve(int64_t n, double r, double beta_l, double beta_r, ge_precisi
                    ge_kernel kernel, int32_t depth, int64_t steps, const void *u0_host,
                    void *u_out_host, void *stream);
 
+/* The tiled solve (GE_KERNEL_TEMPORAL) for callers that may not allocate
+ * device memory: a plug-in inside a host application or server that owns all
+ * device memory through its own pool, a real-time loop that cannot take
+ * cudaMalloc's implicit synchronisation, or a sandbox without driver
+ * allocations after start-up.  The paper has no counterpart; it is a
+ * deployment variant of the same kernel.
+ *   u0_dev      n elements of the initial state (device, caller-owned).
+ *   u_out_dev   n elements receiving the state after `steps` steps from
+ *               step counter 0 (device, caller-owned; may alias u0_dev).
+ *   depth       steps per launch, 0 = built-in default, up to 1023.
+ * It allocates nothing: its working memory (two padded state buffers and the
+ * device error word) is one static device array of 16 MiB + 256 bytes that
+ * every GPU loading the library holds until exit, so n is limited to
+ * 1,048,576 points (GE_EINVAL beyond).  The first call on a device looks the
+ * array's address up (with that device current); make it before any stream
+ * capture.  Every call on a device shares the array: calls whose GPU work
+ * overlaps (other streams, other host threads) race, so serialise them.
+ * Synchronous: returns once u_out_dev holds the result.
+ * Errors: GE_EINVAL (n out of range, bad r, beta, prec, depth, steps, NULL
+ * buffer), GE_ECUDA, GE_ETIMEOUT (a bounded device wait gave up). */
+ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double beta_r, ge_precision prec,
+                           int32_t depth, int64_t steps, const void *u0_dev, void *u_out_dev,
+                           void *stream);
+
 /* Name of a status code (static string). */
 const char *ge_status_str(ge_status status);
 

@@ -23,7 +23,8 @@ GE_KERNEL_AUTO, GE_KERNEL_CANONICAL, GE_KERNEL_ONESTEP, GE_KERNEL_TEMPORAL = 0, 
 
 # Every symbol include/ge.h declares.
 EXPORTS = ("ge_create", "ge_set_kernel", "ge_step_n", "ge_read_state", "ge_write_state",
-           "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_status_str", "ge_last_error")
+           "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_solve_noalloc", "ge_status_str",
+           "ge_last_error")
 
 _lock = threading.Lock()
 _lib = None
@@ -68,6 +69,8 @@ def load(path: str | None = None):
         lib.ge_destroy.restype = None
         lib.ge_solve.argtypes = [_I64, _D, _D, _D, ctypes.c_int, ctypes.c_int, _I32, _I64, _VP, _VP, _VP]
         lib.ge_solve.restype = ctypes.c_int
+        lib.ge_solve_noalloc.argtypes = [_I64, _D, _D, _D, ctypes.c_int, _I32, _I64, _VP, _VP, _VP]
+        lib.ge_solve_noalloc.restype = ctypes.c_int
         lib.ge_status_str.argtypes = [ctypes.c_int]
         lib.ge_status_str.restype = ctypes.c_char_p
         lib.ge_last_error.argtypes = []
@@ -179,6 +182,18 @@ def ge_solve(n: int, r: float, beta_l: float, beta_r: float, prec: int, kernel: 
     _check(load().ge_solve(int(n), float(r), float(beta_l), float(beta_r), int(prec), int(kernel),
                            int(depth), int(steps), u0_host.ctypes.data, u_out_host.ctypes.data,
                            _stream_handle(stream)), "ge_solve")
+
+
+def ge_solve_noalloc(n: int, r: float, beta_l: float, beta_r: float, prec: int, depth: int, steps: int,
+                     u0, u_out, stream=None):
+    """Tiled solve that allocates no device memory (fixed working memory in
+    the library; n <= 1,048,576).  u0 / u_out: CUDA tensors of n elements."""
+    for a in (u0, u_out):
+        if a.numel() < n or a.dtype != dtype_of(prec):
+            raise ValueError("buffers must hold n elements of the precision's dtype")
+    _check(load().ge_solve_noalloc(int(n), float(r), float(beta_l), float(beta_r), int(prec), int(depth),
+                                   int(steps), _dptr(u0), _dptr(u_out), _stream_handle(stream)),
+           "ge_solve_noalloc")
 
 
 def ge_status_str(status: int) -> str:

@@ -64,6 +64,10 @@ int elems_per_row(ge_precision p) { return ge::kRowBytes / (int)elem_size(p); }
 
 }  // namespace
 
+namespace ge {
+void set_last_error(const char *msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+}  // namespace ge
+
 struct ge_ctx {
     CUtensorMap tmap[2];  // one per buffer (source of a tiled launch)
     int64_t n = 0;

@@ -84,4 +84,7 @@ int tb_smem_bytes();
 // output elements U per tile.  False if the reach does not fit a tile.
 bool tb_geometry(int prec, int reach, int *H, int *U);
 
+// Record the calling thread's last-failure text (read by ge_last_error()).
+void set_last_error(const char *msg);
+
 }  // namespace ge
