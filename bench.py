@@ -37,6 +37,24 @@ REF_SAMPLE_STEPS = 10      # --impl reference: 10 GE steps over the full grid pe
 N_SAMPLES = 12             # oracle-checked sample points
 
 
+def measured_traffic(kernel_name: str):
+    """Per-launch DRAM bytes of `kernel_name` from profiles/traffic.txt, or None
+    when absent or when the kernel source changed since the capture."""
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_1310_3422_gb300", "csrc", "ge_tb.cu"), "rb").read()
+        digest = hashlib.sha256(src).hexdigest()
+        for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
+            if line.startswith("#") or not line.strip():
+                continue
+            name, sha, nbytes = line.split()[:3]
+            if name == kernel_name and digest.startswith(sha):
+                return int(nbytes)
+    except Exception:
+        return None
+    return None
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -308,9 +326,12 @@ def main():
     alu_peak = 2.0 * FMA_PER_CLK[args.precision] * SMS * sm_max_mhz * 1e6  # flop/s
     if args.kernel == "temporal":
         achieved = flops_per_update * N_POINTS * (GE_STEPS / n_launch) / (launch_ms / 1e3)
+        kname = "tb_kernel<%s>" % ("double" if prec == B.GE_F64 else "float")
+        traffic = measured_traffic(kname) if (prec == B.GE_F64 and depth == 48) else None
         roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
                     "unit": "TFLOP/s", "frac": achieved / alu_peak,
-                    "traffic": None, "peak_source": "derived: %g FMA/clk/SM x %d SMs x %.0f MHz"
+                    "traffic": traffic, "algorithmic_bytes_per_launch": 2 * bytes_per_update * N_POINTS,
+                    "peak_source": "derived: %g FMA/clk/SM x %d SMs x %.0f MHz"
                     % (FMA_PER_CLK[args.precision], SMS, sm_max_mhz),
                     "kernel": "tb_kernel<%s>" % ("double" if prec == B.GE_F64 else "float")}
     else:
