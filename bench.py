@@ -222,6 +222,57 @@ def measure_e2e(B, torch, u0, prec, kern, depth, steps, world):
             "ms_per_step": t_e2e * 1e3, "timer": "host wall clock around ge_solve (synchronous)"}
 
 
+def measure_batch(B, torch, inputs, dev, steps, warmup):
+    """Batched workload: 4096 problems, N log-uniform in [256, 65536], r in
+    [0.25, 4], 2000 steps.  One CUDA-graph replay per solve (reset from u0 +
+    ge_batch_run); depth autotuned; sampled problems checked against the
+    oracle."""
+    import oracle
+    bt = inputs.uneven_batch()
+    upd = float(bt.n.sum()) * 2000
+    out = {"workload": "4096 problems, N log-uniform [256,65536] even, r U[0.25,4], walls U(-1,1), "
+                       "u0 = linear + 16-mode Fourier (1/k^2), 2000 steps",
+           "updates_per_solve": upd}
+    rng = np.random.default_rng(11)
+    picks = list(rng.choice(len(bt.n), 6, replace=False)) + [int(np.argmin(bt.n)), int(np.argmax(bt.n))]
+    want = {i: oracle.run(bt.u0[bt.offsets[i]:bt.offsets[i] + bt.n[i]], bt.r[i], bt.beta_l[i], bt.beta_r[i], 2000)
+            for i in picks}
+    for name, prec in (("f32", B.GE_F32), ("f32c", B.GE_F32_COMP), ("f64", B.GE_F64)):
+        s = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(s):
+            u0 = torch.from_numpy(bt.u0).to(dev, B.dtype_of(prec))
+            u = u0.clone()
+            plan = B.ge_batch_create(bt.n, bt.r, bt.beta_l, bt.beta_r, bt.offsets, bt.total, prec, stream=s)
+            depth = B.ge_batch_tune(plan, u0, 256)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                u.copy_(u0)
+                B.ge_batch_run(plan, u, 2000)
+            for _ in range(warmup):
+                g.replay()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(steps):
+                g.replay()
+            e1.record(s)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            B.ge_batch_sync(plan)
+            got = u.double().cpu().numpy()
+            errs = []
+            for i in picks:
+                o, n = bt.offsets[i], bt.n[i]
+                w = want[i]
+                errs.append(float(np.max(np.abs(got[o:o + n] - w)) / np.max(np.abs(w))))
+            B.ge_batch_destroy(plan)
+        out[name] = {"updates_per_s": upd / (ms / 1e3), "ms_per_solve": ms, "depth": depth,
+                     "launches_per_solve": (2000 + depth - 1) // depth,
+                     "max_rel_err_sampled": max(errs), "problems_checked": len(picks)}
+    return out
+
+
 def launches_per_solve(kernel, depth):
     if kernel == "canonical":
         return GE_STEPS
@@ -392,6 +443,11 @@ def main():
             del x2, o2
         del flush_buf
 
+    # ---- batched workload (many uneven problems, one graph per solve) ------
+    batched = None
+    if not args.no_variants and world == 1:
+        batched = measure_batch(B, torch, inputs, dev, 3, 2)
+
     # ---- CPU baseline: the oracle on a bounded sample -----------------------
     cpu = None
     if not args.no_cpu:
@@ -422,6 +478,7 @@ def main():
         "clocks": sampler.summary(),
         "accuracy": acc,
         "variants": variants,
+        "batched": batched,
     }
     B.ge_destroy(ctx)
     print(json.dumps(line), flush=True)

@@ -135,6 +135,54 @@ ge_status ge_solve(int64_t n, double r, double beta_l, double beta_r, ge_precisi
                    ge_kernel kernel, int32_t depth, int64_t steps, const void *u0_host,
                    void *u_out_host, void *stream);
 
+/* ---- Batched solves: many independent problems, one packed buffer ---------
+ * Each problem b is the problem of Sec. 2 with its own n[b] interior points,
+ * mesh ratio r[b] and wall values beta_l[b], beta_r[b]; all share the step
+ * count and start from step counter 0.  Its n[b] values sit at u_dev[offsets[b]
+ * .. offsets[b] + n[b]) of one caller-owned device buffer of `total` elements
+ * (type as for ge_create).  offsets[b] must be a multiple of 128 bytes (16
+ * doubles / 32 floats) and problems may not share a 128-byte row; the values
+ * between problems are left untouched.  The batched kernel runs the tiled
+ * right-hand-side scheme of GE_KERNEL_TEMPORAL in its normalised block form
+ * x <- x + 2r/(1+2r) (x_partner - x), each thread taking its problem's
+ * constants and walls, `depth` steps per launch. */
+typedef struct ge_batch ge_batch;   /* opaque plan, owned by the library */
+
+/* Build a plan: checks the layout and uploads the per-problem table (host
+ * arrays, copied).  The plan owns two working copies of the packed buffer
+ * (padded to whole rows), a row -> problem table and the device error word.
+ * Errors: GE_EINVAL (n_problems < 1, NULL array, n[b] < 1, r[b] not finite
+ * and > 0, unaligned or out-of-range offset, overlapping problems),
+ * GE_ENOMEM, GE_ECUDA. */
+ge_status ge_batch_create(ge_batch **out, int32_t n_problems, const int64_t *n, const double *r,
+                          const double *beta_l, const double *beta_r, const int64_t *offsets,
+                          int64_t total, ge_precision prec, void *stream);
+
+/* Steps per launch (1..512, 0 = built-in default).  Errors: GE_EINVAL. */
+ge_status ge_batch_set_depth(ge_batch *plan, int32_t depth);
+ge_status ge_batch_get_depth(const ge_batch *plan, int32_t *depth);
+
+/* Autotune the depth: times each candidate depth on `steps` steps of the data
+ * in u_dev (which is not modified), keeps the fastest and returns it in
+ * *best_depth (may be NULL).  Synchronous.  Errors: GE_EINVAL, GE_ECUDA. */
+ge_status ge_batch_tune(ge_batch *plan, const void *u_dev, int64_t steps, int32_t *best_depth);
+
+/* Advance every problem of the batch by `steps` steps, in place in u_dev.
+ * Asynchronous on the plan's stream; launches and device-to-device copies
+ * only, so a CUDA graph may capture it.  Errors: GE_EINVAL, GE_ECUDA. */
+ge_status ge_batch_run(ge_batch *plan, void *u_dev, int64_t steps);
+
+/* Wait for the plan's stream; report deferred device errors (GE_ETIMEOUT). */
+ge_status ge_batch_sync(ge_batch *plan);
+
+/* Release the plan (NULL is a no-op). */
+void ge_batch_destroy(ge_batch *plan);
+
+/* One-shot: ge_batch_create + ge_batch_run + ge_batch_sync + ge_batch_destroy. */
+ge_status ge_solve_batch(int32_t n_problems, const int64_t *n, const double *r, const double *beta_l,
+                         const double *beta_r, const int64_t *offsets, int64_t total, void *u_dev,
+                         int64_t steps, ge_precision prec, void *stream);
+
 /* The tiled solve (GE_KERNEL_TEMPORAL) for callers that may not allocate
  * device memory: a plug-in inside a host application or server that owns all
  * device memory through its own pool, a real-time loop that cannot take

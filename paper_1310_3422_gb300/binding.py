@@ -23,8 +23,9 @@ GE_KERNEL_AUTO, GE_KERNEL_CANONICAL, GE_KERNEL_ONESTEP, GE_KERNEL_TEMPORAL = 0, 
 
 # Every symbol include/ge.h declares.
 EXPORTS = ("ge_create", "ge_set_kernel", "ge_step_n", "ge_read_state", "ge_write_state",
-           "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_solve_noalloc", "ge_status_str",
-           "ge_last_error")
+           "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_batch_create", "ge_batch_set_depth",
+           "ge_batch_get_depth", "ge_batch_tune", "ge_batch_run", "ge_batch_sync", "ge_batch_destroy",
+           "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error")
 
 _lock = threading.Lock()
 _lib = None
@@ -69,6 +70,25 @@ def load(path: str | None = None):
         lib.ge_destroy.restype = None
         lib.ge_solve.argtypes = [_I64, _D, _D, _D, ctypes.c_int, ctypes.c_int, _I32, _I64, _VP, _VP, _VP]
         lib.ge_solve.restype = ctypes.c_int
+        _PI64 = ctypes.POINTER(ctypes.c_int64)
+        _PD = ctypes.POINTER(ctypes.c_double)
+        lib.ge_batch_create.argtypes = [ctypes.POINTER(_VP), _I32, _PI64, _PD, _PD, _PD, _PI64, _I64,
+                                        ctypes.c_int, _VP]
+        lib.ge_batch_create.restype = ctypes.c_int
+        lib.ge_batch_set_depth.argtypes = [_VP, _I32]
+        lib.ge_batch_set_depth.restype = ctypes.c_int
+        lib.ge_batch_get_depth.argtypes = [_VP, ctypes.POINTER(_I32)]
+        lib.ge_batch_get_depth.restype = ctypes.c_int
+        lib.ge_batch_tune.argtypes = [_VP, _VP, _I64, ctypes.POINTER(_I32)]
+        lib.ge_batch_tune.restype = ctypes.c_int
+        lib.ge_batch_run.argtypes = [_VP, _VP, _I64]
+        lib.ge_batch_run.restype = ctypes.c_int
+        lib.ge_batch_sync.argtypes = [_VP]
+        lib.ge_batch_sync.restype = ctypes.c_int
+        lib.ge_batch_destroy.argtypes = [_VP]
+        lib.ge_batch_destroy.restype = None
+        lib.ge_solve_batch.argtypes = [_I32, _PI64, _PD, _PD, _PD, _PI64, _I64, _VP, _I64, ctypes.c_int, _VP]
+        lib.ge_solve_batch.restype = ctypes.c_int
         lib.ge_solve_noalloc.argtypes = [_I64, _D, _D, _D, ctypes.c_int, _I32, _I64, _VP, _VP, _VP]
         lib.ge_solve_noalloc.restype = ctypes.c_int
         lib.ge_status_str.argtypes = [ctypes.c_int]
@@ -182,6 +202,92 @@ def ge_solve(n: int, r: float, beta_l: float, beta_r: float, prec: int, kernel: 
     _check(load().ge_solve(int(n), float(r), float(beta_l), float(beta_r), int(prec), int(kernel),
                            int(depth), int(steps), u0_host.ctypes.data, u_out_host.ctypes.data,
                            _stream_handle(stream)), "ge_solve")
+
+
+class Batch:
+    """Owner of a ``ge_batch*`` plan."""
+
+    def __init__(self, handle: int, total: int, prec: int):
+        self.handle = handle
+        self.total = total
+        self.prec = prec
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                ge_batch_destroy(self)
+            except Exception:
+                pass
+
+
+def _i64(a):
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _batch_arrays(n, r, beta_l, beta_r, offsets):
+    arrs = [_i64(n), _f64(r), _f64(beta_l), _f64(beta_r), _i64(offsets)]
+    if len({a.size for a in arrs}) != 1:
+        raise ValueError("n, r, beta_l, beta_r and offsets must have one entry per problem")
+    return arrs
+
+
+def ge_batch_create(n, r, beta_l, beta_r, offsets, total: int, prec: int, stream=None) -> Batch:
+    a_n, a_r, a_bl, a_br, a_off = _batch_arrays(n, r, beta_l, beta_r, offsets)
+    h = _VP()
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    PD = ctypes.POINTER(ctypes.c_double)
+    _check(load().ge_batch_create(ctypes.byref(h), a_n.size, a_n.ctypes.data_as(P64), a_r.ctypes.data_as(PD),
+                                  a_bl.ctypes.data_as(PD), a_br.ctypes.data_as(PD), a_off.ctypes.data_as(P64),
+                                  int(total), int(prec), _stream_handle(stream)), "ge_batch_create")
+    return Batch(h.value, int(total), int(prec))
+
+
+def ge_batch_set_depth(plan: Batch, depth: int):
+    _check(load().ge_batch_set_depth(plan.handle, int(depth)), "ge_batch_set_depth")
+
+
+def ge_batch_get_depth(plan: Batch) -> int:
+    v = _I32()
+    _check(load().ge_batch_get_depth(plan.handle, ctypes.byref(v)), "ge_batch_get_depth")
+    return int(v.value)
+
+
+def ge_batch_tune(plan: Batch, u, steps: int) -> int:
+    v = _I32()
+    _check(load().ge_batch_tune(plan.handle, _dptr(u), int(steps), ctypes.byref(v)), "ge_batch_tune")
+    return int(v.value)
+
+
+def ge_batch_run(plan: Batch, u, steps: int):
+    if u.numel() < plan.total or u.dtype != dtype_of(plan.prec):
+        raise ValueError("packed buffer too small or of the wrong dtype")
+    _check(load().ge_batch_run(plan.handle, _dptr(u), int(steps)), "ge_batch_run")
+
+
+def ge_batch_sync(plan: Batch):
+    _check(load().ge_batch_sync(plan.handle), "ge_batch_sync")
+
+
+def ge_batch_destroy(plan: Batch):
+    if plan.handle:
+        load().ge_batch_destroy(plan.handle)
+        plan.handle = None
+
+
+def ge_solve_batch(n, r, beta_l, beta_r, offsets, total: int, u, steps: int, prec: int, stream=None):
+    a_n, a_r, a_bl, a_br, a_off = _batch_arrays(n, r, beta_l, beta_r, offsets)
+    if u.numel() < total or u.dtype != dtype_of(prec):
+        raise ValueError("packed buffer too small or of the wrong dtype")
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    PD = ctypes.POINTER(ctypes.c_double)
+    _check(load().ge_solve_batch(a_n.size, a_n.ctypes.data_as(P64), a_r.ctypes.data_as(PD),
+                                 a_bl.ctypes.data_as(PD), a_br.ctypes.data_as(PD), a_off.ctypes.data_as(P64),
+                                 int(total), _dptr(u), int(steps), int(prec), _stream_handle(stream)),
+           "ge_solve_batch")
 
 
 def ge_solve_noalloc(n: int, r: float, beta_l: float, beta_r: float, prec: int, depth: int, steps: int,

@@ -1,0 +1,366 @@
+// ge_batch.cpp -- batched solves: many independent problems of uneven size and
+// mesh ratio, packed back to back in one device buffer, advanced together by
+// the batched tiled kernel (ge_tb.cu, tbb_kernel).  Host code only; built with
+// -ffp-contract=off like the rest of the C ABI.
+#include "ge.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime_api.h>
+
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "ge_internal.h"
+
+namespace {
+
+ge_status bfail(ge_status st, const char *msg)
+{
+    ge::set_last_error(msg);
+    return st;
+}
+
+ge_status bcuda(cudaError_t e, const char *what)
+{
+    char buf[400];
+    std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    ge::set_last_error(buf);
+    return e == cudaErrorMemoryAllocation ? GE_ENOMEM : GE_ECUDA;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+constexpr int kBatchDefaultDepthF64 = 48;
+constexpr int kBatchDefaultDepthF32 = 64;
+
+}  // namespace
+
+struct ge_batch {
+    CUtensorMap tmap[2];
+    ge_precision prec = GE_F32;
+    cudaStream_t stream = nullptr;
+    int n_problems = 0;
+    int64_t total = 0;       // elements of the caller's packed buffer
+    int64_t n_rows = 0;      // 128-byte rows of the working buffers
+    void *buf[2] = {nullptr, nullptr};
+    int *row_pid = nullptr;
+    ge::BatchDesc *desc = nullptr;
+    int *err = nullptr;
+    int depth = 0;
+    int num_sms = 0, blocks_per_sm = 0;
+};
+
+namespace {
+
+void release_batch(ge_batch *b)
+{
+    if (!b)
+        return;
+    for (int i = 0; i < 2; ++i)
+        if (b->buf[i])
+            cudaFree(b->buf[i]);
+    if (b->row_pid)
+        cudaFree(b->row_pid);
+    if (b->desc)
+        cudaFree(b->desc);
+    if (b->err)
+        cudaFree(b->err);
+    delete b;
+}
+
+int prec_index(ge_precision p) { return p == GE_F64 ? 0 : (p == GE_F32 ? 1 : 2); }
+
+// Enqueue `steps` steps on the working buffers (state in buf[0] on entry);
+// returns the index of the buffer holding the result.
+ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int *result_buf)
+{
+    const int pidx = prec_index(b->prec);
+    int cur = 0;
+    int64_t n0 = 0;
+    while (n0 < steps) {
+        const int64_t L = (steps - n0 < depth) ? steps - n0 : depth;
+        ge::TbbParams p{};
+        const bool last = (n0 + L == steps);
+        p.do_entry = (n0 == 0) ? 1 : 0;
+        p.n_mid = (int)(last ? L - 1 : L);
+        p.do_exit = last ? 1 : 0;
+        p.p_first = (int)(n0 & 1);
+        const int reach = p.do_entry + p.n_mid + p.do_exit;
+        if (!ge::tbb_geometry(pidx, reach, &p.H, &p.U))
+            return bfail(GE_EINVAL, "ge_batch: depth does not fit a tile");
+        p.n_rows = b->n_rows;
+        p.n_tiles = (b->n_rows * (ge::kRowBytes / (b->prec == GE_F64 ? 8 : 4)) + p.U - 1) / p.U;
+        p.row_pid = b->row_pid;
+        p.desc = b->desc;
+        p.err = b->err;
+        p.out = b->buf[cur ^ 1];
+        long long grid = (long long)b->num_sms * b->blocks_per_sm;
+        if (grid > p.n_tiles)
+            grid = p.n_tiles;
+        cudaError_t e = ge::launch_tbb(pidx, &b->tmap[cur], p, (int)grid, b->stream);
+        if (e != cudaSuccess)
+            return bcuda(e, "ge_batch: kernel launch");
+        cur ^= 1;
+        n0 += L;
+    }
+    *result_buf = cur;
+    return GE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ge_status ge_batch_create(ge_batch **out, int32_t n_problems, const int64_t *n, const double *r,
+                          const double *beta_l, const double *beta_r, const int64_t *offsets, int64_t total,
+                          ge_precision prec, void *stream)
+{
+    if (!out)
+        return bfail(GE_EINVAL, "ge_batch_create: out is NULL");
+    *out = nullptr;
+    if (n_problems < 1 || !n || !r || !beta_l || !beta_r || !offsets || total < 1)
+        return bfail(GE_EINVAL, "ge_batch_create: need n_problems >= 1, total >= 1 and non-NULL host arrays");
+    if (prec != GE_F64 && prec != GE_F32 && prec != GE_F32_COMP)
+        return bfail(GE_EINVAL, "ge_batch_create: unknown precision");
+    const int K = ge::kRowBytes / (prec == GE_F64 ? 8 : 4);
+    const int64_t n_rows = (total + K - 1) / K;
+    if (n_rows >= (1LL << 31) - 2 * ge::kTileRows)
+        return bfail(GE_EINVAL, "ge_batch_create: total is too large");
+    std::vector<int> row_pid((size_t)n_rows, -1);
+    std::vector<ge::BatchDesc> desc((size_t)n_problems);
+    for (int32_t i = 0; i < n_problems; ++i) {
+        const double ri = r[i];
+        if (n[i] < 1 || offsets[i] < 0 || offsets[i] % K != 0 || offsets[i] + n[i] > total)
+            return bfail(GE_EINVAL,
+                         "ge_batch_create: each problem needs n >= 1, an offset that is a multiple of "
+                         "128 bytes, and to lie inside the buffer");
+        if (!(ri > 0.0) || !std::isfinite(ri) || !std::isfinite(beta_l[i]) || !std::isfinite(beta_r[i]))
+            return bfail(GE_EINVAL, "ge_batch_create: need finite r > 0 and finite wall values");
+        const int64_t r0 = offsets[i] / K, r1 = (offsets[i] + n[i] + K - 1) / K;
+        for (int64_t row = r0; row < r1; ++row) {
+            if (row_pid[(size_t)row] != -1)
+                return bfail(GE_EINVAL, "ge_batch_create: problems share a 128-byte row (overlap)");
+            row_pid[(size_t)row] = i;
+        }
+        const double det = 1.0 + 2.0 * ri;
+        ge::BatchDesc &d = desc[(size_t)i];
+        d.off = offsets[i];
+        d.n = n[i];
+        d.r = ri;
+        d.omr = 1.0 - ri;
+        d.d = 2.0 * ri / det;
+        d.kappa = (1.0 - ri) / (1.0 + ri);
+        d.f_l = ri * beta_l[i];
+        d.f_r = ri * beta_r[i];
+        d.x1 = (1.0 + ri) / det;
+        d.x2 = ri / det;
+        d.xs = 1.0 / (1.0 + ri);
+    }
+    ge_batch *b = new (std::nothrow) ge_batch();
+    if (!b)
+        return bfail(GE_ENOMEM, "ge_batch_create: host allocation failed");
+    b->prec = prec;
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->n_problems = n_problems;
+    b->total = total;
+    b->n_rows = n_rows;
+    b->depth = prec == GE_F64 ? kBatchDefaultDepthF64 : kBatchDefaultDepthF32;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t bytes = (size_t)n_rows * ge::kRowBytes;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = cudaMalloc(&b->buf[i], bytes);
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void **>(&b->row_pid), row_pid.size() * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void **>(&b->desc), desc.size() * sizeof(ge::BatchDesc));
+    if (e == cudaSuccess)
+        e = cudaMalloc(reinterpret_cast<void **>(&b->err), 256);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->row_pid, row_pid.data(), row_pid.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->desc, desc.data(), desc.size() * sizeof(ge::BatchDesc), cudaMemcpyHostToDevice,
+                            b->stream);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        e = cudaMemsetAsync(b->buf[i], 0, bytes, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->err, 0, 256, b->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess)
+        e = ge::tbb_occupancy(prec_index(prec), &b->blocks_per_sm);
+    if (e != cudaSuccess || b->blocks_per_sm < 1) {
+        release_batch(b);
+        return bcuda(e == cudaSuccess ? cudaErrorInvalidConfiguration : e, "ge_batch_create");
+    }
+    auto enc = encoder();
+    if (!enc) {
+        release_batch(b);
+        return bfail(GE_ECUDA, "ge_batch_create: cuTensorMapEncodeTiled is not available");
+    }
+    for (int i = 0; i < 2; ++i) {
+        cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)n_rows};
+        cuuint64_t strides[1] = {(cuuint64_t)ge::kRowBytes};
+        cuuint32_t box[2] = {(cuuint32_t)K, (cuuint32_t)ge::kTileRows};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult cr = enc(&b->tmap[i], prec == GE_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                          2, b->buf[i], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) {
+            release_batch(b);
+            return bfail(GE_ECUDA, "ge_batch_create: cuTensorMapEncodeTiled failed");
+        }
+    }
+    *out = b;
+    return GE_OK;
+}
+
+ge_status ge_batch_set_depth(ge_batch *b, int32_t depth)
+{
+    if (!b || depth < 0 || depth > ge::kMaxTableSteps)
+        return bfail(GE_EINVAL, "ge_batch_set_depth: NULL plan or depth outside 0..512");
+    b->depth = depth ? depth : (b->prec == GE_F64 ? kBatchDefaultDepthF64 : kBatchDefaultDepthF32);
+    return GE_OK;
+}
+
+ge_status ge_batch_get_depth(const ge_batch *b, int32_t *depth)
+{
+    if (!b || !depth)
+        return bfail(GE_EINVAL, "ge_batch_get_depth: NULL argument");
+    *depth = b->depth;
+    return GE_OK;
+}
+
+ge_status ge_batch_run(ge_batch *b, void *u_dev, int64_t steps)
+{
+    if (!b || !u_dev || steps < 0)
+        return bfail(GE_EINVAL, "ge_batch_run: NULL argument or steps < 0");
+    if (steps == 0)
+        return GE_OK;
+    const size_t bytes = (size_t)b->total * (b->prec == GE_F64 ? 8 : 4);
+    cudaError_t e = cudaMemcpyAsync(b->buf[0], u_dev, bytes, cudaMemcpyDeviceToDevice, b->stream);
+    if (e != cudaSuccess)
+        return bcuda(e, "ge_batch_run: copy in");
+    int res = 0;
+    ge_status st = batch_steps(b, steps, b->depth, &res);
+    if (st != GE_OK)
+        return st;
+    e = cudaMemcpyAsync(u_dev, b->buf[res], bytes, cudaMemcpyDeviceToDevice, b->stream);
+    return e == cudaSuccess ? GE_OK : bcuda(e, "ge_batch_run: copy out");
+}
+
+ge_status ge_batch_tune(ge_batch *b, const void *u_dev, int64_t steps, int32_t *best_depth)
+{
+    if (!b || !u_dev || steps < 1)
+        return bfail(GE_EINVAL, "ge_batch_tune: NULL argument or steps < 1");
+    static const int cand[] = {16, 32, 48, 64, 96, 128, 192, 256};
+    const size_t bytes = (size_t)b->total * (b->prec == GE_F64 ? 8 : 4);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e1);
+    double best = 1e300;
+    int best_d = b->depth;
+    for (int d : cand) {
+        int res = 0;
+        // one untimed run (first use of this launch shape), then a timed one
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+            e = cudaMemcpyAsync(b->buf[0], u_dev, bytes, cudaMemcpyDeviceToDevice, b->stream);
+            if (e == cudaSuccess && rep == 1)
+                e = cudaEventRecord(e0, b->stream);
+            if (e != cudaSuccess)
+                break;
+            ge_status st = batch_steps(b, steps, d, &res);
+            if (st != GE_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return st;
+            }
+            if (rep == 1)
+                e = cudaEventRecord(e1, b->stream);
+        }
+        if (e == cudaSuccess)
+            e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess)
+            e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess)
+            break;
+        if (ms < best) {
+            best = ms;
+            best_d = d;
+        }
+    }
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    if (e != cudaSuccess)
+        return bcuda(e, "ge_batch_tune");
+    b->depth = best_d;
+    if (best_depth)
+        *best_depth = best_d;
+    return GE_OK;
+}
+
+ge_status ge_batch_sync(ge_batch *b)
+{
+    if (!b)
+        return bfail(GE_EINVAL, "ge_batch_sync: NULL plan");
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess)
+        return bcuda(e, "ge_batch_sync");
+    int word = 0;
+    e = cudaMemcpy(&word, b->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess)
+        return bcuda(e, "ge_batch_sync: reading the device error word");
+    if (word == ge::kDevTimeout)
+        return bfail(GE_ETIMEOUT, "ge_batch: a tile load did not complete within the wait limit");
+    return GE_OK;
+}
+
+void ge_batch_destroy(ge_batch *b)
+{
+    if (!b)
+        return;
+    cudaStreamSynchronize(b->stream);
+    release_batch(b);
+}
+
+ge_status ge_solve_batch(int32_t n_problems, const int64_t *n, const double *r, const double *beta_l,
+                         const double *beta_r, const int64_t *offsets, int64_t total, void *u_dev, int64_t steps,
+                         ge_precision prec, void *stream)
+{
+    ge_batch *b = nullptr;
+    ge_status st = ge_batch_create(&b, n_problems, n, r, beta_l, beta_r, offsets, total, prec, stream);
+    if (st != GE_OK)
+        return st;
+    st = ge_batch_run(b, u_dev, steps);
+    if (st == GE_OK)
+        st = ge_batch_sync(b);
+    ge_batch_destroy(b);
+    return st;
+}
+
+}  // extern "C"

@@ -68,6 +68,30 @@ struct TbParams {
     short rs_exp[kMaxRescale];  // exponents of this launch's rescalings
 };
 
+// One problem of a batch (device table, one entry per problem).  The batch
+// kernel uses the normalised block map x <- x + d (x_p - x), so every value
+// here is a plain per-problem constant (no scale bookkeeping).
+struct BatchDesc {
+    long long off;        // element offset of the problem in the packed buffer (row aligned)
+    long long n;          // interior points
+    double r, omr;        // entry: w = (1-r) u + r u_partner
+    double d;             // 2r/(1+2r)
+    double kappa;         // singleton block factor (1-r)/(1+r)
+    double f_l, f_r;      // wall terms r*beta_l, r*beta_r
+    double x1, x2, xs;    // exit: (1+r)/(1+2r), r/(1+2r), 1/(1+r)
+};
+
+// One launch of the batched tiled kernel over the packed buffer.
+struct TbbParams {
+    void *out;
+    int *err;
+    const int *row_pid;        // problem id of every 128-byte row (-1: padding)
+    const BatchDesc *desc;     // per-problem constants
+    long long n_rows, n_tiles;
+    int U, H;
+    int p_first, do_entry, n_mid, do_exit;
+};
+
 // Launchers (return the cudaError_t of the launch).
 cudaError_t launch_canon_f64(const double *in, double *out, long long n, int parity,
                              const CanonCoef &c, cudaStream_t s);
@@ -77,6 +101,9 @@ cudaError_t launch_canon_f32(const float *in, float *out, long long n, int parit
 // prec: 0 = FP64, 1 = FP32, 2 = FP32 compensated.  tmap: 128-byte-aligned
 // CUtensorMap (opaque here) describing the source buffer.
 cudaError_t launch_tb(int prec, const void *tmap, const TbParams &p, int grid, cudaStream_t s);
+cudaError_t launch_tbb(int prec, const void *tmap, const TbbParams &p, int grid, cudaStream_t s);
+cudaError_t tbb_occupancy(int prec, int *blocks_per_sm);
+bool tbb_geometry(int prec, int reach, int *H, int *U);
 // Largest co-resident CTAs per SM for the tiled kernel of this precision.
 cudaError_t tb_occupancy(int prec, int *blocks_per_sm);
 int tb_smem_bytes();

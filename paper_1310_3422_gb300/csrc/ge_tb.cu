@@ -208,7 +208,7 @@ __device__ __forceinline__ void exchange(const Real (&v)[K], Real &L, Real &R, E
     }
 }
 
-enum StageKind { kEntry = 0, kMid = 1, kExit = 2 };
+enum StageKind { kEntry = 0, kMid = 1, kExit = 2, kMidN = 3 };
 
 template <typename Real>
 struct StageC {
@@ -218,6 +218,7 @@ struct StageC {
 // One stage on a thread's K registers.
 //   entry: v <- (1-r) v + r v_p      (a = r, b = 1-r; singleton: b v)
 //   mid:   v <- v + 2r v_p           (a = 2r;         singleton: s v)  scaled form
+//   midN:  v <- v + d (v_p - v)      (a = 2r/(1+2r);  singleton: s v)  normalised form
 //   exit:  v <- x1 v + x2 v_p        (a = x1, b = x2; singleton: s v)
 // Entry and mid add the wall terms fl / fr at points 0 and n-1.  With
 // EDGE = false every point of the thread and every partner lies inside the
@@ -235,6 +236,8 @@ __device__ __forceinline__ void stage(Real (&v)[K], Real L, Real R, Span sp, con
             nv[j] = fma(c.a, p, c.b * v[j]);
         else if (KIND == kMid)
             nv[j] = fma(c.a, p, v[j]);
+        else if (KIND == kMidN)
+            nv[j] = fma(c.a, p - v[j], v[j]);
         else
             nv[j] = fma(c.a, v[j], c.b * p);
     }
@@ -697,6 +700,228 @@ bool geometry(int reach, int *H, int *U)
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// Batched kernel: many independent problems packed back to back in one
+// buffer, each starting on a 128-byte row.  The tiles run over the packed
+// buffer exactly as for one long problem; every thread looks its problem up
+// (row -> problem id), takes that problem's constants and walls, and treats
+// points of other problems like points outside its grid.  Normalised block
+// map, so no scale bookkeeping: every launch starts and ends unscaled.
+// CTA-row layout (one row per thread).
+
+// Entry, block steps and exit of one tile, batched form.
+template <bool EDGE, typename Real, int K, int NW>
+__device__ __forceinline__ void run_batch(Real (&v)[K], const TbbParams &P, const BatchDesc &bd,
+                                          Exch<Real, NW, false> &x, Span sp)
+{
+    Real L = 0, R = 0;
+    if (P.do_entry) {
+        const StageC<Real> c{(Real)bd.r, (Real)bd.omr, (Real)0, (Real)bd.f_l, (Real)bd.f_r};
+        if (((1 - P.p_first) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kEntry, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kEntry, EDGE>(v, L, R, sp, c);
+        }
+    }
+    const StageC<Real> cm{(Real)bd.d, (Real)0, (Real)bd.kappa, (Real)bd.f_l, (Real)bd.f_r};
+    int m = 0;
+    if (P.n_mid > 0 && (P.p_first & 1)) {
+        exchange(v, L, R, x);
+        stage<1, kMidN, EDGE>(v, L, R, sp, cm);
+        m = 1;
+    }
+    for (; m + 1 < P.n_mid; m += 2) {
+        stage<0, kMidN, EDGE>(v, L, R, sp, cm);
+        exchange(v, L, R, x);
+        stage<1, kMidN, EDGE>(v, L, R, sp, cm);
+    }
+    if (m < P.n_mid)
+        stage<0, kMidN, EDGE>(v, L, R, sp, cm);
+    if (P.do_exit) {
+        const StageC<Real> c{(Real)bd.x1, (Real)bd.x2, (Real)bd.xs, (Real)0, (Real)0};
+        if (((P.p_first + P.n_mid) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kExit, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kExit, EDGE>(v, L, R, sp, c);
+        }
+    }
+}
+
+template <bool EDGE, int K, int NW>
+__device__ __forceinline__ void run_batch_comp(float (&v)[K], const TbbParams &P, const BatchDesc &bd,
+                                               Exch<float, NW, false> &x, Span sp)
+{
+    float L = 0.0f, R = 0.0f;
+    if (P.do_entry) {
+        const StageC<float> c{(float)bd.r, (float)bd.omr, 0.0f, (float)bd.f_l, (float)bd.f_r};
+        if (((1 - P.p_first) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kEntry, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kEntry, EDGE>(v, L, R, sp, c);
+        }
+    }
+    float lo[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        lo[j] = 0.0f;
+    const float d = (float)bd.d, km1 = (float)(bd.kappa - 1.0);
+    const float fl = (float)bd.f_l, fr = (float)bd.f_r;
+    TbParams dummy{};
+    dummy.n = 0;
+    int m = 0;
+    if (P.n_mid > 0 && (P.p_first & 1)) {
+        mid_comp<1, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp);
+        m = 1;
+    }
+    for (; m + 1 < P.n_mid; m += 2) {
+        mid_comp<0, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp);
+        mid_comp<1, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp);
+    }
+    if (m < P.n_mid)
+        mid_comp<0, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp);
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        v[j] += lo[j];
+    if (P.do_exit) {
+        const StageC<float> c{(float)bd.x1, (float)bd.x2, (float)bd.xs, 0.0f, 0.0f};
+        if (((P.p_first + P.n_mid) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kExit, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kExit, EDGE>(v, L, R, sp, c);
+        }
+    }
+}
+
+template <typename Real, bool COMP>
+__global__ void __launch_bounds__(kTileRows, 2)
+    tbb_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TbbParams P)
+{
+    constexpr int NT = kTileRows;
+    constexpr int K = kRowBytes / (int)sizeof(Real);
+    constexpr int NW = NT / 32;
+    constexpr int CH = kRowBytes / 16;
+    constexpr uint32_t kTileBytes = kTileRows * kRowBytes;
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *tiles = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ Real slot[2][NW][2];
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int hr = P.H / K, ur = P.U / K;
+    Exch<Real, NW, false> x{slot, 0, lane, warp};
+
+    if (t == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    long long tile = blockIdx.x;
+    if (t == 0 && tile < P.n_tiles) {
+        mbar_arrive_expect_tx(&mbar[0], kTileBytes);
+        tma_load_rows(tiles, &tmap, &mbar[0], (int)(tile * ur - hr));
+    }
+    for (long long it = 0; tile < P.n_tiles; ++it, tile += gridDim.x) {
+        const int b = (int)(it & 1);
+        unsigned char *cur = tiles + b * kTileBytes;
+        const long long next = tile + gridDim.x;
+        const bool prefetch = next < P.n_tiles;
+        if (t == 0 && prefetch) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&mbar[b ^ 1], kTileBytes);
+            tma_load_rows(tiles + (b ^ 1) * kTileBytes, &tmap, &mbar[b ^ 1], (int)(next * ur - hr));
+        }
+        const bool ok = mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) {
+                atomicExch(P.err, kDevTimeout);
+                if (prefetch)
+                    mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            }
+            return;
+        }
+
+        Real v[K];
+        {
+            const unsigned char *rp = cur + t * kRowBytes;
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                chunk_to_regs<K>(rp + ((c ^ (t & 7)) << 4), v, c);
+        }
+        // this thread's problem: rows outside the buffer or in padding have none
+        const long long grow = tile * ur - hr + t;
+        const int pid = (grow >= 0 && grow < P.n_rows) ? __ldg(P.row_pid + grow) : -1;
+        BatchDesc bd{};
+        Span sp{K + 1, K + 1};  // no point of this thread is inside a grid
+        if (pid >= 0) {
+            bd = P.desc[pid];
+            sp = make_span<K>(grow * K - bd.off, bd.n);
+        }
+        const bool edge_thr = !(sp.jlo <= -1 && sp.jhi >= K + 1);
+        const bool edge_warp = __any_sync(0xffffffffu, edge_thr);
+        if constexpr (!COMP) {
+            if (edge_warp)
+                run_batch<true>(v, P, bd, x, sp);
+            else
+                run_batch<false>(v, P, bd, x, sp);
+        } else {
+            if (edge_warp)
+                run_batch_comp<true>(v, P, bd, x, sp);
+            else
+                run_batch_comp<false>(v, P, bd, x, sp);
+        }
+
+        {
+            unsigned char *rp = cur + t * kRowBytes;
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                regs_to_chunk<K>(rp + ((c ^ (t & 7)) << 4), v, c);
+        }
+        __syncthreads();
+        {
+            const long long grow0 = tile * ur;
+            unsigned char *out = static_cast<unsigned char *>(P.out);
+            for (int ch = t; ch < ur * CH; ch += NT) {
+                const int lr = hr + ch / CH;
+                const int c = ch % CH;
+                const long long gr = grow0 + ch / CH;
+                if (gr < P.n_rows) {
+                    const uint4 val = *reinterpret_cast<const uint4 *>(cur + lr * kRowBytes +
+                                                                       ((c ^ (lr & 7)) << 4));
+                    *reinterpret_cast<uint4 *>(out + gr * kRowBytes + c * 16) = val;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename Real, bool COMP>
+cudaError_t launch_batch_one(const void *tmap, const TbbParams &p, int grid, cudaStream_t s)
+{
+    const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
+    tbb_kernel<Real, COMP><<<grid, kTileRows, tb_smem_bytes(), s>>>(*m, p);
+    return cudaGetLastError();
+}
+
+template <typename Real, bool COMP>
+cudaError_t batch_attr_and_occupancy(int *blocks)
+{
+    cudaError_t e = cudaFuncSetAttribute(tbb_kernel<Real, COMP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, tb_smem_bytes());
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tbb_kernel<Real, COMP>, kTileRows,
+                                                         tb_smem_bytes());
+}
+
 }  // namespace
 
 int tb_smem_bytes() { return 2 * kTileRows * kRowBytes + 1024; }
@@ -717,6 +942,33 @@ cudaError_t tb_occupancy(int prec, int *blocks)
     if (prec == 1)
         return set_attr_and_occupancy<float, false>(blocks);
     return set_attr_and_occupancy<float, true>(blocks);
+}
+
+bool tbb_geometry(int prec, int reach, int *H, int *U)
+{
+    const int K = kRowBytes / (prec == 0 ? 8 : 4);
+    const int ht = (reach + K - 1) / K;
+    *H = ht * K;
+    *U = kTileRows * K - 2 * *H;
+    return *U > 0;
+}
+
+cudaError_t tbb_occupancy(int prec, int *blocks)
+{
+    if (prec == 0)
+        return batch_attr_and_occupancy<double, false>(blocks);
+    if (prec == 1)
+        return batch_attr_and_occupancy<float, false>(blocks);
+    return batch_attr_and_occupancy<float, true>(blocks);
+}
+
+cudaError_t launch_tbb(int prec, const void *tmap, const TbbParams &p, int grid, cudaStream_t s)
+{
+    if (prec == 0)
+        return launch_batch_one<double, false>(tmap, p, grid, s);
+    if (prec == 1)
+        return launch_batch_one<float, false>(tmap, p, grid, s);
+    return launch_batch_one<float, true>(tmap, p, grid, s);
 }
 
 cudaError_t launch_tb(int prec, const void *tmap, const TbParams &p, int grid, cudaStream_t s)

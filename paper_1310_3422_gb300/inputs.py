@@ -64,7 +64,8 @@ class Batch:
     """Independent 1D problems packed back to back.
 
     ``offsets[b]`` is the element offset of problem b in ``u0`` (a multiple
-    of ``align`` elements), ``n[b]`` its number of interior points."""
+    of ``align`` elements; 32 keeps every problem on its own 128-byte rows for
+    both FP32 and FP64), ``n[b]`` its number of interior points."""
     n: np.ndarray
     r: np.ndarray
     beta_l: np.ndarray
@@ -76,7 +77,7 @@ class Batch:
 
 def uneven_batch(n_problems: int = 4096, n_min: int = 256, n_max: int = 65536,
                  r_min: float = 0.25, r_max: float = 4.0, seed: int = SEED_BASE + 2,
-                 align: int = 4) -> Batch:
+                 align: int = 32) -> Batch:
     """Batch of problems with N log-uniform in [n_min, n_max] rounded to even,
     r ~ U[r_min, r_max], wall values ~ U(-1, 1), u0 from ``fourier_state``."""
     rng = np.random.default_rng(seed)

@@ -83,3 +83,26 @@ def test_null_context_is_rejected(lib):
 
 def test_solve_rejects_null_host_buffers(lib):
     assert lib.ge_solve(8, 1.0, 0.0, 0.0, 0, 0, 0, 1, None, None, None) == B.GE_EINVAL
+
+
+def test_batch_layout_checks(lib):
+    import numpy as np
+    h = ctypes.c_void_p()
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    PD = ctypes.POINTER(ctypes.c_double)
+
+    def create(n, offs, total, r=None):
+        n = np.array(n, dtype=np.int64)
+        offs = np.array(offs, dtype=np.int64)
+        r = np.array(r if r is not None else [1.0] * len(n))
+        z = np.zeros(len(n))
+        return lib.ge_batch_create(ctypes.byref(h), len(n), n.ctypes.data_as(P64), r.ctypes.data_as(PD),
+                                   z.ctypes.data_as(PD), z.ctypes.data_as(PD), offs.ctypes.data_as(P64),
+                                   total, B.GE_F32, None)
+    assert create([10], [3], 64) == B.GE_EINVAL             # offset not on a 128-byte row
+    assert create([40, 10], [0, 32], 64) == B.GE_EINVAL     # problems share a row
+    assert create([10], [0], 5) == B.GE_EINVAL              # problem outside the buffer
+    assert create([0], [0], 64) == B.GE_EINVAL              # empty problem
+    assert create([10], [0], 64, r=[-1.0]) == B.GE_EINVAL   # bad r
+    assert lib.ge_batch_run(None, None, 1) == B.GE_EINVAL
+    lib.ge_batch_destroy(None)

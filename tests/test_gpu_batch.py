@@ -1,0 +1,140 @@
+"""Batched solves (many uneven problems in one packed buffer) against the
+CPU oracle, problem by problem.  Tolerances as in test_gpu_parity: FP64
+1e-12 * max(1, 2r - 1) relative max-norm, FP32 1e-5 (the batched FP32
+target), per problem."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1310_3422_gb300 import binding as B
+from paper_1310_3422_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def tol(prec, r):
+    return 1e-12 * max(1.0, 2.0 * r - 1.0) if prec == B.GE_F64 else 1e-5
+
+
+def rel(got, want):
+    return float(np.max(np.abs(got - want)) / max(1e-300, np.max(np.abs(want))))
+
+
+def layout(ns, align=32, gap=0):
+    offs, pos = [], 0
+    for n in ns:
+        offs.append(pos)
+        pos += ((n + align - 1) // align) * align + gap
+    return np.array(offs, dtype=np.int64), pos
+
+
+def make_batch(ns, seed, r_lo=0.2, r_hi=5.0, gap=0):
+    rng = np.random.default_rng(seed)
+    offs, total = layout(ns, gap=gap)
+    r = rng.uniform(r_lo, r_hi, len(ns))
+    bl, br = rng.uniform(-1, 1, len(ns)), rng.uniform(-1, 1, len(ns))
+    u = np.full(total, 7.25)  # marks the gaps between problems
+    for i, n in enumerate(ns):
+        u[offs[i]:offs[i] + n] = inputs.fourier_state(n, bl[i], br[i], rng) + 0.01 * rng.standard_normal(n)
+    return np.array(ns, dtype=np.int64), r, bl, br, offs, total, u
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load()
+
+
+MIXED = [1, 2, 3, 5, 31, 32, 33, 64, 100, 1000, 4095, 8191, 9000, 20000, 2, 40001]
+
+
+@pytest.mark.parametrize("prec", [B.GE_F64, B.GE_F32, B.GE_F32_COMP])
+@pytest.mark.parametrize("depth", [1, 7, 64])
+def test_batch_matches_oracle(prec, depth):
+    n, r, bl, br, offs, total, u = make_batch(MIXED, seed=depth, gap=32)
+    x = torch.from_numpy(u).to(DEV, B.dtype_of(prec))
+    plan = B.ge_batch_create(n, r, bl, br, offs, total, prec)
+    B.ge_batch_set_depth(plan, depth)
+    B.ge_batch_run(plan, x, 77)
+    B.ge_batch_sync(plan)
+    got = x.double().cpu().numpy()
+    for i in range(len(n)):
+        want = oracle.run(u[offs[i]:offs[i] + n[i]], r[i], bl[i], br[i], 77)
+        e = rel(got[offs[i]:offs[i] + n[i]], want)
+        assert e <= tol(prec, r[i]), (i, n[i], r[i], e)
+    # the values between problems are left as they were
+    mask = np.ones(total, bool)
+    for i in range(len(n)):
+        mask[offs[i]:offs[i] + n[i]] = False
+    assert np.all(got[mask] == np.float32(7.25))
+
+
+def test_one_shot_equals_plan_and_zero_steps():
+    n, r, bl, br, offs, total, u = make_batch([300, 5000, 777], seed=3)
+    a = torch.from_numpy(u).to(DEV)
+    b = a.clone()
+    B.ge_solve_batch(n, r, bl, br, offs, total, a, 50, B.GE_F64)
+    plan = B.ge_batch_create(n, r, bl, br, offs, total, B.GE_F64)
+    B.ge_batch_run(plan, b, 0)
+    B.ge_batch_sync(plan)
+    assert torch.equal(b, torch.from_numpy(u).to(DEV))
+    B.ge_batch_run(plan, b, 50)
+    B.ge_batch_sync(plan)
+    assert torch.equal(a, b)
+
+
+def test_tune_keeps_results():
+    n, r, bl, br, offs, total, u = make_batch([2000, 30000, 50, 9000], seed=4)
+    x = torch.from_numpy(u).to(DEV, torch.float32)
+    plan = B.ge_batch_create(n, r, bl, br, offs, total, B.GE_F32)
+    best = B.ge_batch_tune(plan, x, 128)
+    assert best in (16, 32, 48, 64, 96, 128, 192, 256)
+    assert B.ge_batch_get_depth(plan) == best
+    assert torch.equal(x, torch.from_numpy(u).to(DEV, torch.float32))  # tuning does not touch u
+    B.ge_batch_run(plan, x, 300)
+    B.ge_batch_sync(plan)
+    got = x.double().cpu().numpy()
+    for i in range(len(n)):
+        want = oracle.run(u[offs[i]:offs[i] + n[i]], r[i], bl[i], br[i], 300)
+        assert rel(got[offs[i]:offs[i] + n[i]], want) <= 1e-5
+
+
+def test_graph_capture_of_a_batch_run():
+    n, r, bl, br, offs, total, u = make_batch([1500, 6000, 123, 20000], seed=5)
+    x = torch.from_numpy(u).to(DEV)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan = B.ge_batch_create(n, r, bl, br, offs, total, B.GE_F64, stream=s)
+        B.ge_batch_set_depth(plan, 32)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            B.ge_batch_run(plan, x, 100)
+        g.replay()
+        g.replay()
+    B.ge_batch_sync(plan)
+    got = x.cpu().numpy()
+    for i in range(len(n)):
+        want = oracle.run(u[offs[i]:offs[i] + n[i]], r[i], bl[i], br[i], 100)
+        want = oracle.run(want, r[i], bl[i], br[i], 100)
+        assert rel(got[offs[i]:offs[i] + n[i]], want) <= tol(B.GE_F64, r[i])
+
+
+@pytest.mark.parametrize("prec", [B.GE_F32, B.GE_F32_COMP, B.GE_F64])
+def test_uneven_batch_full_size_sampled(prec):
+    """4096 problems, N log-uniform in [256, 65536], r in [0.25, 4], 2000
+    steps (the batched workload); eight problems checked against the oracle."""
+    bt = inputs.uneven_batch()
+    x = torch.from_numpy(bt.u0).to(DEV, B.dtype_of(prec))
+    plan = B.ge_batch_create(bt.n, bt.r, bt.beta_l, bt.beta_r, bt.offsets, bt.total, prec)
+    B.ge_batch_run(plan, x, 2000)
+    B.ge_batch_sync(plan)
+    got = x.double().cpu().numpy()
+    rng = np.random.default_rng(7)
+    picks = list(rng.choice(len(bt.n), 6, replace=False)) + [int(np.argmin(bt.n)), int(np.argmax(bt.n))]
+    for i in picks:
+        o, n = bt.offsets[i], bt.n[i]
+        want = oracle.run(bt.u0[o:o + n], bt.r[i], bt.beta_l[i], bt.beta_r[i], 2000)
+        assert rel(got[o:o + n], want) <= tol(prec, bt.r[i]), (i, n, bt.r[i])
