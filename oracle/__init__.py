@@ -53,6 +53,10 @@ def load(path: str | None = None):
     lib.ge_oracle_step.restype = ctypes.c_int
     lib.ge_oracle_run.argtypes = [_I64, _D, _D, _D, _I64, _I64, _PD]
     lib.ge_oracle_run.restype = ctypes.c_int
+    lib.ge_oracle_step_k.argtypes = [_I64, _D, _D, _D, ctypes.c_int, _I64, _PD, _PD]
+    lib.ge_oracle_step_k.restype = ctypes.c_int
+    lib.ge_oracle_run_k.argtypes = [_I64, _D, _D, _D, _I64, _I64, _I64, _PD]
+    lib.ge_oracle_run_k.restype = ctypes.c_int
     lib.ge_oracle_step_periodic.argtypes = [_I64, _D, ctypes.c_int, _PD, _PD]
     lib.ge_oracle_step_periodic.restype = ctypes.c_int
     lib.ge_oracle_run_periodic.argtypes = [_I64, _D, _I64, _I64, _PD]
@@ -103,6 +107,22 @@ class Oracle:
                                     int(step0), int(steps), _ptr(u))
         if rc != 0:
             raise ValueError("ge_oracle_run rejected its arguments")
+        return u
+
+    def step_k(self, u, r, beta_l, beta_r, parity, k) -> np.ndarray:
+        """One step with sub-domain width k (k = 1: the 2-point group step)."""
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.empty_like(u)
+        if self.lib.ge_oracle_step_k(u.size, float(r), float(beta_l), float(beta_r), int(parity), int(k),
+                                     _ptr(u), _ptr(out)):
+            raise ValueError("ge_oracle_step_k rejected its arguments")
+        return out
+
+    def run_k(self, u, r, beta_l, beta_r, k, steps, step0=0) -> np.ndarray:
+        u = np.array(u, dtype=np.float64, copy=True)
+        if self.lib.ge_oracle_run_k(u.size, float(r), float(beta_l), float(beta_r), int(k), int(step0),
+                                    int(steps), _ptr(u)):
+            raise ValueError("ge_oracle_run_k rejected its arguments")
         return u
 
     def step_periodic(self, u, r, parity) -> np.ndarray:
@@ -165,6 +185,14 @@ def run(u, r, beta_l, beta_r, steps, step0=0):
 
 def step_periodic(u, r, parity):
     return default().step_periodic(u, r, parity)
+
+
+def step_k(u, r, beta_l, beta_r, parity, k):
+    return default().step_k(u, r, beta_l, beta_r, parity, k)
+
+
+def run_k(u, r, beta_l, beta_r, k, steps, step0=0):
+    return default().run_k(u, r, beta_l, beta_r, k, steps, step0)
 
 
 def run_periodic(u, r, steps, step0=0):

@@ -148,6 +148,89 @@ int ge_oracle_run(int64_t n, double r, double beta_l, double beta_r, int64_t ste
     return 0;
 }
 
+/* General sub-domain width k (Sec. 2: odd sub-domains [x_{2ik}, x_{2ik+k-1}],
+ * even sub-domains [x_{2ik+k}, x_{2(i+1)k-1}] of the paper's nodes x_0..x_{n+1}).
+ * Paper node j (array index j-1) lies in sub-domain s = floor(j/k); at parity
+ * 0 the odd sub-domains (even s) use Saul'yev A and sweep right from their
+ * left wall, the even ones (odd s) use B and sweep left from their right
+ * wall; parity 1 swaps the roles.  A B node followed by an A node are the two
+ * walls of a confluence: their coupled pair is solved first by Eqs. (cc)/(dd)
+ * (the same group formula as k = 1), then the A runs are swept left to right
+ * and the B runs right to left, each from its new-level neighbour (the wall
+ * value beyond the grid).  k = 1 gives ge_oracle_step bit for bit.
+ * Returns 0, or -1 on invalid arguments. */
+int ge_oracle_step_k(int64_t n, double r, double beta_l, double beta_r, int parity, int64_t k,
+                     const double *u_in, double *u_out)
+{
+    double kc[6];
+    int64_t j;
+    char *paired;
+    if (n < 1 || k < 1 || !(r > 0.0) || !isfinite(r) || (parity != 0 && parity != 1) ||
+        u_in == NULL || u_out == NULL)
+        return -1;
+    ge_oracle_coefficients(r, kc);
+    paired = (char *)calloc((size_t)n + 2, 1);
+    if (paired == NULL)
+        return -1;
+#define OLD(jj) ((jj) == 0 ? beta_l : ((jj) == n + 1 ? beta_r : u_in[(jj) - 1]))
+#define ROLE_A(jj) ((((jj) / k) + parity) % 2 == 0)
+    /* confluence pairs: B at node j, A at node j+1 (paper nodes 1..n) */
+    for (j = 1; j < n; ++j) {
+        if (!ROLE_A(j) && ROLE_A(j + 1)) {
+            group_update(kc, OLD(j - 1), OLD(j), OLD(j + 1), OLD(j + 2), &u_out[j - 1], &u_out[j]);
+            paired[j] = paired[j + 1] = 1;
+        }
+    }
+    /* Saul'yev A runs, left to right from the new left neighbour */
+    for (j = 1; j <= n; ++j) {
+        if (ROLE_A(j) && !paired[j]) {
+            double left_new = (j == 1) ? beta_l : u_out[j - 2];
+            u_out[j - 1] = singleton_update(kc, left_new, u_in[j - 1], OLD(j + 1));
+        }
+    }
+    /* Saul'yev B runs, right to left from the new right neighbour */
+    for (j = n; j >= 1; --j) {
+        if (!ROLE_A(j) && !paired[j]) {
+            double right_new = (j == n) ? beta_r : u_out[j];
+            u_out[j - 1] = singleton_update(kc, right_new, u_in[j - 1], OLD(j - 1));
+        }
+    }
+#undef OLD
+#undef ROLE_A
+    free(paired);
+    return 0;
+}
+
+int ge_oracle_run_k(int64_t n, double r, double beta_l, double beta_r, int64_t k, int64_t step0,
+                    int64_t steps, double *u)
+{
+    double *tmp, *src, *dst;
+    int64_t s;
+    if (n < 1 || k < 1 || steps < 0 || step0 < 0 || u == NULL || !(r > 0.0) || !isfinite(r))
+        return -1;
+    if (steps == 0)
+        return 0;
+    tmp = (double *)malloc((size_t)n * sizeof(double));
+    if (tmp == NULL)
+        return -1;
+    src = u;
+    dst = tmp;
+    for (s = 0; s < steps; ++s) {
+        double *t;
+        if (ge_oracle_step_k(n, r, beta_l, beta_r, (int)((step0 + s) % 2), k, src, dst) != 0) {
+            free(tmp);
+            return -1;
+        }
+        t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != u)
+        memcpy(u, src, (size_t)n * sizeof(double));
+    free(tmp);
+    return 0;
+}
+
 /* Periodic variant (test-only, for the Fourier pin): n even, indices taken
  * modulo n, parity 0 groups (0,1),(2,3),..., parity 1 groups (1,2),...,(n-1,0).
  * No walls, no singletons; the same group formula as the Dirichlet step. */

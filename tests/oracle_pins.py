@@ -24,21 +24,20 @@ R_VALUES = (0.013, 0.3, 0.5, 1.0, 2.0, 7.25, 1.0e4)
 
 
 # ---------------------------------------------------------------- references
-def saulyev_roles(n: int, parity: int):
-    """Role of every interior node in one step (Sec. 2, k = 1).
+def saulyev_roles(n: int, parity: int, k: int = 1):
+    """Role of every interior node in one step (Sec. 2).
 
     Paper nodes j = 1..n (node j is array index j-1), walls j = 0 and n+1.
-    With k = 1 the odd sub-domains are the single nodes x_{2i} and the even
-    ones x_{2i+1}.  First row of each pair of steps (parity 0): odd
-    sub-domains use Saul'yev A (new-level neighbour on the left), even ones
-    Saul'yev B (new-level neighbour on the right); second row (parity 1):
-    the roles swap.  Returns a list of (j, new_nb, old_nb)."""
+    Odd sub-domains are [x_{2ik}, x_{2ik+k-1}], even ones [x_{2ik+k},
+    x_{2(i+1)k-1}]: node j lies in sub-domain floor(j/k), odd when that index
+    is even.  First row of each pair of steps (parity 0): odd sub-domains use
+    Saul'yev A (new-level neighbour on the left), even ones Saul'yev B
+    (new-level neighbour on the right); second row (parity 1): the roles
+    swap.  Returns a list of (j, new_nb, old_nb)."""
     roles = []
     for j in range(1, n + 1):
-        if parity == 0:
-            uses_a = (j % 2 == 0)
-        else:
-            uses_a = (j % 2 == 1)
+        odd_subdomain = ((j // k) % 2 == 0)
+        uses_a = odd_subdomain if parity == 0 else not odd_subdomain
         if uses_a:
             roles.append((j, j - 1, j + 1))   # Eq. (aa)
         else:
@@ -46,7 +45,7 @@ def saulyev_roles(n: int, parity: int):
     return roles
 
 
-def saulyev_dense_step(u, r, bl, br, parity, exact=False):
+def saulyev_dense_step(u, r, bl, br, parity, exact=False, k=1):
     """One step assembled from Eqs. (aa)/(bb) and solved as a dense system:
     (1+r) u'_j - r u'_{new_nb} = (1-r) u_j + r u_{old_nb}, walls fixed."""
     n = len(u)
@@ -58,7 +57,7 @@ def saulyev_dense_step(u, r, bl, br, parity, exact=False):
         old[j] = cvt(u[j - 1])
     A = [[0 * one] * n for _ in range(n)]
     rhs = [0 * one] * n
-    for (j, new_nb, old_nb) in saulyev_roles(n, parity):
+    for (j, new_nb, old_nb) in saulyev_roles(n, parity, k):
         row = j - 1
         A[row][row] = (one + r)
         rhs[row] = (one - r) * old[j] + r * old[old_nb]
@@ -336,6 +335,81 @@ def pin_convergence(orc) -> float:
     return worst
 
 
+K_VALUES = (2, 3, 4, 5, 16)
+
+
+def pin_k_dense_saulyev(orc) -> float:
+    """General sub-domain width k: the step (confluence pairs by Eqs. (cc)/(dd),
+    then Saul'yev A runs left to right and B runs right to left) equals the
+    dense solve of Eqs. (aa)/(bb) with the sub-domain roles of Sec. 2."""
+    rng = np.random.default_rng(17)
+    worst = 0.0
+    for k in K_VALUES:
+        for n in (1, 2, 3, 7, 15, 16, 17, 33, 40):
+            for parity in (0, 1):
+                for r in (0.2, 1.0, 6.0):
+                    u = rng.uniform(-1, 1, n)
+                    bl, br = rng.uniform(-1, 1, 2)
+                    want = saulyev_dense_step(u, r, bl, br, parity, k=k)
+                    got = orc.step_k(u, r, bl, br, parity, k)
+                    worst = max(worst, _rel(got, want) / max(1.0, r))
+    return worst
+
+
+def pin_k1_is_group_step(orc) -> float:
+    """Width k = 1 is the 2-point group step, bit for bit (1.0 if not)."""
+    rng = np.random.default_rng(18)
+    for n in (1, 2, 9, 64):
+        for parity in (0, 1):
+            u = rng.standard_normal(n)
+            if not np.array_equal(orc.step_k(u, 2.5, 0.1, 0.2, parity, 1), orc.step(u, 2.5, 0.1, 0.2, parity)):
+                return 1.0
+    return 0.0
+
+
+def pin_k_fixed_point_and_stability(orc) -> float:
+    """For every k the linear wall-to-wall profile is a fixed point (in units of
+    the round-off bound), and two steps have spectral radius below 1 with
+    zero walls (stability for r from 0.5 to 100)."""
+    worst = 0.0
+    eps = np.finfo(np.float64).eps
+    for k in K_VALUES:
+        n = 40
+        x = np.arange(1, n + 1) / (n + 1.0)
+        u = 0.7 + (-1.3 - 0.7) * x
+        got = orc.run_k(u, 2.0, 0.7, -1.3, k, 6)
+        worst = max(worst, float(np.max(np.abs(got - u))) / (6 * 9 * eps * 1.3))
+        for r in (0.5, 4.0, 100.0):
+            M = np.zeros((24, 24))
+            for j in range(24):
+                e = np.zeros(24)
+                e[j] = 1.0
+                M[:, j] = orc.run_k(e, r, 0.0, 0.0, k, 2)
+            rho = float(np.max(np.abs(np.linalg.eigvals(M))))
+            worst = max(worst, 0.0 if rho < 1.0 - 1e-6 else 2.0)
+    return worst
+
+
+def pin_k_convergence(orc) -> float:
+    """Second order at fixed r for sub-domain widths 4 and 16: halving h
+    divides the error by 3.5 to 5 (0.0 inside)."""
+    worst = 0.0
+    for k in (4, 16):
+        errs = []
+        for M in (128, 256, 512):
+            n = M - 1
+            steps = int(round(0.005 * M * M))
+            x = np.arange(1, n + 1) / float(M)
+            u = orc.run_k(np.sin(np.pi * x), 1.0, 0.0, 0.0, k, steps)
+            t = steps / float(M * M)
+            ex = np.exp(-np.pi ** 2 * t) * np.sin(np.pi * x)
+            errs.append(np.max(np.abs(u - ex)) / np.max(np.abs(ex)))
+        for i in range(len(errs) - 1):
+            ratio = errs[i] / errs[i + 1]
+            worst = max(worst, max(3.5 - ratio, ratio - 5.0, 0.0))
+    return worst
+
+
 PINS = {
     "group_vs_2x2_solve": (pin_group_vs_2x2_solve, 1e-13),
     "dense_saulyev": (pin_dense_saulyev, 1e-12),
@@ -348,4 +422,8 @@ PINS = {
     "fourier_symbol": (pin_fourier_symbol, 64.0),
     "exact_solution": (pin_exact_solution, 1e-7),
     "convergence": (pin_convergence, 0.0),
+    "k_dense_saulyev": (pin_k_dense_saulyev, 1e-12),
+    "k1_is_group_step": (pin_k1_is_group_step, 0.0),
+    "k_fixed_point_and_stability": (pin_k_fixed_point_and_stability, 1.0),
+    "k_convergence": (pin_k_convergence, 0.0),
 }

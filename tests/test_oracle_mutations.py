@@ -38,6 +38,13 @@ MUTATIONS = [
     ("run starts at the wrong parity", "ge_oracle_step(n, r, beta_l, beta_r, (int)((step0 + s) % 2), src, dst);",
      "ge_oracle_step(n, r, beta_l, beta_r, (int)((step0 + s + 1) % 2), src, dst);"),
     ("no right singleton", "if (((n - parity) % 2) == 1) {", "if (0) {"),
+    ("sub-domain roles swapped (width k)", "#define ROLE_A(jj) ((((jj) / k) + parity) % 2 == 0)",
+     "#define ROLE_A(jj) ((((jj) / k) + parity) % 2 == 1)"),
+    ("A run reads its right neighbour from the wrong side (width k)",
+     "u_out[j - 1] = singleton_update(kc, left_new, u_in[j - 1], OLD(j + 1));",
+     "u_out[j - 1] = singleton_update(kc, left_new, u_in[j - 1], OLD(j - 1));"),
+    ("B run starts from the left wall (width k)", "double right_new = (j == n) ? beta_r : u_out[j];",
+     "double right_new = (j == n) ? beta_l : u_out[j];"),
 ]
 
 
