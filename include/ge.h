@@ -99,6 +99,17 @@ ge_status ge_create(ge_ctx **out, int64_t n, double r, double beta_l, double bet
  * GE_KERNEL_CANONICAL with GE_F32_COMP). */
 ge_status ge_set_kernel(ge_ctx *ctx, ge_kernel kernel, int32_t depth);
 
+/* Sub-domain width k (Sec. 2: odd sub-domains [x_{2ik}, x_{2ik+k-1}], even
+ * sub-domains [x_{2ik+k}, x_{2(i+1)k-1}] of the paper's nodes x_0..x_{n+1}).
+ * k = 1 (the default) is the 2-point group scheme every kernel above runs.
+ * For k > 1 each step couples the two wall nodes of every confluence of a B
+ * sub-domain with the A sub-domain to its right by Eqs. (cc)/(dd) and sweeps
+ * Saul'yev A runs to the right and B runs to the left (paper node j uses A
+ * at parity p iff floor(j/k) + p is even); ge_step_n then runs one launch per
+ * step with one thread per confluence unit, whatever ge_set_kernel chose.
+ * Errors: GE_EINVAL (NULL ctx, k < 1, k > 1 with GE_F32_COMP). */
+ge_status ge_set_subdomain_width(ge_ctx *ctx, int64_t k);
+
 /* Advance the state by `steps` GE time steps (steps >= 0), continuing the
  * parity of the step counter, which increases by `steps`.  Asynchronous on
  * the context's stream; may be captured in a CUDA graph once the context

@@ -22,7 +22,7 @@ GE_F64, GE_F32, GE_F32_COMP = 0, 1, 2
 GE_KERNEL_AUTO, GE_KERNEL_CANONICAL, GE_KERNEL_ONESTEP, GE_KERNEL_TEMPORAL = 0, 1, 2, 3
 
 # Every symbol include/ge.h declares.
-EXPORTS = ("ge_create", "ge_set_kernel", "ge_step_n", "ge_read_state", "ge_write_state",
+EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", "ge_read_state", "ge_write_state",
            "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_batch_create", "ge_batch_set_depth",
            "ge_batch_get_depth", "ge_batch_tune", "ge_batch_run", "ge_batch_sync", "ge_batch_destroy",
            "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error")
@@ -56,6 +56,8 @@ def load(path: str | None = None):
         lib.ge_create.restype = ctypes.c_int
         lib.ge_set_kernel.argtypes = [_VP, ctypes.c_int, _I32]
         lib.ge_set_kernel.restype = ctypes.c_int
+        lib.ge_set_subdomain_width.argtypes = [_VP, _I64]
+        lib.ge_set_subdomain_width.restype = ctypes.c_int
         lib.ge_step_n.argtypes = [_VP, _I64]
         lib.ge_step_n.restype = ctypes.c_int
         lib.ge_read_state.argtypes = [_VP, _VP]
@@ -158,6 +160,10 @@ def ge_create(n: int, r: float, beta_l: float, beta_r: float, prec: int, u0=None
 
 def ge_set_kernel(ctx: Ctx, kernel: int, depth: int = 0):
     _check(load().ge_set_kernel(ctx.handle, int(kernel), int(depth)), "ge_set_kernel")
+
+
+def ge_set_subdomain_width(ctx: Ctx, k: int):
+    _check(load().ge_set_subdomain_width(ctx.handle, int(k)), "ge_set_subdomain_width")
 
 
 def ge_step_n(ctx: Ctx, steps: int):

@@ -81,6 +81,7 @@ struct ge_ctx {
     int64_t step = 0;    // global step counter
     ge_kernel kernel = GE_KERNEL_AUTO;
     int depth = 0;
+    int64_t width = 1;   // sub-domain width k
     int *err_dev = nullptr;
     int num_sms = 0;
     int tb_blocks_per_sm = 0;
@@ -226,6 +227,27 @@ ge_status run_tiled(ge_ctx *c, int64_t steps, int depth)
     return GE_OK;
 }
 
+// General sub-domain width k: one launch per step (ge_sweep.cu).
+ge_status run_sweep(ge_ctx *c, int64_t steps)
+{
+    for (int64_t s = 0; s < steps; ++s) {
+        const int parity = (int)((c->step + s) & 1);
+        cudaError_t e;
+        if (c->prec == GE_F64)
+            e = ge::launch_sweep_f64(static_cast<const double *>(c->buf[c->cur]),
+                                     static_cast<double *>(c->buf[c->cur ^ 1]), c->n, parity, c->width,
+                                     c->canon, c->stream);
+        else
+            e = ge::launch_sweep_f32(static_cast<const float *>(c->buf[c->cur]),
+                                     static_cast<float *>(c->buf[c->cur ^ 1]), c->n, parity, c->width,
+                                     c->canon, c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "sub-domain sweep kernel launch");
+        c->cur ^= 1;
+    }
+    return GE_OK;
+}
+
 ge_status run_canonical(ge_ctx *c, int64_t steps)
 {
     for (int64_t s = 0; s < steps; ++s) {
@@ -367,6 +389,18 @@ ge_status ge_set_kernel(ge_ctx *c, ge_kernel kernel, int32_t depth)
     return GE_OK;
 }
 
+ge_status ge_set_subdomain_width(ge_ctx *c, int64_t k)
+{
+    if (!c)
+        return fail(GE_EINVAL, "ge_set_subdomain_width: ctx is NULL");
+    if (k < 1)
+        return fail(GE_EINVAL, "ge_set_subdomain_width: k = %lld, need k >= 1", (long long)k);
+    if (k > 1 && c->prec == GE_F32_COMP)
+        return fail(GE_EINVAL, "ge_set_subdomain_width: no compensated variant for k > 1");
+    c->width = k;
+    return GE_OK;
+}
+
 ge_status ge_step_n(ge_ctx *c, int64_t steps)
 {
     if (!c)
@@ -376,6 +410,12 @@ ge_status ge_step_n(ge_ctx *c, int64_t steps)
     if (steps == 0)
         return GE_OK;
     ge_status st;
+    if (c->width > 1) {
+        st = run_sweep(c, steps);
+        if (st == GE_OK)
+            c->step += steps;
+        return st;
+    }
     switch (c->kernel) {
     case GE_KERNEL_CANONICAL:
         st = run_canonical(c, steps);

@@ -97,6 +97,11 @@ cudaError_t launch_canon_f64(const double *in, double *out, long long n, int par
                              const CanonCoef &c, cudaStream_t s);
 cudaError_t launch_canon_f32(const float *in, float *out, long long n, int parity,
                              const CanonCoef &c, cudaStream_t s);
+// General sub-domain width k (ge_sweep.cu), one step.
+cudaError_t launch_sweep_f64(const double *in, double *out, long long n, int parity, long long k,
+                             const CanonCoef &c, cudaStream_t s);
+cudaError_t launch_sweep_f32(const float *in, float *out, long long n, int parity, long long k,
+                             const CanonCoef &c, cudaStream_t s);
 
 // prec: 0 = FP64, 1 = FP32, 2 = FP32 compensated.  tmap: 128-byte-aligned
 // CUtensorMap (opaque here) describing the source buffer.

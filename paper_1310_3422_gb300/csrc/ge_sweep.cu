@@ -1,0 +1,120 @@
+// ge_sweep.cu -- the GE step with general sub-domain width k (arXiv:1310.3422
+// Sec. 2: odd sub-domains [x_{2ik}, x_{2ik+k-1}], even sub-domains
+// [x_{2ik+k}, x_{2(i+1)k-1}], Saul'yev A / B alternating between them and
+// between the two steps of each pair, Eqs. (cc)/(dd) at the confluences).
+//
+// Paper node j (array index j-1, walls at j = 0 and n+1) lies in sub-domain
+// s = floor(j/k).  At parity p it uses Saul'yev A (new-level neighbour on the
+// left) when s + p is even, else Saul'yev B.  Where a B sub-domain meets the
+// A sub-domain to its right, their two wall nodes form a coupled pair solved
+// by Eqs. (cc)/(dd); from that pair the A run is swept to the right and the
+// B run to the left.  One thread owns one such confluence unit (a B
+// sub-domain followed by an A sub-domain, 2k nodes), the paper's own thread
+// mapping ("sub-domain couples", Sec. 3): the sweeps are sequential
+// recurrences.  A unit at the left wall has only its A part (swept from the
+// wall value beta_l), one at the right wall only its B part (from beta_r).
+//
+// Every sum of products is a chain of fused multiply-adds in the order the
+// equation prints its terms, so the FP64 result is bit-identical to a serial
+// FP64 evaluation in that order.  k = 1 gives the 2-point group step.
+#include "ge_internal.h"
+
+namespace ge {
+namespace {
+
+template <typename Real>
+struct SweepCoef {
+    Real c1, c2, c3, c4, s0, s1, bl, br;
+};
+
+__device__ __forceinline__ double f_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float f_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double f_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float f_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+template <typename Real>
+__global__ void __launch_bounds__(256) sweep_kernel(const Real *__restrict__ in, Real *__restrict__ out,
+                                                    long long n, int parity, long long k, long long n_units,
+                                                    SweepCoef<Real> c)
+{
+    // old value of paper node j (walls outside 1..n)
+    auto old = [&](long long j) -> Real { return j == 0 ? c.bl : (j == n + 1 ? c.br : in[j - 1]); };
+    // Saul'yev A / B at node j from its new-level neighbour `nb` and its
+    // old-level far neighbour: (r nb + (1-r) u_j + r far) / (1+r)
+    auto saulyev = [&](Real nb, long long j, long long far) -> Real {
+        return f_fma(c.s0, old(far), f_fma(c.s1, in[j - 1], f_mul(c.s0, nb)));
+    };
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < n_units; u += stride) {
+        const long long bA = 2 * u + parity;       // the unit's A sub-domain
+        const long long a_lo = bA * k < 1 ? 1 : bA * k;
+        const long long a_hi = bA * k + k - 1 > n ? n : bA * k + k - 1;
+        const long long b_lo = (bA - 1) * k < 1 ? 1 : (bA - 1) * k;
+        const long long b_hi = bA * k - 1 > n ? n : bA * k - 1;
+        const bool has_a = a_lo <= a_hi, has_b = b_lo <= b_hi;
+        if (has_a && has_b) {
+            // confluence pair (j, j+1): B at j, A at j+1 -- Eqs. (cc), (dd)
+            const long long j = bA * k - 1;
+            const Real a = old(j - 1), b = old(j), cc = old(j + 1), d = old(j + 2);
+            const Real y = f_fma(c.c4, d, f_fma(c.c3, cc, f_fma(c.c2, b, f_mul(c.c1, a))));
+            const Real z = f_fma(c.c1, d, f_fma(c.c2, cc, f_fma(c.c3, b, f_mul(c.c4, a))));
+            out[j - 1] = y;
+            out[j] = z;
+            Real prev = z;
+            for (long long m = j + 2; m <= a_hi; ++m) {  // A run to the right
+                prev = saulyev(prev, m, m + 1);
+                out[m - 1] = prev;
+            }
+            prev = y;
+            for (long long m = j - 1; m >= b_lo; --m) {  // B run to the left
+                prev = saulyev(prev, m, m - 1);
+                out[m - 1] = prev;
+            }
+        } else if (has_a) {  // left wall: A run from beta_l
+            Real prev = c.bl;
+            for (long long m = a_lo; m <= a_hi; ++m) {
+                prev = saulyev(prev, m, m + 1);
+                out[m - 1] = prev;
+            }
+        } else if (has_b) {  // right wall: B run from beta_r
+            Real prev = c.br;
+            for (long long m = b_hi; m >= b_lo; --m) {
+                prev = saulyev(prev, m, m - 1);
+                out[m - 1] = prev;
+            }
+        }
+    }
+}
+
+template <typename Real>
+cudaError_t launch_sweep_t(const Real *in, Real *out, long long n, int parity, long long k, const CanonCoef &cf,
+                           cudaStream_t s)
+{
+    SweepCoef<Real> c{(Real)cf.c1, (Real)cf.c2, (Real)cf.c3, (Real)cf.c4,
+                      (Real)cf.s0, (Real)cf.s1, (Real)cf.beta_l, (Real)cf.beta_r};
+    // units u = 0.. cover sub-domains up to floor(n / k)
+    const long long last_block = n / k;
+    const long long n_units = (last_block + 1 - parity) / 2 + 1;
+    const int threads = 256;
+    long long blocks = (n_units + threads - 1) / threads;
+    if (blocks > (1LL << 20))
+        blocks = 1LL << 20;
+    sweep_kernel<Real><<<(unsigned)blocks, threads, 0, s>>>(in, out, n, parity, k, n_units, c);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sweep_f64(const double *in, double *out, long long n, int parity, long long k,
+                             const CanonCoef &c, cudaStream_t s)
+{
+    return launch_sweep_t<double>(in, out, n, parity, k, c, s);
+}
+
+cudaError_t launch_sweep_f32(const float *in, float *out, long long n, int parity, long long k,
+                             const CanonCoef &c, cudaStream_t s)
+{
+    return launch_sweep_t<float>(in, out, n, parity, k, c, s);
+}
+
+}  // namespace ge
