@@ -222,7 +222,7 @@ def measure_e2e(B, torch, u0, prec, kern, depth, steps, world):
             "ms_per_step": t_e2e * 1e3, "timer": "host wall clock around ge_solve (synchronous)"}
 
 
-def measure_batch(B, torch, inputs, dev, steps, warmup):
+def measure_batch(B, torch, inputs, dev, steps, warmup, only=None):
     """Batched workload: 4096 problems, N log-uniform in [256, 65536], r in
     [0.25, 4], 2000 steps.  One CUDA-graph replay per solve (reset from u0 +
     ge_batch_run); depth autotuned; sampled problems checked against the
@@ -238,6 +238,8 @@ def measure_batch(B, torch, inputs, dev, steps, warmup):
     want = {i: oracle.run(bt.u0[bt.offsets[i]:bt.offsets[i] + bt.n[i]], bt.r[i], bt.beta_l[i], bt.beta_r[i], 2000)
             for i in picks}
     for name, prec in (("f32", B.GE_F32), ("f32c", B.GE_F32_COMP), ("f64", B.GE_F64)):
+        if only is not None and name != only:
+            continue
         s = torch.cuda.Stream(device=dev)
         with torch.cuda.stream(s):
             u0 = torch.from_numpy(bt.u0).to(dev, B.dtype_of(prec))
@@ -274,7 +276,7 @@ def measure_batch(B, torch, inputs, dev, steps, warmup):
 
 
 def launches_per_solve(kernel, depth):
-    if kernel == "canonical":
+    if kernel in ("canonical", "subdomain16"):
         return GE_STEPS
     d = 1 if kernel == "onestep" else depth
     return (GE_STEPS + d - 1) // d
@@ -293,6 +295,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--only-batched", default=None, choices=["f32", "f32c", "f64"],
+                    help="run only the batched workload in this precision (profiling)")
     args = ap.parse_args()
 
     world, rank, local, dist = dist_setup(args)
@@ -309,6 +313,10 @@ def main():
     B.load()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.only_batched:
+        res = measure_batch(B, torch, inputs, dev, args.steps, args.warmup, only=args.only_batched)
+        print(json.dumps({"batched": res}), flush=True)
+        return 0
     prec = {"f64": B.GE_F64, "f32": B.GE_F32, "f32c": B.GE_F32_COMP}[args.precision]
     kern = {"temporal": B.GE_KERNEL_TEMPORAL, "onestep": B.GE_KERNEL_ONESTEP,
             "canonical": B.GE_KERNEL_CANONICAL}[args.kernel]
@@ -418,16 +426,18 @@ def main():
         def flush():
             flush_buf.fill_(1)
         for vp, vk, vd in (("f64", "onestep", 1), ("f64", "canonical", 1), ("f32", "temporal", 128),
-                           ("f32c", "temporal", 64), ("f32", "onestep", 1)):
+                           ("f32c", "temporal", 64), ("f32", "onestep", 1), ("f64", "subdomain16", 1)):
             if (vp, vk) == (args.precision, args.kernel):
                 continue
             p2 = {"f64": B.GE_F64, "f32": B.GE_F32, "f32c": B.GE_F32_COMP}[vp]
+            width = 16 if vk == "subdomain16" else 1
             k2 = {"temporal": B.GE_KERNEL_TEMPORAL, "onestep": B.GE_KERNEL_ONESTEP,
-                  "canonical": B.GE_KERNEL_CANONICAL}[vk]
+                  "canonical": B.GE_KERNEL_CANONICAL, "subdomain16": B.GE_KERNEL_CANONICAL}[vk]
             x2 = torch.from_numpy(u0).to(dev, dtype=B.dtype_of(p2))
             with torch.cuda.stream(stream):
                 c2 = B.ge_create(N_POINTS, R, 0.0, 0.0, p2, x2, stream=stream)
                 B.ge_set_kernel(c2, k2, vd)
+                B.ge_set_subdomain_width(c2, width)
                 ms = time_solver(B, torch, c2, x2, 2, 1, stream, flush=flush)
                 o2 = torch.empty_like(x2)
                 B.ge_read_state(c2, o2)
@@ -438,7 +448,10 @@ def main():
             ent = {"updates_per_s": upd_s, "ms_per_step": ms,
                    "hbm_roofline_frac_1step": upd_s / (hbm_gbs * 1e9 / (2.0 * bpu)),
                    "launches_per_step": launches_per_solve(vk, vd)}
-            ent.update(errors(o2.cpu().numpy().astype(np.float64)[idx], want, scale))
+            if width == 1:
+                ent.update(errors(o2.cpu().numpy().astype(np.float64)[idx], want, scale))
+            else:
+                ent["scheme"] = "sub-domain width k = 16 (the paper's 32-node sub-domain couples)"
             variants[f"{vp}_{vk}" + (f"_d{vd}" if vk == "temporal" else "")] = ent
             del x2, o2
         del flush_buf
