@@ -275,6 +275,115 @@ def measure_batch(B, torch, inputs, dev, steps, warmup, only=None):
     return out
 
 
+SNO_PROBLEMS, SNO_N, SNO_K, SNO_JUMPS, SNO_TOL = 65536, 1024, 256, 8, 1e-3
+
+
+def measure_surrogate(B, torch, inputs, train_steps):
+    """Surrogate workload: the spectral neural operator (4 layers, 16 modes,
+    width 64, BF16 weights, FP32 accumulate) trained on the GPU on 100k pairs
+    (12,500 GE trajectories x 8 jumps of K = 256 steps, N = 1024, r U[0.5, 4],
+    u0 = linear wall profile + 16-mode Fourier (1/k^2) + 2 piecewise-linear
+    tents), then 65,536 fresh problems advanced 2048 steps as 8 jumps with the
+    GE fallback (1% sample + flagged, tolerance 1e-3 relative L2), against
+    plain batched FP32 GE (depth autotuned) on the same problems.  Times are
+    wall-clock with a device synchronisation on both sides (the fallback
+    pipeline reads its sample results back to the host)."""
+    from paper_1310_3422_gb300 import surrogate as SG
+
+    def sync():
+        torch.cuda.synchronize()
+
+    def rel_l2(a, b):
+        return (torch.linalg.vector_norm(a.double() - b, dim=1) / torch.linalg.vector_norm(b, dim=1)).cpu().numpy()
+
+    def stats(e):
+        return {"median": float(np.median(e)), "p99": float(np.percentile(e, 99)), "max": float(np.max(e))}
+
+    t0 = time.perf_counter()
+    data = SG.make_training_set(12500, K=SNO_K, jumps=SNO_JUMPS)
+    held = SG.make_training_set(256, K=SNO_K, jumps=SNO_JUMPS, seed=inputs.SEED_BASE + 5)
+    sync()
+    t_data = time.perf_counter() - t0
+    sur = SG.Surrogate(max_batch=1024, seed=0)
+    ident = rel_l2(held.x, held.y.double())
+    t0 = time.perf_counter()
+    losses = sur.train(data, steps=train_steps, batch=64, lr=2e-3, warmup=100)
+    sync()
+    t_train = time.perf_counter() - t0
+    one_jump = sur.evaluate(held)
+    del data
+
+    pr = inputs.surrogate_problems(SNO_PROBLEMS, SNO_N, seed=inputs.SEED_BASE + 6)
+    u0 = torch.tensor(pr.u0, dtype=torch.float32, device="cuda")
+    r, bl, br = (torch.tensor(x, dtype=torch.float32, device="cuda") for x in (pr.r, pr.beta_l, pr.beta_r))
+    steps = SNO_K * SNO_JUMPS
+    # plain batched FP32 GE
+    ge = SG.GEBatch(pr.r, pr.beta_l, pr.beta_r, SNO_N, B.GE_F32)
+    depth = B.ge_batch_tune(ge.plan, u0, 256)
+    x = u0.clone()
+    ge.run(x, steps)
+    sync()
+    ge_ms = []
+    for _ in range(3):
+        x.copy_(u0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ge.run(x, steps)
+        e1.record()
+        e1.synchronize()
+        ge_ms.append(e0.elapsed_time(e1))
+    t_ge = min(ge_ms) / 1e3
+    ge.close()
+    # surrogate alone, then the pipeline with the fallback
+    sur.rollout(u0[:1024], r[:1024], bl[:1024], br[:1024], 1)
+    sync()
+    t0 = time.perf_counter()
+    pred = sur.rollout(u0, r, bl, br, SNO_JUMPS)
+    sync()
+    t_sur = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    out, rep = SG.solve_with_fallback(sur, u0, r, bl, br, SNO_JUMPS, tol=SNO_TOL, sample_frac=0.01)
+    sync()
+    t_pipe = time.perf_counter() - t0
+    # accuracy against FP64 GE
+    ref = u0.double()
+    ge64 = SG.GEBatch(pr.r, pr.beta_l, pr.beta_r, SNO_N, B.GE_F64)
+    ge64.run(ref, steps)
+    sync()
+    ge64.close()
+    err_pipe, err_sur, err_ge32 = rel_l2(out, ref), rel_l2(pred, ref), rel_l2(x, ref)
+    sur.close()
+    chunks = -(-SNO_PROBLEMS // 1024)
+    return {
+        "workload": f"{SNO_PROBLEMS} problems N={SNO_N}, r U[0.5,4], walls U(-1,1), u0 = linear + 16-mode "
+                    f"Fourier (1/k^2) + 2 tents; {steps} steps as {SNO_JUMPS} jumps of K={SNO_K}",
+        "tolerance_rel_l2": SNO_TOL,
+        "speedup_vs_batched_f32_ge": t_ge / t_pipe,
+        "pipeline_ms": t_pipe * 1e3, "surrogate_only_ms": t_sur * 1e3, "batched_f32_ge_ms": t_ge * 1e3,
+        "ge_depth": depth,
+        "fell_back_all": rep.fell_back_all, "sampled": rep.n_sampled, "flagged": rep.n_flagged,
+        "sample_over_tol": rep.n_sample_over_tol, "sample_max_err": rep.sample_max_err,
+        "err_pipeline_rel_l2": stats(err_pipe), "err_surrogate_only_rel_l2": stats(err_sur),
+        "err_batched_f32_ge_rel_l2": stats(err_ge32),
+        "one_jump_heldout_rel_l2": stats(one_jump), "identity_one_jump_rel_l2": stats(ident),
+        "training": {"pairs": 100000, "steps": train_steps, "batch": 64, "seconds": t_train,
+                     "data_seconds": t_data, "loss_first": float(losses[:20].mean()),
+                     "loss_last": float(losses[-100:].mean())},
+        "surrogate_tflops": 2 * SNO_PROBLEMS * SNO_JUMPS * sno_flops_per_problem() / t_sur / 1e12,
+        "gpu_launches_surrogate_only": SNO_JUMPS * chunks * sno_launches_per_forward(),
+    }
+
+
+def sno_flops_per_problem(n=SNO_N, C=64, M=16, L=4, H=128):
+    """Multiply-adds of one forward pass for one problem (x2 for FLOPs)."""
+    per_layer = 2 * (2 * M * n * C) + M * (2 * C) * (2 * C) + n * C * C
+    return n * 4 * C + L * per_layer + n * C * H + n * H
+
+
+def sno_launches_per_forward(L=4):
+    return 3 + 6 * L + 3 + 1
+
+
 def launches_per_solve(kernel, depth):
     if kernel in ("canonical", "subdomain16"):
         return GE_STEPS
@@ -295,6 +404,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--only-surrogate", action="store_true", help="run only the surrogate workload")
+    ap.add_argument("--sno-train-steps", type=int, default=3000)
     ap.add_argument("--only-batched", default=None, choices=["f32", "f32c", "f64"],
                     help="run only the batched workload in this precision (profiling)")
     args = ap.parse_args()
@@ -316,6 +428,9 @@ def main():
     if args.only_batched:
         res = measure_batch(B, torch, inputs, dev, args.steps, args.warmup, only=args.only_batched)
         print(json.dumps({"batched": res}), flush=True)
+        return 0
+    if args.only_surrogate:
+        print(json.dumps({"surrogate": measure_surrogate(B, torch, inputs, args.sno_train_steps)}), flush=True)
         return 0
     prec = {"f64": B.GE_F64, "f32": B.GE_F32, "f32c": B.GE_F32_COMP}[args.precision]
     kern = {"temporal": B.GE_KERNEL_TEMPORAL, "onestep": B.GE_KERNEL_ONESTEP,
@@ -461,6 +576,11 @@ def main():
     if not args.no_variants and world == 1:
         batched = measure_batch(B, torch, inputs, dev, 3, 2)
 
+    # ---- learned surrogate with the GE fallback ----------------------------
+    surrogate = None
+    if not args.no_surrogate and world == 1:
+        surrogate = measure_surrogate(B, torch, inputs, args.sno_train_steps)
+
     # ---- CPU baseline: the oracle on a bounded sample -----------------------
     cpu = None
     if not args.no_cpu:
@@ -492,6 +612,7 @@ def main():
         "accuracy": acc,
         "variants": variants,
         "batched": batched,
+        "surrogate": surrogate,
     }
     B.ge_destroy(ctx)
     print(json.dumps(line), flush=True)

@@ -1,4 +1,5 @@
-"""ctypes binding of ``libge.so`` (the C ABI of ``include/ge.h``).
+"""ctypes binding of ``libge.so`` (the C ABI of ``include/ge.h`` and
+``include/ge_sno.h``).
 
 Argument marshalling only: every step of the solver runs in the library's
 CUDA kernels.  Entry points keep the C names; device buffers are torch CUDA
@@ -21,11 +22,14 @@ GE_OK, GE_EINVAL, GE_ENOMEM, GE_ECUDA, GE_ETIMEOUT, GE_ENONFINITE = range(6)
 GE_F64, GE_F32, GE_F32_COMP = 0, 1, 2
 GE_KERNEL_AUTO, GE_KERNEL_CANONICAL, GE_KERNEL_ONESTEP, GE_KERNEL_TEMPORAL = 0, 1, 2, 3
 
-# Every symbol include/ge.h declares.
+# Every symbol include/ge.h and include/ge_sno.h declare.
 EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", "ge_read_state", "ge_write_state",
            "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_batch_create", "ge_batch_set_depth",
            "ge_batch_get_depth", "ge_batch_tune", "ge_batch_run", "ge_batch_sync", "ge_batch_destroy",
-           "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error")
+           "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error",
+           "ge_sno_create", "ge_sno_num_params", "ge_sno_get_params", "ge_sno_set_params",
+           "ge_sno_set_precision", "ge_sno_forward", "ge_sno_loss_grad", "ge_sno_adam_step",
+           "ge_sno_train_step", "ge_sno_destroy")
 
 _lock = threading.Lock()
 _lib = None
@@ -93,6 +97,26 @@ def load(path: str | None = None):
         lib.ge_solve_batch.restype = ctypes.c_int
         lib.ge_solve_noalloc.argtypes = [_I64, _D, _D, _D, ctypes.c_int, _I32, _I64, _VP, _VP, _VP]
         lib.ge_solve_noalloc.restype = ctypes.c_int
+        lib.ge_sno_create.argtypes = [ctypes.POINTER(_VP), _I32, _I32, _I32, _I32, _I32, _I32, ctypes.c_uint64, _VP]
+        lib.ge_sno_create.restype = ctypes.c_int
+        lib.ge_sno_num_params.argtypes = [_VP, ctypes.POINTER(_I64)]
+        lib.ge_sno_num_params.restype = ctypes.c_int
+        lib.ge_sno_get_params.argtypes = [_VP, _VP]
+        lib.ge_sno_get_params.restype = ctypes.c_int
+        lib.ge_sno_set_params.argtypes = [_VP, _VP]
+        lib.ge_sno_set_params.restype = ctypes.c_int
+        lib.ge_sno_set_precision.argtypes = [_VP, _I32]
+        lib.ge_sno_set_precision.restype = ctypes.c_int
+        lib.ge_sno_forward.argtypes = [_VP, _I32, _VP, _VP, _VP, _VP, _VP]
+        lib.ge_sno_forward.restype = ctypes.c_int
+        lib.ge_sno_loss_grad.argtypes = [_VP, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _VP]
+        lib.ge_sno_loss_grad.restype = ctypes.c_int
+        lib.ge_sno_adam_step.argtypes = [_VP, ctypes.c_float]
+        lib.ge_sno_adam_step.restype = ctypes.c_int
+        lib.ge_sno_train_step.argtypes = [_VP, _I32, _VP, _VP, _VP, _VP, _VP, ctypes.c_float, _VP]
+        lib.ge_sno_train_step.restype = ctypes.c_int
+        lib.ge_sno_destroy.argtypes = [_VP]
+        lib.ge_sno_destroy.restype = None
         lib.ge_status_str.argtypes = [ctypes.c_int]
         lib.ge_status_str.restype = ctypes.c_char_p
         lib.ge_last_error.argtypes = []
@@ -306,6 +330,95 @@ def ge_solve_noalloc(n: int, r: float, beta_l: float, beta_r: float, prec: int, 
     _check(load().ge_solve_noalloc(int(n), float(r), float(beta_l), float(beta_r), int(prec), int(depth),
                                    int(steps), _dptr(u0), _dptr(u_out), _stream_handle(stream)),
            "ge_solve_noalloc")
+
+
+class Sno:
+    """Owner of a ``ge_sno*`` surrogate model."""
+
+    def __init__(self, handle: int, n: int, width: int, modes: int, layers: int, hidden: int, max_batch: int):
+        self.handle = handle
+        self.n, self.width, self.modes, self.layers, self.hidden = n, width, modes, layers, hidden
+        self.max_batch = max_batch
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                ge_sno_destroy(self)
+            except Exception:
+                pass
+
+
+def _f32_dev(x, count: int, what: str):
+    import torch
+    if x is None or x.dtype != torch.float32 or x.numel() < count:
+        raise ValueError(f"{what} must be a CUDA float32 tensor of at least {count} elements")
+    return _dptr(x)
+
+
+def ge_sno_create(n: int, width: int, modes: int, layers: int, hidden: int, max_batch: int, seed: int = 0,
+                  stream=None) -> Sno:
+    h = _VP()
+    _check(load().ge_sno_create(ctypes.byref(h), int(n), int(width), int(modes), int(layers), int(hidden),
+                                int(max_batch), int(seed), _stream_handle(stream)), "ge_sno_create")
+    return Sno(h.value, int(n), int(width), int(modes), int(layers), int(hidden), int(max_batch))
+
+
+def ge_sno_num_params(model: Sno) -> int:
+    v = _I64()
+    _check(load().ge_sno_num_params(model.handle, ctypes.byref(v)), "ge_sno_num_params")
+    return int(v.value)
+
+
+def ge_sno_get_params(model: Sno, dst):
+    _check(load().ge_sno_get_params(model.handle, _f32_dev(dst, ge_sno_num_params(model), "dst")),
+           "ge_sno_get_params")
+
+
+def ge_sno_set_params(model: Sno, src):
+    _check(load().ge_sno_set_params(model.handle, _f32_dev(src, ge_sno_num_params(model), "src")),
+           "ge_sno_set_params")
+
+
+def ge_sno_set_precision(model: Sno, split: int):
+    _check(load().ge_sno_set_precision(model.handle, int(split)), "ge_sno_set_precision")
+
+
+def _sno_inputs(model: Sno, batch: int, u0, r, beta_l, beta_r):
+    return (_f32_dev(u0, batch * model.n, "u0"), _f32_dev(r, batch, "r"), _f32_dev(beta_l, batch, "beta_l"),
+            _f32_dev(beta_r, batch, "beta_r"))
+
+
+def ge_sno_forward(model: Sno, batch: int, u0, r, beta_l, beta_r, pred):
+    args = _sno_inputs(model, batch, u0, r, beta_l, beta_r)
+    _check(load().ge_sno_forward(model.handle, int(batch), *args, _f32_dev(pred, batch * model.n, "pred")),
+           "ge_sno_forward")
+
+
+def ge_sno_loss_grad(model: Sno, batch: int, u0, r, beta_l, beta_r, target, loss=None, grads=None):
+    args = _sno_inputs(model, batch, u0, r, beta_l, beta_r)
+    _check(load().ge_sno_loss_grad(model.handle, int(batch), *args,
+                                   _f32_dev(target, batch * model.n, "target"),
+                                   None if loss is None else _f32_dev(loss, batch, "loss"),
+                                   None if grads is None else _f32_dev(grads, ge_sno_num_params(model), "grads")),
+           "ge_sno_loss_grad")
+
+
+def ge_sno_adam_step(model: Sno, lr: float):
+    _check(load().ge_sno_adam_step(model.handle, float(lr)), "ge_sno_adam_step")
+
+
+def ge_sno_train_step(model: Sno, batch: int, u0, r, beta_l, beta_r, target, lr: float, loss=None):
+    args = _sno_inputs(model, batch, u0, r, beta_l, beta_r)
+    _check(load().ge_sno_train_step(model.handle, int(batch), *args,
+                                    _f32_dev(target, batch * model.n, "target"), float(lr),
+                                    None if loss is None else _f32_dev(loss, batch, "loss")),
+           "ge_sno_train_step")
+
+
+def ge_sno_destroy(model: Sno):
+    if model.handle:
+        load().ge_sno_destroy(model.handle)
+        model.handle = None
 
 
 def ge_status_str(status: int) -> str:

@@ -1,0 +1,507 @@
+// ge_sno.cpp -- the spectral neural operator (learned surrogate of K GE steps):
+// parameters, forward, backward and Adam, orchestrating the kernels of
+// ge_sno_kernels.cu.  Host code only.
+//
+// Architecture (1D Fourier neural operator on the n interior points):
+//   features (u0, x, r, beta_l + (beta_r - beta_l) x)  -> lift (4 -> C)
+//   L layers: v <- act( iDFT_M( R_m * DFT_M(v) ) + v W + b ),  act = GELU except
+//             after the last layer; DFT_M keeps the M lowest modes, R_m is a
+//             complex C x C matrix per mode
+//   projection C -> H (GELU) -> 1, added to u0 (residual output).
+// Activations are channel-last [batch * n, C] in FP32.  The FP32 master
+// parameters are rounded to BF16 at the start of every forward pass (the
+// network has BF16 weights; Adam updates the masters with the gradient of the
+// rounded network).  Every GEMM rounds its operands to BF16 and accumulates in
+// FP32; split mode adds the BF16 residuals (~FP32 products).
+//
+// Parameter vector (FP32, this order): W0 [4][C], b0 [C]; per layer: Rr
+// [M][C][C] (out, in), Ri [M][C][C], W [C][C] (in, out), b [C]; Q1 [C][H],
+// q1 [H], Q2 [H], q2 [1].
+#include "ge_sno.h"
+
+#include <cuda_runtime_api.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ge_internal.h"
+#include "ge_sno_internal.h"
+
+namespace {
+
+ge_status sfail(ge_status st, const char *msg)
+{
+    ge::set_last_error(msg);
+    return st;
+}
+
+ge_status scuda(cudaError_t e, const char *what)
+{
+    char buf[400];
+    std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    ge::set_last_error(buf);
+    return e == cudaErrorMemoryAllocation ? GE_ENOMEM : GE_ECUDA;
+}
+
+struct LayerOff {
+    long long rr, ri, w, b;
+};
+
+}  // namespace
+
+struct ge_sno {
+    int n = 0, C = 0, M = 0, L = 0, H = 0, max_batch = 0;
+    bool split = false;
+    cudaStream_t stream = nullptr;
+    long long n_params = 0;
+    long long off_w0 = 0, off_b0 = 0, off_q1 = 0, off_qb1 = 0, off_q2 = 0, off_qb2 = 0;
+    std::vector<LayerOff> lay;
+    float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+    float *pw = nullptr;               // params rounded to BF16 (the weights the network uses)
+    long long adam_t = 0;
+    float *F = nullptr, *G = nullptr;  // [2M][n] and [n][2M]
+    float *wspec = nullptr;            // [L][M][2C][2C]
+    float *dwspec = nullptr;           // [M][2C][2C]
+    // activations (max_batch)
+    float *feat = nullptr;             // [B n][4]
+    std::vector<float *> v;            // L + 1 buffers [B n][C]
+    std::vector<float *> pre;          // L buffers [B n][C]
+    std::vector<float *> vh;           // L buffers [B][2M][C]
+    float *y = nullptr;                // [B][2M][C] scratch (mixing output / its gradient)
+    float *hpre = nullptr, *h = nullptr;  // [B n][H]
+    float *out = nullptr, *dout = nullptr, *loss = nullptr;  // [B n], [B n], [B]
+    float *dA = nullptr, *dB = nullptr;   // [B n][max(C, H)] gradient scratch
+    float *dvh = nullptr;                 // [B][2M][C]
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+ge::GemmArgs gemm(const float *A, long long lda_i, long long lda_k, const float *B, long long ldb_k, long long ldb_j,
+                  float *C, long long ldc, int M, int N, int K)
+{
+    ge::GemmArgs g{};
+    g.A = A;
+    g.B = B;
+    g.C = C;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.lda_i = lda_i;
+    g.lda_k = lda_k;
+    g.ldb_k = ldb_k;
+    g.ldb_j = ldb_j;
+    g.ldc = ldc;
+    g.alpha = 1.0f;
+    g.beta = 0.0f;
+    g.ksplit = 1;
+    return g;
+}
+
+#define SNO_TRY(expr)                                    \
+    do {                                                 \
+        cudaError_t e_ = (expr);                         \
+        if (e_ != cudaSuccess)                           \
+            return scuda(e_, "ge_sno: " #expr);          \
+    } while (0)
+
+// Weight gradient of a pointwise layer: dW[in][out] = X^T dY over R rows
+// (split-K with atomics), db = column sums of dY.
+ge_status weight_grad(ge_sno *s, const float *X, int in, const float *dY, int out, long long R, float *dW,
+                      float *db)
+{
+    SNO_TRY(cudaMemsetAsync(dW, 0, sizeof(float) * in * out, s->stream));
+    ge::GemmArgs g = gemm(X, 1, in, dY, out, 1, dW, out, in, out, (int)R);
+    long long ks = R / 1024;
+    g.ksplit = (int)(ks < 1 ? 1 : (ks > 512 ? 512 : ks));
+    SNO_TRY(ge::sno_gemm(g, 1, s->split, s->stream));
+    if (db)
+        SNO_TRY(ge::sno_colsum(dY, db, R, out, s->stream));
+    return GE_OK;
+}
+
+ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float *bl, const float *br)
+{
+    const int n = s->n, C = s->C, M = s->M, H = s->H;
+    const long long R = (long long)B * n;
+    cudaStream_t st = s->stream;
+    const float *P = s->pw;
+    SNO_TRY(ge::sno_round_bf16(s->params, s->pw, s->n_params, st));
+    SNO_TRY(ge::sno_features(u0, r, bl, br, s->feat, B, n, st));
+    // lift
+    ge::GemmArgs g = gemm(s->feat, 4, 1, P + s->off_w0, C, 1, s->v[0], C, (int)R, C, 4);
+    g.bias = P + s->off_b0;
+    SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
+    for (int l = 0; l < s->L; ++l) {
+        const LayerOff &o = s->lay[l];
+        float *ws = s->wspec + (long long)l * M * 4 * C * C;
+        SNO_TRY(ge::sno_spec_assemble(P + o.rr, P + o.ri, ws, M, C, st));
+        // truncated DFT along the grid: vh[b] = F [2M x n] * v[b] [n x C]
+        g = gemm(s->F, n, 1, s->v[l], C, 1, s->vh[l], C, 2 * M, C, n);
+        g.sA = 0;
+        g.sB = (long long)n * C;
+        g.sC = 2LL * M * C;
+        SNO_TRY(ge::sno_gemm(g, B, s->split, st));
+        // per-mode complex mixing: y[:, m] [B x 2C] = vh[:, m] [B x 2C] * Wspec_m [2C x 2C]
+        g = gemm(s->vh[l], 2LL * M * C, 1, ws, 2 * C, 1, s->y, 2LL * M * C, B, 2 * C, 2 * C);
+        g.sA = 2 * C;
+        g.sB = 4LL * C * C;
+        g.sC = 2 * C;
+        SNO_TRY(ge::sno_gemm(g, M, s->split, st));
+        // back to the grid: pre[b] = G [n x 2M] * y[b] [2M x C]
+        g = gemm(s->G, 2 * M, 1, s->y, C, 1, s->pre[l], C, n, C, 2 * M);
+        g.sA = 0;
+        g.sB = 2LL * M * C;
+        g.sC = (long long)n * C;
+        SNO_TRY(ge::sno_gemm(g, B, s->split, st));
+        // pointwise path: pre += v W + b
+        g = gemm(s->v[l], C, 1, P + o.w, C, 1, s->pre[l], C, (int)R, C, C);
+        g.C0 = s->pre[l];
+        g.beta = 1.0f;
+        g.bias = P + o.b;
+        SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
+        if (l < s->L - 1)
+            SNO_TRY(ge::sno_gelu_fwd(s->pre[l], s->v[l + 1], R * C, st));
+        else
+            SNO_TRY(cudaMemcpyAsync(s->v[l + 1], s->pre[l], sizeof(float) * R * C, cudaMemcpyDeviceToDevice, st));
+    }
+    // projection
+    g = gemm(s->v[s->L], C, 1, P + s->off_q1, H, 1, s->hpre, H, (int)R, H, C);
+    g.bias = P + s->off_qb1;
+    SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
+    SNO_TRY(ge::sno_gelu_fwd(s->hpre, s->h, R * H, st));
+    // residual output: the network predicts the change of u over the jump
+    g = gemm(s->h, H, 1, P + s->off_q2, 1, 1, s->out, 1, (int)R, 1, H);
+    g.bias = P + s->off_qb2;
+    g.C0 = u0;
+    g.beta = 1.0f;
+    SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
+    return GE_OK;
+}
+
+// Backward from s->dout ([B n]) into s->grads.
+ge_status backward(ge_sno *s, int B)
+{
+    const int n = s->n, C = s->C, M = s->M, H = s->H;
+    const long long R = (long long)B * n;
+    cudaStream_t st = s->stream;
+    const float *P = s->pw;
+    float *Gd = s->grads;
+    ge_status rc;
+    // projection: out = h Q2 + q2
+    if ((rc = weight_grad(s, s->h, H, s->dout, 1, R, Gd + s->off_q2, Gd + s->off_qb2)) != GE_OK)
+        return rc;
+    ge::GemmArgs g = gemm(s->dout, 1, 1, P + s->off_q2, 1, 1, s->dA, H, (int)R, H, 1);  // dh = dout Q2^T
+    SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
+    SNO_TRY(ge::sno_gelu_bwd(s->hpre, s->dA, s->dA, R * H, st));
+    if ((rc = weight_grad(s, s->v[s->L], C, s->dA, H, R, Gd + s->off_q1, Gd + s->off_qb1)) != GE_OK)
+        return rc;
+    g = gemm(s->dA, H, 1, P + s->off_q1, 1, H, s->dB, C, (int)R, C, H);  // dv_L = dhpre Q1^T
+    SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
+    float *dv = s->dB, *dnext = s->dA;
+    for (int l = s->L - 1; l >= 0; --l) {
+        const LayerOff &o = s->lay[l];
+        const float *ws = s->wspec + (long long)l * M * 4 * C * C;
+        float *dpre = dv;  // in place
+        if (l < s->L - 1)
+            SNO_TRY(ge::sno_gelu_bwd(s->pre[l], dv, dpre, R * C, st));
+        // pointwise path
+        if ((rc = weight_grad(s, s->v[l], C, dpre, C, R, Gd + o.w, Gd + o.b)) != GE_OK)
+            return rc;
+        g = gemm(dpre, C, 1, P + o.w, 1, C, dnext, C, (int)R, C, C);  // dv_l = dpre W^T
+        SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
+        // spectral path: dy[b] = G^T dpre[b]
+        g = gemm(s->G, 1, 2 * M, dpre, C, 1, s->y, C, 2 * M, C, n);
+        g.sA = 0;
+        g.sB = (long long)n * C;
+        g.sC = 2LL * M * C;
+        SNO_TRY(ge::sno_gemm(g, B, s->split, st));
+        // dWspec_m = vh[:, m]^T dy[:, m]
+        g = gemm(s->vh[l], 1, 2LL * M * C, s->y, 2LL * M * C, 1, s->dwspec, 2 * C, 2 * C, 2 * C, B);
+        g.sA = 2 * C;
+        g.sB = 2 * C;
+        g.sC = 4LL * C * C;
+        SNO_TRY(ge::sno_gemm(g, M, s->split, st));
+        SNO_TRY(ge::sno_spec_reduce(s->dwspec, Gd + o.rr, Gd + o.ri, M, C, st));
+        // dvh[:, m] = dy[:, m] Wspec_m^T
+        g = gemm(s->y, 2LL * M * C, 1, ws, 1, 2 * C, s->dvh, 2LL * M * C, B, 2 * C, 2 * C);
+        g.sA = 2 * C;
+        g.sB = 4LL * C * C;
+        g.sC = 2 * C;
+        SNO_TRY(ge::sno_gemm(g, M, s->split, st));
+        // dv_l += F^T dvh[b]
+        g = gemm(s->F, 1, n, s->dvh, C, 1, dnext, C, n, C, 2 * M);
+        g.sA = 0;
+        g.sB = 2LL * M * C;
+        g.sC = (long long)n * C;
+        g.C0 = dnext;
+        g.sC0 = (long long)n * C;
+        g.beta = 1.0f;
+        SNO_TRY(ge::sno_gemm(g, B, s->split, st));
+        float *t = dv;
+        dv = dnext;
+        dnext = t;
+    }
+    // lift
+    return weight_grad(s, s->feat, 4, dv, C, R, Gd + s->off_w0, Gd + s->off_b0);
+}
+
+void release_sno(ge_sno *s)
+{
+    if (!s)
+        return;
+    for (void *p : s->allocs)
+        cudaFree(p);
+    delete s;
+}
+
+// splitmix64 + Box-Muller, for the initial weights
+struct Rng {
+    unsigned long long x;
+    double next()
+    {
+        unsigned long long z = (x += 0x9E3779B97F4A7C15ULL);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        z = z ^ (z >> 31);
+        return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    }
+    double uniform(double a) { return (2.0 * next() - 1.0) * a; }
+};
+
+}  // namespace
+
+extern "C" {
+
+ge_status ge_sno_create(ge_sno **out, int32_t n, int32_t width, int32_t modes, int32_t layers, int32_t hidden,
+                        int32_t max_batch, uint64_t seed, void *stream)
+{
+    if (!out)
+        return sfail(GE_EINVAL, "ge_sno_create: out is NULL");
+    *out = nullptr;
+    if (n < 4 || width < 1 || modes < 1 || 2 * modes > n || layers < 1 || hidden < 1 || max_batch < 1)
+        return sfail(GE_EINVAL, "ge_sno_create: need n >= 4, 1 <= modes <= n/2, width, layers, hidden, max_batch >= 1");
+    ge_sno *s = new (std::nothrow) ge_sno();
+    if (!s)
+        return sfail(GE_ENOMEM, "ge_sno_create: host allocation failed");
+    s->n = n;
+    s->C = width;
+    s->M = modes;
+    s->L = layers;
+    s->H = hidden;
+    s->max_batch = max_batch;
+    s->stream = static_cast<cudaStream_t>(stream);
+    const long long C = width, M = modes, H = hidden;
+    long long off = 0;
+    s->off_w0 = off;
+    off += 4 * C;
+    s->off_b0 = off;
+    off += C;
+    for (int l = 0; l < layers; ++l) {
+        LayerOff o;
+        o.rr = off;
+        off += M * C * C;
+        o.ri = off;
+        off += M * C * C;
+        o.w = off;
+        off += C * C;
+        o.b = off;
+        off += C;
+        s->lay.push_back(o);
+    }
+    s->off_q1 = off;
+    off += C * H;
+    s->off_qb1 = off;
+    off += H;
+    s->off_q2 = off;
+    off += H;
+    s->off_qb2 = off;
+    off += 1;
+    s->n_params = off;
+
+    const long long R = (long long)max_batch * n;
+    auto alloc = [&](float **p, long long count) -> cudaError_t {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), sizeof(float) * (count > 0 ? count : 1));
+        if (e == cudaSuccess)
+            s->allocs.push_back(*p);
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    e = e ? e : alloc(&s->params, off);
+    e = e ? e : alloc(&s->grads, off);
+    e = e ? e : alloc(&s->pw, off);
+    e = e ? e : alloc(&s->adam_m, off);
+    e = e ? e : alloc(&s->adam_v, off);
+    e = e ? e : alloc(&s->F, 2 * M * n);
+    e = e ? e : alloc(&s->G, 2 * M * n);
+    e = e ? e : alloc(&s->wspec, layers * M * 4 * C * C);
+    e = e ? e : alloc(&s->dwspec, M * 4 * C * C);
+    e = e ? e : alloc(&s->feat, R * 4);
+    s->v.assign(layers + 1, nullptr);
+    s->pre.assign(layers, nullptr);
+    s->vh.assign(layers, nullptr);
+    for (int l = 0; l <= layers && e == cudaSuccess; ++l)
+        e = alloc(&s->v[l], R * C);
+    for (int l = 0; l < layers && e == cudaSuccess; ++l)
+        e = alloc(&s->pre[l], R * C);
+    for (int l = 0; l < layers && e == cudaSuccess; ++l)
+        e = alloc(&s->vh[l], (long long)max_batch * 2 * M * C);
+    e = e ? e : alloc(&s->y, (long long)max_batch * 2 * M * C);
+    e = e ? e : alloc(&s->dvh, (long long)max_batch * 2 * M * C);
+    e = e ? e : alloc(&s->hpre, R * H);
+    e = e ? e : alloc(&s->h, R * H);
+    e = e ? e : alloc(&s->out, R);
+    e = e ? e : alloc(&s->dout, R);
+    e = e ? e : alloc(&s->loss, max_batch);
+    e = e ? e : alloc(&s->dA, R * (C > H ? C : H));
+    e = e ? e : alloc(&s->dB, R * (C > H ? C : H));
+    if (e != cudaSuccess) {
+        release_sno(s);
+        return scuda(e, "ge_sno_create: device allocation");
+    }
+    // DFT bases: F[2m][j] = cos(2 pi m j / n), F[2m+1][j] = -sin(...);
+    // G[j][2m] = w_m cos(...), G[j][2m+1] = -w_m sin(...), w_0 = 1/n, w_m = 2/n
+    std::vector<float> F(2 * M * n), Gm(2 * M * n);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (long long m = 0; m < M; ++m)
+        for (long long j = 0; j < n; ++j) {
+            const double th = two_pi * (double)((m * j) % n) / (double)n;
+            const double w = (m == 0 ? 1.0 : 2.0) / (double)n;
+            F[(2 * m) * n + j] = (float)std::cos(th);
+            F[(2 * m + 1) * n + j] = (float)(-std::sin(th));
+            Gm[j * 2 * M + 2 * m] = (float)(w * std::cos(th));
+            Gm[j * 2 * M + 2 * m + 1] = (float)(-w * std::sin(th));
+        }
+    // initial parameters (seeded)
+    std::vector<float> p((size_t)off, 0.0f);
+    Rng rng{seed * 0x2545F4914F6CDD1DULL + 12345};
+    for (long long i = 0; i < 4 * C; ++i)
+        p[s->off_w0 + i] = (float)rng.uniform(1.0 / std::sqrt(4.0));
+    for (int l = 0; l < layers; ++l) {
+        const double a = 1.0 / (double)(C * C);
+        for (long long i = 0; i < M * C * C; ++i) {
+            p[s->lay[l].rr + i] = (float)(a * rng.next());
+            p[s->lay[l].ri + i] = (float)(a * rng.next());
+        }
+        for (long long i = 0; i < C * C; ++i)
+            p[s->lay[l].w + i] = (float)rng.uniform(1.0 / std::sqrt((double)C));
+    }
+    for (long long i = 0; i < C * H; ++i)
+        p[s->off_q1 + i] = (float)rng.uniform(1.0 / std::sqrt((double)C));
+    for (long long i = 0; i < H; ++i)
+        p[s->off_q2 + i] = (float)rng.uniform(1.0 / std::sqrt((double)H));
+    e = cudaMemcpyAsync(s->F, F.data(), sizeof(float) * F.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->G, Gm.data(), sizeof(float) * Gm.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->params, p.data(), sizeof(float) * p.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(s->adam_m, 0, sizeof(float) * off, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(s->adam_v, 0, sizeof(float) * off, s->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+        release_sno(s);
+        return scuda(e, "ge_sno_create: initialisation");
+    }
+    *out = s;
+    return GE_OK;
+}
+
+ge_status ge_sno_num_params(const ge_sno *s, int64_t *count)
+{
+    if (!s || !count)
+        return sfail(GE_EINVAL, "ge_sno_num_params: NULL argument");
+    *count = s->n_params;
+    return GE_OK;
+}
+
+ge_status ge_sno_get_params(ge_sno *s, float *dst_dev)
+{
+    if (!s || !dst_dev)
+        return sfail(GE_EINVAL, "ge_sno_get_params: NULL argument");
+    cudaError_t e = cudaMemcpyAsync(dst_dev, s->params, sizeof(float) * s->n_params, cudaMemcpyDeviceToDevice, s->stream);
+    return e == cudaSuccess ? GE_OK : scuda(e, "ge_sno_get_params");
+}
+
+ge_status ge_sno_set_params(ge_sno *s, const float *src_dev)
+{
+    if (!s || !src_dev)
+        return sfail(GE_EINVAL, "ge_sno_set_params: NULL argument");
+    cudaError_t e = cudaMemcpyAsync(s->params, src_dev, sizeof(float) * s->n_params, cudaMemcpyDeviceToDevice, s->stream);
+    return e == cudaSuccess ? GE_OK : scuda(e, "ge_sno_set_params");
+}
+
+ge_status ge_sno_set_precision(ge_sno *s, int32_t split)
+{
+    if (!s || (split != 0 && split != 1))
+        return sfail(GE_EINVAL, "ge_sno_set_precision: NULL model or mode not 0/1");
+    s->split = split != 0;
+    return GE_OK;
+}
+
+ge_status ge_sno_forward(ge_sno *s, int32_t batch, const float *u0, const float *r, const float *bl, const float *br,
+                         float *pred)
+{
+    if (!s || !u0 || !r || !bl || !br || !pred || batch < 1 || batch > s->max_batch)
+        return sfail(GE_EINVAL, "ge_sno_forward: NULL argument or batch outside 1..max_batch");
+    ge_status st = forward(s, batch, u0, r, bl, br);
+    if (st != GE_OK)
+        return st;
+    cudaError_t e = cudaMemcpyAsync(pred, s->out, sizeof(float) * (size_t)batch * s->n, cudaMemcpyDeviceToDevice, s->stream);
+    return e == cudaSuccess ? GE_OK : scuda(e, "ge_sno_forward: copy out");
+}
+
+ge_status ge_sno_loss_grad(ge_sno *s, int32_t batch, const float *u0, const float *r, const float *bl,
+                           const float *br, const float *target, float *loss_dev, float *grads_dev)
+{
+    if (!s || !u0 || !r || !bl || !br || !target || batch < 1 || batch > s->max_batch)
+        return sfail(GE_EINVAL, "ge_sno_loss_grad: NULL argument or batch outside 1..max_batch");
+    ge_status st = forward(s, batch, u0, r, bl, br);
+    if (st != GE_OK)
+        return st;
+    cudaError_t e = ge::sno_rel_l2(s->out, target, s->dout, s->loss, s->n, batch, s->stream);
+    if (e != cudaSuccess)
+        return scuda(e, "ge_sno_loss_grad: loss");
+    st = backward(s, batch);
+    if (st != GE_OK)
+        return st;
+    if (loss_dev)
+        e = cudaMemcpyAsync(loss_dev, s->loss, sizeof(float) * batch, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess && grads_dev)
+        e = cudaMemcpyAsync(grads_dev, s->grads, sizeof(float) * s->n_params, cudaMemcpyDeviceToDevice, s->stream);
+    return e == cudaSuccess ? GE_OK : scuda(e, "ge_sno_loss_grad: copy out");
+}
+
+ge_status ge_sno_adam_step(ge_sno *s, float lr)
+{
+    if (!s || !(lr >= 0.0f))
+        return sfail(GE_EINVAL, "ge_sno_adam_step: NULL model or bad learning rate");
+    s->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.0f - (float)std::pow(b1, (double)s->adam_t), c2 = 1.0f - (float)std::pow(b2, (double)s->adam_t);
+    cudaError_t e = ge::sno_adam(s->params, s->grads, s->adam_m, s->adam_v, s->n_params, lr, b1, b2, 1e-8f, c1, c2,
+                                 s->stream);
+    return e == cudaSuccess ? GE_OK : scuda(e, "ge_sno_adam_step");
+}
+
+ge_status ge_sno_train_step(ge_sno *s, int32_t batch, const float *u0, const float *r, const float *bl,
+                            const float *br, const float *target, float lr, float *loss_dev)
+{
+    ge_status st = ge_sno_loss_grad(s, batch, u0, r, bl, br, target, loss_dev, nullptr);
+    return st == GE_OK ? ge_sno_adam_step(s, lr) : st;
+}
+
+void ge_sno_destroy(ge_sno *s)
+{
+    if (!s)
+        return;
+    cudaStreamSynchronize(s->stream);
+    release_sno(s);
+}
+
+}  // extern "C"

@@ -95,3 +95,35 @@ def uneven_batch(n_problems: int = 4096, n_min: int = 256, n_max: int = 65536,
     for b in range(n_problems):
         u0[offsets[b]:offsets[b] + n[b]] = fourier_state(int(n[b]), bl[b], br[b], rng)
     return Batch(n=n, r=r, beta_l=bl, beta_r=br, offsets=offsets, u0=u0, total=total)
+
+
+@dataclass
+class SurrogateProblems:
+    """Equal-size problems for the learned surrogate: ``u0`` is [P, n]."""
+    u0: np.ndarray
+    r: np.ndarray
+    beta_l: np.ndarray
+    beta_r: np.ndarray
+
+
+def surrogate_problems(n_problems: int, n: int = 1024, seed: int = SEED_BASE + 4, r_min: float = 0.5,
+                       r_max: float = 4.0, n_modes: int = 16, n_tents: int = 2) -> SurrogateProblems:
+    """P problems on n points: r ~ U[r_min, r_max], walls ~ U(-1, 1), u0 = the
+    linear profile between the walls + sum_{k<=n_modes} a_k / k^2 sin(k pi x)
+    (a_k ~ N(0, 1)) + `n_tents` piecewise-linear tents c (1 - |x - x_c| / w)_+
+    with x_c ~ U(0.1, 0.9), w ~ U(0.02, 0.2), c ~ N(0, 0.5^2)."""
+    rng = np.random.default_rng(seed)
+    x = grid(n)
+    r = rng.uniform(r_min, r_max, n_problems)
+    bl = rng.uniform(-1.0, 1.0, n_problems)
+    br = rng.uniform(-1.0, 1.0, n_problems)
+    k = np.arange(1, n_modes + 1, dtype=np.float64)
+    basis = np.sin(np.pi * k[:, None] * x[None, :]) / (k * k)[:, None]
+    u0 = rng.standard_normal((n_problems, n_modes)) @ basis
+    u0 += bl[:, None] + (br - bl)[:, None] * x[None, :]
+    for _ in range(n_tents):
+        xc = rng.uniform(0.1, 0.9, n_problems)[:, None]
+        w = rng.uniform(0.02, 0.2, n_problems)[:, None]
+        c = rng.normal(0.0, 0.5, n_problems)[:, None]
+        u0 += c * np.maximum(0.0, 1.0 - np.abs(x[None, :] - xc) / w)
+    return SurrogateProblems(u0=u0, r=r, beta_l=bl, beta_r=br)

@@ -106,3 +106,30 @@ def test_batch_layout_checks(lib):
     assert create([10], [0], 64, r=[-1.0]) == B.GE_EINVAL   # bad r
     assert lib.ge_batch_run(None, None, 1) == B.GE_EINVAL
     lib.ge_batch_destroy(None)
+
+
+@pytest.mark.parametrize("n,width,modes,layers,hidden,max_batch", [
+    (2, 8, 1, 1, 1, 1),      # n < 4
+    (64, 8, 33, 1, 1, 1),    # modes > n / 2
+    (64, 8, 0, 1, 1, 1),
+    (64, 0, 4, 1, 1, 1),
+    (64, 8, 4, 0, 1, 1),
+    (64, 8, 4, 1, 0, 1),
+    (64, 8, 4, 1, 1, 0),
+])
+def test_sno_create_rejects_bad_sizes(lib, n, width, modes, layers, hidden, max_batch):
+    h = ctypes.c_void_p()
+    st = lib.ge_sno_create(ctypes.byref(h), n, width, modes, layers, hidden, max_batch, 0, None)
+    assert st == B.GE_EINVAL and h.value is None
+    assert "ge_sno_create" in B.ge_last_error()
+
+
+def test_sno_calls_on_null_model(lib):
+    cnt = ctypes.c_int64(-1)
+    assert lib.ge_sno_num_params(None, ctypes.byref(cnt)) == B.GE_EINVAL
+    assert lib.ge_sno_set_precision(None, 0) == B.GE_EINVAL
+    assert lib.ge_sno_forward(None, 1, 1, 1, 1, 1, 1) == B.GE_EINVAL
+    assert lib.ge_sno_loss_grad(None, 1, 1, 1, 1, 1, 1, None, None) == B.GE_EINVAL
+    assert lib.ge_sno_adam_step(None, 1e-3) == B.GE_EINVAL
+    assert lib.ge_sno_train_step(None, 1, 1, 1, 1, 1, 1, 1e-3, None) == B.GE_EINVAL
+    lib.ge_sno_destroy(None)

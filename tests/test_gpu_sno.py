@@ -1,0 +1,205 @@
+"""The surrogate's CUDA forward and backward passes against the FP64 CPU
+reference (oracle/sno.py), training on GE data, and the GE fallback.
+
+Tolerances: split mode (two-part BF16 operands) is accurate to about FP32, so
+the prediction must match to 1e-4 relative L2 per problem and every
+parameter block's gradient to 2e-3 relative L2; plain BF16 operands (unit
+roundoff 2^-8 per operand) to 3e-2."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sno as S
+from paper_1310_3422_gb300 import binding as B
+from paper_1310_3422_gb300 import inputs
+from paper_1310_3422_gb300 import surrogate as SG
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+SMALL = S.Arch(n=64, width=16, modes=8, layers=2, hidden=32)
+FULL = S.Arch(n=1024, width=64, modes=16, layers=4, hidden=128)
+
+
+def make_model(a: S.Arch, max_batch: int, seed: int = 1, split: int = 1):
+    m = B.ge_sno_create(a.n, a.width, a.modes, a.layers, a.hidden, max_batch, seed)
+    B.ge_sno_set_precision(m, split)
+    return m
+
+
+def get_params(m) -> np.ndarray:
+    p = torch.empty(B.ge_sno_num_params(m), dtype=torch.float32, device=DEV)
+    B.ge_sno_get_params(m, p)
+    torch.cuda.synchronize()
+    return p.cpu().numpy()
+
+
+def problem_batch(a: S.Arch, batch: int, seed: int):
+    pr = inputs.surrogate_problems(batch, a.n, seed=seed)
+    return pr.u0.astype(np.float32), pr.r.astype(np.float32), pr.beta_l.astype(np.float32), \
+        pr.beta_r.astype(np.float32)
+
+
+def dev(*arrs):
+    return [torch.tensor(np.ascontiguousarray(x), device=DEV) for x in arrs]
+
+
+def rel_rows(got, want):
+    return np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+
+
+def oracle_params(m) -> np.ndarray:
+    return S.round_bf16(torch.tensor(get_params(m))).numpy()
+
+
+def test_num_params_matches_layout():
+    for a in (SMALL, FULL):
+        m = make_model(a, 2)
+        assert B.ge_sno_num_params(m) == S.num_params(a)
+        B.ge_sno_destroy(m)
+
+
+@pytest.mark.parametrize("a,batch", [(SMALL, 5), (FULL, 3)])
+@pytest.mark.parametrize("split,tol", [(1, 1e-4), (0, 3e-2)])
+def test_forward_parity(a, batch, split, tol):
+    m = make_model(a, 8, split=split)
+    u0, r, bl, br = problem_batch(a, batch, 11)
+    pred = torch.empty(batch, a.n, dtype=torch.float32, device=DEV)
+    B.ge_sno_forward(m, batch, *dev(u0, r, bl, br), pred)
+    torch.cuda.synchronize()
+    want = S.predict(oracle_params(m), a, u0, r, bl, br)
+    err = rel_rows(pred.cpu().numpy().astype(np.float64), want)
+    assert np.all(err <= tol), err
+    B.ge_sno_destroy(m)
+
+
+def blocks(a: S.Arch, g: np.ndarray) -> dict:
+    return {k: v.numpy() for k, v in S.unpack(torch.tensor(g), a).items()}
+
+
+@pytest.mark.parametrize("a,batch", [(SMALL, 4), (FULL, 2)])
+def test_gradient_parity(a, batch):
+    m = make_model(a, 8, split=1)
+    u0, r, bl, br = problem_batch(a, batch, 12)
+    target = (u0 + 0.1 * np.random.default_rng(13).standard_normal(u0.shape)).astype(np.float32)
+    loss = torch.empty(batch, dtype=torch.float32, device=DEV)
+    grads = torch.empty(B.ge_sno_num_params(m), dtype=torch.float32, device=DEV)
+    B.ge_sno_loss_grad(m, batch, *dev(u0, r, bl, br, target), loss, grads)
+    torch.cuda.synchronize()
+    want_loss, want_grad = S.loss_and_grad(oracle_params(m), a, u0, r, bl, br, target)
+    np.testing.assert_allclose(loss.cpu().numpy(), want_loss, rtol=1e-4)
+    got = blocks(a, grads.cpu().numpy().astype(np.float64))
+    ref = blocks(a, want_grad)
+    for k in ref:
+        den = max(np.linalg.norm(ref[k]), 1e-12)
+        assert np.linalg.norm(got[k] - ref[k]) <= 2e-3 * den, (k, np.linalg.norm(got[k] - ref[k]) / den)
+    B.ge_sno_destroy(m)
+
+
+def test_adam_step_matches_reference_update():
+    a = SMALL
+    m = make_model(a, 4, split=1)
+    u0, r, bl, br = problem_batch(a, 3, 14)
+    target = np.roll(u0, 3, axis=1).astype(np.float32)
+    p0 = get_params(m).astype(np.float64)
+    B.ge_sno_loss_grad(m, 3, *dev(u0, r, bl, br, target), None, None)
+    B.ge_sno_adam_step(m, 1e-3)
+    torch.cuda.synchronize()
+    p1 = get_params(m).astype(np.float64)
+    _, g = S.loss_and_grad(S.round_bf16(torch.tensor(p0)).numpy(), a, u0, r, bl, br, target)
+    # first bias-corrected Adam step: p - lr * g / (|g| + eps) (elementwise sign step)
+    want = p0 - 1e-3 * g / (np.abs(g) + 1e-8)
+    big = np.abs(g) > 1e-4 * np.abs(g).max()
+    np.testing.assert_allclose(p1[big], want[big], rtol=0, atol=2e-6)
+
+
+def test_invalid_arguments_are_rejected():
+    m = make_model(SMALL, 4)
+    x = torch.zeros(5 * SMALL.n, dtype=torch.float32, device=DEV)
+    v = torch.zeros(5, dtype=torch.float32, device=DEV)
+    with pytest.raises(B.GeError):
+        B.ge_sno_forward(m, 5, x, v, v, v, x)     # batch > max_batch
+    with pytest.raises(B.GeError):
+        B.ge_sno_set_precision(m, 2)
+    with pytest.raises(B.GeError):
+        B.ge_sno_adam_step(m, float("nan"))
+    B.ge_sno_destroy(m)
+
+
+@pytest.fixture(scope="module")
+def trained():
+    """The full-size surrogate trained briefly on GE trajectories (K = 256)."""
+    data = SG.make_training_set(1024, K=256, jumps=8, seed=inputs.SEED_BASE + 40)
+    held = SG.make_training_set(64, K=256, jumps=8, seed=inputs.SEED_BASE + 41)
+    sur = SG.Surrogate(max_batch=64, seed=3)
+    untrained = sur.evaluate(held)
+    losses = sur.train(data, steps=600, batch=32, lr=2e-3, warmup=50)
+    yield sur, data, held, untrained, losses
+    sur.close()
+
+
+def test_training_reduces_the_loss(trained):
+    sur, data, held, untrained, losses = trained
+    assert np.all(np.isfinite(losses))
+    assert losses[-50:].mean() < 0.2 * losses[:20].mean()
+
+
+def test_trained_network_gains_over_the_baselines(trained):
+    """What training buys: one jump of the trained network is far closer to
+    GE than the same network untrained and than the do-nothing prediction
+    u_K = u_0, on trajectories it has not seen."""
+    sur, data, held, untrained, _ = trained
+    err = sur.evaluate(held)
+    ident = (torch.linalg.vector_norm(held.x - held.y, dim=1) / torch.linalg.vector_norm(held.y, dim=1)).cpu().numpy()
+    assert np.median(err) < 0.1 * np.median(untrained)
+    assert np.median(err) < 0.5 * np.median(ident)
+
+
+def ge_reference(u0, r, bl, br, steps, prec=B.GE_F32):
+    ref = u0.to(torch.float64 if prec == B.GE_F64 else torch.float32).clone()
+    ge = SG.GEBatch(r.double().cpu().numpy(), bl.double().cpu().numpy(), br.double().cpu().numpy(),
+                    u0.shape[1], prec)
+    ge.run(ref, steps)
+    torch.cuda.synchronize()
+    ge.close()
+    return ref.float()
+
+
+def test_fallback_takes_over_when_the_sample_misses(trained):
+    """A tolerance no network meets: every problem ends up with GE's answer."""
+    sur = trained[0]
+    pr = inputs.surrogate_problems(300, 1024, seed=inputs.SEED_BASE + 42)
+    u0, r, bl, br = dev(pr.u0.astype(np.float32), *(x.astype(np.float32) for x in (pr.r, pr.beta_l, pr.beta_r)))
+    out, rep = SG.solve_with_fallback(sur, u0, r, bl, br, jumps=2, tol=1e-9, sample_frac=0.05)
+    assert rep.fell_back_all and rep.n_sample_over_tol > 0
+    assert torch.equal(out, ge_reference(u0, r, bl, br, 2 * 256))
+
+
+def test_fallback_replaces_flagged_and_sampled_rows(trained):
+    sur = trained[0]
+    pr = inputs.surrogate_problems(200, 1024, seed=inputs.SEED_BASE + 43)
+    r_np = pr.r.astype(np.float32)
+    r_np[[5, 77]] = 6.0                           # outside the trained range: flagged
+    u0, r, bl, br = dev(pr.u0.astype(np.float32), r_np, pr.beta_l.astype(np.float32), pr.beta_r.astype(np.float32))
+    out, rep = SG.solve_with_fallback(sur, u0, r, bl, br, jumps=1, tol=1e9, sample_frac=0.02)
+    assert not rep.fell_back_all and rep.n_flagged == 2
+    ref = ge_reference(u0, r, bl, br, 256)
+    rows = np.union1d(rep.sample, [5, 77])
+    assert torch.equal(out[rows], ref[rows])
+    surrogate_only = sur.predict(u0, r, bl, br)
+    others = np.setdiff1d(np.arange(200), rows)
+    assert torch.equal(out[others], surrogate_only[others])
+
+
+def test_non_finite_predictions_are_flagged():
+    a = SG.SnoArch()
+    sur = SG.Surrogate(a, max_batch=16, seed=5)
+    p = sur.params()
+    p[:] = float("nan")
+    sur.set_params(p)
+    pr = inputs.surrogate_problems(40, a.n, seed=inputs.SEED_BASE + 44)
+    u0, r, bl, br = dev(pr.u0.astype(np.float32), *(x.astype(np.float32) for x in (pr.r, pr.beta_l, pr.beta_r)))
+    out, rep = SG.solve_with_fallback(sur, u0, r, bl, br, jumps=1, tol=1e-3)
+    assert rep.n_flagged == 40 and not rep.fell_back_all
+    assert torch.equal(out, ge_reference(u0, r, bl, br, 256))
+    sur.close()
