@@ -123,7 +123,10 @@ ge_status weight_grad(ge_sno *s, const float *X, int in, const float *dY, int ou
     return GE_OK;
 }
 
-ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float *bl, const float *br)
+// Forward pass for B problems into out ([B n]).  keep: also store the
+// pre-activations the backward pass needs (training).
+ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float *bl, const float *br, float *out,
+                  bool keep)
 {
     const int n = s->n, C = s->C, M = s->M, H = s->H;
     const long long R = (long long)B * n;
@@ -151,30 +154,36 @@ ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float
         g.sB = 4LL * C * C;
         g.sC = 2 * C;
         SNO_TRY(ge::sno_gemm(g, M, s->split, st));
-        // back to the grid: pre[b] = G [n x 2M] * y[b] [2M x C]
-        g = gemm(s->G, 2 * M, 1, s->y, C, 1, s->pre[l], C, n, C, 2 * M);
+        // back to the grid and the pointwise path in one pass:
+        // pre[b] = G [n x 2M] y[b] [2M x C] + v[b] W + b, next v = GELU(pre)
+        // (the last layer has no activation: next v = pre)
+        const bool last = l == s->L - 1;
+        g = gemm(s->G, 2 * M, 1, s->y, C, 1, last ? s->v[l + 1] : (keep ? s->pre[l] : nullptr), C, n, C, 2 * M);
         g.sA = 0;
         g.sB = 2LL * M * C;
         g.sC = (long long)n * C;
-        SNO_TRY(ge::sno_gemm(g, B, s->split, st));
-        // pointwise path: pre += v W + b
-        g = gemm(s->v[l], C, 1, P + o.w, C, 1, s->pre[l], C, (int)R, C, C);
-        g.C0 = s->pre[l];
-        g.beta = 1.0f;
+        g.A2 = s->v[l];
+        g.lda2_i = C;
+        g.lda2_k = 1;
+        g.sA2 = (long long)n * C;
+        g.B2 = P + o.w;
+        g.ldb2_k = C;
+        g.ldb2_j = 1;
+        g.K2 = C;
         g.bias = P + o.b;
-        SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
-        if (l < s->L - 1)
-            SNO_TRY(ge::sno_gelu_fwd(s->pre[l], s->v[l + 1], R * C, st));
-        else
-            SNO_TRY(cudaMemcpyAsync(s->v[l + 1], s->pre[l], sizeof(float) * R * C, cudaMemcpyDeviceToDevice, st));
+        if (!last) {
+            g.act = s->v[l + 1];
+            g.sAct = (long long)n * C;
+        }
+        SNO_TRY(ge::sno_gemm(g, B, s->split, st));
     }
     // projection
-    g = gemm(s->v[s->L], C, 1, P + s->off_q1, H, 1, s->hpre, H, (int)R, H, C);
+    g = gemm(s->v[s->L], C, 1, P + s->off_q1, H, 1, keep ? s->hpre : nullptr, H, (int)R, H, C);
     g.bias = P + s->off_qb1;
+    g.act = s->h;
     SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
-    SNO_TRY(ge::sno_gelu_fwd(s->hpre, s->h, R * H, st));
     // residual output: the network predicts the change of u over the jump
-    g = gemm(s->h, H, 1, P + s->off_q2, 1, 1, s->out, 1, (int)R, 1, H);
+    g = gemm(s->h, H, 1, P + s->off_q2, 1, 1, out, 1, (int)R, 1, H);
     g.bias = P + s->off_qb2;
     g.C0 = u0;
     g.beta = 1.0f;
@@ -194,25 +203,25 @@ ge_status backward(ge_sno *s, int B)
     // projection: out = h Q2 + q2
     if ((rc = weight_grad(s, s->h, H, s->dout, 1, R, Gd + s->off_q2, Gd + s->off_qb2)) != GE_OK)
         return rc;
-    ge::GemmArgs g = gemm(s->dout, 1, 1, P + s->off_q2, 1, 1, s->dA, H, (int)R, H, 1);  // dh = dout Q2^T
+    // dhpre = (dout Q2^T) * GELU'(hpre)
+    ge::GemmArgs g = gemm(s->dout, 1, 1, P + s->off_q2, 1, 1, s->dA, H, (int)R, H, 1);
+    g.dgelu_pre = s->hpre;
     SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
-    SNO_TRY(ge::sno_gelu_bwd(s->hpre, s->dA, s->dA, R * H, st));
     if ((rc = weight_grad(s, s->v[s->L], C, s->dA, H, R, Gd + s->off_q1, Gd + s->off_qb1)) != GE_OK)
         return rc;
     g = gemm(s->dA, H, 1, P + s->off_q1, 1, H, s->dB, C, (int)R, C, H);  // dv_L = dhpre Q1^T
     SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
+    // dv holds the gradient of the current layer's pre-activation: the last
+    // layer has no activation, and every lower one's GELU' is applied in the
+    // epilogue of the GEMM that makes its gradient.
     float *dv = s->dB, *dnext = s->dA;
     for (int l = s->L - 1; l >= 0; --l) {
         const LayerOff &o = s->lay[l];
         const float *ws = s->wspec + (long long)l * M * 4 * C * C;
-        float *dpre = dv;  // in place
-        if (l < s->L - 1)
-            SNO_TRY(ge::sno_gelu_bwd(s->pre[l], dv, dpre, R * C, st));
-        // pointwise path
+        const float *dpre = dv;
+        // pointwise path weights
         if ((rc = weight_grad(s, s->v[l], C, dpre, C, R, Gd + o.w, Gd + o.b)) != GE_OK)
             return rc;
-        g = gemm(dpre, C, 1, P + o.w, 1, C, dnext, C, (int)R, C, C);  // dv_l = dpre W^T
-        SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
         // spectral path: dy[b] = G^T dpre[b]
         g = gemm(s->G, 1, 2 * M, dpre, C, 1, s->y, C, 2 * M, C, n);
         g.sA = 0;
@@ -232,14 +241,25 @@ ge_status backward(ge_sno *s, int B)
         g.sB = 4LL * C * C;
         g.sC = 2 * C;
         SNO_TRY(ge::sno_gemm(g, M, s->split, st));
-        // dv_l += F^T dvh[b]
-        g = gemm(s->F, 1, n, s->dvh, C, 1, dnext, C, n, C, 2 * M);
-        g.sA = 0;
-        g.sB = 2LL * M * C;
+        // gradient of v_l, both paths in one pass: dpre[b] W^T + F^T dvh[b],
+        // times GELU'(pre_{l-1}) when v_l is an activation
+        g = gemm(dpre, C, 1, P + o.w, 1, C, dnext, C, n, C, C);
+        g.sA = (long long)n * C;
+        g.sB = 0;
         g.sC = (long long)n * C;
-        g.C0 = dnext;
-        g.sC0 = (long long)n * C;
-        g.beta = 1.0f;
+        g.A2 = s->F;
+        g.lda2_i = 1;
+        g.lda2_k = n;
+        g.sA2 = 0;
+        g.B2 = s->dvh;
+        g.ldb2_k = C;
+        g.ldb2_j = 1;
+        g.sB2 = 2LL * M * C;
+        g.K2 = 2 * M;
+        if (l > 0) {
+            g.dgelu_pre = s->pre[l - 1];
+            g.sDg = (long long)n * C;
+        }
         SNO_TRY(ge::sno_gemm(g, B, s->split, st));
         float *t = dv;
         dv = dnext;
@@ -449,11 +469,7 @@ ge_status ge_sno_forward(ge_sno *s, int32_t batch, const float *u0, const float 
 {
     if (!s || !u0 || !r || !bl || !br || !pred || batch < 1 || batch > s->max_batch)
         return sfail(GE_EINVAL, "ge_sno_forward: NULL argument or batch outside 1..max_batch");
-    ge_status st = forward(s, batch, u0, r, bl, br);
-    if (st != GE_OK)
-        return st;
-    cudaError_t e = cudaMemcpyAsync(pred, s->out, sizeof(float) * (size_t)batch * s->n, cudaMemcpyDeviceToDevice, s->stream);
-    return e == cudaSuccess ? GE_OK : scuda(e, "ge_sno_forward: copy out");
+    return forward(s, batch, u0, r, bl, br, pred, false);
 }
 
 ge_status ge_sno_loss_grad(ge_sno *s, int32_t batch, const float *u0, const float *r, const float *bl,
@@ -461,7 +477,7 @@ ge_status ge_sno_loss_grad(ge_sno *s, int32_t batch, const float *u0, const floa
 {
     if (!s || !u0 || !r || !bl || !br || !target || batch < 1 || batch > s->max_batch)
         return sfail(GE_EINVAL, "ge_sno_loss_grad: NULL argument or batch outside 1..max_batch");
-    ge_status st = forward(s, batch, u0, r, bl, br);
+    ge_status st = forward(s, batch, u0, r, bl, br, s->out, true);
     if (st != GE_OK)
         return st;
     cudaError_t e = ge::sno_rel_l2(s->out, target, s->dout, s->loss, s->n, batch, s->stream);
