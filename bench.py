@@ -374,6 +374,32 @@ def measure_surrogate(B, torch, inputs, train_steps):
     }
 
 
+def measure_sno_forward(torch, inputs, steps, warmup, problems=4096):
+    """Forward passes of the surrogate (untrained, BF16 mode) over `problems`
+    problems of N = 1024 in chunks of 1024: time per problem and tensor
+    throughput.  For profiling the network's kernels alone."""
+    from paper_1310_3422_gb300 import surrogate as SG
+    pr = inputs.surrogate_problems(problems, SNO_N, seed=inputs.SEED_BASE + 6)
+    u0 = torch.tensor(pr.u0, dtype=torch.float32, device="cuda")
+    r, bl, br = (torch.tensor(x, dtype=torch.float32, device="cuda") for x in (pr.r, pr.beta_l, pr.beta_r))
+    sur = SG.Surrogate(max_batch=1024, seed=0)
+    out = torch.empty_like(u0)
+    for _ in range(warmup):
+        sur.predict(u0, r, bl, br, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        sur.predict(u0, r, bl, br, out=out)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    sur.close()
+    return {"problems": problems, "ms_per_forward_pass": ms, "us_per_problem": ms * 1e3 / problems,
+            "tflops": 2 * problems * sno_flops_per_problem() / (ms / 1e3) / 1e12,
+            "launches": -(-problems // 1024) * sno_launches_per_forward()}
+
+
 def sno_flops_per_problem(n=SNO_N, C=64, M=16, L=4, H=128):
     """Multiply-adds of one forward pass for one problem (x2 for FLOPs)."""
     per_layer = 2 * (2 * M * n * C) + M * (2 * C) * (2 * C) + n * C * C
@@ -381,7 +407,7 @@ def sno_flops_per_problem(n=SNO_N, C=64, M=16, L=4, H=128):
 
 
 def sno_launches_per_forward(L=4):
-    return 3 + 6 * L + 3 + 1
+    return 3 + 4 * L + 2
 
 
 def launches_per_solve(kernel, depth):
@@ -407,6 +433,10 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--only-surrogate", action="store_true", help="run only the surrogate workload")
     ap.add_argument("--sno-train-steps", type=int, default=3000)
+    ap.add_argument("--sno-forward-only", action="store_true",
+                    help="time only surrogate forward passes (untrained weights; profiling)")
+    ap.add_argument("--subdomain", type=int, default=1,
+                    help="sub-domain width k of the main solve (k > 1 needs --kernel canonical)")
     ap.add_argument("--only-batched", default=None, choices=["f32", "f32c", "f64"],
                     help="run only the batched workload in this precision (profiling)")
     args = ap.parse_args()
@@ -432,6 +462,10 @@ def main():
     if args.only_surrogate:
         print(json.dumps({"surrogate": measure_surrogate(B, torch, inputs, args.sno_train_steps)}), flush=True)
         return 0
+    if args.sno_forward_only:
+        print(json.dumps({"surrogate_forward": measure_sno_forward(torch, inputs, args.steps, args.warmup)}),
+              flush=True)
+        return 0
     prec = {"f64": B.GE_F64, "f32": B.GE_F32, "f32c": B.GE_F32_COMP}[args.precision]
     kern = {"temporal": B.GE_KERNEL_TEMPORAL, "onestep": B.GE_KERNEL_ONESTEP,
             "canonical": B.GE_KERNEL_CANONICAL}[args.kernel]
@@ -445,6 +479,8 @@ def main():
     with torch.cuda.stream(stream):
         ctx = B.ge_create(N_POINTS, R, 0.0, 0.0, prec, u0_dev, stream=stream)
         B.ge_set_kernel(ctx, kern, depth)
+        if args.subdomain > 1:
+            B.ge_set_subdomain_width(ctx, args.subdomain)
 
         # ---- timed region: K full solves --------------------------------
         for _ in range(args.warmup):

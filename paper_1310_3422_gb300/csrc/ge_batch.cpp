@@ -94,6 +94,9 @@ ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int *result_buf)
     const int pidx = prec_index(b->prec);
     int cur = 0;
     int64_t n0 = 0;
+    const int dmax = ge::tbb_max_depth(pidx);
+    if (depth > dmax)
+        depth = dmax;
     while (n0 < steps) {
         const int64_t L = (steps - n0 < depth) ? steps - n0 : depth;
         ge::TbbParams p{};

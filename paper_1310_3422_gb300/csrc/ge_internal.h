@@ -109,6 +109,9 @@ cudaError_t launch_tb(int prec, const void *tmap, const TbParams &p, int grid, c
 cudaError_t launch_tbb(int prec, const void *tmap, const TbbParams &p, int grid, cudaStream_t s);
 cudaError_t tbb_occupancy(int prec, int *blocks_per_sm);
 bool tbb_geometry(int prec, int reach, int *H, int *U);
+// Largest steps per launch whose reach (steps + 2 stages) fits the batched
+// kernel's tile for this precision.
+int tbb_max_depth(int prec);
 // Largest co-resident CTAs per SM for the tiled kernel of this precision.
 cudaError_t tb_occupancy(int prec, int *blocks_per_sm);
 int tb_smem_bytes();

@@ -38,8 +38,10 @@ struct GemmArgs {
     long long sDg;
     float *act;
     long long sAct;
-    // set by sno_gemm: float4 staging allowed for A, B, A2, B2
+    // set by sno_gemm: float4 staging allowed for A, B, A2, B2; float2
+    // epilogue accesses allowed
     int vec[4];
+    int pairs;
 };
 
 cudaError_t sno_gemm(const GemmArgs &g, int batch, bool split, cudaStream_t s);

@@ -27,18 +27,33 @@ namespace {
 constexpr int BM = 64, BN = 64, BK = 32, PADK = BK + 8;  // bf16 elements per smem row
 constexpr int NT = 128;                                  // threads per GEMM CTA
 
-__device__ __forceinline__ float gelu(float x)
+// tanh: the library function (EXACT, split mode) or the hardware
+// approximation (tanh.approx.f32, relative error about 2^-11, below the
+// 2^-8 of the BF16 operands it feeds in the plain mode).
+template <bool EXACT>
+__device__ __forceinline__ float tanh_sel(float x)
 {
-    // tanh form of GELU
-    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-    return 0.5f * x * (1.0f + tanhf(k0 * (x + k1 * x * x * x)));
+    if (EXACT)
+        return tanhf(x);
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
 
+// tanh form of GELU and its derivative
+template <bool EXACT>
+__device__ __forceinline__ float gelu(float x)
+{
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    return 0.5f * x * (1.0f + tanh_sel<EXACT>(k0 * (x + k1 * x * x * x)));
+}
+
+template <bool EXACT>
 __device__ __forceinline__ float gelu_grad(float x)
 {
     const float k0 = 0.7978845608028654f, k1 = 0.044715f;
     const float u = k0 * (x + k1 * x * x * x);
-    const float th = tanhf(u);
+    const float th = tanh_sel<EXACT>(u);
     const float du = k0 * (1.0f + 3.0f * k1 * x * x);
     return 0.5f * (1.0f + th) + 0.5f * x * (1.0f - th * th) * du;
 }
@@ -59,75 +74,210 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+// Shared-memory tile of one operand: 64 rows x BK k-values in BF16, stored
+// k-contiguous ([row][PADK]) when the operand is k-contiguous in global
+// memory and row-contiguous ([k][PADT]) otherwise.  Both are written with
+// packed 8-byte stores and read with ldmatrix (.trans for the second); the
+// row pitches (80 and 144 bytes) keep ldmatrix free of bank conflicts.
+constexpr int PADT = BM + 8;
+constexpr int TILE = BM * PADK;
+static_assert(BK * PADT <= TILE, "both tile layouts fit one buffer");
+
+__device__ __forceinline__ int at_k(int r, int k) { return r * PADK + k; }
+__device__ __forceinline__ int at_r(int r, int k) { return k * PADT + r; }
+
 template <bool SPLIT>
-__device__ __forceinline__ void put(__nv_bfloat16 (*S)[BM][PADK], int r, int kk, float x)
+__device__ __forceinline__ void put1(__nv_bfloat16 (*S)[TILE], int idx, float x)
 {
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    S[0][r][kk] = h;
+    S[0][idx] = h;
     if (SPLIT)
-        S[SPLIT ? 1 : 0][r][kk] = __float2bfloat16_rn(x - __bfloat162float(h));
+        S[SPLIT ? 1 : 0][idx] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
-// Stage the 64 x BK tile of an operand whose element (row, k) is
-// X[row * s_r + k * s_k] (rows r0.., rows < rmax and k0.. < kend are read,
-// the rest is zero) as S[.][row - r0][k - k0].  The element order follows
-// the unit-stride dimension so a warp's loads coalesce; `vec` (checked by
-// the launcher: that dimension's extent, the other stride and the base all
-// multiples of 4 floats / 16 bytes) loads four elements at once.
+// Four values that are adjacent in the tile's contiguous dimension (idx a
+// multiple of 4): two packed BF16 pairs, one 8-byte store per part.
 template <bool SPLIT>
-__device__ __forceinline__ void stage(__nv_bfloat16 (*S)[BM][PADK], const float *__restrict__ X, long long s_r,
-                                      long long s_k, int r0, int rmax, int k0, int kend, bool vec, int t)
+__device__ __forceinline__ void put4(__nv_bfloat16 (*S)[TILE], int idx, float a, float b, float c, float d)
+{
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b), h1 = __floats2bfloat162_rn(c, d);
+    uint2 w;
+    w.x = *reinterpret_cast<const uint32_t *>(&h0);
+    w.y = *reinterpret_cast<const uint32_t *>(&h1);
+    *reinterpret_cast<uint2 *>(&S[0][idx]) = w;
+    if (SPLIT) {
+        const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+        const __nv_bfloat162 l0 = __floats2bfloat162_rn(a - f0.x, b - f0.y);
+        const __nv_bfloat162 l1 = __floats2bfloat162_rn(c - f1.x, d - f1.y);
+        w.x = *reinterpret_cast<const uint32_t *>(&l0);
+        w.y = *reinterpret_cast<const uint32_t *>(&l1);
+        *reinterpret_cast<uint2 *>(&S[SPLIT ? 1 : 0][idx]) = w;
+    }
+}
+
+// Tiles of an operand whose element (row, k) is X[row * s_r + k * s_k]:
+// rows r0.. (< rmax) and k0.. (< kend) are read, the rest is zero.  Each
+// thread holds 16 values between the global load (`load`) and the
+// shared-memory store (`store`), so the next tile's loads are in flight
+// while the current one is multiplied.  The element order follows the
+// unit-stride dimension so a warp's loads coalesce; VEC (checked by the
+// launcher: that dimension's extent, the other stride and the base all
+// multiples of 4 floats / 16 bytes) loads four elements at once.
+constexpr int PER_T = BM * BK / NT;  // 16 values per thread and tile
+
+template <bool VEC>
+__device__ __forceinline__ void load(float (&x)[PER_T], const float *__restrict__ X, long long s_r, long long s_k,
+                                     int r0, int rmax, int k0, int kend, int t)
 {
     if (s_k == 1) {
-        if (vec) {
-            for (int e = t; e < BM * BK / 4; e += NT) {
-                const int r = e / (BK / 4), kk = (e % (BK / 4)) * 4;
-                const int row = r0 + r, k = k0 + kk;
-                float4 x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (VEC) {
+#pragma unroll
+            for (int q = 0; q < PER_T / 4; ++q) {
+                const int e = t + q * NT;
+                const int row = r0 + e / (BK / 4), k = k0 + (e % (BK / 4)) * 4;
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (row < rmax && k < kend)
-                    x = __ldg(reinterpret_cast<const float4 *>(X + (long long)row * s_r + k));
-                put<SPLIT>(S, r, kk, x.x);
-                put<SPLIT>(S, r, kk + 1, x.y);
-                put<SPLIT>(S, r, kk + 2, x.z);
-                put<SPLIT>(S, r, kk + 3, x.w);
+                    v = __ldg(reinterpret_cast<const float4 *>(X + (long long)row * s_r + k));
+                x[4 * q] = v.x, x[4 * q + 1] = v.y, x[4 * q + 2] = v.z, x[4 * q + 3] = v.w;
             }
         } else {
-            for (int e = t; e < BM * BK; e += NT) {
-                const int r = e / BK, kk = e % BK;
-                const int row = r0 + r, k = k0 + kk;
-                put<SPLIT>(S, r, kk, (row < rmax && k < kend) ? __ldg(X + (long long)row * s_r + k) : 0.0f);
+#pragma unroll
+            for (int q = 0; q < PER_T; ++q) {
+                const int e = t + q * NT;
+                const int row = r0 + e / BK, k = k0 + e % BK;
+                x[q] = (row < rmax && k < kend) ? __ldg(X + (long long)row * s_r + k) : 0.0f;
             }
         }
     } else {
-        if (vec) {
-            for (int e = t; e < BM * BK / 4; e += NT) {
-                const int r = (e % (BM / 4)) * 4, kk = e / (BM / 4);
-                const int row = r0 + r, k = k0 + kk;
-                float4 x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (VEC) {
+#pragma unroll
+            for (int q = 0; q < PER_T / 4; ++q) {
+                const int e = t + q * NT;
+                const int row = r0 + (e % (BM / 4)) * 4, k = k0 + e / (BM / 4);
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (row < rmax && k < kend)
-                    x = __ldg(reinterpret_cast<const float4 *>(X + row + (long long)k * s_k));
-                put<SPLIT>(S, r, kk, x.x);
-                put<SPLIT>(S, r + 1, kk, x.y);
-                put<SPLIT>(S, r + 2, kk, x.z);
-                put<SPLIT>(S, r + 3, kk, x.w);
+                    v = __ldg(reinterpret_cast<const float4 *>(X + row + (long long)k * s_k));
+                x[4 * q] = v.x, x[4 * q + 1] = v.y, x[4 * q + 2] = v.z, x[4 * q + 3] = v.w;
             }
         } else {
-            for (int e = t; e < BM * BK; e += NT) {
-                const int r = e % BM, kk = e / BM;
-                const int row = r0 + r, k = k0 + kk;
-                put<SPLIT>(S, r, kk,
-                           (row < rmax && k < kend) ? __ldg(X + (long long)row * s_r + (long long)k * s_k) : 0.0f);
+#pragma unroll
+            for (int q = 0; q < PER_T; ++q) {
+                const int e = t + q * NT;
+                const int row = r0 + e % BM, k = k0 + e / BM;
+                x[q] = (row < rmax && k < kend) ? __ldg(X + (long long)row * s_r + (long long)k * s_k) : 0.0f;
             }
         }
     }
 }
 
-// 64x64 output tile per CTA, 4 warps (2 x 2), each warp 32x32 = 2 x 4 mma tiles.
-template <bool SPLIT>
-__global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g)
+template <bool SPLIT, bool VEC>
+__device__ __forceinline__ void store(__nv_bfloat16 (*S)[TILE], const float (&x)[PER_T], bool kfast, int t)
 {
-    __shared__ __nv_bfloat16 As[SPLIT ? 2 : 1][BM][PADK];
-    __shared__ __nv_bfloat16 Bs[SPLIT ? 2 : 1][BN][PADK];
+    if (kfast) {
+        if (VEC) {
+#pragma unroll
+            for (int q = 0; q < PER_T / 4; ++q) {
+                const int e = t + q * NT;
+                put4<SPLIT>(S, at_k(e / (BK / 4), (e % (BK / 4)) * 4), x[4 * q], x[4 * q + 1], x[4 * q + 2],
+                            x[4 * q + 3]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < PER_T; ++q) {
+                const int e = t + q * NT;
+                put1<SPLIT>(S, at_k(e / BK, e % BK), x[q]);
+            }
+        }
+    } else {
+        if (VEC) {
+#pragma unroll
+            for (int q = 0; q < PER_T / 4; ++q) {
+                const int e = t + q * NT;
+                put4<SPLIT>(S, at_r((e % (BM / 4)) * 4, e / (BM / 4)), x[4 * q], x[4 * q + 1], x[4 * q + 2],
+                            x[4 * q + 3]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < PER_T; ++q) {
+                const int e = t + q * NT;
+                put1<SPLIT>(S, at_r(e % BM, e / BM), x[q]);
+            }
+        }
+    }
+}
+
+// Four 8x8 BF16 matrices from shared memory (one 16-byte row address per lane).
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p)
+{
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+// The same, each 8x8 matrix transposed.
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p)
+{
+    const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+// Products of one staged BK slice: the warp's 32x32 block of the tile.  The
+// fragments of m16n8k16 come from ldmatrix: A as 16x16 blocks (rows, k), B
+// as pairs of n8 x k16 blocks; a row-contiguous tile is read transposed.
+template <bool SPLIT>
+__device__ __forceinline__ void mma_tile(const __nv_bfloat16 (*As)[TILE], const __nv_bfloat16 (*Bs)[TILE],
+                                         float (&acc)[2][4][4], int wm, int wn, int lane, bool a_kfast, bool b_kfast)
+{
+    const int q = lane >> 3, l8 = lane & 7;
+#pragma unroll
+    for (int ks = 0; ks < BK; ks += 16) {
+        uint32_t af[SPLIT ? 2 : 1][2][4], bf[SPLIT ? 2 : 1][4][2];
+#pragma unroll
+        for (int s = 0; s < (SPLIT ? 2 : 1); ++s) {
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+                if (a_kfast)
+                    ldsm_x4(af[s][mi], &As[s][at_k(wm + mi * 16 + (lane & 15), ks + (lane >> 4) * 8)]);
+                else
+                    ldsm_x4_t(af[s][mi], &As[s][at_r(wm + mi * 16 + (q & 1) * 8, ks + (q >> 1) * 8 + l8)]);
+            }
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                uint32_t r4[4];
+                if (b_kfast)
+                    ldsm_x4(r4, &Bs[s][at_k(wn + p * 16 + l8 + ((lane >> 4) << 3), ks + (q & 1) * 8)]);
+                else
+                    ldsm_x4_t(r4, &Bs[s][at_r(wn + p * 16 + (q >> 1) * 8, ks + (q & 1) * 8 + l8)]);
+                bf[s][2 * p][0] = r4[0];
+                bf[s][2 * p][1] = r4[1];
+                bf[s][2 * p + 1][0] = r4[2];
+                bf[s][2 * p + 1][1] = r4[3];
+            }
+        }
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < 4; ++ni) {
+                mma_bf16(acc[mi][ni], af[0][mi], bf[0][ni]);
+                if (SPLIT) {
+                    mma_bf16(acc[mi][ni], af[0][mi], bf[SPLIT ? 1 : 0][ni]);
+                    mma_bf16(acc[mi][ni], af[SPLIT ? 1 : 0][mi], bf[0][ni]);
+                }
+            }
+    }
+}
+
+// 64x64 output tile per CTA, 4 warps (2 x 2), each warp 32x32 = 2 x 4 mma tiles.
+// VEC: every operand is staged with float4 loads (the launcher checks that
+// all of them allow it); otherwise all use scalar loads.
+template <bool SPLIT, bool VEC>
+__global__ void __launch_bounds__(NT, VEC ? 4 : 1) gemm_kernel(GemmArgs g)
+{
+    __shared__ __align__(16) __nv_bfloat16 As[SPLIT ? 2 : 1][TILE];
+    __shared__ __align__(16) __nv_bfloat16 Bs[SPLIT ? 2 : 1][TILE];
     const int ks_n = g.ksplit > 1 ? g.ksplit : 1;
     const int bz = blockIdx.z / ks_n, kslice = blockIdx.z % ks_n;
     const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
@@ -148,7 +298,6 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g)
         const float *A, *Bm;
         long long la_i, la_k, lb_k, lb_j;
         int kbeg, kend;
-        bool va, vb;
         if (seg == 0) {
             const int kchunk = ((g.K + ks_n - 1) / ks_n + BK - 1) / BK * BK;
             kbeg = kslice * kchunk;
@@ -156,7 +305,6 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g)
             A = g.A + (long long)bz * g.sA;
             Bm = g.B + (long long)bz * g.sB;
             la_i = g.lda_i, la_k = g.lda_k, lb_k = g.ldb_k, lb_j = g.ldb_j;
-            va = g.vec[0] != 0, vb = g.vec[1] != 0;
         } else {
             if (!g.A2 || g.K2 <= 0)
                 break;
@@ -165,45 +313,27 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g)
             A = g.A2 + (long long)bz * g.sA2;
             Bm = g.B2 + (long long)bz * g.sB2;
             la_i = g.lda2_i, la_k = g.lda2_k, lb_k = g.ldb2_k, lb_j = g.ldb2_j;
-            va = g.vec[2] != 0, vb = g.vec[3] != 0;
+        }
+        if (kbeg >= kend)
+            continue;
+        float xa[PER_T], xb[PER_T];
+        if (VEC) {
+            load<VEC>(xa, A, la_i, la_k, i0, g.M, kbeg, kend, t);
+            load<VEC>(xb, Bm, lb_j, lb_k, j0, g.N, kbeg, kend, t);
         }
         for (int k0 = kbeg; k0 < kend; k0 += BK) {
-            stage<SPLIT>(As, A, la_i, la_k, i0, g.M, k0, kend, va, t);
-            stage<SPLIT>(Bs, Bm, lb_j, lb_k, j0, g.N, k0, kend, vb, t);
-            __syncthreads();
-#pragma unroll
-            for (int ks = 0; ks < BK; ks += 16) {
-                uint32_t af[SPLIT ? 2 : 1][2][4], bf[SPLIT ? 2 : 1][4][2];
-#pragma unroll
-                for (int s = 0; s < (SPLIT ? 2 : 1); ++s) {
-#pragma unroll
-                    for (int mi = 0; mi < 2; ++mi) {
-                        const int r = wm + mi * 16 + grp;
-                        const int kc = ks + tig * 2;
-                        af[s][mi][0] = pack_bf16(As[s][r][kc], As[s][r][kc + 1]);
-                        af[s][mi][1] = pack_bf16(As[s][r + 8][kc], As[s][r + 8][kc + 1]);
-                        af[s][mi][2] = pack_bf16(As[s][r][kc + 8], As[s][r][kc + 9]);
-                        af[s][mi][3] = pack_bf16(As[s][r + 8][kc + 8], As[s][r + 8][kc + 9]);
-                    }
-#pragma unroll
-                    for (int ni = 0; ni < 4; ++ni) {
-                        const int c = wn + ni * 8 + grp;
-                        const int kc = ks + tig * 2;
-                        bf[s][ni][0] = pack_bf16(Bs[s][c][kc], Bs[s][c][kc + 1]);
-                        bf[s][ni][1] = pack_bf16(Bs[s][c][kc + 8], Bs[s][c][kc + 9]);
-                    }
-                }
-#pragma unroll
-                for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-                    for (int ni = 0; ni < 4; ++ni) {
-                        mma_bf16(acc[mi][ni], af[0][mi], bf[0][ni]);
-                        if (SPLIT) {
-                            mma_bf16(acc[mi][ni], af[0][mi], bf[SPLIT ? 1 : 0][ni]);
-                            mma_bf16(acc[mi][ni], af[SPLIT ? 1 : 0][mi], bf[0][ni]);
-                        }
-                    }
+            if (!VEC) {  // scalar staging: no prefetch (registers)
+                load<VEC>(xa, A, la_i, la_k, i0, g.M, k0, kend, t);
+                load<VEC>(xb, Bm, lb_j, lb_k, j0, g.N, k0, kend, t);
             }
+            store<SPLIT, VEC>(As, xa, la_k == 1, t);
+            store<SPLIT, VEC>(Bs, xb, lb_k == 1, t);
+            __syncthreads();
+            if (VEC && k0 + BK < kend) {  // next tile's loads overlap this tile's products
+                load<VEC>(xa, A, la_i, la_k, i0, g.M, k0 + BK, kend, t);
+                load<VEC>(xb, Bm, lb_j, lb_k, j0, g.N, k0 + BK, kend, t);
+            }
+            mma_tile<SPLIT>(As, Bs, acc, wm, wn, lane, la_k == 1, lb_k == 1);
             __syncthreads();
         }
     }
@@ -212,31 +342,63 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g)
     const float *C0 = g.C0 ? g.C0 + (long long)bz * g.sC0 : nullptr;
     const float *Dg = g.dgelu_pre ? g.dgelu_pre + (long long)bz * g.sDg : nullptr;
     float *act = g.act ? g.act + (long long)bz * g.sAct : nullptr;
+    // one row and two adjacent columns at a time (float2 when the launcher
+    // found every epilogue array 8-byte aligned with an even pitch)
 #pragma unroll
     for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
         for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int i = i0 + wm + mi * 16 + grp + (h >= 2 ? 8 : 0);
-                const int j = j0 + wn + ni * 8 + tig * 2 + (h & 1);
-                if (i < g.M && j < g.N) {
-                    float v = g.alpha * acc[mi][ni][h];
-                    const long long off = (long long)i * g.ldc + j;
-                    if (ks_n > 1) {
-                        atomicAdd(&C[off], v);
-                        continue;
+            for (int hh = 0; hh < 2; ++hh) {
+                const int i = i0 + wm + mi * 16 + grp + hh * 8;
+                const int j = j0 + wn + ni * 8 + tig * 2;
+                if (i >= g.M || j >= g.N)
+                    continue;
+                const long long off = (long long)i * g.ldc + j;
+                float v[2] = {g.alpha * acc[mi][ni][2 * hh], g.alpha * acc[mi][ni][2 * hh + 1]};
+                if (ks_n > 1) {
+                    atomicAdd(&C[off], v[0]);
+                    if (j + 1 < g.N)
+                        atomicAdd(&C[off + 1], v[1]);
+                    continue;
+                }
+                if (g.pairs && j + 1 < g.N) {
+                    if (C0) {
+                        const float2 c = *reinterpret_cast<const float2 *>(C0 + off);
+                        v[0] += g.beta * c.x;
+                        v[1] += g.beta * c.y;
                     }
-                    if (C0)
-                        v += g.beta * C0[off];
-                    if (g.bias)
-                        v += g.bias[j];
-                    if (Dg)
-                        v *= gelu_grad(Dg[off]);
+                    if (g.bias) {
+                        const float2 b = *reinterpret_cast<const float2 *>(g.bias + j);
+                        v[0] += b.x;
+                        v[1] += b.y;
+                    }
+                    if (Dg) {
+                        const float2 d = *reinterpret_cast<const float2 *>(Dg + off);
+                        v[0] *= gelu_grad<SPLIT>(d.x);
+                        v[1] *= gelu_grad<SPLIT>(d.y);
+                    }
                     if (C)
-                        C[off] = v;
+                        *reinterpret_cast<float2 *>(C + off) = make_float2(v[0], v[1]);
                     if (act)
-                        act[off] = gelu(v);
+                        *reinterpret_cast<float2 *>(act + off) = make_float2(gelu<SPLIT>(v[0]), gelu<SPLIT>(v[1]));
+                    continue;
+                }
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (j + c >= g.N)
+                        break;
+                    float w = v[c];
+                    if (C0)
+                        w += g.beta * C0[off + c];
+                    if (g.bias)
+                        w += g.bias[j + c];
+                    if (Dg)
+                        w *= gelu_grad<SPLIT>(Dg[off + c]);
+                    if (C)
+                        C[off + c] = w;
+                    if (act)
+                        act[off + c] = gelu<SPLIT>(w);
                 }
             }
 }
@@ -414,11 +576,15 @@ cudaError_t sno_gemm(const GemmArgs &g0, int batch, bool split, cudaStream_t s)
     g.vec[1] = vec_ok(g.B, g.ldb_j, g.ldb_k, g.N, g.K, g.sB, batch);
     g.vec[2] = g.A2 ? vec_ok(g.A2, g.lda2_i, g.lda2_k, g.M, g.K2, g.sA2, batch) : 0;
     g.vec[3] = g.A2 ? vec_ok(g.B2, g.ldb2_j, g.ldb2_k, g.N, g.K2, g.sB2, batch) : 0;
+    const bool vec = g.vec[0] && g.vec[1] && (!g.A2 || (g.vec[2] && g.vec[3]));
+    auto al8 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; };
+    g.pairs = (g.ldc % 2 == 0) && al8(g.C) && al8(g.C0) && al8(g.dgelu_pre) && al8(g.act) && al8(g.bias) &&
+              (batch == 1 || (g.sC % 2 == 0 && g.sC0 % 2 == 0 && g.sDg % 2 == 0 && g.sAct % 2 == 0));
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, batch * ks);
     if (split)
-        gemm_kernel<true><<<grid, NT, 0, s>>>(g);
+        vec ? gemm_kernel<true, true><<<grid, NT, 0, s>>>(g) : gemm_kernel<true, false><<<grid, NT, 0, s>>>(g);
     else
-        gemm_kernel<false><<<grid, NT, 0, s>>>(g);
+        vec ? gemm_kernel<false, true><<<grid, NT, 0, s>>>(g) : gemm_kernel<false, false><<<grid, NT, 0, s>>>(g);
     return cudaGetLastError();
 }
 

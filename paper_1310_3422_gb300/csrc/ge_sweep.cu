@@ -86,6 +86,110 @@ __global__ void __launch_bounds__(256) sweep_kernel(const Real *__restrict__ in,
     }
 }
 
+// The same step with the CTA's units staged in shared memory: blockDim.x
+// consecutive units (2k nodes each) are loaded with coalesced reads, every
+// thread runs its unit's recurrences on its own padded shared-memory row
+// (pitch 2k + 1 elements, odd, so the threads' rows fall in different
+// banks), and the results leave with coalesced writes.  A thread reads the
+// two old values just outside its unit (owned by its neighbours) before the
+// barrier that precedes any update, so the in-place update is race free.
+// Same arithmetic, in the same order, as sweep_kernel.
+template <typename Real>
+__global__ void __launch_bounds__(256) sweep_smem_kernel(const Real *__restrict__ in, Real *__restrict__ out,
+                                                         long long n, int parity, int k, long long n_units,
+                                                         SweepCoef<Real> c)
+{
+    extern __shared__ unsigned char sweep_smem[];
+    Real *sm = reinterpret_cast<Real *>(sweep_smem);
+    const int T = blockDim.x, t = threadIdx.x;
+    const int w = 2 * k, pitch = 2 * k + 1;
+    for (long long U0 = (long long)blockIdx.x * T; U0 < n_units; U0 += (long long)gridDim.x * T) {
+        const long long base = (2 * U0 + parity - 1) * (long long)k;  // first node of unit U0
+        const int units = (int)((n_units - U0) < T ? (n_units - U0) : T);
+        const int span = units * w;
+        for (int e = t; e < span; e += T) {
+            const long long j = base + e;
+            if (j >= 1 && j <= n)
+                sm[(e / w) * pitch + e % w] = in[j - 1];
+        }
+        __syncthreads();
+        const long long u = U0 + t;
+        const long long ub = base + (long long)t * w;  // first node of this unit
+        Real *row = sm + t * pitch;
+        Real left = (Real)0, right = (Real)0;  // old values of nodes ub - 1 and ub + w
+        if (t < units) {
+            const long long jl = ub - 1, jr = ub + w;
+            left = jl <= 0 ? c.bl : (jl > n ? c.br : (t > 0 ? sm[(t - 1) * pitch + w - 1] : in[jl - 1]));
+            right = jr <= 0 ? c.bl : (jr > n ? c.br : (t + 1 < units ? sm[(t + 1) * pitch] : in[jr - 1]));
+        }
+        __syncthreads();
+        if (t < units) {
+            auto old = [&](long long j) -> Real {
+                if (j == 0)
+                    return c.bl;
+                if (j == n + 1)
+                    return c.br;
+                if (j < ub)
+                    return left;
+                if (j >= ub + w)
+                    return right;
+                return row[j - ub];
+            };
+            auto saulyev = [&](Real nb, long long j, long long far) -> Real {
+                return f_fma(c.s0, old(far), f_fma(c.s1, row[j - ub], f_mul(c.s0, nb)));
+            };
+            const long long bA = 2 * u + parity;
+            const long long a_lo = bA * k < 1 ? 1 : bA * k;
+            const long long a_hi = bA * k + k - 1 > n ? n : bA * k + k - 1;
+            const long long b_lo = (bA - 1) * k < 1 ? 1 : (bA - 1) * k;
+            const long long b_hi = bA * k - 1 > n ? n : bA * k - 1;
+            const bool has_a = a_lo <= a_hi, has_b = b_lo <= b_hi;
+            if (has_a && has_b) {
+                const long long j = bA * k - 1;
+                const Real a = old(j - 1), b = old(j), cc = old(j + 1), d = old(j + 2);
+                const Real y = f_fma(c.c4, d, f_fma(c.c3, cc, f_fma(c.c2, b, f_mul(c.c1, a))));
+                const Real z = f_fma(c.c1, d, f_fma(c.c2, cc, f_fma(c.c3, b, f_mul(c.c4, a))));
+                Real prev = z;
+                // A run to the right: reads old values at m and m + 1 before m is overwritten
+                for (long long m = j + 2; m <= a_hi; ++m) {
+                    const Real nv = saulyev(prev, m, m + 1);
+                    row[m - ub] = nv;
+                    prev = nv;
+                }
+                prev = y;
+                for (long long m = j - 1; m >= b_lo; --m) {  // B run to the left
+                    const Real nv = saulyev(prev, m, m - 1);
+                    row[m - ub] = nv;
+                    prev = nv;
+                }
+                row[j - ub] = y;
+                row[j + 1 - ub] = z;
+            } else if (has_a) {
+                Real prev = c.bl;
+                for (long long m = a_lo; m <= a_hi; ++m) {
+                    const Real nv = saulyev(prev, m, m + 1);
+                    row[m - ub] = nv;
+                    prev = nv;
+                }
+            } else if (has_b) {
+                Real prev = c.br;
+                for (long long m = b_hi; m >= b_lo; --m) {
+                    const Real nv = saulyev(prev, m, m - 1);
+                    row[m - ub] = nv;
+                    prev = nv;
+                }
+            }
+        }
+        __syncthreads();
+        for (int e = t; e < span; e += T) {
+            const long long j = base + e;
+            if (j >= 1 && j <= n)
+                out[j - 1] = sm[(e / w) * pitch + e % w];
+        }
+        __syncthreads();
+    }
+}
+
 template <typename Real>
 cudaError_t launch_sweep_t(const Real *in, Real *out, long long n, int parity, long long k, const CanonCoef &cf,
                            cudaStream_t s)
@@ -95,7 +199,24 @@ cudaError_t launch_sweep_t(const Real *in, Real *out, long long n, int parity, l
     // units u = 0.. cover sub-domains up to floor(n / k)
     const long long last_block = n / k;
     const long long n_units = (last_block + 1 - parity) / 2 + 1;
-    const int threads = 256;
+    // staged in shared memory when 32 or more units fit a CTA's 227 KB
+    const long long per_unit = (2 * k + 1) * (long long)sizeof(Real);
+    const long long max_smem = 227 * 1024;
+    int threads = 256;
+    while (threads > 32 && threads * per_unit > max_smem)
+        threads -= 32;
+    if (threads * per_unit <= max_smem) {
+        const int smem = (int)(threads * per_unit);
+        cudaError_t e = cudaFuncSetAttribute(sweep_smem_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess)
+            return e;
+        long long blocks = (n_units + threads - 1) / threads;
+        if (blocks > (1LL << 20))
+            blocks = 1LL << 20;
+        sweep_smem_kernel<Real><<<(unsigned)blocks, threads, smem, s>>>(in, out, n, parity, (int)k, n_units, c);
+        return cudaGetLastError();
+    }
+    threads = 256;
     long long blocks = (n_units + threads - 1) / threads;
     if (blocks > (1LL << 20))
         blocks = 1LL << 20;

@@ -710,9 +710,9 @@ bool geometry(int reach, int *H, int *U)
 // CTA-row layout (one row per thread).
 
 // Entry, block steps and exit of one tile, batched form.
-template <bool EDGE, typename Real, int K, int NW>
+template <bool EDGE, typename Real, int K, int NW, bool WT>
 __device__ __forceinline__ void run_batch(Real (&v)[K], const TbbParams &P, const BatchDesc &bd,
-                                          Exch<Real, NW, false> &x, Span sp)
+                                          Exch<Real, NW, WT> &x, Span sp)
 {
     Real L = 0, R = 0;
     if (P.do_entry) {
@@ -749,9 +749,9 @@ __device__ __forceinline__ void run_batch(Real (&v)[K], const TbbParams &P, cons
     }
 }
 
-template <bool EDGE, int K, int NW>
+template <bool EDGE, int K, int NW, bool WT>
 __device__ __forceinline__ void run_batch_comp(float (&v)[K], const TbbParams &P, const BatchDesc &bd,
-                                               Exch<float, NW, false> &x, Span sp)
+                                               Exch<float, NW, WT> &x, Span sp)
 {
     float L = 0.0f, R = 0.0f;
     if (P.do_entry) {
@@ -796,10 +796,23 @@ __device__ __forceinline__ void run_batch_comp(float (&v)[K], const TbbParams &P
     }
 }
 
+// Layout of the batched kernel: GE_TBB_WT_F32 = 1 gives plain FP32 warp
+// windows (no barrier in the step loop); FP64 and compensated FP32 use CTA
+// rows.
+#ifndef GE_TBB_WT_F32
+#define GE_TBB_WT_F32 0
+#endif
+
+template <typename Real, bool COMP>
+struct BatchLayout {
+    static constexpr bool WT = sizeof(Real) == 4 && !COMP && GE_TBB_WT_F32 != 0;
+};
+
 template <typename Real, bool COMP>
 __global__ void __launch_bounds__(kTileRows, 2)
     tbb_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TbbParams P)
 {
+    constexpr bool WT = BatchLayout<Real, COMP>::WT;
     constexpr int NT = kTileRows;
     constexpr int K = kRowBytes / (int)sizeof(Real);
     constexpr int NW = NT / 32;
@@ -814,7 +827,11 @@ __global__ void __launch_bounds__(kTileRows, 2)
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int hr = P.H / K, ur = P.U / K;
-    Exch<Real, NW, false> x{slot, 0, lane, warp};
+    // tile row of this thread: CTA rows -> row t; warp windows -> warp w
+    // starts where warp w-1's output ends (windows overlap by 2 halos)
+    const int my_row = WT ? warp * (32 - 2 * hr) + lane : t;
+    const bool writes = WT ? (lane >= hr && lane < 32 - hr) : true;
+    Exch<Real, NW, WT> x{slot, 0, lane, warp};
 
     if (t == 0) {
         mbar_init(&mbar[0], 1);
@@ -850,13 +867,15 @@ __global__ void __launch_bounds__(kTileRows, 2)
 
         Real v[K];
         {
-            const unsigned char *rp = cur + t * kRowBytes;
+            const unsigned char *rp = cur + my_row * kRowBytes;
 #pragma unroll
             for (int c = 0; c < CH; ++c)
-                chunk_to_regs<K>(rp + ((c ^ (t & 7)) << 4), v, c);
+                chunk_to_regs<K>(rp + ((c ^ (my_row & 7)) << 4), v, c);
         }
+        if constexpr (WT)
+            __syncthreads();  // windows overlap: every load before any write-back
         // this thread's problem: rows outside the buffer or in padding have none
-        const long long grow = tile * ur - hr + t;
+        const long long grow = tile * ur - hr + my_row;
         const int pid = (grow >= 0 && grow < P.n_rows) ? __ldg(P.row_pid + grow) : -1;
         BatchDesc bd{};
         Span sp{K + 1, K + 1};  // no point of this thread is inside a grid
@@ -878,11 +897,11 @@ __global__ void __launch_bounds__(kTileRows, 2)
                 run_batch_comp<false>(v, P, bd, x, sp);
         }
 
-        {
-            unsigned char *rp = cur + t * kRowBytes;
+        if (writes) {
+            unsigned char *rp = cur + my_row * kRowBytes;
 #pragma unroll
             for (int c = 0; c < CH; ++c)
-                regs_to_chunk<K>(rp + ((c ^ (t & 7)) << 4), v, c);
+                regs_to_chunk<K>(rp + ((c ^ (my_row & 7)) << 4), v, c);
         }
         __syncthreads();
         {
@@ -948,9 +967,24 @@ bool tbb_geometry(int prec, int reach, int *H, int *U)
 {
     const int K = kRowBytes / (prec == 0 ? 8 : 4);
     const int ht = (reach + K - 1) / K;
+    const bool wt = prec == 1 ? BatchLayout<float, false>::WT : false;
     *H = ht * K;
+    if (wt) {
+        if (2 * ht >= 32)
+            return false;
+        *U = (kTileRows / 32) * (32 - 2 * ht) * K;
+        return true;
+    }
     *U = kTileRows * K - 2 * *H;
     return *U > 0;
+}
+
+int tbb_max_depth(int prec)
+{
+    int H, U, d = kMaxTableSteps;
+    while (d > 1 && !tbb_geometry(prec, d + 2, &H, &U))
+        --d;
+    return d;
 }
 
 cudaError_t tbb_occupancy(int prec, int *blocks)

@@ -78,3 +78,13 @@ def test_subdomain_width_checks():
     with pytest.raises(B.GeError):
         B.ge_set_subdomain_width(ctx, 0)
     B.ge_destroy(ctx)
+
+
+@pytest.mark.parametrize("k,n", [(200, 6001), (500, 6001), (2000, 9000), (33, 70001)])
+def test_subdomain_wide_and_many_units(k, n):
+    """Wide sub-domains (fewer units per CTA in shared memory, or the
+    unstaged kernel once 32 units no longer fit) and many CTAs."""
+    u0 = np.random.default_rng(k + n).standard_normal(n)
+    for step0 in (0, 1):
+        want = oracle.run_k(u0, 0.7, -0.2, 0.9, k, 5, step0=step0)
+        assert np.array_equal(run_k(u0, 0.7, -0.2, 0.9, k, 5, step0=step0), want)
