@@ -154,9 +154,14 @@ ge_status ge_solve(int64_t n, double r, double beta_l, double beta_r, ge_precisi
  * (type as for ge_create).  offsets[b] must be a multiple of 128 bytes (16
  * doubles / 32 floats) and problems may not share a 128-byte row; the values
  * between problems are left untouched.  The batched kernel runs the tiled
- * right-hand-side scheme of GE_KERNEL_TEMPORAL in its normalised block form
- * x <- x + 2r/(1+2r) (x_partner - x), each thread taking its problem's
- * constants and walls, `depth` steps per launch. */
+ * right-hand-side scheme of GE_KERNEL_TEMPORAL, each thread taking its
+ * problem's constants, `depth` steps per launch.  GE_F64 and GE_F32 run it
+ * in the scaled form x <- x + 2r x_partner on each problem minus its linear
+ * wall profile (a fixed point of the step, so the shifted problem has zero
+ * walls), with per-problem power-of-two rescalings and the inverse scale
+ * applied at each launch end (the same data range as ge_create's tiled
+ * kernel); GE_F32_COMP runs the normalised form
+ * x <- x + 2r/(1+2r) (x_partner - x) with Kahan-summed updates. */
 typedef struct ge_batch ge_batch;   /* opaque plan, owned by the library */
 
 /* Build a plan: checks the layout and uploads the per-problem table (host

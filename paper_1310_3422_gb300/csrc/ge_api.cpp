@@ -37,9 +37,6 @@ ge_status cuda_fail(cudaError_t e, const char *what)
     return fail(GE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#ifndef GE_F32_HEADROOM
-#define GE_F32_HEADROOM 64.0
-#endif
 constexpr int kDefaultDepthF64 = 48;
 constexpr int kDefaultDepthF32 = 128;
 constexpr int kMaxDepth = 1023;
@@ -72,6 +69,7 @@ struct ge_ctx {
     CUtensorMap tmap[2];  // one per buffer (source of a tiled launch)
     int64_t n = 0;
     double r = 0, beta_l = 0, beta_r = 0;
+    double onepg_lo = 0;  // low part of the scaled map's growth factor (see fill_coefficients)
     ge_precision prec = GE_F64;
     cudaStream_t stream = nullptr;
     int device = 0;
@@ -109,7 +107,12 @@ void fill_coefficients(ge_ctx *c)
 
     ge::TbParams &p = c->tb;
     p.g = 2.0 * r;
-    p.onepg = 1.0 + 2.0 * r;
+    // The scaled block map x <- x + g x_partner multiplies the symmetric part
+    // of every pair by exactly 1 + g, with g the coefficient the kernel holds
+    // (rounded to FP32 on the FP32 path).  The host's scale mirror uses that
+    // factor, carried as a double-double (onepg + onepg_lo == 1 + g exactly),
+    // so no systematic scale error builds up over many steps.
+    ge::scaled_growth(r, c->prec == GE_F32, &p.onepg, &c->onepg_lo);
     p.r = r;
     p.omr = 1.0 - r;
     p.d = 2.0 * r / det;
@@ -173,7 +176,7 @@ ge_status run_tiled(ge_ctx *c, int64_t steps, int depth)
     if (depth > ge::kMaxTableSteps)
         depth = ge::kMaxTableSteps;
     const int prec = c->prec == GE_F64 ? 0 : (c->prec == GE_F32 ? 1 : 2);
-    double sigma = 1.0;
+    double sigma = 1.0, sigma_lo = 0.0;  // double-double scale
     int until = every;
     int64_t n0 = 0;
     while (n0 < steps) {
@@ -189,7 +192,7 @@ ge_status run_tiled(ge_ctx *c, int64_t steps, int depth)
         if (every > 0) {
             int ev = 0;
             for (int m = 0; m < p.n_mid; ++m) {
-                sigma *= p.onepg;
+                ge::dd_mul(sigma, sigma_lo, p.onepg, c->onepg_lo);
                 if (--until == 0) {
                     until = every;
                     int e2 = 0;
@@ -197,13 +200,14 @@ ge_status run_tiled(ge_ctx *c, int64_t steps, int depth)
                     const int e = e2 - 1;  // sigma * 2^-e in [1, 2)
                     p.rs_exp[ev++] = (short)e;
                     sigma = std::ldexp(sigma, -e);
+                    sigma_lo = std::ldexp(sigma_lo, -e);
                 }
             }
         }
         if (p.do_exit) {
-            p.x1 = c->tb.x1 / sigma;
-            p.x2 = c->tb.x2 / sigma;
-            p.xs = c->tb.xs / sigma;
+            p.x1 = ge::dd_div(c->tb.x1, sigma, sigma_lo);
+            p.x2 = ge::dd_div(c->tb.x2, sigma, sigma_lo);
+            p.xs = ge::dd_div(c->tb.xs, sigma, sigma_lo);
         }
         const int reach = p.do_entry + p.n_mid + p.do_exit;
         if (!ge::tb_geometry(prec, reach, &p.H, &p.U))

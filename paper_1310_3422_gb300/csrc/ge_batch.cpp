@@ -65,6 +65,13 @@ struct ge_batch {
     int *err = nullptr;
     int depth = 0;
     int num_sms = 0, blocks_per_sm = 0;
+    // scaled form (FP64, plain FP32): rescale exponents [n_problems][Q] and
+    // end-factor slots, one per launch length n_mid met so far
+    short *exps = nullptr;
+    void *endf = nullptr;
+    int R = 0, Q = 0;
+    std::vector<int> slot_nmid;
+    std::vector<char> slot_ready;
 };
 
 namespace {
@@ -82,10 +89,45 @@ void release_batch(ge_batch *b)
         cudaFree(b->desc);
     if (b->err)
         cudaFree(b->err);
+    if (b->exps)
+        cudaFree(b->exps);
+    if (b->endf)
+        cudaFree(b->endf);
     delete b;
 }
 
 int prec_index(ge_precision p) { return p == GE_F64 ? 0 : (p == GE_F32 ? 1 : 2); }
+
+constexpr int kEndfSlots = 64;
+
+// End-factor slot of launches with n_mid block steps, computed on the plan's
+// stream the first time (a kernel, so stream capture records it).  A slot
+// filled inside a capture is not marked ready: the next direct run fills it
+// again, since the captured graph may never be launched.  -1 when all slots
+// are taken (that launch then uses the normalised form).
+int endf_slot(ge_batch *b, int n_mid, cudaError_t *err)
+{
+    const bool f32 = b->prec == GE_F32;
+    size_t i = 0;
+    while (i < b->slot_nmid.size() && b->slot_nmid[i] != n_mid)
+        ++i;
+    if (i == b->slot_nmid.size()) {
+        if ((int)i >= kEndfSlots)
+            return -1;
+        b->slot_nmid.push_back(n_mid);
+        b->slot_ready.push_back(0);
+    }
+    if (!b->slot_ready[i]) {
+        void *dst = static_cast<char *>(b->endf) + i * (size_t)b->n_problems * 8;
+        *err = ge::batch_endf(b->desc, b->exps, b->n_problems, b->R, b->Q, n_mid, f32 ? 1 : 0, dst, b->stream);
+        if (*err != cudaSuccess)
+            return -1;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(b->stream, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone)
+            b->slot_ready[i] = 1;
+    }
+    return (int)i;
+}
 
 // Enqueue `steps` steps on the working buffers (state in buf[0] on entry);
 // returns the index of the buffer holding the result.
@@ -113,6 +155,19 @@ ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int *result_buf)
         p.row_pid = b->row_pid;
         p.desc = b->desc;
         p.err = b->err;
+        if (b->exps) {
+            cudaError_t se = cudaSuccess;
+            const int slot = endf_slot(b, p.n_mid, &se);
+            if (se != cudaSuccess)
+                return bcuda(se, "ge_batch: end factors");
+            if (slot >= 0) {
+                p.scaled = 1;
+                p.R = b->R;
+                p.Q = b->Q;
+                p.exps = b->exps;
+                p.endf = static_cast<const char *>(b->endf) + (size_t)slot * b->n_problems * 8;
+            }
+        }
         p.out = b->buf[cur ^ 1];
         long long grid = (long long)b->num_sms * b->blocks_per_sm;
         if (grid > p.n_tiles)
@@ -148,6 +203,7 @@ ge_status ge_batch_create(ge_batch **out, int32_t n_problems, const int64_t *n, 
         return bfail(GE_EINVAL, "ge_batch_create: total is too large");
     std::vector<int> row_pid((size_t)n_rows, -1);
     std::vector<ge::BatchDesc> desc((size_t)n_problems);
+    double r_max = 0.0;
     for (int32_t i = 0; i < n_problems; ++i) {
         const double ri = r[i];
         if (n[i] < 1 || offsets[i] < 0 || offsets[i] % K != 0 || offsets[i] + n[i] > total)
@@ -175,6 +231,12 @@ ge_status ge_batch_create(ge_batch **out, int32_t n_problems, const int64_t *n, 
         d.x1 = (1.0 + ri) / det;
         d.x2 = ri / det;
         d.xs = 1.0 / (1.0 + ri);
+        const double g_used = (prec == GE_F32) ? (double)(float)(2.0 * ri) : 2.0 * ri;
+        d.g = 2.0 * ri;
+        d.kap_s = (1.0 + g_used) * (1.0 - ri) / (1.0 + ri);
+        d.ustar_a = beta_l[i];
+        d.ustar_b = (beta_r[i] - beta_l[i]) / (double)(n[i] + 1);
+        r_max = ri > r_max ? ri : r_max;
     }
     ge_batch *b = new (std::nothrow) ge_batch();
     if (!b)
@@ -208,6 +270,20 @@ ge_status ge_batch_create(ge_batch **out, int32_t n_problems, const int64_t *n, 
         e = cudaMemsetAsync(b->buf[i], 0, bytes, b->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(b->err, 0, 256, b->stream);
+    if (e == cudaSuccess && prec != GE_F32_COMP) {
+        // scaled form: rescale every R block steps, R chosen so the scale
+        // stays below 2^headroom (as for one problem: inputs up to about
+        // 2^(max exponent - headroom) are safe)
+        const double headroom = prec == GE_F64 ? 256.0 : GE_F32_HEADROOM;
+        const int R = (int)std::floor(headroom / std::log2(1.0 + 2.0 * r_max));
+        b->R = R < 1 ? 1 : (R > ge::kMaxTableSteps ? ge::kMaxTableSteps : R);
+        b->Q = (ge::kMaxTableSteps + b->R - 1) / b->R;
+        e = cudaMalloc(reinterpret_cast<void **>(&b->exps), (size_t)n_problems * b->Q * sizeof(short));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&b->endf, (size_t)kEndfSlots * n_problems * 8);
+        if (e == cudaSuccess)
+            e = ge::batch_exps(b->desc, n_problems, b->R, b->Q, prec == GE_F32 ? 1 : 0, b->exps, b->stream);
+    }
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(b->stream);
     if (e == cudaSuccess)

@@ -3,6 +3,7 @@
 // Plain C++: no device code, no CUDA headers beyond the runtime API.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime_api.h>
 
@@ -14,6 +15,12 @@ constexpr int kRowBytes = 128;
 // Rows of 128 bytes in one tile of the tiled kernels (8192 floats or 4096
 // doubles), the box of their 2D TMA load.
 constexpr int kTileRows = 256;
+
+// Headroom (in powers of two) of the scaled forms' data between rescalings:
+// data magnitudes up to about 2^(largest exponent - headroom) are safe.
+#ifndef GE_F32_HEADROOM
+#define GE_F32_HEADROOM 64.0
+#endif
 
 // Device error codes written to the context's error word.
 enum DevErr : int { kDevOk = 0, kDevTimeout = 1 };
@@ -79,6 +86,12 @@ struct BatchDesc {
     double kappa;         // singleton block factor (1-r)/(1+r)
     double f_l, f_r;      // wall terms r*beta_l, r*beta_r
     double x1, x2, xs;    // exit: (1+r)/(1+2r), r/(1+2r), 1/(1+r)
+    // scaled form (FP64 and plain FP32): the state minus the linear wall
+    // profile u*_j = ustar_a + ustar_b (j + 1), an exact fixed point of the
+    // step, so the shifted problem has zero walls
+    double g;             // 2r
+    double kap_s;         // singleton factor (1 + g)(1-r)/(1+r)
+    double ustar_a, ustar_b;
 };
 
 // One launch of the batched tiled kernel over the packed buffer.
@@ -90,7 +103,49 @@ struct TbbParams {
     long long n_rows, n_tiles;
     int U, H;
     int p_first, do_entry, n_mid, do_exit;
+    // scaled form (scaled != 0): after every R block steps the data of
+    // problem b are multiplied by 2^-exps[b * Q + q]; at the launch end by
+    // endf[b] (FP32: float2 hi + lo, FP64: double), which brings them back to
+    // the normalised state
+    int scaled, R, Q;
+    const short *exps;
+    const void *endf;
 };
+
+// Rescale exponents of the batched scaled form (one row of Q per problem) and
+// the end factor of a launch with n_mid block steps (kernels in ge_tb.cu).
+cudaError_t batch_exps(const BatchDesc *desc, int n_problems, int R, int Q, int f32, short *exps, cudaStream_t s);
+cudaError_t batch_endf(const BatchDesc *desc, const short *exps, int n_problems, int R, int Q, int n_mid, int f32,
+                       void *endf, cudaStream_t s);
+
+// Host-side scale bookkeeping of the scaled block map x <- x + g x_partner
+// (tiled kernels).  That map multiplies the symmetric part of every pair by
+// exactly 1 + g, with g the coefficient the kernel holds: 2r, rounded to FP32
+// on the FP32 path.  The host mirrors the product of those factors as a
+// double-double so that no systematic scale error builds up over many steps.
+inline void scaled_growth(double r, bool f32, double *hi, double *lo)
+{
+    const double g = f32 ? (double)(float)(2.0 * r) : 2.0 * r;
+    *hi = 1.0 + g;
+    *lo = (1.0 - *hi) + g;  // exact: 1 + g == hi + lo
+}
+
+// (h, l) <- (h, l) * (bh, bl) in double-double arithmetic.
+inline void dd_mul(double &h, double &l, double bh, double bl)
+{
+    const double p = h * bh;
+    const double e = std::fma(h, bh, -p);
+    const double t = e + (h * bl + l * bh);
+    h = p + t;
+    l = t - (h - p);
+}
+
+// x / (h + l) to double precision.
+inline double dd_div(double x, double h, double l)
+{
+    const double q = x / h;
+    return q - q * (l / h);
+}
 
 // Launchers (return the cudaError_t of the launch).
 cudaError_t launch_canon_f64(const double *in, double *out, long long n, int parity,

@@ -168,7 +168,8 @@ extern "C" ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double
         const double det = 1.0 + 2.0 * r;
         ge::TbParams base_p{};
         base_p.g = 2.0 * r;
-        base_p.onepg = 1.0 + 2.0 * r;
+        double onepg_lo = 0.0;
+        ge::scaled_growth(r, prec == GE_F32, &base_p.onepg, &onepg_lo);
         base_p.r = r;
         base_p.omr = 1.0 - r;
         base_p.d = 2.0 * r / det;
@@ -201,7 +202,7 @@ extern "C" ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double
         if (e != cudaSuccess || bps < 1)
             return nfail(GE_ECUDA, "ge_solve_noalloc: occupancy query failed");
 
-        double sigma = 1.0;
+        double sigma = 1.0, sigma_lo = 0.0;  // double-double scale
         int until = every;
         long long n0 = 0;
         while (n0 < steps) {
@@ -217,19 +218,20 @@ extern "C" ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double
             if (every > 0) {
                 int ev = 0;
                 for (int m = 0; m < p.n_mid; ++m) {
-                    sigma *= p.onepg;
+                    ge::dd_mul(sigma, sigma_lo, p.onepg, onepg_lo);
                     if (--until == 0) {
                         until = every;
                         int e2 = 0;
                         std::frexp(sigma, &e2);
                         p.rs_exp[ev++] = (short)(e2 - 1);
                         sigma = std::ldexp(sigma, -(e2 - 1));
+                        sigma_lo = std::ldexp(sigma_lo, -(e2 - 1));
                     }
                 }
             }
-            p.x1 = x1 / sigma;
-            p.x2 = x2 / sigma;
-            p.xs = xs / sigma;
+            p.x1 = ge::dd_div(x1, sigma, sigma_lo);
+            p.x2 = ge::dd_div(x2, sigma, sigma_lo);
+            p.xs = ge::dd_div(xs, sigma, sigma_lo);
             const int reach = p.do_entry + p.n_mid + p.do_exit;
             if (!ge::tb_geometry(pidx, reach, &p.H, &p.U))
                 return nfail(GE_EINVAL, "ge_solve_noalloc: depth %d does not fit a tile", d);

@@ -796,6 +796,90 @@ __device__ __forceinline__ void run_batch_comp(float (&v)[K], const TbbParams &P
     }
 }
 
+// Scaled batched form (FP64 and plain FP32).  The thread's problem is
+// shifted by its linear wall profile u* (an exact fixed point of the step:
+// the shifted problem has zero walls, so no wall terms and no scale in the
+// edge warps), advanced with the scaled block map x <- x + g x_partner (one
+// FMA per point and step; singletons x <- kap_s x), multiplied by the
+// problem's power of two 2^-e after every R block steps, and brought back to
+// the normalised state at the launch end by the factor endf (the inverse of
+// the accumulated scale, computed in double-double by batch_endf_kernel).
+// Only points inside the problem change: padding keeps its values.
+template <bool EDGE, typename Real, int K, int NW, bool WT>
+__device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &P, const BatchDesc &bd, int pid,
+                                                 long long g0, Exch<Real, NW, WT> &x, Span sp)
+{
+    Real L = 0, R = 0;
+    const Real ua = (Real)bd.ustar_a, ub = (Real)bd.ustar_b;
+    if (P.do_entry) {
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (!EDGE || (j >= sp.jlo && j < sp.jhi))
+                v[j] -= ua + ub * (Real)(g0 + j + 1);
+        const StageC<Real> c{(Real)bd.r, (Real)bd.omr, (Real)0, (Real)0, (Real)0};
+        if (((1 - P.p_first) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kEntry, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kEntry, EDGE>(v, L, R, sp, c);
+        }
+    }
+    const StageC<Real> cm{(Real)bd.g, (Real)0, (Real)bd.kap_s, (Real)0, (Real)0};
+    int m = 0, q = 0;
+    while (m < P.n_mid) {
+        const int cnt = (P.n_mid - m < P.R) ? P.n_mid - m : P.R;
+        int i = 0;
+        if (((P.p_first + m) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kMid, EDGE>(v, L, R, sp, cm);
+            i = 1;
+        }
+        for (; i + 1 < cnt; i += 2) {
+            stage<0, kMid, EDGE>(v, L, R, sp, cm);
+            exchange(v, L, R, x);
+            stage<1, kMid, EDGE>(v, L, R, sp, cm);
+        }
+        if (i < cnt)
+            stage<0, kMid, EDGE>(v, L, R, sp, cm);
+        m += cnt;
+        if (cnt == P.R && pid >= 0) {
+            const Real sc = pow2neg<Real>(P.exps[(long long)pid * P.Q + q]);
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (!EDGE || (j >= sp.jlo && j < sp.jhi))
+                    v[j] *= sc;
+        }
+        ++q;
+    }
+    if (pid >= 0) {
+        Real fh, fl;
+        if constexpr (sizeof(Real) == 4) {
+            const float2 f = reinterpret_cast<const float2 *>(P.endf)[pid];
+            fh = f.x, fl = f.y;
+        } else {
+            fh = reinterpret_cast<const double *>(P.endf)[pid];
+            fl = 0;
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (!EDGE || (j >= sp.jlo && j < sp.jhi))
+                v[j] = fma(v[j], fh, v[j] * fl);
+    }
+    if (P.do_exit) {
+        const StageC<Real> c{(Real)bd.x1, (Real)bd.x2, (Real)bd.xs, (Real)0, (Real)0};
+        if (((P.p_first + P.n_mid) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kExit, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kExit, EDGE>(v, L, R, sp, c);
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (!EDGE || (j >= sp.jlo && j < sp.jhi))
+                v[j] += ua + ub * (Real)(g0 + j + 1);
+    }
+}
+
 // Layout of the batched kernel: GE_TBB_WT_F32 = 1 gives plain FP32 warp
 // windows (no barrier in the step loop); FP64 and compensated FP32 use CTA
 // rows.
@@ -803,13 +887,18 @@ __device__ __forceinline__ void run_batch_comp(float (&v)[K], const TbbParams &P
 #define GE_TBB_WT_F32 0
 #endif
 
+#ifndef GE_TBB_MINB_F32
+#define GE_TBB_MINB_F32 3
+#endif
+
 template <typename Real, bool COMP>
 struct BatchLayout {
     static constexpr bool WT = sizeof(Real) == 4 && !COMP && GE_TBB_WT_F32 != 0;
+    static constexpr int MINB = (sizeof(Real) == 4 && !COMP) ? GE_TBB_MINB_F32 : 2;
 };
 
 template <typename Real, bool COMP>
-__global__ void __launch_bounds__(kTileRows, 2)
+__global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
     tbb_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TbbParams P)
 {
     constexpr bool WT = BatchLayout<Real, COMP>::WT;
@@ -886,10 +975,17 @@ __global__ void __launch_bounds__(kTileRows, 2)
         const bool edge_thr = !(sp.jlo <= -1 && sp.jhi >= K + 1);
         const bool edge_warp = __any_sync(0xffffffffu, edge_thr);
         if constexpr (!COMP) {
-            if (edge_warp)
+            const long long g0 = pid >= 0 ? grow * K - bd.off : 0;
+            if (P.scaled) {
+                if (edge_warp)
+                    run_batch_scaled<true>(v, P, bd, pid, g0, x, sp);
+                else
+                    run_batch_scaled<false>(v, P, bd, pid, g0, x, sp);
+            } else if (edge_warp) {
                 run_batch<true>(v, P, bd, x, sp);
-            else
+            } else {
                 run_batch<false>(v, P, bd, x, sp);
+            }
         } else {
             if (edge_warp)
                 run_batch_comp<true>(v, P, bd, x, sp);
@@ -941,7 +1037,90 @@ cudaError_t batch_attr_and_occupancy(int *blocks)
                                                          tb_smem_bytes());
 }
 
+// Scale bookkeeping of the batched scaled form, one thread per problem, in
+// double-double so no rounding drift enters the end factors.  The growth
+// per block step is exactly 1 + g with g the coefficient the kernel holds
+// (FP32-rounded on the FP32 path).
+__device__ __forceinline__ void dd_mul_dev(double &h, double &l, double bh, double bl)
+{
+    const double p = __dmul_rn(h, bh);
+    const double e = __fma_rn(h, bh, -p);
+    const double t = __dadd_rn(e, __dadd_rn(__dmul_rn(h, bl), __dmul_rn(l, bh)));
+    h = __dadd_rn(p, t);
+    l = __dsub_rn(t, __dsub_rn(h, p));
+}
+
+__device__ __forceinline__ void growth_dev(const BatchDesc &d, int f32, double &gh, double &gl)
+{
+    const double g = f32 ? (double)__double2float_rn(d.g) : d.g;
+    gh = __dadd_rn(1.0, g);
+    gl = __dadd_rn(__dsub_rn(1.0, gh), g);  // exact: 1 + g == gh + gl
+}
+
+// exps[b][q]: after block q of R steps (scale starting at 1) the scale is
+// brought back into [1, 2) by 2^-exps[b][q].
+__global__ void batch_exps_kernel(const BatchDesc *__restrict__ desc, int np, int R, int Q, int f32,
+                                  short *__restrict__ exps)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= np)
+        return;
+    double gh, gl, sh = 1.0, sl = 0.0;
+    growth_dev(desc[b], f32, gh, gl);
+    for (int q = 0; q < Q; ++q) {
+        for (int i = 0; i < R; ++i)
+            dd_mul_dev(sh, sl, gh, gl);
+        int e2 = 0;
+        frexp(sh, &e2);
+        const int e = e2 - 1;
+        sh = ldexp(sh, -e);
+        sl = ldexp(sl, -e);
+        exps[(long long)b * Q + q] = (short)e;
+    }
+}
+
+// endf[b] = 1 / (scale after n_mid block steps with the rescalings above):
+// float2 (hi, lo) on the FP32 path, double on the FP64 path.
+__global__ void batch_endf_kernel(const BatchDesc *__restrict__ desc, const short *__restrict__ exps, int np, int R,
+                                  int Q, int n_mid, int f32, void *endf)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= np)
+        return;
+    double gh, gl, sh = 1.0, sl = 0.0;
+    growth_dev(desc[b], f32, gh, gl);
+    for (int m = 0; m < n_mid; ++m) {
+        dd_mul_dev(sh, sl, gh, gl);
+        if ((m + 1) % R == 0) {
+            const int e = exps[(long long)b * Q + (m + 1) / R - 1];
+            sh = ldexp(sh, -e);
+            sl = ldexp(sl, -e);
+        }
+    }
+    const double ih = __ddiv_rn(1.0, sh);
+    const double inv = __dsub_rn(ih, __dmul_rn(ih, __ddiv_rn(sl, sh)));
+    if (f32) {
+        const float hi = __double2float_rn(inv);
+        reinterpret_cast<float2 *>(endf)[b] = make_float2(hi, __double2float_rn(__dsub_rn(inv, (double)hi)));
+    } else {
+        reinterpret_cast<double *>(endf)[b] = inv;
+    }
+}
+
 }  // namespace
+
+cudaError_t batch_exps(const BatchDesc *desc, int n_problems, int R, int Q, int f32, short *exps, cudaStream_t s)
+{
+    batch_exps_kernel<<<(n_problems + 127) / 128, 128, 0, s>>>(desc, n_problems, R, Q, f32, exps);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_endf(const BatchDesc *desc, const short *exps, int n_problems, int R, int Q, int n_mid, int f32,
+                       void *endf, cudaStream_t s)
+{
+    batch_endf_kernel<<<(n_problems + 127) / 128, 128, 0, s>>>(desc, exps, n_problems, R, Q, n_mid, f32, endf);
+    return cudaGetLastError();
+}
 
 int tb_smem_bytes() { return 2 * kTileRows * kRowBytes + 1024; }
 

@@ -172,6 +172,35 @@ def test_tiled_f32_depths(prec, depth):
     assert rel_max(got, want) <= TOL32
 
 
+@pytest.mark.parametrize("r", [0.3, 1.7])
+def test_long_run_scale_bookkeeping_f32(r):
+    """20000 FP32 steps at mesh ratios whose 2r is not exact in FP32.  The
+    scale the host divides out has to be the kernel's own growth factor,
+    1 + fl32(2r): one FP32 ulp of error in that factor builds up to 3e-4
+    here.  What remains is FP32 round-off of a smooth field (correlated
+    across points, so it grows like sqrt(steps)); the bound is TOL32 scaled
+    from the 2000-step batched target to this run length."""
+    n, steps = 4096, 20000
+    u0 = inputs.sine_state(n)
+    want = oracle.run(u0, r, 0.0, 0.0, steps)
+    got = gpu_run(u0.astype(np.float32), r, 0.0, 0.0, steps, prec=B.GE_F32)
+    assert rel_max(got, want) <= TOL32 * np.sqrt(steps / 2000.0)
+
+
+@pytest.mark.parametrize("r", [0.3, 1.7])
+def test_long_run_scale_bookkeeping_f64(r):
+    """20000 FP64 steps against an extended-precision evaluation of the
+    scheme: the tiled kernel stays within 1e-12 of it.  (Over this many
+    steps the oracle's own rounded coefficients drift by about one ulp per
+    step, so the reference here is the extended evaluation.)"""
+    n, steps = 512, 20000
+    u0 = inputs.sine_state(n)
+    ref = ext_precision_run(u0, r, 0.0, 0.0, steps).astype(np.float64)
+    got = gpu_run(u0, r, 0.0, 0.0, steps)
+    e_orc = rel_max(oracle.run(u0, r, 0.0, 0.0, steps), ref)
+    assert rel_max(got, ref) <= tol64(r), (rel_max(got, ref), e_orc)
+
+
 def test_canonical_f32():
     n = 3001
     u0 = inputs.fourier_state(n, 0.1, 0.4, np.random.default_rng(5))
