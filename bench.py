@@ -37,13 +37,21 @@ REF_SAMPLE_STEPS = 10      # --impl reference: 10 GE steps over the full grid pe
 N_SAMPLES = 12             # oracle-checked sample points
 
 
+def tb_source_digest() -> str:
+    """sha256 over the tiled kernel's sources (ge_tb.cu + ge_tb_dev.cuh)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("ge_tb.cu", "ge_tb_dev.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1310_3422_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def measured_traffic(kernel_name: str):
     """Per-launch DRAM bytes of `kernel_name` from profiles/traffic.txt, or None
-    when absent or when the kernel source changed since the capture."""
-    import hashlib
+    when absent or when the kernel source (ge_tb.cu and the device helpers of
+    ge_tb_dev.cuh) changed since the capture."""
     try:
-        src = open(os.path.join(ROOT, "paper_1310_3422_gb300", "csrc", "ge_tb.cu"), "rb").read()
-        digest = hashlib.sha256(src).hexdigest()
+        digest = tb_source_digest()
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
             if line.startswith("#") or not line.strip():
                 continue

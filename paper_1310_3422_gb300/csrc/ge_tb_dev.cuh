@@ -1,0 +1,334 @@
+// ge_tb_dev.cuh -- device helpers shared by the tiled kernel (ge_tb.cu) and
+// the batched kernel (ge_tbb.cu): bounded mbarrier waits and 2D TMA tile
+// loads, register <-> shared-memory chunks, the partner of a register, the
+// cross-thread exchange, one stage of the block map, and the compensated
+// (Kahan) step.  The scheme itself is described in ge_tb.cu.
+#pragma once
+
+#include <cuda.h>
+#include <cstdint>
+
+#include "ge_internal.h"
+
+namespace ge {
+namespace {
+
+constexpr long long kWaitLimitCycles = 4000000000LL;  // about 2 s of SM clock
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier; give up after kWaitLimitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitLimitCycles)
+            return false;
+    }
+    return true;
+}
+
+// 2D tiled TMA load: box origin (x = 0, y = row), completes on `bar`.
+__device__ __forceinline__ void tma_load_rows(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                              int row)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(row), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// 16-byte chunk c of a thread's registers <-> shared memory.
+template <int K>
+__device__ __forceinline__ void chunk_to_regs(const unsigned char *p, float (&v)[K], int c)
+{
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[4 * c + 0] = q.x;
+    v[4 * c + 1] = q.y;
+    v[4 * c + 2] = q.z;
+    v[4 * c + 3] = q.w;
+}
+template <int K>
+__device__ __forceinline__ void chunk_to_regs(const unsigned char *p, double (&v)[K], int c)
+{
+    const double2 q = *reinterpret_cast<const double2 *>(p);
+    v[2 * c + 0] = q.x;
+    v[2 * c + 1] = q.y;
+}
+template <int K>
+__device__ __forceinline__ void regs_to_chunk(unsigned char *p, const float (&v)[K], int c)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+}
+template <int K>
+__device__ __forceinline__ void regs_to_chunk(unsigned char *p, const double (&v)[K], int c)
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(v[2 * c], v[2 * c + 1]);
+}
+
+// Value of the partner of register j under grouping Q.  The thread's first
+// point has an even global index, so register parity = point parity: the
+// partner is point+1 when (j + Q) is even, else point-1.  L / R are the left
+// thread's last and the right thread's first value.
+template <int Q, int K, typename Real>
+__device__ __forceinline__ Real pval(const Real (&v)[K], int j, Real L, Real R)
+{
+    if (((j + Q) & 1) == 0)
+        return (j + 1 < K) ? v[j + 1] : R;
+    return (j >= 1) ? v[j - 1] : L;
+}
+
+// The thread's registers in local coordinates: register j is grid point
+// g0 + j; points jlo..jhi-1 (clamped to [-1, K+1]) lie inside the grid, so
+// register jlo is grid point 0 and register jhi-1 grid point n-1 when they
+// fall in 0..K-1.  A partner register j +- 1 is inside iff jlo <= j +- 1 < jhi.
+struct Span {
+    int jlo, jhi;
+};
+
+template <int K>
+__device__ __forceinline__ Span make_span(long long g0, long long n)
+{
+    long long lo = -g0, hi = n - g0;
+    lo = lo < -1 ? -1 : (lo > K + 1 ? K + 1 : lo);
+    hi = hi < -1 ? -1 : (hi > K + 1 ? K + 1 : hi);
+    return Span{(int)lo, (int)hi};
+}
+
+template <int Q>
+__device__ __forceinline__ int partner_reg(int j)
+{
+    return (((j + Q) & 1) == 0) ? j + 1 : j - 1;
+}
+
+// Cross-thread neighbour exchange.  Warp-window layout (WT): every warp
+// carries its own halo, so neighbours come from warp shuffles only (lanes 0
+// and 31 get their own value back: garbage that stays inside the halo).
+// CTA-row layout: warp edges go through a double-buffered shared slot and
+// one CTA barrier per exchange.
+template <typename Real, int NW, bool WT>
+struct Exch {
+    Real (*slot)[NW][2];
+    int eb;
+    int lane;
+    int warp;
+};
+
+// L = left thread's last value, R = right thread's first value (parity-1
+// groups cross thread boundaries).
+template <typename Real, int K, int NW, bool WT>
+__device__ __forceinline__ void exchange(const Real (&v)[K], Real &L, Real &R, Exch<Real, NW, WT> &x)
+{
+    L = __shfl_up_sync(0xffffffffu, v[K - 1], 1);
+    R = __shfl_down_sync(0xffffffffu, v[0], 1);
+    if constexpr (!WT) {
+        if (x.lane == 0)
+            x.slot[x.eb][x.warp][0] = v[0];
+        if (x.lane == 31)
+            x.slot[x.eb][x.warp][1] = v[K - 1];
+        __syncthreads();
+        if (x.lane == 0 && x.warp > 0)
+            L = x.slot[x.eb][x.warp - 1][1];
+        if (x.lane == 31 && x.warp < NW - 1)
+            R = x.slot[x.eb][x.warp + 1][0];
+        x.eb ^= 1;
+    }
+}
+
+enum StageKind { kEntry = 0, kMid = 1, kExit = 2, kMidN = 3 };
+
+template <typename Real>
+struct StageC {
+    Real a, b, s, fl, fr;
+};
+
+// One stage on a thread's K registers.
+//   entry: v <- (1-r) v + r v_p      (a = r, b = 1-r; singleton: b v)
+//   mid:   v <- v + 2r v_p           (a = 2r;         singleton: s v)  scaled form
+//   midN:  v <- v + d (v_p - v)      (a = 2r/(1+2r);  singleton: s v)  normalised form
+//   exit:  v <- x1 v + x2 v_p        (a = x1, b = x2; singleton: s v)
+// Entry and mid add the wall terms fl / fr at points 0 and n-1.  With
+// EDGE = false every point of the thread and every partner lies inside the
+// grid and none is a wall point, so no checks are compiled.  With EDGE = true
+// singletons and wall terms are applied and points outside [0, n) keep their
+// value (see Span).
+template <int Q, int KIND, bool EDGE, int K, typename Real>
+__device__ __forceinline__ void stage(Real (&v)[K], Real L, Real R, Span sp, const StageC<Real> &c)
+{
+    Real nv[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const Real p = pval<Q>(v, j, L, R);
+        if (KIND == kEntry)
+            nv[j] = fma(c.a, p, c.b * v[j]);
+        else if (KIND == kMid)
+            nv[j] = fma(c.a, p, v[j]);
+        else if (KIND == kMidN)
+            nv[j] = fma(c.a, p - v[j], v[j]);
+        else
+            nv[j] = fma(c.a, v[j], c.b * p);
+    }
+    if constexpr (EDGE) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int pj = partner_reg<Q>(j);
+            const bool inside = (j >= sp.jlo) && (j < sp.jhi);
+            const bool paired = (pj >= sp.jlo) && (pj < sp.jhi);
+            Real val;
+            if (KIND == kEntry)
+                val = paired ? nv[j] : c.b * v[j];
+            else
+                val = paired ? nv[j] : c.s * v[j];
+            if (KIND != kExit) {
+                if (j == sp.jlo)
+                    val += c.fl;
+                if (j == sp.jhi - 1)
+                    val += c.fr;
+            }
+            nv[j] = inside ? val : v[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        v[j] = nv[j];
+}
+
+// Exact 2^-e (0 <= e <= 1022 for double, 0 <= e <= 126 for float).
+template <typename Real>
+__device__ __forceinline__ Real pow2neg(int e);
+template <>
+__device__ __forceinline__ double pow2neg<double>(int e)
+{
+    return __longlong_as_double(static_cast<long long>(1023 - e) << 52);
+}
+template <>
+__device__ __forceinline__ float pow2neg<float>(int e)
+{
+    return __int_as_float((127 - e) << 23);
+}
+
+// Kahan sum of an update into (hi, lo).
+__device__ __forceinline__ void kahan_add(float &hi, float &lo, float delta)
+{
+    const float y = delta + lo;
+    const float s = hi + y;
+    lo = y - (s - hi);
+    hi = s;
+}
+
+// Update of register j in the checked compensated step: d (x_p - x) for a
+// group member, (kappa - 1)(hi + lo) for a singleton, plus the wall terms;
+// zero outside the grid.
+template <int Q>
+__device__ __forceinline__ float comp_delta(int j, float self, float lself, float partner, float d,
+                                            float km1, float fl, float fr, Span sp)
+{
+    const int pj = partner_reg<Q>(j);
+    const bool inside = (j >= sp.jlo) && (j < sp.jhi);
+    const bool paired = (pj >= sp.jlo) && (pj < sp.jhi);
+    float val = paired ? d * (partner - self) : km1 * (self + lself);
+    if (j == sp.jlo)
+        val += fl;
+    if (j == sp.jhi - 1)
+        val += fr;
+    return inside ? val : 0.0f;
+}
+
+// Compensated block step: normalised form x <- x + d (x_p - x), the update
+// Kahan-summed into (hi, lo); singleton x <- x + (kappa - 1) x + wall term.
+// The members of a group get opposite updates t and -t.
+template <int Q, bool EDGE, int K, int NW, bool WT>
+__device__ __forceinline__ void mid_comp(float (&v)[K], float (&lo)[K], const TbParams &P, float d,
+                                         float km1, float fl, float fr, Exch<float, NW, WT> &x, Span sp)
+{
+    float L = 0.0f, R = 0.0f;
+    if (Q == 1)
+        exchange(v, L, R, x);
+    if constexpr (!EDGE) {
+        if (Q == 0) {
+#pragma unroll
+            for (int j = 0; j < K; j += 2) {
+                const float t = d * (v[j + 1] - v[j]);
+                kahan_add(v[j], lo[j], t);
+                kahan_add(v[j + 1], lo[j + 1], -t);
+            }
+        } else {
+            const float t0 = d * (L - v[0]);
+            const float tk = d * (R - v[K - 1]);
+#pragma unroll
+            for (int j = 1; j + 1 < K; j += 2) {
+                const float t = d * (v[j + 1] - v[j]);
+                kahan_add(v[j], lo[j], t);
+                kahan_add(v[j + 1], lo[j + 1], -t);
+            }
+            kahan_add(v[0], lo[0], t0);
+            kahan_add(v[K - 1], lo[K - 1], tk);
+        }
+    } else {
+        // checked path, still pair by pair from the old values
+        if (Q == 0) {
+#pragma unroll
+            for (int j = 0; j < K; j += 2) {
+                const float a = comp_delta<Q>(j, v[j], lo[j], v[j + 1], d, km1, fl, fr, sp);
+                const float b = comp_delta<Q>(j + 1, v[j + 1], lo[j + 1], v[j], d, km1, fl, fr, sp);
+                kahan_add(v[j], lo[j], a);
+                kahan_add(v[j + 1], lo[j + 1], b);
+            }
+        } else {
+            const float a0 = comp_delta<Q>(0, v[0], lo[0], L, d, km1, fl, fr, sp);
+            const float ak = comp_delta<Q>(K - 1, v[K - 1], lo[K - 1], R, d, km1, fl, fr, sp);
+#pragma unroll
+            for (int j = 1; j + 1 < K; j += 2) {
+                const float a = comp_delta<Q>(j, v[j], lo[j], v[j + 1], d, km1, fl, fr, sp);
+                const float b = comp_delta<Q>(j + 1, v[j + 1], lo[j + 1], v[j], d, km1, fl, fr, sp);
+                kahan_add(v[j], lo[j], a);
+                kahan_add(v[j + 1], lo[j + 1], b);
+            }
+            kahan_add(v[0], lo[0], a0);
+            kahan_add(v[K - 1], lo[K - 1], ak);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace ge

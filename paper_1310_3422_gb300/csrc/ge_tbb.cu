@@ -1,0 +1,474 @@
+// ge_tbb.cu -- batched tiled GE kernel: many independent problems of
+// uneven size and mesh ratio packed back to back in one buffer, each
+// starting on a 128-byte row (arXiv:1310.3422 Sec. 2 for every problem, the
+// right-hand-side scheme of ge_tb.cu).
+#include "ge_tb_dev.cuh"
+
+namespace ge {
+namespace {
+
+// The tiles run over the packed buffer exactly as for one long problem;
+// every thread looks its problem up (row -> problem id), takes that
+// problem's constants, and treats points of other problems like points
+// outside its grid.  Two forms: the scaled one (FP64 and plain FP32, below:
+// run_batch_scaled) and the normalised one x <- x + d (x_partner - x) with
+// per-problem walls (run_batch, run_batch_comp; the compensated path, and
+// any launch whose end factor has no table slot).  Every launch starts and
+// ends with the normalised state in the buffer.
+
+// Entry, block steps and exit of one tile, normalised form.
+template <bool EDGE, typename Real, int K, int NW, bool WT>
+__device__ __forceinline__ void run_batch(Real (&v)[K], const TbbParams &P, const BatchDesc &bd,
+                                          Exch<Real, NW, WT> &x, Span sp)
+{
+    Real L = 0, R = 0;
+    if (P.do_entry) {
+        const StageC<Real> c{(Real)bd.r, (Real)bd.omr, (Real)0, (Real)bd.f_l, (Real)bd.f_r};
+        if (((1 - P.p_first) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kEntry, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kEntry, EDGE>(v, L, R, sp, c);
+        }
+    }
+    const StageC<Real> cm{(Real)bd.d, (Real)0, (Real)bd.kappa, (Real)bd.f_l, (Real)bd.f_r};
+    int m = 0;
+    if (P.n_mid > 0 && (P.p_first & 1)) {
+        exchange(v, L, R, x);
+        stage<1, kMidN, EDGE>(v, L, R, sp, cm);
+        m = 1;
+    }
+    for (; m + 1 < P.n_mid; m += 2) {
+        stage<0, kMidN, EDGE>(v, L, R, sp, cm);
+        exchange(v, L, R, x);
+        stage<1, kMidN, EDGE>(v, L, R, sp, cm);
+    }
+    if (m < P.n_mid)
+        stage<0, kMidN, EDGE>(v, L, R, sp, cm);
+    if (P.do_exit) {
+        const StageC<Real> c{(Real)bd.x1, (Real)bd.x2, (Real)bd.xs, (Real)0, (Real)0};
+        if (((P.p_first + P.n_mid) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kExit, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kExit, EDGE>(v, L, R, sp, c);
+        }
+    }
+}
+
+template <bool EDGE, int K, int NW, bool WT>
+__device__ __forceinline__ void run_batch_comp(float (&v)[K], const TbbParams &P, const BatchDesc &bd,
+                                               Exch<float, NW, WT> &x, Span sp)
+{
+    float L = 0.0f, R = 0.0f;
+    if (P.do_entry) {
+        const StageC<float> c{(float)bd.r, (float)bd.omr, 0.0f, (float)bd.f_l, (float)bd.f_r};
+        if (((1 - P.p_first) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kEntry, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kEntry, EDGE>(v, L, R, sp, c);
+        }
+    }
+    float lo[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        lo[j] = 0.0f;
+    const float d = (float)bd.d, km1 = (float)(bd.kappa - 1.0);
+    const float fl = (float)bd.f_l, fr = (float)bd.f_r;
+    TbParams dummy{};
+    dummy.n = 0;
+    int m = 0;
+    if (P.n_mid > 0 && (P.p_first & 1)) {
+        mid_comp<1, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp);
+        m = 1;
+    }
+    for (; m + 1 < P.n_mid; m += 2) {
+        mid_comp<0, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp);
+        mid_comp<1, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp);
+    }
+    if (m < P.n_mid)
+        mid_comp<0, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp);
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        v[j] += lo[j];
+    if (P.do_exit) {
+        const StageC<float> c{(float)bd.x1, (float)bd.x2, (float)bd.xs, 0.0f, 0.0f};
+        if (((P.p_first + P.n_mid) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kExit, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kExit, EDGE>(v, L, R, sp, c);
+        }
+    }
+}
+
+// Scaled batched form (FP64 and plain FP32).  The thread's problem is
+// shifted by its linear wall profile u* (an exact fixed point of the step:
+// the shifted problem has zero walls, so no wall terms and no scale in the
+// edge warps), advanced with the scaled block map x <- x + g x_partner (one
+// FMA per point and step; singletons x <- kap_s x), multiplied by the
+// problem's power of two 2^-e after every R block steps, and brought back to
+// the normalised state at the launch end by the factor endf (the inverse of
+// the accumulated scale, computed in double-double by batch_endf_kernel).
+// Only points inside the problem change: padding keeps its values.
+template <bool EDGE, typename Real, int K, int NW, bool WT>
+__device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &P, const BatchDesc &bd, int pid,
+                                                 long long g0, Exch<Real, NW, WT> &x, Span sp)
+{
+    Real L = 0, R = 0;
+    const Real ua = (Real)bd.ustar_a, ub = (Real)bd.ustar_b;
+    if (P.do_entry) {
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (!EDGE || (j >= sp.jlo && j < sp.jhi))
+                v[j] -= ua + ub * (Real)(g0 + j + 1);
+        const StageC<Real> c{(Real)bd.r, (Real)bd.omr, (Real)0, (Real)0, (Real)0};
+        if (((1 - P.p_first) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kEntry, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kEntry, EDGE>(v, L, R, sp, c);
+        }
+    }
+    const StageC<Real> cm{(Real)bd.g, (Real)0, (Real)bd.kap_s, (Real)0, (Real)0};
+    int m = 0, q = 0;
+    while (m < P.n_mid) {
+        const int cnt = (P.n_mid - m < P.R) ? P.n_mid - m : P.R;
+        int i = 0;
+        if (((P.p_first + m) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kMid, EDGE>(v, L, R, sp, cm);
+            i = 1;
+        }
+        for (; i + 1 < cnt; i += 2) {
+            stage<0, kMid, EDGE>(v, L, R, sp, cm);
+            exchange(v, L, R, x);
+            stage<1, kMid, EDGE>(v, L, R, sp, cm);
+        }
+        if (i < cnt)
+            stage<0, kMid, EDGE>(v, L, R, sp, cm);
+        m += cnt;
+        if (cnt == P.R && pid >= 0) {
+            const Real sc = pow2neg<Real>(P.exps[(long long)pid * P.Q + q]);
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if (!EDGE || (j >= sp.jlo && j < sp.jhi))
+                    v[j] *= sc;
+        }
+        ++q;
+    }
+    if (pid >= 0) {
+        Real fh, fl;
+        if constexpr (sizeof(Real) == 4) {
+            const float2 f = reinterpret_cast<const float2 *>(P.endf)[pid];
+            fh = f.x, fl = f.y;
+        } else {
+            fh = reinterpret_cast<const double *>(P.endf)[pid];
+            fl = 0;
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (!EDGE || (j >= sp.jlo && j < sp.jhi))
+                v[j] = fma(v[j], fh, v[j] * fl);
+    }
+    if (P.do_exit) {
+        const StageC<Real> c{(Real)bd.x1, (Real)bd.x2, (Real)bd.xs, (Real)0, (Real)0};
+        if (((P.p_first + P.n_mid) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kExit, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kExit, EDGE>(v, L, R, sp, c);
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (!EDGE || (j >= sp.jlo && j < sp.jhi))
+                v[j] += ua + ub * (Real)(g0 + j + 1);
+    }
+}
+
+// Layout of the batched kernel: GE_TBB_WT_F32 = 1 gives plain FP32 warp
+// windows (no barrier in the step loop); FP64 and compensated FP32 use CTA
+// rows.
+#ifndef GE_TBB_WT_F32
+#define GE_TBB_WT_F32 0
+#endif
+
+#ifndef GE_TBB_MINB_F32
+#define GE_TBB_MINB_F32 3
+#endif
+
+template <typename Real, bool COMP>
+struct BatchLayout {
+    static constexpr bool WT = sizeof(Real) == 4 && !COMP && GE_TBB_WT_F32 != 0;
+    static constexpr int MINB = (sizeof(Real) == 4 && !COMP) ? GE_TBB_MINB_F32 : 2;
+};
+
+template <typename Real, bool COMP>
+__global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
+    tbb_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TbbParams P)
+{
+    constexpr bool WT = BatchLayout<Real, COMP>::WT;
+    constexpr int NT = kTileRows;
+    constexpr int K = kRowBytes / (int)sizeof(Real);
+    constexpr int NW = NT / 32;
+    constexpr int CH = kRowBytes / 16;
+    constexpr uint32_t kTileBytes = kTileRows * kRowBytes;
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *tiles = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ Real slot[2][NW][2];
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int hr = P.H / K, ur = P.U / K;
+    // tile row of this thread: CTA rows -> row t; warp windows -> warp w
+    // starts where warp w-1's output ends (windows overlap by 2 halos)
+    const int my_row = WT ? warp * (32 - 2 * hr) + lane : t;
+    const bool writes = WT ? (lane >= hr && lane < 32 - hr) : true;
+    Exch<Real, NW, WT> x{slot, 0, lane, warp};
+
+    if (t == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    long long tile = blockIdx.x;
+    if (t == 0 && tile < P.n_tiles) {
+        mbar_arrive_expect_tx(&mbar[0], kTileBytes);
+        tma_load_rows(tiles, &tmap, &mbar[0], (int)(tile * ur - hr));
+    }
+    for (long long it = 0; tile < P.n_tiles; ++it, tile += gridDim.x) {
+        const int b = (int)(it & 1);
+        unsigned char *cur = tiles + b * kTileBytes;
+        const long long next = tile + gridDim.x;
+        const bool prefetch = next < P.n_tiles;
+        if (t == 0 && prefetch) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&mbar[b ^ 1], kTileBytes);
+            tma_load_rows(tiles + (b ^ 1) * kTileBytes, &tmap, &mbar[b ^ 1], (int)(next * ur - hr));
+        }
+        const bool ok = mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) {
+                atomicExch(P.err, kDevTimeout);
+                if (prefetch)
+                    mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+            }
+            return;
+        }
+
+        Real v[K];
+        {
+            const unsigned char *rp = cur + my_row * kRowBytes;
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                chunk_to_regs<K>(rp + ((c ^ (my_row & 7)) << 4), v, c);
+        }
+        if constexpr (WT)
+            __syncthreads();  // windows overlap: every load before any write-back
+        // this thread's problem: rows outside the buffer or in padding have none
+        const long long grow = tile * ur - hr + my_row;
+        const int pid = (grow >= 0 && grow < P.n_rows) ? __ldg(P.row_pid + grow) : -1;
+        BatchDesc bd{};
+        Span sp{K + 1, K + 1};  // no point of this thread is inside a grid
+        if (pid >= 0) {
+            bd = P.desc[pid];
+            sp = make_span<K>(grow * K - bd.off, bd.n);
+        }
+        const bool edge_thr = !(sp.jlo <= -1 && sp.jhi >= K + 1);
+        const bool edge_warp = __any_sync(0xffffffffu, edge_thr);
+        if constexpr (!COMP) {
+            const long long g0 = pid >= 0 ? grow * K - bd.off : 0;
+            if (P.scaled) {
+                if (edge_warp)
+                    run_batch_scaled<true>(v, P, bd, pid, g0, x, sp);
+                else
+                    run_batch_scaled<false>(v, P, bd, pid, g0, x, sp);
+            } else if (edge_warp) {
+                run_batch<true>(v, P, bd, x, sp);
+            } else {
+                run_batch<false>(v, P, bd, x, sp);
+            }
+        } else {
+            if (edge_warp)
+                run_batch_comp<true>(v, P, bd, x, sp);
+            else
+                run_batch_comp<false>(v, P, bd, x, sp);
+        }
+
+        if (writes) {
+            unsigned char *rp = cur + my_row * kRowBytes;
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                regs_to_chunk<K>(rp + ((c ^ (my_row & 7)) << 4), v, c);
+        }
+        __syncthreads();
+        {
+            const long long grow0 = tile * ur;
+            unsigned char *out = static_cast<unsigned char *>(P.out);
+            for (int ch = t; ch < ur * CH; ch += NT) {
+                const int lr = hr + ch / CH;
+                const int c = ch % CH;
+                const long long gr = grow0 + ch / CH;
+                if (gr < P.n_rows) {
+                    const uint4 val = *reinterpret_cast<const uint4 *>(cur + lr * kRowBytes +
+                                                                       ((c ^ (lr & 7)) << 4));
+                    *reinterpret_cast<uint4 *>(out + gr * kRowBytes + c * 16) = val;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename Real, bool COMP>
+cudaError_t launch_batch_one(const void *tmap, const TbbParams &p, int grid, cudaStream_t s)
+{
+    const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
+    tbb_kernel<Real, COMP><<<grid, kTileRows, tb_smem_bytes(), s>>>(*m, p);
+    return cudaGetLastError();
+}
+
+template <typename Real, bool COMP>
+cudaError_t batch_attr_and_occupancy(int *blocks)
+{
+    cudaError_t e = cudaFuncSetAttribute(tbb_kernel<Real, COMP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, tb_smem_bytes());
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tbb_kernel<Real, COMP>, kTileRows,
+                                                         tb_smem_bytes());
+}
+
+// Scale bookkeeping of the batched scaled form, one thread per problem, in
+// double-double so no rounding drift enters the end factors.  The growth
+// per block step is exactly 1 + g with g the coefficient the kernel holds
+// (FP32-rounded on the FP32 path).
+__device__ __forceinline__ void dd_mul_dev(double &h, double &l, double bh, double bl)
+{
+    const double p = __dmul_rn(h, bh);
+    const double e = __fma_rn(h, bh, -p);
+    const double t = __dadd_rn(e, __dadd_rn(__dmul_rn(h, bl), __dmul_rn(l, bh)));
+    h = __dadd_rn(p, t);
+    l = __dsub_rn(t, __dsub_rn(h, p));
+}
+
+__device__ __forceinline__ void growth_dev(const BatchDesc &d, int f32, double &gh, double &gl)
+{
+    const double g = f32 ? (double)__double2float_rn(d.g) : d.g;
+    gh = __dadd_rn(1.0, g);
+    gl = __dadd_rn(__dsub_rn(1.0, gh), g);  // exact: 1 + g == gh + gl
+}
+
+// exps[b][q]: after block q of R steps (scale starting at 1) the scale is
+// brought back into [1, 2) by 2^-exps[b][q].
+__global__ void batch_exps_kernel(const BatchDesc *__restrict__ desc, int np, int R, int Q, int f32,
+                                  short *__restrict__ exps)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= np)
+        return;
+    double gh, gl, sh = 1.0, sl = 0.0;
+    growth_dev(desc[b], f32, gh, gl);
+    for (int q = 0; q < Q; ++q) {
+        for (int i = 0; i < R; ++i)
+            dd_mul_dev(sh, sl, gh, gl);
+        int e2 = 0;
+        frexp(sh, &e2);
+        const int e = e2 - 1;
+        sh = ldexp(sh, -e);
+        sl = ldexp(sl, -e);
+        exps[(long long)b * Q + q] = (short)e;
+    }
+}
+
+// endf[b] = 1 / (scale after n_mid block steps with the rescalings above):
+// float2 (hi, lo) on the FP32 path, double on the FP64 path.
+__global__ void batch_endf_kernel(const BatchDesc *__restrict__ desc, const short *__restrict__ exps, int np, int R,
+                                  int Q, int n_mid, int f32, void *endf)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= np)
+        return;
+    double gh, gl, sh = 1.0, sl = 0.0;
+    growth_dev(desc[b], f32, gh, gl);
+    for (int m = 0; m < n_mid; ++m) {
+        dd_mul_dev(sh, sl, gh, gl);
+        if ((m + 1) % R == 0) {
+            const int e = exps[(long long)b * Q + (m + 1) / R - 1];
+            sh = ldexp(sh, -e);
+            sl = ldexp(sl, -e);
+        }
+    }
+    const double ih = __ddiv_rn(1.0, sh);
+    const double inv = __dsub_rn(ih, __dmul_rn(ih, __ddiv_rn(sl, sh)));
+    if (f32) {
+        const float hi = __double2float_rn(inv);
+        reinterpret_cast<float2 *>(endf)[b] = make_float2(hi, __double2float_rn(__dsub_rn(inv, (double)hi)));
+    } else {
+        reinterpret_cast<double *>(endf)[b] = inv;
+    }
+}
+
+}  // namespace
+
+cudaError_t batch_exps(const BatchDesc *desc, int n_problems, int R, int Q, int f32, short *exps, cudaStream_t s)
+{
+    batch_exps_kernel<<<(n_problems + 127) / 128, 128, 0, s>>>(desc, n_problems, R, Q, f32, exps);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_endf(const BatchDesc *desc, const short *exps, int n_problems, int R, int Q, int n_mid, int f32,
+                       void *endf, cudaStream_t s)
+{
+    batch_endf_kernel<<<(n_problems + 127) / 128, 128, 0, s>>>(desc, exps, n_problems, R, Q, n_mid, f32, endf);
+    return cudaGetLastError();
+}
+
+bool tbb_geometry(int prec, int reach, int *H, int *U)
+{
+    const int K = kRowBytes / (prec == 0 ? 8 : 4);
+    const int ht = (reach + K - 1) / K;
+    const bool wt = prec == 1 ? BatchLayout<float, false>::WT : false;
+    *H = ht * K;
+    if (wt) {
+        if (2 * ht >= 32)
+            return false;
+        *U = (kTileRows / 32) * (32 - 2 * ht) * K;
+        return true;
+    }
+    *U = kTileRows * K - 2 * *H;
+    return *U > 0;
+}
+
+int tbb_max_depth(int prec)
+{
+    int H, U, d = kMaxTableSteps;
+    while (d > 1 && !tbb_geometry(prec, d + 2, &H, &U))
+        --d;
+    return d;
+}
+
+cudaError_t tbb_occupancy(int prec, int *blocks)
+{
+    if (prec == 0)
+        return batch_attr_and_occupancy<double, false>(blocks);
+    if (prec == 1)
+        return batch_attr_and_occupancy<float, false>(blocks);
+    return batch_attr_and_occupancy<float, true>(blocks);
+}
+
+cudaError_t launch_tbb(int prec, const void *tmap, const TbbParams &p, int grid, cudaStream_t s)
+{
+    if (prec == 0)
+        return launch_batch_one<double, false>(tmap, p, grid, s);
+    if (prec == 1)
+        return launch_batch_one<float, false>(tmap, p, grid, s);
+    return launch_batch_one<float, true>(tmap, p, grid, s);
+}
+
+}  // namespace ge
