@@ -7,6 +7,7 @@ import pytest
 import torch
 
 import oracle
+from ext_reference import ext_precision_run
 from paper_1310_3422_gb300 import binding as B
 from paper_1310_3422_gb300 import inputs
 
@@ -138,3 +139,58 @@ def test_uneven_batch_full_size_sampled(prec):
         o, n = bt.offsets[i], bt.n[i]
         want = oracle.run(bt.u0[o:o + n], bt.r[i], bt.beta_l[i], bt.beta_r[i], 2000)
         assert rel(got[o:o + n], want) <= tol(prec, bt.r[i]), (i, n, bt.r[i])
+
+
+@pytest.mark.parametrize("prec", [B.GE_F64, B.GE_F32])
+def test_end_factor_slots_exhausted_use_the_normalised_form(prec):
+    """Runs of 1..70 steps: every distinct launch length takes an end-factor
+    slot of the scaled form; past the 64 slots the launches fall back to the
+    normalised form.  Each run starts from step counter 0."""
+    n, r, bl, br, offs, total, u = make_batch([37, 200, 64, 5], seed=11)
+    x = torch.from_numpy(u).to(DEV, B.dtype_of(prec))
+    plan = B.ge_batch_create(n, r, bl, br, offs, total, prec)
+    B.ge_batch_set_depth(plan, 128)
+    want = [u[offs[i]:offs[i] + n[i]].copy() for i in range(len(n))]
+    for steps in range(1, 71):
+        B.ge_batch_run(plan, x, steps)
+        want = [oracle.run(want[i], r[i], bl[i], br[i], steps) for i in range(len(n))]
+    B.ge_batch_sync(plan)
+    got = x.double().cpu().numpy()
+    for i in range(len(n)):
+        assert rel(got[offs[i]:offs[i] + n[i]], want[i]) <= tol(prec, r[i]), i
+
+
+@pytest.mark.parametrize("prec,r_hi", [(B.GE_F64, 300.0), (B.GE_F32, 30.0)])
+def test_batch_large_r_rescales_often(prec, r_hi):
+    """Large mesh ratios shorten the rescaling interval of the scaled form.
+    Tolerances scale with the step's max-norm 2r - 1, as for one problem
+    (FP32: relative to the batched workload's r <= 4)."""
+    n, r, bl, br, offs, total, u = make_batch([900, 4000, 33], seed=12, r_lo=r_hi / 2, r_hi=r_hi)
+    x = torch.from_numpy(u).to(DEV, B.dtype_of(prec))
+    plan = B.ge_batch_create(n, r, bl, br, offs, total, prec)
+    B.ge_batch_run(plan, x, 150)
+    B.ge_batch_sync(plan)
+    got = x.double().cpu().numpy()
+    for i in range(len(n)):
+        want = oracle.run(u[offs[i]:offs[i] + n[i]], r[i], bl[i], br[i], 150)
+        t = tol(prec, r[i]) if prec == B.GE_F64 else 1e-5 * max(1.0, (2 * r[i] - 1) / 7.0)
+        assert rel(got[offs[i]:offs[i] + n[i]], want) <= t, (i, r[i])
+
+
+def test_batch_huge_r_error_is_conditioning():
+    """At r ~ 3e4 (rescaling after every block step in FP64) the scheme
+    barely damps its highest mode, so every FP64 evaluation carries
+    round-off of order (2r - 1) eps per step: the batched kernel stays as
+    close to an extended-precision evaluation as the oracle itself."""
+    n, r, bl, br, offs, total, u = make_batch([900, 33], seed=12, r_lo=2.5e4, r_hi=5.0e4)
+    x = torch.from_numpy(u).to(DEV)
+    plan = B.ge_batch_create(n, r, bl, br, offs, total, B.GE_F64)
+    B.ge_batch_run(plan, x, 100)
+    B.ge_batch_sync(plan)
+    got = x.cpu().numpy()
+    for i in range(len(n)):
+        u0 = u[offs[i]:offs[i] + n[i]]
+        ref = ext_precision_run(u0, r[i], bl[i], br[i], 100).astype(np.float64)
+        e_orc = rel(oracle.run(u0, r[i], bl[i], br[i], 100), ref)
+        e_gpu = rel(got[offs[i]:offs[i] + n[i]], ref)
+        assert e_gpu <= 4.0 * e_orc + 1e-15, (i, e_gpu, e_orc)
