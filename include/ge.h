@@ -121,7 +121,8 @@ ge_status ge_step_n(ge_ctx *ctx, int64_t steps);
 ge_status ge_read_state(ge_ctx *ctx, void *out_dev);
 
 /* Replace the state by in_dev (n elements) and set the step counter to
- * step_count >= 0 (resume from a checkpoint).  Asynchronous.
+ * step_count >= 0 (resume from a checkpoint).  Also clears a recorded
+ * device failure (the state it spoiled is replaced).  Asynchronous.
  * Errors: GE_EINVAL, GE_ECUDA. */
 ge_status ge_write_state(ge_ctx *ctx, const void *in_dev, int64_t step_count);
 
@@ -129,8 +130,18 @@ ge_status ge_write_state(ge_ctx *ctx, const void *in_dev, int64_t step_count);
 ge_status ge_get_step(const ge_ctx *ctx, int64_t *step_count);
 
 /* Wait for the context's stream and report deferred device errors
- * (GE_ETIMEOUT) and launch errors (GE_ECUDA). */
+ * (GE_ETIMEOUT) and launch errors (GE_ECUDA).  A GE_ETIMEOUT stays reported
+ * (the state is not valid) until ge_write_state replaces the state. */
 ge_status ge_sync(ge_ctx *ctx);
+
+/* Diagnostic (failure handling without a GPU fault): with cycles > 0 every
+ * tile-load wait of the context's tiled launches polls a barrier that
+ * nothing arrives on, gives up after `cycles` SM clock cycles, and takes the
+ * path of a tile load that never completes: the kernel records GE_ETIMEOUT,
+ * lets its own copies in flight land (each within the normal limit of about
+ * 2 s) and returns, so the context stays usable.  cycles = 0 turns it off.
+ * Errors: GE_EINVAL (NULL ctx, cycles < 0). */
+ge_status ge_debug_stall(ge_ctx *ctx, int64_t cycles);
 
 /* Release the context and its buffers (after finishing its stream's work).
  * NULL is a no-op. */
@@ -188,8 +199,18 @@ ge_status ge_batch_tune(ge_batch *plan, const void *u_dev, int64_t steps, int32_
  * only, so a CUDA graph may capture it.  Errors: GE_EINVAL, GE_ECUDA. */
 ge_status ge_batch_run(ge_batch *plan, void *u_dev, int64_t steps);
 
-/* Wait for the plan's stream; report deferred device errors (GE_ETIMEOUT). */
+/* Wait for the plan's stream; report deferred device errors (GE_ETIMEOUT),
+ * then clear them (every run starts again from the caller's buffer). */
 ge_status ge_batch_sync(ge_batch *plan);
+
+/* Scan the packed buffer u_dev (the plan's layout and type) for NaN and Inf:
+ * status_dev[b] (device, n_problems int32, caller-owned) receives GE_OK or
+ * GE_ENONFINITE for problem b.  Only values inside problems are read.
+ * Asynchronous on the plan's stream.  Errors: GE_EINVAL, GE_ECUDA. */
+ge_status ge_batch_check(ge_batch *plan, const void *u_dev, int32_t *status_dev);
+
+/* Diagnostic, as ge_debug_stall for the plan's launches. */
+ge_status ge_batch_debug_stall(ge_batch *plan, int64_t cycles);
 
 /* Release the plan (NULL is a no-op). */
 void ge_batch_destroy(ge_batch *plan);

@@ -26,7 +26,8 @@ GE_KERNEL_AUTO, GE_KERNEL_CANONICAL, GE_KERNEL_ONESTEP, GE_KERNEL_TEMPORAL = 0, 
 EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", "ge_read_state", "ge_write_state",
            "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_batch_create", "ge_batch_set_depth",
            "ge_batch_get_depth", "ge_batch_tune", "ge_batch_run", "ge_batch_sync", "ge_batch_destroy",
-           "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error",
+           "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error", "ge_debug_stall",
+           "ge_batch_debug_stall", "ge_batch_check",
            "ge_sno_create", "ge_sno_num_params", "ge_sno_get_params", "ge_sno_set_params",
            "ge_sno_set_precision", "ge_sno_forward", "ge_sno_loss_grad", "ge_sno_adam_step",
            "ge_sno_train_step", "ge_sno_destroy")
@@ -117,6 +118,12 @@ def load(path: str | None = None):
         lib.ge_sno_train_step.restype = ctypes.c_int
         lib.ge_sno_destroy.argtypes = [_VP]
         lib.ge_sno_destroy.restype = None
+        lib.ge_debug_stall.argtypes = [_VP, _I64]
+        lib.ge_debug_stall.restype = ctypes.c_int
+        lib.ge_batch_debug_stall.argtypes = [_VP, _I64]
+        lib.ge_batch_debug_stall.restype = ctypes.c_int
+        lib.ge_batch_check.argtypes = [_VP, _VP, _VP]
+        lib.ge_batch_check.restype = ctypes.c_int
         lib.ge_status_str.argtypes = [ctypes.c_int]
         lib.ge_status_str.restype = ctypes.c_char_p
         lib.ge_last_error.argtypes = []
@@ -222,6 +229,10 @@ def ge_destroy(ctx: Ctx):
         ctx.handle = None
 
 
+def ge_debug_stall(ctx: Ctx, cycles: int):
+    _check(load().ge_debug_stall(ctx.handle, int(cycles)), "ge_debug_stall")
+
+
 def ge_solve(n: int, r: float, beta_l: float, beta_r: float, prec: int, kernel: int, depth: int,
              steps: int, u0_host: np.ndarray, u_out_host: np.ndarray, stream=None):
     """One-shot solve from host memory (numpy arrays of n float64/float32)."""
@@ -237,10 +248,11 @@ def ge_solve(n: int, r: float, beta_l: float, beta_r: float, prec: int, kernel: 
 class Batch:
     """Owner of a ``ge_batch*`` plan."""
 
-    def __init__(self, handle: int, total: int, prec: int):
+    def __init__(self, handle: int, total: int, prec: int, n_problems: int = 0):
         self.handle = handle
         self.total = total
         self.prec = prec
+        self.n_problems = n_problems
 
     def __del__(self):
         if getattr(self, "handle", None):
@@ -273,7 +285,7 @@ def ge_batch_create(n, r, beta_l, beta_r, offsets, total: int, prec: int, stream
     _check(load().ge_batch_create(ctypes.byref(h), a_n.size, a_n.ctypes.data_as(P64), a_r.ctypes.data_as(PD),
                                   a_bl.ctypes.data_as(PD), a_br.ctypes.data_as(PD), a_off.ctypes.data_as(P64),
                                   int(total), int(prec), _stream_handle(stream)), "ge_batch_create")
-    return Batch(h.value, int(total), int(prec))
+    return Batch(h.value, int(total), int(prec), int(a_n.size))
 
 
 def ge_batch_set_depth(plan: Batch, depth: int):
@@ -300,6 +312,21 @@ def ge_batch_run(plan: Batch, u, steps: int):
 
 def ge_batch_sync(plan: Batch):
     _check(load().ge_batch_sync(plan.handle), "ge_batch_sync")
+
+
+def ge_batch_check(plan: Batch, u, status):
+    """Per-problem status (GE_OK / GE_ENONFINITE) of the packed buffer u into
+    `status` (CUDA int32 tensor with one entry per problem)."""
+    import torch
+    if status.dtype != torch.int32 or status.numel() < plan.n_problems:
+        raise ValueError("status must be an int32 CUDA tensor with one entry per problem")
+    if u.numel() < plan.total or u.dtype != dtype_of(plan.prec):
+        raise ValueError("packed buffer too small or of the wrong dtype")
+    _check(load().ge_batch_check(plan.handle, _dptr(u), _dptr(status)), "ge_batch_check")
+
+
+def ge_batch_debug_stall(plan: Batch, cycles: int):
+    _check(load().ge_batch_debug_stall(plan.handle, int(cycles)), "ge_batch_debug_stall")
 
 
 def ge_batch_destroy(plan: Batch):

@@ -60,7 +60,7 @@ def build(verbose: bool = False, defines=(), lib_path: str = LIB_PATH, obj_dir: 
     objs = [os.path.join(obj_dir, s + ".o") for s in CU_SOURCES + CPP_SOURCES]
     tmp = lib_path + ".tmp"
     _run(["g++", "-shared", "-o", tmp, *objs, "-L" + os.path.join(CUDA_HOME, "lib64"),
-          "-lcudart", "-Wl,-rpath," + os.path.join(CUDA_HOME, "lib64")])
+          "-lcudart", "-ldl", "-Wl,-rpath," + os.path.join(CUDA_HOME, "lib64")])
     os.replace(tmp, lib_path)
     return lib_path
 

@@ -113,6 +113,7 @@ void fill_coefficients(ge_ctx *c)
     // factor, carried as a double-double (onepg + onepg_lo == 1 + g exactly),
     // so no systematic scale error builds up over many steps.
     ge::scaled_growth(r, c->prec == GE_F32, &p.onepg, &c->onepg_lo);
+    p.stall = 0;
     p.r = r;
     p.omr = 1.0 - r;
     p.d = 2.0 * r / det;
@@ -407,6 +408,7 @@ ge_status ge_set_subdomain_width(ge_ctx *c, int64_t k)
 
 ge_status ge_step_n(ge_ctx *c, int64_t steps)
 {
+    ge::NvtxRange nvtx("ge_step_n");
     if (!c)
         return fail(GE_EINVAL, "ge_step_n: ctx is NULL");
     if (steps < 0)
@@ -456,9 +458,19 @@ ge_status ge_write_state(ge_ctx *c, const void *in_dev, int64_t step_count)
         return fail(GE_EINVAL, "ge_write_state: step_count < 0");
     cudaError_t e = cudaMemcpyAsync(c->buf[c->cur], in_dev, (size_t)c->n * elem_size(c->prec),
                                     cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)  // a new state: earlier device failures no longer apply
+        e = cudaMemsetAsync(c->err_dev, 0, sizeof(int), c->stream);
     if (e != cudaSuccess)
         return cuda_fail(e, "ge_write_state");
     c->step = step_count;
+    return GE_OK;
+}
+
+ge_status ge_debug_stall(ge_ctx *c, int64_t cycles)
+{
+    if (!c || cycles < 0)
+        return fail(GE_EINVAL, "ge_debug_stall: NULL ctx or cycles < 0");
+    c->tb.stall = (long long)cycles;
     return GE_OK;
 }
 
@@ -497,6 +509,7 @@ void ge_destroy(ge_ctx *c)
 ge_status ge_solve(int64_t n, double r, double beta_l, double beta_r, ge_precision prec, ge_kernel kernel,
                    int32_t depth, int64_t steps, const void *u0_host, void *u_out_host, void *stream)
 {
+    ge::NvtxRange nvtx("ge_solve");
     if (!u0_host || !u_out_host)
         return fail(GE_EINVAL, "ge_solve: NULL host buffer");
     if (steps < 0)

@@ -70,6 +70,7 @@ struct ge_batch {
     short *exps = nullptr;
     void *endf = nullptr;
     int R = 0, Q = 0;
+    long long stall = 0;  // diagnostic (ge_batch_debug_stall)
     std::vector<int> slot_nmid;
     std::vector<char> slot_ready;
 };
@@ -155,6 +156,7 @@ ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int *result_buf)
         p.row_pid = b->row_pid;
         p.desc = b->desc;
         p.err = b->err;
+        p.stall = b->stall;
         if (b->exps) {
             cudaError_t se = cudaSuccess;
             const int slot = endf_slot(b, p.n_mid, &se);
@@ -333,6 +335,7 @@ ge_status ge_batch_get_depth(const ge_batch *b, int32_t *depth)
 
 ge_status ge_batch_run(ge_batch *b, void *u_dev, int64_t steps)
 {
+    ge::NvtxRange nvtx("ge_batch_run");
     if (!b || !u_dev || steps < 0)
         return bfail(GE_EINVAL, "ge_batch_run: NULL argument or steps < 0");
     if (steps == 0)
@@ -351,6 +354,7 @@ ge_status ge_batch_run(ge_batch *b, void *u_dev, int64_t steps)
 
 ge_status ge_batch_tune(ge_batch *b, const void *u_dev, int64_t steps, int32_t *best_depth)
 {
+    ge::NvtxRange nvtx("ge_batch_tune");
     if (!b || !u_dev || steps < 1)
         return bfail(GE_EINVAL, "ge_batch_tune: NULL argument or steps < 1");
     static const int cand[] = {16, 32, 48, 64, 96, 128, 192, 256};
@@ -414,8 +418,40 @@ ge_status ge_batch_sync(ge_batch *b)
     e = cudaMemcpy(&word, b->err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess)
         return bcuda(e, "ge_batch_sync: reading the device error word");
+    if (word != ge::kDevOk) {
+        // reported once: the next run starts from the caller's buffer again
+        e = cudaMemset(b->err, 0, sizeof(int));
+        if (e != cudaSuccess)
+            return bcuda(e, "ge_batch_sync: clearing the device error word");
+    }
     if (word == ge::kDevTimeout)
         return bfail(GE_ETIMEOUT, "ge_batch: a tile load did not complete within the wait limit");
+    return GE_OK;
+}
+
+ge_status ge_batch_check(ge_batch *b, const void *u_dev, int32_t *status_dev)
+{
+    if (!b || !u_dev || !status_dev)
+        return bfail(GE_EINVAL, "ge_batch_check: NULL argument");
+    static_assert(sizeof(int32_t) == sizeof(int), "status words are int");
+    cudaError_t e = cudaMemsetAsync(status_dev, 0, sizeof(int32_t) * (size_t)b->n_problems, b->stream);
+    if (e == cudaSuccess) {
+        // rows of the caller's buffer only (the plan's rows cover total rounded up)
+        const int K = ge::kRowBytes / (b->prec == GE_F64 ? 8 : 4);
+        const long long rows = (b->total + K - 1) / K;
+        // the last row may reach past `total`: problems end inside it, and the
+        // kernel reads only elements inside a problem
+        e = ge::batch_check(b->prec == GE_F64 ? 0 : 1, u_dev, b->row_pid, b->desc, rows,
+                            reinterpret_cast<int *>(status_dev), b->stream);
+    }
+    return e == cudaSuccess ? GE_OK : bcuda(e, "ge_batch_check");
+}
+
+ge_status ge_batch_debug_stall(ge_batch *b, int64_t cycles)
+{
+    if (!b || cycles < 0)
+        return bfail(GE_EINVAL, "ge_batch_debug_stall: NULL plan or cycles < 0");
+    b->stall = (long long)cycles;
     return GE_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cuda_runtime_api.h>
+#include <nvtx3/nvToolsExt.h>
 
 namespace ge {
 
@@ -16,6 +17,15 @@ constexpr int kRowBytes = 128;
 // doubles), the box of their 2D TMA load.
 constexpr int kTileRows = 256;
 
+// NVTX range around a library call (visible in Nsight timelines; a no-op
+// when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 // Headroom (in powers of two) of the scaled forms' data between rescalings:
 // data magnitudes up to about 2^(largest exponent - headroom) are safe.
 #ifndef GE_F32_HEADROOM
@@ -24,6 +34,9 @@ constexpr int kTileRows = 256;
 
 // Device error codes written to the context's error word.
 enum DevErr : int { kDevOk = 0, kDevTimeout = 1 };
+
+// Limit of a tile load wait in the tiled kernels: about 2 s of SM clock.
+constexpr long long kWaitLimitCycles = 4000000000LL;
 
 // Coefficients of the literal step (Eqs. (cc)/(dd), (aa)/(bb)), FP64 on the
 // host; the FP32 kernels round them once.
@@ -57,6 +70,8 @@ struct TbParams {
     long long n_tiles;    // tiles of U output elements
     int U;                // output elements per tile (multiple of K)
     int H;                // halo elements per side (multiple of K, >= reach)
+    long long stall;      // diagnostic: > 0 makes every tile wait poll a barrier nothing
+                          // arrives on for this many cycles (the timeout path runs)
     int p_first;          // parity of the first step of this launch
     int do_entry;         // convert u -> w at the start
     int n_mid;            // block steps w_n -> w_{n+1} in this launch
@@ -101,6 +116,7 @@ struct TbbParams {
     const int *row_pid;        // problem id of every 128-byte row (-1: padding)
     const BatchDesc *desc;     // per-problem constants
     long long n_rows, n_tiles;
+    long long stall;           // diagnostic, as in TbParams
     int U, H;
     int p_first, do_entry, n_mid, do_exit;
     // scaled form (scaled != 0): after every R block steps the data of
@@ -111,6 +127,10 @@ struct TbbParams {
     const short *exps;
     const void *endf;
 };
+
+// Per-problem non-finite scan of a packed buffer (status zeroed first).
+cudaError_t batch_check(int prec, const void *u, const int *row_pid, const BatchDesc *desc, long long n_rows,
+                        int *status, cudaStream_t s);
 
 // Rescale exponents of the batched scaled form (one row of Q per problem) and
 // the end factor of a launch with n_mid block steps (kernels in ge_tb.cu).

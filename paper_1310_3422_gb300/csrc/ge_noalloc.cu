@@ -187,6 +187,7 @@ extern "C" ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double
                 every = 1;
         }
         base_p.rescale_every = every;
+        base_p.stall = 0;
         int d = depth > 0 ? depth : (prec == GE_F64 ? 48 : 128);
         if (every > 0 && d > (ge::kMaxRescale - 1) * every)
             d = (ge::kMaxRescale - 1) * every;

@@ -467,6 +467,7 @@ ge_status ge_sno_set_precision(ge_sno *s, int32_t split)
 ge_status ge_sno_forward(ge_sno *s, int32_t batch, const float *u0, const float *r, const float *bl, const float *br,
                          float *pred)
 {
+    ge::NvtxRange nvtx("ge_sno_forward");
     if (!s || !u0 || !r || !bl || !br || !pred || batch < 1 || batch > s->max_batch)
         return sfail(GE_EINVAL, "ge_sno_forward: NULL argument or batch outside 1..max_batch");
     return forward(s, batch, u0, r, bl, br, pred, false);
@@ -475,6 +476,7 @@ ge_status ge_sno_forward(ge_sno *s, int32_t batch, const float *u0, const float 
 ge_status ge_sno_loss_grad(ge_sno *s, int32_t batch, const float *u0, const float *r, const float *bl,
                            const float *br, const float *target, float *loss_dev, float *grads_dev)
 {
+    ge::NvtxRange nvtx("ge_sno_loss_grad");
     if (!s || !u0 || !r || !bl || !br || !target || batch < 1 || batch > s->max_batch)
         return sfail(GE_EINVAL, "ge_sno_loss_grad: NULL argument or batch outside 1..max_batch");
     ge_status st = forward(s, batch, u0, r, bl, br, s->out, true);

@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(Layout<Real, COMP>::NT, Layout<Real, COMP>::MI
     extern __shared__ unsigned char smem_raw[];
     unsigned char *tiles = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[3];  // two tile buffers, and one nothing arrives on
     __shared__ Real slot[2][NW][2];
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -254,6 +254,7 @@ __global__ void __launch_bounds__(Layout<Real, COMP>::NT, Layout<Real, COMP>::MI
     if (t == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
+        mbar_init(&mbar[2], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -273,13 +274,10 @@ __global__ void __launch_bounds__(Layout<Real, COMP>::NT, Layout<Real, COMP>::MI
             mbar_arrive_expect_tx(&mbar[b ^ 1], kTileBytes);
             tma_load_rows(tiles + (b ^ 1) * kTileBytes, &tmap, &mbar[b ^ 1], (int)(next * ur - hr));
         }
-        const bool ok = mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1));
+        const bool ok = tile_wait(mbar, &mbar[2], b, it, P.stall);
         if (__syncthreads_or(!ok)) {
-            if (t == 0) {
-                atomicExch(P.err, kDevTimeout);
-                if (prefetch)  // let our own copy in flight land before leaving
-                    mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
-            }
+            if (t == 0)
+                tile_wait_failed(P.err, mbar, b, it, prefetch);
             return;
         }
 

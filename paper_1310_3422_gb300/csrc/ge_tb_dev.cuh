@@ -13,7 +13,6 @@
 namespace ge {
 namespace {
 
-constexpr long long kWaitLimitCycles = 4000000000LL;  // about 2 s of SM clock
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
@@ -56,15 +55,37 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 
-// Wait for phase `parity` of the barrier; give up after kWaitLimitCycles.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Wait for phase `parity` of the barrier; give up after `limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit)
 {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitLimitCycles)
+        if (clock64() - t0 > limit)
             return false;
     }
     return true;
+}
+
+// Wait for the tile in buffer b (phase from the iteration).  With the
+// diagnostic `stall` > 0 the wait polls `never`, a barrier no thread or copy
+// arrives on, and so runs out after `stall` cycles: the failure path below
+// then runs exactly as for a tile load that never completes.
+__device__ __forceinline__ bool tile_wait(uint64_t *mbar, uint64_t *never, int b, long long it, long long stall)
+{
+    if (stall > 0)
+        return mbar_wait_bounded(never, 0, stall);
+    return mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1), kWaitLimitCycles);
+}
+
+// A tile wait gave up: record GE_ETIMEOUT and let this CTA's own TMA copies
+// still in flight (the tile waited for, and the prefetch) land before the
+// CTA leaves, each within the default limit.  Called by thread 0 only.
+__device__ __forceinline__ void tile_wait_failed(int *err, uint64_t *mbar, int b, long long it, bool prefetch)
+{
+    atomicExch(err, kDevTimeout);
+    mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1), kWaitLimitCycles);
+    if (prefetch)
+        mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimitCycles);
 }
 
 // 2D tiled TMA load: box origin (x = 0, y = row), completes on `bar`.

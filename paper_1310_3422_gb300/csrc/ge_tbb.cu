@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
     extern __shared__ unsigned char smem_raw[];
     unsigned char *tiles = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[3];  // two tile buffers, and one nothing arrives on
     __shared__ Real slot[2][NW][2];
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
     if (t == 0) {
         mbar_init(&mbar[0], 1);
         mbar_init(&mbar[1], 1);
+        mbar_init(&mbar[2], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -251,13 +252,10 @@ __global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
             mbar_arrive_expect_tx(&mbar[b ^ 1], kTileBytes);
             tma_load_rows(tiles + (b ^ 1) * kTileBytes, &tmap, &mbar[b ^ 1], (int)(next * ur - hr));
         }
-        const bool ok = mbar_wait_bounded(&mbar[b], (uint32_t)((it >> 1) & 1));
+        const bool ok = tile_wait(mbar, &mbar[2], b, it, P.stall);
         if (__syncthreads_or(!ok)) {
-            if (t == 0) {
-                atomicExch(P.err, kDevTimeout);
-                if (prefetch)
-                    mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
-            }
+            if (t == 0)
+                tile_wait_failed(P.err, mbar, b, it, prefetch);
             return;
         }
 
@@ -414,7 +412,47 @@ __global__ void batch_endf_kernel(const BatchDesc *__restrict__ desc, const shor
     }
 }
 
+// status[b] = GE_ENONFINITE (5) when a value of problem b is NaN or Inf
+// (status zeroed by the caller); one thread per 128-byte row.
+template <typename Real>
+__global__ void batch_check_kernel(const Real *__restrict__ u, const int *__restrict__ row_pid,
+                                   const BatchDesc *__restrict__ desc, long long n_rows, int *__restrict__ status)
+{
+    constexpr int K = kRowBytes / (int)sizeof(Real);
+    for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < n_rows;
+         row += (long long)gridDim.x * blockDim.x) {
+        const int pid = row_pid[row];
+        if (pid < 0)
+            continue;
+        const long long lo = desc[pid].off, hi = lo + desc[pid].n;
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const long long e = row * K + j;
+            if (e >= lo && e < hi && !isfinite(u[e]))
+                bad = true;
+        }
+        if (bad)
+            atomicExch(&status[pid], 5);
+    }
+}
+
 }  // namespace
+
+cudaError_t batch_check(int prec, const void *u, const int *row_pid, const BatchDesc *desc, long long n_rows,
+                        int *status, cudaStream_t s)
+{
+    long long blocks = (n_rows + 255) / 256;
+    if (blocks > 4096)
+        blocks = 4096;
+    if (prec == 0)
+        batch_check_kernel<double><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const double *>(u), row_pid, desc,
+                                                                    n_rows, status);
+    else
+        batch_check_kernel<float><<<(unsigned)blocks, 256, 0, s>>>(static_cast<const float *>(u), row_pid, desc,
+                                                                   n_rows, status);
+    return cudaGetLastError();
+}
 
 cudaError_t batch_exps(const BatchDesc *desc, int n_problems, int R, int Q, int f32, short *exps, cudaStream_t s)
 {

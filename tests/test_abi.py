@@ -133,3 +133,8 @@ def test_sno_calls_on_null_model(lib):
     assert lib.ge_sno_adam_step(None, 1e-3) == B.GE_EINVAL
     assert lib.ge_sno_train_step(None, 1, 1, 1, 1, 1, 1, 1e-3, None) == B.GE_EINVAL
     lib.ge_sno_destroy(None)
+
+
+def test_debug_stall_checks_its_arguments(lib):
+    assert lib.ge_debug_stall(None, 0) == B.GE_EINVAL
+    assert lib.ge_batch_debug_stall(None, 0) == B.GE_EINVAL

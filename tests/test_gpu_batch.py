@@ -194,3 +194,22 @@ def test_batch_huge_r_error_is_conditioning():
         e_orc = rel(oracle.run(u0, r[i], bl[i], br[i], 100), ref)
         e_gpu = rel(got[offs[i]:offs[i] + n[i]], ref)
         assert e_gpu <= 4.0 * e_orc + 1e-15, (i, e_gpu, e_orc)
+
+
+@pytest.mark.parametrize("prec", [B.GE_F64, B.GE_F32, B.GE_F32_COMP])
+def test_batch_check_flags_non_finite_problems(prec):
+    n, r, bl, br, offs, total, u = make_batch([100, 2000, 33, 700, 64], seed=13, gap=32)
+    u = u.copy()
+    u[offs[2] + 5] = np.nan
+    u[offs[4] + 63] = np.inf
+    x = torch.from_numpy(u).to(DEV, B.dtype_of(prec))
+    plan = B.ge_batch_create(n, r, bl, br, offs, total, prec)
+    B.ge_batch_run(plan, x, 20)
+    status = torch.full((len(n),), -1, dtype=torch.int32, device=DEV)
+    B.ge_batch_check(plan, x, status)
+    B.ge_batch_sync(plan)
+    assert status.cpu().tolist() == [0, 0, B.GE_ENONFINITE, 0, B.GE_ENONFINITE]
+    got = x.double().cpu().numpy()
+    for i in (0, 1, 3):  # the other problems are untouched by their neighbours' NaN / Inf
+        want = oracle.run(u[offs[i]:offs[i] + n[i]], r[i], bl[i], br[i], 20)
+        assert rel(got[offs[i]:offs[i] + n[i]], want) <= tol(prec, r[i])
