@@ -1,4 +1,4 @@
-"""Learned surrogate of K GE steps with the GE solver as its fallback and judge.
+"""Learned surrogate of K GE steps with the GE solver as its fallback and arbiter.
 
 The surrogate (the spectral neural operator of ``include/ge_sno.h``, run by
 the library's own forward / backward / Adam kernels) maps the state of an
@@ -6,7 +6,7 @@ n-point problem to its state K GE steps later.  The GE solver
 
   * generates its training data (pairs (u_{jK}, u_{(j+1)K}) along GE
     trajectories, so the network sees the states a rollout meets),
-  * judges it: ``solve_with_fallback`` re-solves a random sample of the
+  * checks it: ``solve_with_fallback`` re-solves a random sample of the
     problems (plus every flagged one) with GE and compares, and
   * takes over: flagged and sampled problems get GE's answer, and when any
     sampled problem misses the tolerance the whole batch is re-solved by GE.
