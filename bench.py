@@ -144,6 +144,50 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
+def _oracle_window(task):
+    """One worker of the all-core oracle baseline: the oracle, as it stands,
+    on one window of the grid; returns its own compute seconds."""
+    import oracle
+    u, r, bl, br, steps = task
+    t0 = time.perf_counter()
+    oracle.run(u, r, bl, br, steps)
+    return time.perf_counter() - t0
+
+
+def oracle_all_cores(u0, r, steps):
+    """The serial oracle run concurrently on every host core, one window per
+    core: core q advances points [a_q - m, b_q + m) with m = steps + 4 (the
+    dependency cone of `steps` steps, so the owned range [a_q, b_q) is exact).
+    Processes are spawned (the parent holds a CUDA context).  Returns
+    (updates/s over the whole grid, cores used, wall seconds)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    n = u0.size
+    m = steps + 4
+    m += m % 2
+    cuts = [2 * ((n * q) // (2 * cores)) for q in range(cores)] + [n]
+    tasks = []
+    for q in range(cores):
+        lo, hi = max(0, cuts[q] - m), min(n, cuts[q + 1] + m)
+        tasks.append((np.ascontiguousarray(u0[lo:hi]), r, 0.0, 0.0, steps))
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        # start-up outside the timing; every wait is bounded (a worker that
+        # dies would otherwise leave the pool waiting)
+        pool.map_async(_oracle_window, [(np.zeros(8), r, 0.0, 0.0, 1)] * cores).get(timeout=300)
+        t0 = time.perf_counter()
+        pool.map_async(_oracle_window, tasks, chunksize=1).get(timeout=600)
+        wall = time.perf_counter() - t0
+    return n * steps / wall, cores, wall
+
+
+PAPER_CONTEXT = {
+    "hardware": "NVIDIA GeForce GT 335M (72 stream processors) against an Intel Core i7-720QM (4 cores, 8 threads)",
+    "gpu_vs_cpu_1_thread": 5.0, "gpu_vs_cpu_8_threads": 2.0,
+    "note": "ratios stated in the paper's text (Sec. 4); its absolute runtimes are only in figures, so there is "
+            "no absolute figure to compare with (context only)"}
+
+
 def sample_indices(n):
     rng = np.random.default_rng(20240613)
     return sorted(set([0, 1, n // 2, n - 2, n - 1] + [int(i) for i in rng.integers(0, n, N_SAMPLES - 5)]))
@@ -560,6 +604,16 @@ def main():
                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
                     "kernel": "canon_kernel" if args.kernel == "canonical" else "tb_kernel (1 step/launch)"}
     hbm_roof_updates = hbm_gbs * 1e9 / (2.0 * bytes_per_update)
+    # HBM fraction from the bytes the dominant kernel actually moves (ncu DRAM counters per launch)
+    hbm_actual = None
+    if roofline.get("traffic"):
+        steps_per_launch = GE_STEPS / n_launch
+        gbs = roofline["traffic"] / (launch_ms / 1e3) / 1e9
+        hbm_actual = {"bytes_per_launch": roofline["traffic"], "steps_per_launch": steps_per_launch,
+                      "bytes_per_step": roofline["traffic"] / steps_per_launch, "achieved_gbs": gbs,
+                      "peak_gbs": hbm_gbs, "frac": gbs / hbm_gbs,
+                      "source": "dram__bytes_read.sum + dram__bytes_write.sum of one launch (profiles/traffic.txt) "
+                                "over the live average launch time"}
 
     # ---- accuracy against the oracle (sampled) ----------------------------
     idx = sample_indices(N_POINTS)
@@ -635,6 +689,16 @@ def main():
         cpu = {"value": N_POINTS * CPU_SAMPLE_STEPS / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{CPU_SAMPLE_STEPS} GE steps over the full N=2^24 grid (serial FP64 C)",
                "seconds": t_cpu}
+        try:
+            v_all, cores, wall = oracle_all_cores(u0, R, CPU_SAMPLE_STEPS)
+            cpu_all = {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+                       "sample": f"{CPU_SAMPLE_STEPS} GE steps over the full N=2^24 grid, the serial oracle on "
+                                 f"one dependency-cone window per core ({cores} spawned processes)",
+                       "seconds": wall}
+        except Exception as exc:  # reported, not fatal: the one-core baseline stands
+            cpu_all = {"unavailable": f"{type(exc).__name__}: {exc}"}
+    else:
+        cpu_all = None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -647,8 +711,11 @@ def main():
                    "l2": "inputs larger than L2 (two %d MB state buffers); no flush"
                          % (N_POINTS * bytes_per_update >> 20)},
         "roofline": roofline,
+        "hbm_actual": hbm_actual,
         "hbm_roofline_frac_effective": value / world / hbm_roof_updates,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
+        "paper_context": PAPER_CONTEXT,
         "e2e": e2e,
         "gpu_launches": n_launch * args.steps,
         "kernel_ms_per_launch": launch_ms,
