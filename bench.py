@@ -32,7 +32,7 @@ R = 2.0
 GE_STEPS = 10000
 WORKLOAD = ("single large 1D GE solve: N=2^24 interior points, r=2.0, 10000 steps, Dirichlet zero "
             "walls, u0 = sum of 8 seeded sine modes k in [1,64], amplitudes U(-1,1)")
-CPU_SAMPLE_STEPS = 100     # oracle baseline: 100 GE steps over the full grid
+CPU_SAMPLE_STEPS = 1000    # oracle baseline: 1000 GE steps over the full grid (about 11 s on one core)
 REF_SAMPLE_STEPS = 10      # --impl reference: 10 GE steps over the full grid per step
 N_SAMPLES = 12             # oracle-checked sample points
 
