@@ -215,10 +215,12 @@ ge_status ge_batch_debug_stall(ge_batch *plan, int64_t cycles);
 /* Release the plan (NULL is a no-op). */
 void ge_batch_destroy(ge_batch *plan);
 
-/* One-shot: ge_batch_create + ge_batch_run + ge_batch_sync + ge_batch_destroy. */
+/* One-shot: ge_batch_create + ge_batch_run [+ ge_batch_check into
+ * status_dev, n_problems int32 on the device, when not NULL] +
+ * ge_batch_sync + ge_batch_destroy.  Synchronous. */
 ge_status ge_solve_batch(int32_t n_problems, const int64_t *n, const double *r, const double *beta_l,
                          const double *beta_r, const int64_t *offsets, int64_t total, void *u_dev,
-                         int64_t steps, ge_precision prec, void *stream);
+                         int32_t *status_dev, int64_t steps, ge_precision prec, void *stream);
 
 /* The tiled solve (GE_KERNEL_TEMPORAL) for callers that may not allocate
  * device memory: a plug-in inside a host application or server that owns all

@@ -94,7 +94,7 @@ def load(path: str | None = None):
         lib.ge_batch_sync.restype = ctypes.c_int
         lib.ge_batch_destroy.argtypes = [_VP]
         lib.ge_batch_destroy.restype = None
-        lib.ge_solve_batch.argtypes = [_I32, _PI64, _PD, _PD, _PD, _PI64, _I64, _VP, _I64, ctypes.c_int, _VP]
+        lib.ge_solve_batch.argtypes = [_I32, _PI64, _PD, _PD, _PD, _PI64, _I64, _VP, _VP, _I64, ctypes.c_int, _VP]
         lib.ge_solve_batch.restype = ctypes.c_int
         lib.ge_solve_noalloc.argtypes = [_I64, _D, _D, _D, ctypes.c_int, _I32, _I64, _VP, _VP, _VP]
         lib.ge_solve_noalloc.restype = ctypes.c_int
@@ -335,15 +335,21 @@ def ge_batch_destroy(plan: Batch):
         plan.handle = None
 
 
-def ge_solve_batch(n, r, beta_l, beta_r, offsets, total: int, u, steps: int, prec: int, stream=None):
+def ge_solve_batch(n, r, beta_l, beta_r, offsets, total: int, u, steps: int, prec: int, stream=None, status=None):
+    """One-shot batched solve in place in u; `status` (optional CUDA int32
+    tensor, one entry per problem) receives GE_OK / GE_ENONFINITE."""
+    import torch
     a_n, a_r, a_bl, a_br, a_off = _batch_arrays(n, r, beta_l, beta_r, offsets)
     if u.numel() < total or u.dtype != dtype_of(prec):
         raise ValueError("packed buffer too small or of the wrong dtype")
+    if status is not None and (status.dtype != torch.int32 or status.numel() < a_n.size):
+        raise ValueError("status must be an int32 CUDA tensor with one entry per problem")
     P64 = ctypes.POINTER(ctypes.c_int64)
     PD = ctypes.POINTER(ctypes.c_double)
     _check(load().ge_solve_batch(a_n.size, a_n.ctypes.data_as(P64), a_r.ctypes.data_as(PD),
                                  a_bl.ctypes.data_as(PD), a_br.ctypes.data_as(PD), a_off.ctypes.data_as(P64),
-                                 int(total), _dptr(u), int(steps), int(prec), _stream_handle(stream)),
+                                 int(total), _dptr(u), _dptr(status), int(steps), int(prec),
+                                 _stream_handle(stream)),
            "ge_solve_batch")
 
 

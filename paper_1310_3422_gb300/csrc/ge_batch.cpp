@@ -464,14 +464,16 @@ void ge_batch_destroy(ge_batch *b)
 }
 
 ge_status ge_solve_batch(int32_t n_problems, const int64_t *n, const double *r, const double *beta_l,
-                         const double *beta_r, const int64_t *offsets, int64_t total, void *u_dev, int64_t steps,
-                         ge_precision prec, void *stream)
+                         const double *beta_r, const int64_t *offsets, int64_t total, void *u_dev,
+                         int32_t *status_dev, int64_t steps, ge_precision prec, void *stream)
 {
     ge_batch *b = nullptr;
     ge_status st = ge_batch_create(&b, n_problems, n, r, beta_l, beta_r, offsets, total, prec, stream);
     if (st != GE_OK)
         return st;
     st = ge_batch_run(b, u_dev, steps);
+    if (st == GE_OK && status_dev)
+        st = ge_batch_check(b, u_dev, status_dev);
     if (st == GE_OK)
         st = ge_batch_sync(b);
     ge_batch_destroy(b);

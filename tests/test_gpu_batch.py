@@ -77,7 +77,9 @@ def test_one_shot_equals_plan_and_zero_steps():
     n, r, bl, br, offs, total, u = make_batch([300, 5000, 777], seed=3)
     a = torch.from_numpy(u).to(DEV)
     b = a.clone()
-    B.ge_solve_batch(n, r, bl, br, offs, total, a, 50, B.GE_F64)
+    status = torch.full((len(n),), -1, dtype=torch.int32, device=DEV)
+    B.ge_solve_batch(n, r, bl, br, offs, total, a, 50, B.GE_F64, status=status)
+    assert status.cpu().tolist() == [B.GE_OK] * len(n)
     plan = B.ge_batch_create(n, r, bl, br, offs, total, B.GE_F64)
     B.ge_batch_run(plan, b, 0)
     B.ge_batch_sync(plan)
