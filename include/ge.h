@@ -89,6 +89,11 @@ typedef struct ge_ctx ge_ctx;  /* opaque; owned by the library */
  *   stream     stream all later work of this context is enqueued on.
  * The context owns two device buffers of n elements (padded to whole
  * 128-byte rows).  The step counter starts at 0 (next step has parity 0).
+ * The tiled kernel's steps per launch start at the built-in default, or at
+ * the first line of the tuning table named by the environment variable
+ * GE_TUNE_TABLE that matches: lines "<f64|f32|f32c> <n_min> <n_max>
+ * <depth>", '#' comments, malformed lines skipped (ge_tune writes what to
+ * put there).
  * Errors: GE_EINVAL (bad n, r, beta, prec, out == NULL), GE_ENOMEM, GE_ECUDA. */
 ge_status ge_create(ge_ctx **out, int64_t n, double r, double beta_l, double beta_r,
                     ge_precision prec, const void *u0_dev, void *stream);
@@ -98,6 +103,19 @@ ge_status ge_create(ge_ctx **out, int64_t n, double r, double beta_l, double bet
  * Errors: GE_EINVAL (NULL ctx, unknown kernel, depth out of range,
  * GE_KERNEL_CANONICAL with GE_F32_COMP). */
 ge_status ge_set_kernel(ge_ctx *ctx, ge_kernel kernel, int32_t depth);
+
+/* The kernel in use and the tiled kernel's steps per launch (the default
+ * resolved).  Errors: GE_EINVAL. */
+ge_status ge_get_kernel(const ge_ctx *ctx, ge_kernel *kernel, int32_t *depth);
+
+/* Autotune the tiled kernel's steps per launch: times `steps` steps from the
+ * current state at each candidate depth (FP64: 24, 32, 48, 64, 96; FP32:
+ * 64 ... 256), keeps the fastest (returned in *best_depth, may be NULL) and
+ * leaves the state and the step counter as they were.  A context on the
+ * canonical, one-step or width-k path keeps its setting.  Synchronous;
+ * allocates one scratch copy of the state.  Errors: GE_EINVAL, GE_ENOMEM,
+ * GE_ECUDA. */
+ge_status ge_tune(ge_ctx *ctx, int64_t steps, int32_t *best_depth);
 
 /* Sub-domain width k (Sec. 2: odd sub-domains [x_{2ik}, x_{2ik+k-1}], even
  * sub-domains [x_{2ik+k}, x_{2(i+1)k-1}] of the paper's nodes x_0..x_{n+1}).

@@ -27,7 +27,7 @@ EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", 
            "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_batch_create", "ge_batch_set_depth",
            "ge_batch_get_depth", "ge_batch_tune", "ge_batch_run", "ge_batch_sync", "ge_batch_destroy",
            "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error", "ge_debug_stall",
-           "ge_batch_debug_stall", "ge_batch_check",
+           "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune",
            "ge_sno_create", "ge_sno_num_params", "ge_sno_get_params", "ge_sno_set_params",
            "ge_sno_set_precision", "ge_sno_forward", "ge_sno_loss_grad", "ge_sno_adam_step",
            "ge_sno_train_step", "ge_sno_destroy")
@@ -118,6 +118,10 @@ def load(path: str | None = None):
         lib.ge_sno_train_step.restype = ctypes.c_int
         lib.ge_sno_destroy.argtypes = [_VP]
         lib.ge_sno_destroy.restype = None
+        lib.ge_get_kernel.argtypes = [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I32)]
+        lib.ge_get_kernel.restype = ctypes.c_int
+        lib.ge_tune.argtypes = [_VP, _I64, ctypes.POINTER(_I32)]
+        lib.ge_tune.restype = ctypes.c_int
         lib.ge_debug_stall.argtypes = [_VP, _I64]
         lib.ge_debug_stall.restype = ctypes.c_int
         lib.ge_batch_debug_stall.argtypes = [_VP, _I64]
@@ -191,6 +195,19 @@ def ge_create(n: int, r: float, beta_l: float, beta_r: float, prec: int, u0=None
 
 def ge_set_kernel(ctx: Ctx, kernel: int, depth: int = 0):
     _check(load().ge_set_kernel(ctx.handle, int(kernel), int(depth)), "ge_set_kernel")
+
+
+def ge_get_kernel(ctx: Ctx):
+    """(kernel, steps per launch of the tiled kernel)."""
+    k, d = ctypes.c_int(), _I32()
+    _check(load().ge_get_kernel(ctx.handle, ctypes.byref(k), ctypes.byref(d)), "ge_get_kernel")
+    return int(k.value), int(d.value)
+
+
+def ge_tune(ctx: Ctx, steps: int) -> int:
+    d = _I32()
+    _check(load().ge_tune(ctx.handle, int(steps), ctypes.byref(d)), "ge_tune")
+    return int(d.value)
 
 
 def ge_set_subdomain_width(ctx: Ctx, k: int):

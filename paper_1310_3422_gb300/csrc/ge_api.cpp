@@ -9,6 +9,7 @@
 #include <cuda_runtime_api.h>
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -163,6 +164,39 @@ bool valid_kernel(int k)
 {
     return k == GE_KERNEL_AUTO || k == GE_KERNEL_CANONICAL || k == GE_KERNEL_ONESTEP ||
            k == GE_KERNEL_TEMPORAL;
+}
+
+// Depth of the tiled kernel from the tuning table named by GE_TUNE_TABLE
+// (lines "<f64|f32|f32c> <n_min> <n_max> <depth>", '#' starts a comment,
+// the first matching line wins, malformed lines are skipped); 0 = none.
+int table_depth(ge_precision prec, int64_t n)
+{
+    const char *path = std::getenv("GE_TUNE_TABLE");
+    if (!path || !*path)
+        return 0;
+    FILE *f = std::fopen(path, "r");
+    if (!f)
+        return 0;
+    char line[256];
+    int found = 0;
+    while (!found && std::fgets(line, sizeof(line), f)) {
+        char p[16];
+        long long lo = 0, hi = 0;
+        int d = 0;
+        if (line[0] == '#' || std::sscanf(line, "%15s %lld %lld %d", p, &lo, &hi, &d) != 4)
+            continue;
+        const int pp = !std::strcmp(p, "f64") ? GE_F64 : !std::strcmp(p, "f32") ? GE_F32
+                       : !std::strcmp(p, "f32c") ? GE_F32_COMP : -1;
+        if (pp == (int)prec && n >= lo && n <= hi && d >= 1 && d <= kMaxDepth)
+            found = d;
+    }
+    std::fclose(f);
+    return found;
+}
+
+int effective_depth(const ge_ctx *c)
+{
+    return c->depth ? c->depth : ((c->prec == GE_F64) ? kDefaultDepthF64 : kDefaultDepthF32);
 }
 
 // Advance `steps` steps with the tiled kernel, `depth` steps per launch.
@@ -363,6 +397,7 @@ ge_status ge_create(ge_ctx **out, int64_t n, double r, double beta_l, double bet
         return cuda_fail(e, "ge_create: initialising buffers");
     }
     fill_coefficients(c);
+    c->depth = table_depth(prec, n);
     ge_status st = make_tensor_maps(c);
     if (st != GE_OK) {
         release(c);
@@ -391,6 +426,87 @@ ge_status ge_set_kernel(ge_ctx *c, ge_kernel kernel, int32_t depth)
         return fail(GE_EINVAL, "ge_set_kernel: the canonical kernel has no compensated variant");
     c->kernel = kernel;
     c->depth = depth;
+    return GE_OK;
+}
+
+ge_status ge_get_kernel(const ge_ctx *c, ge_kernel *kernel, int32_t *depth)
+{
+    if (!c || !kernel || !depth)
+        return fail(GE_EINVAL, "ge_get_kernel: NULL argument");
+    *kernel = c->kernel;
+    *depth = effective_depth(c);
+    return GE_OK;
+}
+
+ge_status ge_tune(ge_ctx *c, int64_t steps, int32_t *best_depth)
+{
+    if (!c || steps < 1)
+        return fail(GE_EINVAL, "ge_tune: NULL ctx or steps < 1");
+    if (c->width > 1 || c->kernel == GE_KERNEL_CANONICAL || c->kernel == GE_KERNEL_ONESTEP) {
+        if (best_depth)
+            *best_depth = effective_depth(c);
+        return GE_OK;  // nothing to tune
+    }
+    ge::NvtxRange nvtx("ge_tune");
+    static const int cand64[] = {24, 32, 48, 64, 96};
+    static const int cand32[] = {64, 96, 128, 192, 256};
+    const int *cand = c->prec == GE_F64 ? cand64 : cand32;
+    const size_t bytes = (size_t)c->n * elem_size(c->prec);
+    void *saved = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&saved, bytes);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(saved, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e0);
+    if (e == cudaSuccess)
+        e = cudaEventCreate(&e1);
+    const int64_t step0 = c->step;
+    double best = 1e300;
+    int best_d = effective_depth(c);
+    ge_status st = GE_OK;
+    for (int i = 0; i < 5 && e == cudaSuccess && st == GE_OK; ++i) {
+        // one untimed run (first use of the launch shape), then a timed one,
+        // each from the saved state and step counter
+        for (int rep = 0; rep < 2 && e == cudaSuccess && st == GE_OK; ++rep) {
+            e = cudaMemcpyAsync(c->buf[c->cur], saved, bytes, cudaMemcpyDeviceToDevice, c->stream);
+            c->step = step0;
+            if (e == cudaSuccess && rep == 1)
+                e = cudaEventRecord(e0, c->stream);
+            if (e == cudaSuccess)
+                st = run_tiled(c, steps, cand[i]);
+            if (e == cudaSuccess && st == GE_OK && rep == 1)
+                e = cudaEventRecord(e1, c->stream);
+        }
+        float ms = 0.0f;
+        if (e == cudaSuccess && st == GE_OK)
+            e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess && st == GE_OK)
+            e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && st == GE_OK && ms < best) {
+            best = ms;
+            best_d = cand[i];
+        }
+    }
+    // the state and the step counter as they were
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->buf[c->cur], saved, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    c->step = step0;
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    if (saved)
+        cudaFree(saved);
+    if (st != GE_OK)
+        return st;
+    if (e != cudaSuccess)
+        return cuda_fail(e, "ge_tune");
+    c->depth = best_d;
+    if (best_depth)
+        *best_depth = best_d;
     return GE_OK;
 }
 
@@ -429,12 +545,8 @@ ge_status ge_step_n(ge_ctx *c, int64_t steps)
     case GE_KERNEL_ONESTEP:
         st = run_tiled(c, steps, 1);
         break;
-    default: {
-        int depth = c->depth;
-        if (depth == 0)
-            depth = (c->prec == GE_F64) ? kDefaultDepthF64 : kDefaultDepthF32;
-        st = run_tiled(c, steps, depth);
-    }
+    default:
+        st = run_tiled(c, steps, effective_depth(c));
     }
     if (st == GE_OK)
         c->step += steps;

@@ -307,3 +307,45 @@ def test_full_size_f64_sampled():
     scale = np.max(np.abs(u0))
     assert np.max(np.abs(got[idx] - want)) / scale <= tol64(r)
     assert np.all(np.isfinite(got))
+
+
+def test_tune_keeps_state_and_counter_and_picks_a_candidate():
+    n, r = 300001, 1.3
+    u0 = inputs.random_state(n, seed=31)
+    x = torch.tensor(u0, device=DEV)
+    ctx = B.ge_create(n, r, 0.1, 0.2, B.GE_F64, x)
+    B.ge_step_n(ctx, 7)
+    before = torch.empty_like(x)
+    B.ge_read_state(ctx, before)
+    best = B.ge_tune(ctx, 200)
+    assert best in (24, 32, 48, 64, 96)
+    assert B.ge_get_kernel(ctx) == (B.GE_KERNEL_AUTO, best)
+    assert B.ge_get_step(ctx) == 7
+    after = torch.empty_like(x)
+    B.ge_read_state(ctx, after)
+    B.ge_sync(ctx)
+    assert torch.equal(before, after)
+    B.ge_step_n(ctx, 50)
+    out = torch.empty_like(x)
+    B.ge_read_state(ctx, out)
+    B.ge_sync(ctx)
+    B.ge_destroy(ctx)
+    idx = np.linspace(0, n - 1, 7).astype(np.int64)
+    want = oracle.sample(u0, r, 0.1, 0.2, 57, idx)
+    assert rel_max(out.cpu().numpy()[idx], want) <= tol64(r)
+
+
+def test_tuning_table_sets_the_default_depth(tmp_path, monkeypatch):
+    table = tmp_path / "tune.txt"
+    table.write_text("# precision n_min n_max depth\nf32 1 999 64\nbad line\nf64 1000 5000 32\nf64 1 1000000 96\n")
+    monkeypatch.setenv("GE_TUNE_TABLE", str(table))
+    ctx = B.ge_create(3000, 1.0, 0.0, 0.0, B.GE_F64)
+    assert B.ge_get_kernel(ctx)[1] == 32
+    B.ge_destroy(ctx)
+    ctx = B.ge_create(500, 1.0, 0.0, 0.0, B.GE_F32)
+    assert B.ge_get_kernel(ctx)[1] == 64
+    B.ge_destroy(ctx)
+    monkeypatch.setenv("GE_TUNE_TABLE", str(tmp_path / "missing.txt"))
+    ctx = B.ge_create(500, 1.0, 0.0, 0.0, B.GE_F64)
+    assert B.ge_get_kernel(ctx)[1] == 48  # built-in default
+    B.ge_destroy(ctx)
