@@ -23,10 +23,11 @@
  * Arithmetic: the parameters are FP32 masters that every forward pass rounds
  * to BF16 (the network's weights are BF16 values; ge_sno_adam_step updates
  * the masters with the gradient of the rounded network).  Activations are
- * FP32; every matrix product rounds its operands to BF16 and accumulates in
- * FP32 on the tensor cores, and GELU uses the hardware tanh approximation
- * (relative error about 2^-11).  With ge_sno_set_precision(model, 1) each operand
- * is split into two BF16 parts and three products are summed, so activations
+ * stored as BF16; every matrix product takes BF16 operands and accumulates
+ * in FP32 on the tensor cores, and GELU uses the hardware tanh approximation
+ * (relative error about 2^-11).  With ge_sno_set_precision(model, 1) the
+ * activations are stored in FP32 and each operand is split into two BF16
+ * parts and three products are summed, so activations
  * and the DFT bases enter at about FP32 accuracy (the weights, already BF16,
  * are exact) and GELU uses the library tanh; this mode is also the one
  * checked against an FP64 reference.

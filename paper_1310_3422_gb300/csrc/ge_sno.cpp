@@ -8,11 +8,12 @@
 //             after the last layer; DFT_M keeps the M lowest modes, R_m is a
 //             complex C x C matrix per mode
 //   projection C -> H (GELU) -> 1, added to u0 (residual output).
-// Activations are channel-last [batch * n, C] in FP32.  The FP32 master
-// parameters are rounded to BF16 at the start of every forward pass (the
-// network has BF16 weights; Adam updates the masters with the gradient of the
-// rounded network).  Every GEMM rounds its operands to BF16 and accumulates in
-// FP32; split mode adds the BF16 residuals (~FP32 products).
+// Activations are channel-last [batch * n, C]: BF16 in the plain mode (the
+// GEMMs round their operands to BF16 anyway), FP32 in split mode.  The FP32
+// master parameters are rounded to BF16 at the start of every forward pass
+// (the network has BF16 weights; Adam updates the masters with the gradient
+// of the rounded network).  Every GEMM accumulates in FP32; split mode adds
+// the BF16 residuals of FP32 operands (~FP32 products).
 //
 // Parameter vector (FP32, this order): W0 [4][C], b0 [C]; per layer: Rr
 // [M][C][C] (out, in), Ri [M][C][C], W [C][C] (in, out), b [C]; Q1 [C][H],
@@ -22,6 +23,7 @@
 #include <cuda_runtime_api.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -60,13 +62,15 @@ struct ge_sno {
     long long off_w0 = 0, off_b0 = 0, off_q1 = 0, off_qb1 = 0, off_q2 = 0, off_qb2 = 0;
     std::vector<LayerOff> lay;
     float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
-    float *pw = nullptr;               // params rounded to BF16 (the weights the network uses)
+    float *pw = nullptr;               // params rounded to BF16 (the weights the network uses), FP32
+    void *pw16 = nullptr;              // the same as BF16 (plain mode)
     long long adam_t = 0;
     float *F = nullptr, *G = nullptr;  // [2M][n] and [n][2M]
-    float *wspec = nullptr;            // [L][M][2C][2C]
+    void *F16 = nullptr, *G16 = nullptr;  // the same rounded to BF16 (plain mode)
+    float *wspec = nullptr;            // [L][M][2C][2C] (BF16 in the plain mode)
     float *dwspec = nullptr;           // [M][2C][2C]
     // activations (max_batch)
-    float *feat = nullptr;             // [B n][4]
+    float *feat = nullptr;             // [B n][4] FP32, or [B n][8] BF16 in the plain mode
     std::vector<float *> v;            // L + 1 buffers [B n][C]
     std::vector<float *> pre;          // L buffers [B n][C]
     std::vector<float *> vh;           // L buffers [B][2M][C]
@@ -80,8 +84,8 @@ struct ge_sno {
 
 namespace {
 
-ge::GemmArgs gemm(const float *A, long long lda_i, long long lda_k, const float *B, long long ldb_k, long long ldb_j,
-                  float *C, long long ldc, int M, int N, int K)
+ge::GemmArgs gemm(const void *A, long long lda_i, long long lda_k, const void *B, long long ldb_k, long long ldb_j,
+                  void *C, long long ldc, int M, int N, int K)
 {
     ge::GemmArgs g{};
     g.A = A;
@@ -108,22 +112,52 @@ ge::GemmArgs gemm(const float *A, long long lda_i, long long lda_k, const float 
             return scuda(e_, "ge_sno: " #expr);          \
     } while (0)
 
+// Storage of the plain mode: BF16 activations, weights and DFT bases (the
+// GEMMs round their operands to BF16 anyway, so the forward values are the
+// same); split mode keeps FP32 everywhere.
+bool bf16_mode(const ge_sno *s) { return !s->split; }
+
+// Element `off` of a buffer in the mode's storage type.
+const void *at(const void *base, long long off, bool bf)
+{
+    return static_cast<const char *>(base) + off * (bf ? 2 : 4);
+}
+
+void *at(void *base, long long off, bool bf) { return static_cast<char *>(base) + off * (bf ? 2 : 4); }
+
+// The weights as the GEMMs read them: BF16 copy or FP32 rounded values.
+const void *weight(const ge_sno *s, long long off)
+{
+    return bf16_mode(s) ? at(s->pw16, off, true) : static_cast<const void *>(s->pw + off);
+}
+
+// Activation in/out format of a GEMM: BF16 in the plain mode.
+ge::GemmArgs &act_fmt(ge::GemmArgs &g, bool bf)
+{
+    g.in_bf16 = bf ? 1 : 0;
+    g.out_bf16 = bf ? 1 : 0;
+    g.dg_bf16 = bf ? 1 : 0;
+    return g;
+}
+
 // Weight gradient of a pointwise layer: dW[in][out] = X^T dY over R rows
-// (split-K with atomics), db = column sums of dY.
-ge_status weight_grad(ge_sno *s, const float *X, int in, const float *dY, int out, long long R, float *dW,
+// (X rows ldx apart; split-K with atomics, FP32), db = column sums of dY.
+ge_status weight_grad(ge_sno *s, const void *X, int in, int ldx, const void *dY, int out, long long R, float *dW,
                       float *db)
 {
+    const bool bf = bf16_mode(s);
     SNO_TRY(cudaMemsetAsync(dW, 0, sizeof(float) * in * out, s->stream));
-    ge::GemmArgs g = gemm(X, 1, in, dY, out, 1, dW, out, in, out, (int)R);
+    ge::GemmArgs g = gemm(X, 1, ldx, dY, out, 1, dW, out, in, out, (int)R);
+    act_fmt(g, bf).out_bf16 = 0;
     long long ks = R / 1024;
     g.ksplit = (int)(ks < 1 ? 1 : (ks > 512 ? 512 : ks));
     SNO_TRY(ge::sno_gemm(g, 1, s->split, s->stream));
     if (db)
-        SNO_TRY(ge::sno_colsum(dY, db, R, out, s->stream));
+        SNO_TRY(ge::sno_colsum(dY, db, R, out, bf ? 1 : 0, s->stream));
     return GE_OK;
 }
 
-// Forward pass for B problems into out ([B n]).  keep: also store the
+// Forward pass for B problems into out ([B n], FP32).  keep: also store the
 // pre-activations the backward pass needs (training).
 ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float *bl, const float *br, float *out,
                   bool keep)
@@ -131,34 +165,38 @@ ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float
     const int n = s->n, C = s->C, M = s->M, H = s->H;
     const long long R = (long long)B * n;
     cudaStream_t st = s->stream;
-    const float *P = s->pw;
-    SNO_TRY(ge::sno_round_bf16(s->params, s->pw, s->n_params, st));
-    SNO_TRY(ge::sno_features(u0, r, bl, br, s->feat, B, n, st));
+    const bool bf = bf16_mode(s);
+    const float *P = s->pw;  // FP32 rounded weights: biases and the spectral matrices' source
+    const void *F = bf ? s->F16 : static_cast<const void *>(s->F);
+    const void *G = bf ? s->G16 : static_cast<const void *>(s->G);
+    const int ldf = bf ? 8 : 4;
+    SNO_TRY(ge::sno_round_bf16(s->params, s->pw, bf ? s->pw16 : nullptr, s->n_params, st));
+    SNO_TRY(ge::sno_features(u0, r, bl, br, s->feat, B, n, bf ? 1 : 0, st));
     // lift
-    ge::GemmArgs g = gemm(s->feat, 4, 1, P + s->off_w0, C, 1, s->v[0], C, (int)R, C, 4);
+    ge::GemmArgs g = gemm(s->feat, ldf, 1, weight(s, s->off_w0), C, 1, s->v[0], C, (int)R, C, 4);
     g.bias = P + s->off_b0;
-    SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
+    SNO_TRY(ge::sno_gemm(act_fmt(g, bf), 1, s->split, st));
     for (int l = 0; l < s->L; ++l) {
         const LayerOff &o = s->lay[l];
-        float *ws = s->wspec + (long long)l * M * 4 * C * C;
-        SNO_TRY(ge::sno_spec_assemble(P + o.rr, P + o.ri, ws, M, C, st));
+        void *ws = at(s->wspec, (long long)l * M * 4 * C * C, bf);
+        SNO_TRY(ge::sno_spec_assemble(P + o.rr, P + o.ri, ws, M, C, bf ? 1 : 0, st));
         // truncated DFT along the grid: vh[b] = F [2M x n] * v[b] [n x C]
-        g = gemm(s->F, n, 1, s->v[l], C, 1, s->vh[l], C, 2 * M, C, n);
+        g = gemm(F, n, 1, s->v[l], C, 1, s->vh[l], C, 2 * M, C, n);
         g.sA = 0;
         g.sB = (long long)n * C;
         g.sC = 2LL * M * C;
-        SNO_TRY(ge::sno_gemm(g, B, s->split, st));
+        SNO_TRY(ge::sno_gemm(act_fmt(g, bf), B, s->split, st));
         // per-mode complex mixing: y[:, m] [B x 2C] = vh[:, m] [B x 2C] * Wspec_m [2C x 2C]
         g = gemm(s->vh[l], 2LL * M * C, 1, ws, 2 * C, 1, s->y, 2LL * M * C, B, 2 * C, 2 * C);
         g.sA = 2 * C;
         g.sB = 4LL * C * C;
         g.sC = 2 * C;
-        SNO_TRY(ge::sno_gemm(g, M, s->split, st));
+        SNO_TRY(ge::sno_gemm(act_fmt(g, bf), M, s->split, st));
         // back to the grid and the pointwise path in one pass:
         // pre[b] = G [n x 2M] y[b] [2M x C] + v[b] W + b, next v = GELU(pre)
         // (the last layer has no activation: next v = pre)
         const bool last = l == s->L - 1;
-        g = gemm(s->G, 2 * M, 1, s->y, C, 1, last ? s->v[l + 1] : (keep ? s->pre[l] : nullptr), C, n, C, 2 * M);
+        g = gemm(G, 2 * M, 1, s->y, C, 1, last ? s->v[l + 1] : (keep ? s->pre[l] : nullptr), C, n, C, 2 * M);
         g.sA = 0;
         g.sB = 2LL * M * C;
         g.sC = (long long)n * C;
@@ -166,7 +204,7 @@ ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float
         g.lda2_i = C;
         g.lda2_k = 1;
         g.sA2 = (long long)n * C;
-        g.B2 = P + o.w;
+        g.B2 = weight(s, o.w);
         g.ldb2_k = C;
         g.ldb2_j = 1;
         g.K2 = C;
@@ -175,18 +213,19 @@ ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float
             g.act = s->v[l + 1];
             g.sAct = (long long)n * C;
         }
-        SNO_TRY(ge::sno_gemm(g, B, s->split, st));
+        SNO_TRY(ge::sno_gemm(act_fmt(g, bf), B, s->split, st));
     }
     // projection
-    g = gemm(s->v[s->L], C, 1, P + s->off_q1, H, 1, keep ? s->hpre : nullptr, H, (int)R, H, C);
+    g = gemm(s->v[s->L], C, 1, weight(s, s->off_q1), H, 1, keep ? s->hpre : nullptr, H, (int)R, H, C);
     g.bias = P + s->off_qb1;
     g.act = s->h;
-    SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
-    // residual output: the network predicts the change of u over the jump
-    g = gemm(s->h, H, 1, P + s->off_q2, 1, 1, out, 1, (int)R, 1, H);
+    SNO_TRY(ge::sno_gemm(act_fmt(g, bf), 1, s->split, st));
+    // residual output (FP32): the network predicts the change of u over the jump
+    g = gemm(s->h, H, 1, weight(s, s->off_q2), 1, 1, out, 1, (int)R, 1, H);
     g.bias = P + s->off_qb2;
     g.C0 = u0;
     g.beta = 1.0f;
+    act_fmt(g, bf).out_bf16 = 0;
     SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
     return GE_OK;
 }
@@ -197,42 +236,46 @@ ge_status backward(ge_sno *s, int B)
     const int n = s->n, C = s->C, M = s->M, H = s->H;
     const long long R = (long long)B * n;
     cudaStream_t st = s->stream;
-    const float *P = s->pw;
+    const bool bf = bf16_mode(s);
+    const void *F = bf ? s->F16 : static_cast<const void *>(s->F);
+    const void *G = bf ? s->G16 : static_cast<const void *>(s->G);
+    const int ldf = bf ? 8 : 4;
     float *Gd = s->grads;
     ge_status rc;
     // projection: out = h Q2 + q2
-    if ((rc = weight_grad(s, s->h, H, s->dout, 1, R, Gd + s->off_q2, Gd + s->off_qb2)) != GE_OK)
+    if ((rc = weight_grad(s, s->h, H, H, s->dout, 1, R, Gd + s->off_q2, Gd + s->off_qb2)) != GE_OK)
         return rc;
     // dhpre = (dout Q2^T) * GELU'(hpre)
-    ge::GemmArgs g = gemm(s->dout, 1, 1, P + s->off_q2, 1, 1, s->dA, H, (int)R, H, 1);
+    ge::GemmArgs g = gemm(s->dout, 1, 1, weight(s, s->off_q2), 1, 1, s->dA, H, (int)R, H, 1);
     g.dgelu_pre = s->hpre;
-    SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
-    if ((rc = weight_grad(s, s->v[s->L], C, s->dA, H, R, Gd + s->off_q1, Gd + s->off_qb1)) != GE_OK)
+    SNO_TRY(ge::sno_gemm(act_fmt(g, bf), 1, s->split, st));
+    if ((rc = weight_grad(s, s->v[s->L], C, C, s->dA, H, R, Gd + s->off_q1, Gd + s->off_qb1)) != GE_OK)
         return rc;
-    g = gemm(s->dA, H, 1, P + s->off_q1, 1, H, s->dB, C, (int)R, C, H);  // dv_L = dhpre Q1^T
-    SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
+    g = gemm(s->dA, H, 1, weight(s, s->off_q1), 1, H, s->dB, C, (int)R, C, H);  // dv_L = dhpre Q1^T
+    SNO_TRY(ge::sno_gemm(act_fmt(g, bf), 1, s->split, st));
     // dv holds the gradient of the current layer's pre-activation: the last
     // layer has no activation, and every lower one's GELU' is applied in the
     // epilogue of the GEMM that makes its gradient.
-    float *dv = s->dB, *dnext = s->dA;
+    void *dv = s->dB, *dnext = s->dA;
     for (int l = s->L - 1; l >= 0; --l) {
         const LayerOff &o = s->lay[l];
-        const float *ws = s->wspec + (long long)l * M * 4 * C * C;
-        const float *dpre = dv;
+        const void *ws = at(s->wspec, (long long)l * M * 4 * C * C, bf);
+        const void *dpre = dv;
         // pointwise path weights
-        if ((rc = weight_grad(s, s->v[l], C, dpre, C, R, Gd + o.w, Gd + o.b)) != GE_OK)
+        if ((rc = weight_grad(s, s->v[l], C, C, dpre, C, R, Gd + o.w, Gd + o.b)) != GE_OK)
             return rc;
         // spectral path: dy[b] = G^T dpre[b]
-        g = gemm(s->G, 1, 2 * M, dpre, C, 1, s->y, C, 2 * M, C, n);
+        g = gemm(G, 1, 2 * M, dpre, C, 1, s->y, C, 2 * M, C, n);
         g.sA = 0;
         g.sB = (long long)n * C;
         g.sC = 2LL * M * C;
-        SNO_TRY(ge::sno_gemm(g, B, s->split, st));
-        // dWspec_m = vh[:, m]^T dy[:, m]
+        SNO_TRY(ge::sno_gemm(act_fmt(g, bf), B, s->split, st));
+        // dWspec_m = vh[:, m]^T dy[:, m]  (FP32)
         g = gemm(s->vh[l], 1, 2LL * M * C, s->y, 2LL * M * C, 1, s->dwspec, 2 * C, 2 * C, 2 * C, B);
         g.sA = 2 * C;
         g.sB = 2 * C;
         g.sC = 4LL * C * C;
+        act_fmt(g, bf).out_bf16 = 0;
         SNO_TRY(ge::sno_gemm(g, M, s->split, st));
         SNO_TRY(ge::sno_spec_reduce(s->dwspec, Gd + o.rr, Gd + o.ri, M, C, st));
         // dvh[:, m] = dy[:, m] Wspec_m^T
@@ -240,14 +283,14 @@ ge_status backward(ge_sno *s, int B)
         g.sA = 2 * C;
         g.sB = 4LL * C * C;
         g.sC = 2 * C;
-        SNO_TRY(ge::sno_gemm(g, M, s->split, st));
+        SNO_TRY(ge::sno_gemm(act_fmt(g, bf), M, s->split, st));
         // gradient of v_l, both paths in one pass: dpre[b] W^T + F^T dvh[b],
         // times GELU'(pre_{l-1}) when v_l is an activation
-        g = gemm(dpre, C, 1, P + o.w, 1, C, dnext, C, n, C, C);
+        g = gemm(dpre, C, 1, weight(s, o.w), 1, C, dnext, C, n, C, C);
         g.sA = (long long)n * C;
         g.sB = 0;
         g.sC = (long long)n * C;
-        g.A2 = s->F;
+        g.A2 = F;
         g.lda2_i = 1;
         g.lda2_k = n;
         g.sA2 = 0;
@@ -260,13 +303,22 @@ ge_status backward(ge_sno *s, int B)
             g.dgelu_pre = s->pre[l - 1];
             g.sDg = (long long)n * C;
         }
-        SNO_TRY(ge::sno_gemm(g, B, s->split, st));
-        float *t = dv;
+        SNO_TRY(ge::sno_gemm(act_fmt(g, bf), B, s->split, st));
+        void *t = dv;
         dv = dnext;
         dnext = t;
     }
     // lift
-    return weight_grad(s, s->feat, 4, dv, C, R, Gd + s->off_w0, Gd + s->off_b0);
+    return weight_grad(s, s->feat, 4, ldf, dv, C, R, Gd + s->off_w0, Gd + s->off_b0);
+}
+
+// Bits of the BF16 value nearest to a finite float (ties to even).
+uint16_t bf16_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, sizeof(u));
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
 }
 
 void release_sno(ge_sno *s)
@@ -349,8 +401,17 @@ ge_status ge_sno_create(ge_sno **out, int32_t n, int32_t width, int32_t modes, i
             s->allocs.push_back(*p);
         return e;
     };
+    auto alloc_bytes = [&](void **p, long long bytes) -> cudaError_t {
+        cudaError_t e = cudaMalloc(p, (size_t)(bytes > 16 ? bytes : 16));
+        if (e == cudaSuccess)
+            s->allocs.push_back(*p);
+        return e;
+    };
     cudaError_t e = cudaSuccess;
     e = e ? e : alloc(&s->params, off);
+    e = e ? e : alloc_bytes(&s->pw16, 2 * off);
+    e = e ? e : alloc_bytes(&s->F16, 2 * 2 * M * n);
+    e = e ? e : alloc_bytes(&s->G16, 2 * 2 * M * n);
     e = e ? e : alloc(&s->grads, off);
     e = e ? e : alloc(&s->pw, off);
     e = e ? e : alloc(&s->adam_m, off);
@@ -413,9 +474,18 @@ ge_status ge_sno_create(ge_sno **out, int32_t n, int32_t width, int32_t modes, i
         p[s->off_q1 + i] = (float)rng.uniform(1.0 / std::sqrt((double)C));
     for (long long i = 0; i < H; ++i)
         p[s->off_q2 + i] = (float)rng.uniform(1.0 / std::sqrt((double)H));
+    std::vector<uint16_t> F16(F.size()), G16(Gm.size());
+    for (size_t i = 0; i < F.size(); ++i) {
+        F16[i] = bf16_bits(F[i]);
+        G16[i] = bf16_bits(Gm[i]);
+    }
     e = cudaMemcpyAsync(s->F, F.data(), sizeof(float) * F.size(), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->G, Gm.data(), sizeof(float) * Gm.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->F16, F16.data(), 2 * F16.size(), cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->G16, G16.data(), 2 * G16.size(), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->params, p.data(), sizeof(float) * p.size(), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
@@ -482,7 +552,7 @@ ge_status ge_sno_loss_grad(ge_sno *s, int32_t batch, const float *u0, const floa
     ge_status st = forward(s, batch, u0, r, bl, br, s->out, true);
     if (st != GE_OK)
         return st;
-    cudaError_t e = ge::sno_rel_l2(s->out, target, s->dout, s->loss, s->n, batch, s->stream);
+    cudaError_t e = ge::sno_rel_l2(s->out, target, s->dout, s->loss, s->n, batch, bf16_mode(s) ? 1 : 0, s->stream);
     if (e != cudaSuccess)
         return scuda(e, "ge_sno_loss_grad: loss");
     st = backward(s, batch);

@@ -19,10 +19,14 @@ namespace ge {
 // the first product is cut into ksplit slices whose partial products are
 // added into C with atomics (C must be zeroed first; no second product, C0,
 // bias or epilogue).
+//
+// Element formats: A, B, A2, B2 are FP32, or all BF16 when in_bf16 (then no
+// split mode); C and act are FP32, or BF16 when out_bf16 (not with ksplit);
+// dgelu_pre is BF16 when dg_bf16; C0 and bias are always FP32.
 struct GemmArgs {
-    const float *A;
-    const float *B;
-    float *C;
+    const void *A;
+    const void *B;
+    void *C;
     const float *C0;
     const float *bias;
     int M, N, K;
@@ -30,30 +34,31 @@ struct GemmArgs {
     long long sA, sB, sC, sC0;
     float alpha, beta;
     int ksplit;
-    const float *A2;
-    const float *B2;
+    const void *A2;
+    const void *B2;
     int K2;
     long long lda2_i, lda2_k, ldb2_k, ldb2_j, sA2, sB2;
-    const float *dgelu_pre;
+    const void *dgelu_pre;
     long long sDg;
-    float *act;
+    void *act;
     long long sAct;
-    // set by sno_gemm: float4 staging allowed for A, B, A2, B2; float2
-    // epilogue accesses allowed
+    int in_bf16, out_bf16, dg_bf16;
+    // set by sno_gemm: vector staging allowed for A, B, A2, B2 (float4 for
+    // FP32, 16-byte cp.async chunks of 8 elements for BF16); paired epilogue
     int vec[4];
     int pairs;
 };
 
 cudaError_t sno_gemm(const GemmArgs &g, int batch, bool split, cudaStream_t s);
-cudaError_t sno_features(const float *u0, const float *r, const float *bl, const float *br, float *f, int batch,
-                         int n, cudaStream_t s);
-cudaError_t sno_spec_assemble(const float *rr, const float *ri, float *w, int modes, int c, cudaStream_t s);
+cudaError_t sno_features(const float *u0, const float *r, const float *bl, const float *br, void *f, int batch,
+                         int n, int bf16, cudaStream_t s);
+cudaError_t sno_spec_assemble(const float *rr, const float *ri, void *w, int modes, int c, int bf16, cudaStream_t s);
 cudaError_t sno_spec_reduce(const float *dw, float *drr, float *dri, int modes, int c, cudaStream_t s);
-cudaError_t sno_colsum(const float *x, float *out, long long rows, int cols, cudaStream_t s);
-cudaError_t sno_rel_l2(const float *pred, const float *target, float *dpred, float *loss, int n, int batch,
+cudaError_t sno_colsum(const void *x, float *out, long long rows, int cols, int bf16, cudaStream_t s);
+cudaError_t sno_rel_l2(const float *pred, const float *target, void *dpred, float *loss, int n, int batch, int bf16,
                        cudaStream_t s);
 cudaError_t sno_adam(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
                      float eps, float c1, float c2, cudaStream_t s);
-cudaError_t sno_round_bf16(const float *x, float *y, long long n, cudaStream_t s);
+cudaError_t sno_round_bf16(const float *x, float *y, void *y16, long long n, cudaStream_t s);
 
 }  // namespace ge

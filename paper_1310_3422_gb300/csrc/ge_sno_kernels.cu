@@ -270,14 +270,279 @@ __device__ __forceinline__ void mma_tile(const __nv_bfloat16 (*As)[TILE], const 
     }
 }
 
-// 64x64 output tile per CTA, 4 warps (2 x 2), each warp 32x32 = 2 x 4 mma tiles.
-// VEC: every operand is staged with float4 loads (the launcher checks that
-// all of them allow it); otherwise all use scalar loads.
-template <bool SPLIT, bool VEC>
-__global__ void __launch_bounds__(NT, VEC ? 4 : 1) gemm_kernel(GemmArgs g)
+// ---- BF16 operands: 16-byte cp.async chunks (8 elements along the
+// unit-stride dimension, zero-filled outside the operand) or 2-byte loads
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid)
 {
-    __shared__ __align__(16) __nv_bfloat16 As[SPLIT ? 2 : 1][TILE];
-    __shared__ __align__(16) __nv_bfloat16 Bs[SPLIT ? 2 : 1][TILE];
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One BK slice of a BF16 operand into the tile S (layout as in `store`).
+// `chunk` (checked by the launcher: the unit-stride extent, the other
+// stride and the batch stride multiples of 8, the base 16-byte aligned)
+// copies whole 16-byte chunks asynchronously; otherwise 2-byte loads.
+__device__ __forceinline__ void stage_bf16(__nv_bfloat16 *S, const __nv_bfloat16 *__restrict__ X, long long s_r,
+                                           long long s_k, int r0, int rmax, int k0, int kend, bool chunk, int t)
+{
+    if (s_k == 1) {
+        if (chunk) {
+#pragma unroll
+            for (int q = 0; q < BM * BK / 8 / NT; ++q) {
+                const int e = t + q * NT;
+                const int r = e / (BK / 8), kc = (e % (BK / 8)) * 8;
+                const int row = r0 + r, k = k0 + kc;
+                const bool ok = row < rmax && k < kend;
+                cp_async16(&S[at_k(r, kc)], ok ? X + (long long)row * s_r + k : X, ok);
+            }
+        } else {
+            for (int e = t; e < BM * BK; e += NT) {
+                const int r = e / BK, kk = e % BK;
+                const int row = r0 + r, k = k0 + kk;
+                S[at_k(r, kk)] = (row < rmax && k < kend) ? X[(long long)row * s_r + k] : __float2bfloat16_rn(0.0f);
+            }
+        }
+    } else {
+        if (chunk) {
+#pragma unroll
+            for (int q = 0; q < BM * BK / 8 / NT; ++q) {
+                const int e = t + q * NT;
+                const int r = (e % (BM / 8)) * 8, kk = e / (BM / 8);
+                const int row = r0 + r, k = k0 + kk;
+                const bool ok = row < rmax && k < kend;
+                cp_async16(&S[at_r(r, kk)], ok ? X + row + (long long)k * s_k : X, ok);
+            }
+        } else {
+            for (int e = t; e < BM * BK; e += NT) {
+                const int r = e % BM, kk = e / BM;
+                const int row = r0 + r, k = k0 + kk;
+                S[at_r(r, kk)] = (row < rmax && k < kend) ? X[(long long)row * s_r + (long long)k * s_k]
+                                                          : __float2bfloat16_rn(0.0f);
+            }
+        }
+    }
+}
+
+// Operands of one product (segment) of the GEMM for batch entry bz.
+struct Seg {
+    const void *A, *B;
+    long long la_i, la_k, lb_k, lb_j;
+    int kbeg, kend;
+    int va, vb;
+};
+
+__device__ __forceinline__ Seg segment(const GemmArgs &g, int seg, int bz, int kslice, int ks_n, int esize)
+{
+    Seg s;
+    if (seg == 0) {
+        const int kchunk = ((g.K + ks_n - 1) / ks_n + BK - 1) / BK * BK;
+        s.kbeg = kslice * kchunk;
+        s.kend = (s.kbeg + kchunk < g.K) ? s.kbeg + kchunk : g.K;
+        s.A = static_cast<const char *>(g.A) + (long long)bz * g.sA * esize;
+        s.B = static_cast<const char *>(g.B) + (long long)bz * g.sB * esize;
+        s.la_i = g.lda_i, s.la_k = g.lda_k, s.lb_k = g.ldb_k, s.lb_j = g.ldb_j;
+        s.va = g.vec[0], s.vb = g.vec[1];
+    } else {
+        s.kbeg = 0;
+        s.kend = (g.A2 && g.K2 > 0) ? g.K2 : 0;
+        s.A = g.A2 ? static_cast<const char *>(g.A2) + (long long)bz * g.sA2 * esize : nullptr;
+        s.B = g.B2 ? static_cast<const char *>(g.B2) + (long long)bz * g.sB2 * esize : nullptr;
+        s.la_i = g.lda2_i, s.la_k = g.lda2_k, s.lb_k = g.ldb2_k, s.lb_j = g.ldb2_j;
+        s.va = g.vec[2], s.vb = g.vec[3];
+    }
+    return s;
+}
+
+// Main loop, FP32 operands: staged as BF16 (and split residuals) through
+// registers; VEC: float4 loads of the next slice overlap this slice's MMAs.
+template <bool SPLIT, bool VEC>
+__device__ __forceinline__ void mainloop_f32(const GemmArgs &g, int bz, int kslice, int ks_n, int i0, int j0,
+                                             float (&acc)[2][4][4], __nv_bfloat16 (*As)[TILE],
+                                             __nv_bfloat16 (*Bs)[TILE], int t, int wm, int wn, int lane)
+{
+    for (int seg = 0; seg < 2; ++seg) {
+        const Seg sg = segment(g, seg, bz, kslice, ks_n, 4);
+        if (sg.kbeg >= sg.kend)
+            continue;
+        const float *A = static_cast<const float *>(sg.A), *Bm = static_cast<const float *>(sg.B);
+        float xa[PER_T], xb[PER_T];
+        if (VEC) {
+            load<VEC>(xa, A, sg.la_i, sg.la_k, i0, g.M, sg.kbeg, sg.kend, t);
+            load<VEC>(xb, Bm, sg.lb_j, sg.lb_k, j0, g.N, sg.kbeg, sg.kend, t);
+        }
+        for (int k0 = sg.kbeg; k0 < sg.kend; k0 += BK) {
+            if (!VEC) {  // scalar staging: no prefetch (registers)
+                load<VEC>(xa, A, sg.la_i, sg.la_k, i0, g.M, k0, sg.kend, t);
+                load<VEC>(xb, Bm, sg.lb_j, sg.lb_k, j0, g.N, k0, sg.kend, t);
+            }
+            store<SPLIT, VEC>(As, xa, sg.la_k == 1, t);
+            store<SPLIT, VEC>(Bs, xb, sg.lb_k == 1, t);
+            __syncthreads();
+            if (VEC && k0 + BK < sg.kend) {
+                load<VEC>(xa, A, sg.la_i, sg.la_k, i0, g.M, k0 + BK, sg.kend, t);
+                load<VEC>(xb, Bm, sg.lb_j, sg.lb_k, j0, g.N, k0 + BK, sg.kend, t);
+            }
+            mma_tile<SPLIT>(As, Bs, acc, wm, wn, lane, sg.la_k == 1, sg.lb_k == 1);
+            __syncthreads();
+        }
+    }
+}
+
+// Main loop, BF16 operands: the slices of both products run through two
+// shared-memory stages; the copies of slice i+1 are in flight while slice i
+// is multiplied.
+__device__ __forceinline__ void mainloop_bf16(const GemmArgs &g, int bz, int kslice, int ks_n, int i0, int j0,
+                                              float (&acc)[2][4][4], __nv_bfloat16 (*As)[TILE],
+                                              __nv_bfloat16 (*Bs)[TILE], int t, int wm, int wn, int lane)
+{
+    const Seg s0 = segment(g, 0, bz, kslice, ks_n, 2), s1 = segment(g, 1, bz, kslice, ks_n, 2);
+    const int n0 = s0.kend > s0.kbeg ? (s0.kend - s0.kbeg + BK - 1) / BK : 0;
+    const int n1 = s1.kend > s1.kbeg ? (s1.kend - s1.kbeg + BK - 1) / BK : 0;
+    const int nt = n0 + n1;
+    auto issue = [&](int i) {
+        const Seg &sg = i < n0 ? s0 : s1;
+        const int k0 = sg.kbeg + (i < n0 ? i : i - n0) * BK;
+        __nv_bfloat16 *as = As[i & 1], *bs = Bs[i & 1];
+        stage_bf16(as, static_cast<const __nv_bfloat16 *>(sg.A), sg.la_i, sg.la_k, i0, g.M, k0, sg.kend, sg.va, t);
+        stage_bf16(bs, static_cast<const __nv_bfloat16 *>(sg.B), sg.lb_j, sg.lb_k, j0, g.N, k0, sg.kend, sg.vb, t);
+        cp_async_commit();
+    };
+    if (nt > 0)
+        issue(0);
+    for (int i = 0; i < nt; ++i) {
+        if (i + 1 < nt) {
+            issue(i + 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const Seg &sg = i < n0 ? s0 : s1;
+        mma_tile<false>(As + (i & 1), Bs + (i & 1), acc, wm, wn, lane, sg.la_k == 1, sg.lb_k == 1);
+        __syncthreads();
+    }
+}
+
+// Two adjacent outputs (columns j, j+1) in FP32 or BF16 storage.
+__device__ __forceinline__ float2 ld2(const void *base, long long off, bool bf16)
+{
+    if (bf16)
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(static_cast<const __nv_bfloat16 *>(base) + off));
+    return *reinterpret_cast<const float2 *>(static_cast<const float *>(base) + off);
+}
+
+__device__ __forceinline__ void st2(void *base, long long off, float a, float b, bool bf16)
+{
+    if (bf16)
+        *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(base) + off) = __floats2bfloat162_rn(a, b);
+    else
+        *reinterpret_cast<float2 *>(static_cast<float *>(base) + off) = make_float2(a, b);
+}
+
+__device__ __forceinline__ float ld1(const void *base, long long off, bool bf16)
+{
+    return bf16 ? __bfloat162float(static_cast<const __nv_bfloat16 *>(base)[off]) : static_cast<const float *>(base)[off];
+}
+
+__device__ __forceinline__ void st1(void *base, long long off, float a, bool bf16)
+{
+    if (bf16)
+        static_cast<__nv_bfloat16 *>(base)[off] = __float2bfloat16_rn(a);
+    else
+        static_cast<float *>(base)[off] = a;
+}
+
+// Epilogue: alpha * acc + beta * C0 + bias[j], then GELU' / store / GELU,
+// one row and two adjacent columns at a time (paired accesses when the
+// launcher found every epilogue array aligned with an even pitch).
+template <bool SPLIT>
+__device__ __forceinline__ void epilogue(const GemmArgs &g, int bz, int ks_n, int i0, int j0, const float (&acc)[2][4][4],
+                                         int wm, int wn, int grp, int tig)
+{
+    const bool ob = g.out_bf16 != 0, db = g.dg_bf16 != 0;
+    const int oes = ob ? 2 : 4, des = db ? 2 : 4;
+    void *C = g.C ? static_cast<char *>(g.C) + (long long)bz * g.sC * oes : nullptr;
+    const float *C0 = g.C0 ? g.C0 + (long long)bz * g.sC0 : nullptr;
+    const void *Dg = g.dgelu_pre ? static_cast<const char *>(g.dgelu_pre) + (long long)bz * g.sDg * des : nullptr;
+    void *act = g.act ? static_cast<char *>(g.act) + (long long)bz * g.sAct * oes : nullptr;
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int i = i0 + wm + mi * 16 + grp + hh * 8;
+                const int j = j0 + wn + ni * 8 + tig * 2;
+                if (i >= g.M || j >= g.N)
+                    continue;
+                const long long off = (long long)i * g.ldc + j;
+                float v[2] = {g.alpha * acc[mi][ni][2 * hh], g.alpha * acc[mi][ni][2 * hh + 1]};
+                if (ks_n > 1) {
+                    float *Cf = static_cast<float *>(C);
+                    atomicAdd(&Cf[off], v[0]);
+                    if (j + 1 < g.N)
+                        atomicAdd(&Cf[off + 1], v[1]);
+                    continue;
+                }
+                if (g.pairs && j + 1 < g.N) {
+                    if (C0) {
+                        const float2 c = *reinterpret_cast<const float2 *>(C0 + off);
+                        v[0] += g.beta * c.x;
+                        v[1] += g.beta * c.y;
+                    }
+                    if (g.bias) {
+                        const float2 b = *reinterpret_cast<const float2 *>(g.bias + j);
+                        v[0] += b.x;
+                        v[1] += b.y;
+                    }
+                    if (Dg) {
+                        const float2 d = ld2(Dg, off, db);
+                        v[0] *= gelu_grad<SPLIT>(d.x);
+                        v[1] *= gelu_grad<SPLIT>(d.y);
+                    }
+                    if (C)
+                        st2(C, off, v[0], v[1], ob);
+                    if (act)
+                        st2(act, off, gelu<SPLIT>(v[0]), gelu<SPLIT>(v[1]), ob);
+                    continue;
+                }
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    if (j + c >= g.N)
+                        break;
+                    float w = v[c];
+                    if (C0)
+                        w += g.beta * C0[off + c];
+                    if (g.bias)
+                        w += g.bias[j + c];
+                    if (Dg)
+                        w *= gelu_grad<SPLIT>(ld1(Dg, off + c, db));
+                    if (C)
+                        st1(C, off + c, w, ob);
+                    if (act)
+                        st1(act, off + c, gelu<SPLIT>(w), ob);
+                }
+            }
+}
+
+// 64x64 output tile per CTA, 4 warps (2 x 2), each warp 32x32 = 2 x 4 mma
+// tiles.  MODE 0: FP32 operands, scalar loads; 1: FP32 operands, float4
+// loads (the launcher checks every operand allows it); 2: BF16 operands.
+template <bool SPLIT, int MODE>
+__global__ void __launch_bounds__(NT, MODE == 0 ? 1 : 4) gemm_kernel(GemmArgs g)
+{
+    constexpr int NS = (SPLIT || MODE == 2) ? 2 : 1;  // split parts, or pipeline stages
+    __shared__ __align__(16) __nv_bfloat16 As[NS][TILE];
+    __shared__ __align__(16) __nv_bfloat16 Bs[NS][TILE];
     const int ks_n = g.ksplit > 1 ? g.ksplit : 1;
     const int bz = blockIdx.z / ks_n, kslice = blockIdx.z % ks_n;
     const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
@@ -293,129 +558,35 @@ __global__ void __launch_bounds__(NT, VEC ? 4 : 1) gemm_kernel(GemmArgs g)
 #pragma unroll
             for (int c = 0; c < 4; ++c)
                 acc[a][b][c] = 0.0f;
-
-    for (int seg = 0; seg < 2; ++seg) {
-        const float *A, *Bm;
-        long long la_i, la_k, lb_k, lb_j;
-        int kbeg, kend;
-        if (seg == 0) {
-            const int kchunk = ((g.K + ks_n - 1) / ks_n + BK - 1) / BK * BK;
-            kbeg = kslice * kchunk;
-            kend = (kbeg + kchunk < g.K) ? kbeg + kchunk : g.K;
-            A = g.A + (long long)bz * g.sA;
-            Bm = g.B + (long long)bz * g.sB;
-            la_i = g.lda_i, la_k = g.lda_k, lb_k = g.ldb_k, lb_j = g.ldb_j;
-        } else {
-            if (!g.A2 || g.K2 <= 0)
-                break;
-            kbeg = 0;
-            kend = g.K2;
-            A = g.A2 + (long long)bz * g.sA2;
-            Bm = g.B2 + (long long)bz * g.sB2;
-            la_i = g.lda2_i, la_k = g.lda2_k, lb_k = g.ldb2_k, lb_j = g.ldb2_j;
-        }
-        if (kbeg >= kend)
-            continue;
-        float xa[PER_T], xb[PER_T];
-        if (VEC) {
-            load<VEC>(xa, A, la_i, la_k, i0, g.M, kbeg, kend, t);
-            load<VEC>(xb, Bm, lb_j, lb_k, j0, g.N, kbeg, kend, t);
-        }
-        for (int k0 = kbeg; k0 < kend; k0 += BK) {
-            if (!VEC) {  // scalar staging: no prefetch (registers)
-                load<VEC>(xa, A, la_i, la_k, i0, g.M, k0, kend, t);
-                load<VEC>(xb, Bm, lb_j, lb_k, j0, g.N, k0, kend, t);
-            }
-            store<SPLIT, VEC>(As, xa, la_k == 1, t);
-            store<SPLIT, VEC>(Bs, xb, lb_k == 1, t);
-            __syncthreads();
-            if (VEC && k0 + BK < kend) {  // next tile's loads overlap this tile's products
-                load<VEC>(xa, A, la_i, la_k, i0, g.M, k0 + BK, kend, t);
-                load<VEC>(xb, Bm, lb_j, lb_k, j0, g.N, k0 + BK, kend, t);
-            }
-            mma_tile<SPLIT>(As, Bs, acc, wm, wn, lane, la_k == 1, lb_k == 1);
-            __syncthreads();
-        }
-    }
-    // epilogue: alpha * acc + beta * C0 + bias[j], then GELU' / store / GELU
-    float *C = g.C ? g.C + (long long)bz * g.sC : nullptr;
-    const float *C0 = g.C0 ? g.C0 + (long long)bz * g.sC0 : nullptr;
-    const float *Dg = g.dgelu_pre ? g.dgelu_pre + (long long)bz * g.sDg : nullptr;
-    float *act = g.act ? g.act + (long long)bz * g.sAct : nullptr;
-    // one row and two adjacent columns at a time (float2 when the launcher
-    // found every epilogue array 8-byte aligned with an even pitch)
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni)
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-                const int i = i0 + wm + mi * 16 + grp + hh * 8;
-                const int j = j0 + wn + ni * 8 + tig * 2;
-                if (i >= g.M || j >= g.N)
-                    continue;
-                const long long off = (long long)i * g.ldc + j;
-                float v[2] = {g.alpha * acc[mi][ni][2 * hh], g.alpha * acc[mi][ni][2 * hh + 1]};
-                if (ks_n > 1) {
-                    atomicAdd(&C[off], v[0]);
-                    if (j + 1 < g.N)
-                        atomicAdd(&C[off + 1], v[1]);
-                    continue;
-                }
-                if (g.pairs && j + 1 < g.N) {
-                    if (C0) {
-                        const float2 c = *reinterpret_cast<const float2 *>(C0 + off);
-                        v[0] += g.beta * c.x;
-                        v[1] += g.beta * c.y;
-                    }
-                    if (g.bias) {
-                        const float2 b = *reinterpret_cast<const float2 *>(g.bias + j);
-                        v[0] += b.x;
-                        v[1] += b.y;
-                    }
-                    if (Dg) {
-                        const float2 d = *reinterpret_cast<const float2 *>(Dg + off);
-                        v[0] *= gelu_grad<SPLIT>(d.x);
-                        v[1] *= gelu_grad<SPLIT>(d.y);
-                    }
-                    if (C)
-                        *reinterpret_cast<float2 *>(C + off) = make_float2(v[0], v[1]);
-                    if (act)
-                        *reinterpret_cast<float2 *>(act + off) = make_float2(gelu<SPLIT>(v[0]), gelu<SPLIT>(v[1]));
-                    continue;
-                }
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    if (j + c >= g.N)
-                        break;
-                    float w = v[c];
-                    if (C0)
-                        w += g.beta * C0[off + c];
-                    if (g.bias)
-                        w += g.bias[j + c];
-                    if (Dg)
-                        w *= gelu_grad<SPLIT>(Dg[off + c]);
-                    if (C)
-                        C[off + c] = w;
-                    if (act)
-                        act[off + c] = gelu<SPLIT>(w);
-                }
-            }
+    if constexpr (MODE == 2)
+        mainloop_bf16(g, bz, kslice, ks_n, i0, j0, acc, As, Bs, t, wm, wn, lane);
+    else
+        mainloop_f32<SPLIT, MODE == 1>(g, bz, kslice, ks_n, i0, j0, acc, As, Bs, t, wm, wn, lane);
+    epilogue<SPLIT>(g, bz, ks_n, i0, j0, acc, wm, wn, grp, tig);
 }
 
 // Input features per point: (u0, x, r, wall profile beta_l + (beta_r - beta_l) x).
+// FP32 rows of 4, or BF16 rows of 8 (the last 4 zero, so rows stay 16 bytes).
 __global__ void features_kernel(const float *__restrict__ u0, const float *__restrict__ r,
-                                const float *__restrict__ bl, const float *__restrict__ br, float *__restrict__ f,
-                                int batch, int n)
+                                const float *__restrict__ bl, const float *__restrict__ br, void *__restrict__ f,
+                                int batch, int n, int bf16)
 {
     const long long total = (long long)batch * n;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
         const int b = (int)(i / n), j = (int)(i % n);
         const float x = (float)(j + 1) / (float)(n + 1);
-        f[i * 4 + 0] = u0[i];
-        f[i * 4 + 1] = x;
-        f[i * 4 + 2] = r[b];
-        f[i * 4 + 3] = bl[b] + (br[b] - bl[b]) * x;
+        const float v[4] = {u0[i], x, r[b], bl[b] + (br[b] - bl[b]) * x};
+        if (bf16) {
+            __nv_bfloat16 *fb = static_cast<__nv_bfloat16 *>(f) + i * 8;
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                fb[c] = __float2bfloat16_rn(c < 4 ? v[c] : 0.0f);
+        } else {
+            float *ff = static_cast<float *>(f) + i * 4;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                ff[c] = v[c];
+        }
     }
 }
 
@@ -423,7 +594,7 @@ __global__ void features_kernel(const float *__restrict__ u0, const float *__res
 // vector (re, im): [[Rr^T, Ri^T], [-Ri^T, Rr^T]] with R = Rr + i Ri (C x C,
 // out x in).  Layout of rr/ri: [m][out][in]; of w: [m][2C][2C].
 __global__ void spec_assemble_kernel(const float *__restrict__ rr, const float *__restrict__ ri,
-                                     float *__restrict__ w, int modes, int c)
+                                     void *__restrict__ w, int modes, int c, int bf16)
 {
     const long long total = (long long)modes * 2 * c * 2 * c;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
@@ -442,7 +613,10 @@ __global__ void spec_assemble_kernel(const float *__restrict__ rr, const float *
             v = -ri[ro];
         else
             v = rr[ro];
-        w[e] = v;
+        if (bf16)
+            static_cast<__nv_bfloat16 *>(w)[e] = __float2bfloat16_rn(v);
+        else
+            static_cast<float *>(w)[e] = v;
     }
 }
 
@@ -462,13 +636,15 @@ __global__ void spec_reduce_kernel(const float *__restrict__ dw, float *__restri
     }
 }
 
-// Column sums (bias gradients): out[j] = sum_i x[i, j], x is rows x cols.
-__global__ void colsum_kernel(const float *__restrict__ x, float *__restrict__ out, long long rows, int cols)
+// Column sums (bias gradients): out[j] = sum_i x[i, j], x is rows x cols
+// (FP32 or BF16).
+__global__ void colsum_kernel(const void *__restrict__ x, float *__restrict__ out, long long rows, int cols, int bf16)
 {
     const int j = blockIdx.x;
     float s = 0.0f;
     for (long long i = threadIdx.x; i < rows; i += blockDim.x)
-        s += x[i * cols + j];
+        s += bf16 ? __bfloat162float(static_cast<const __nv_bfloat16 *>(x)[i * cols + j])
+                  : static_cast<const float *>(x)[i * cols + j];
     __shared__ float red[256];
     red[threadIdx.x] = s;
     __syncthreads();
@@ -484,7 +660,7 @@ __global__ void colsum_kernel(const float *__restrict__ x, float *__restrict__ o
 // Relative L2 loss per sample and its gradient: loss_b = ||p - y|| / ||y||,
 // mean over the batch; dp = (p - y) / (||p - y|| ||y|| batch).
 __global__ void rel_l2_kernel(const float *__restrict__ pred, const float *__restrict__ target,
-                              float *__restrict__ dpred, float *__restrict__ loss_per_sample, int n, int batch)
+                              void *__restrict__ dpred, float *__restrict__ loss_per_sample, int n, int batch, int bf16)
 {
     const int b = blockIdx.x;
     const float *p = pred + (long long)b * n;
@@ -511,8 +687,13 @@ __global__ void rel_l2_kernel(const float *__restrict__ pred, const float *__res
         loss_per_sample[b] = ne / ny;
     if (dpred) {
         const float sc = 1.0f / (fmaxf(ne, 1e-30f) * ny * (float)batch);
-        for (int j = threadIdx.x; j < n; j += blockDim.x)
-            dpred[(long long)b * n + j] = (p[j] - y[j]) * sc;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const float d = (p[j] - y[j]) * sc;
+            if (bf16)
+                static_cast<__nv_bfloat16 *>(dpred)[(long long)b * n + j] = __float2bfloat16_rn(d);
+            else
+                static_cast<float *>(dpred)[(long long)b * n + j] = d;
+        }
     }
 }
 
@@ -531,12 +712,17 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
     }
 }
 
-// Round to the nearest BF16 value (kept in FP32 storage): the network's
-// weights as the BF16 model sees them.
-__global__ void round_bf16_kernel(const float *__restrict__ x, float *__restrict__ y, long long n)
+// Round to the nearest BF16 value: the network's weights as the BF16 model
+// sees them, kept in FP32 storage (y) and, when y16 is set, as BF16.
+__global__ void round_bf16_kernel(const float *__restrict__ x, float *__restrict__ y, __nv_bfloat16 *__restrict__ y16,
+                                  long long n)
 {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        y[i] = __bfloat162float(__float2bfloat16_rn(x[i]));
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x[i]);
+        y[i] = __bfloat162float(h);
+        if (y16)
+            y16[i] = h;
+    }
 }
 
 int grid_for(long long n)
@@ -549,16 +735,17 @@ int grid_for(long long n)
 
 namespace {
 
-// float4 staging is allowed when the unit-stride dimension's extent, the
-// other stride, the batch stride and the base are all multiples of 4 floats.
-int vec_ok(const float *X, long long s_r, long long s_k, int rmax, int kdim, long long sbatch, int batch)
+// Vector staging (16 bytes: 4 floats or 8 BF16 values along the unit-stride
+// dimension) is allowed when that dimension's extent, the other stride, the
+// batch stride and the base are all whole multiples of 16 bytes.
+int vec_ok(const void *X, long long s_r, long long s_k, int rmax, int kdim, long long sbatch, int batch, int q)
 {
-    if (!X || (reinterpret_cast<uintptr_t>(X) & 15) != 0 || (batch > 1 && sbatch % 4 != 0))
+    if (!X || (reinterpret_cast<uintptr_t>(X) & 15) != 0 || (batch > 1 && sbatch % q != 0))
         return 0;
     if (s_k == 1)
-        return (kdim % 4 == 0 && s_r % 4 == 0) ? 1 : 0;
+        return (kdim % q == 0 && s_r % q == 0) ? 1 : 0;
     if (s_r == 1)
-        return (rmax % 4 == 0 && s_k % 4 == 0) ? 1 : 0;
+        return (rmax % q == 0 && s_k % q == 0) ? 1 : 0;
     return 0;
 }
 
@@ -570,34 +757,39 @@ cudaError_t sno_gemm(const GemmArgs &g0, int batch, bool split, cudaStream_t s)
         return cudaSuccess;
     GemmArgs g = g0;
     const int ks = g.ksplit > 1 ? g.ksplit : 1;
-    if (ks > 1 && (g.A2 || g.C0 || g.bias || g.dgelu_pre || g.act || !g.C))
+    if (ks > 1 && (g.A2 || g.C0 || g.bias || g.dgelu_pre || g.act || !g.C || g.out_bf16))
         return cudaErrorInvalidValue;
-    g.vec[0] = vec_ok(g.A, g.lda_i, g.lda_k, g.M, g.K, g.sA, batch);
-    g.vec[1] = vec_ok(g.B, g.ldb_j, g.ldb_k, g.N, g.K, g.sB, batch);
-    g.vec[2] = g.A2 ? vec_ok(g.A2, g.lda2_i, g.lda2_k, g.M, g.K2, g.sA2, batch) : 0;
-    g.vec[3] = g.A2 ? vec_ok(g.B2, g.ldb2_j, g.ldb2_k, g.N, g.K2, g.sB2, batch) : 0;
+    if (g.in_bf16 && split)
+        return cudaErrorInvalidValue;
+    const int q = g.in_bf16 ? 8 : 4;
+    g.vec[0] = vec_ok(g.A, g.lda_i, g.lda_k, g.M, g.K, g.sA, batch, q);
+    g.vec[1] = vec_ok(g.B, g.ldb_j, g.ldb_k, g.N, g.K, g.sB, batch, q);
+    g.vec[2] = g.A2 ? vec_ok(g.A2, g.lda2_i, g.lda2_k, g.M, g.K2, g.sA2, batch, q) : 0;
+    g.vec[3] = g.A2 ? vec_ok(g.B2, g.ldb2_j, g.ldb2_k, g.N, g.K2, g.sB2, batch, q) : 0;
     const bool vec = g.vec[0] && g.vec[1] && (!g.A2 || (g.vec[2] && g.vec[3]));
     auto al8 = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 7) == 0; };
     g.pairs = (g.ldc % 2 == 0) && al8(g.C) && al8(g.C0) && al8(g.dgelu_pre) && al8(g.act) && al8(g.bias) &&
               (batch == 1 || (g.sC % 2 == 0 && g.sC0 % 2 == 0 && g.sDg % 2 == 0 && g.sAct % 2 == 0));
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, batch * ks);
-    if (split)
-        vec ? gemm_kernel<true, true><<<grid, NT, 0, s>>>(g) : gemm_kernel<true, false><<<grid, NT, 0, s>>>(g);
+    if (g.in_bf16)
+        gemm_kernel<false, 2><<<grid, NT, 0, s>>>(g);
+    else if (split)
+        vec ? gemm_kernel<true, 1><<<grid, NT, 0, s>>>(g) : gemm_kernel<true, 0><<<grid, NT, 0, s>>>(g);
     else
-        vec ? gemm_kernel<false, true><<<grid, NT, 0, s>>>(g) : gemm_kernel<false, false><<<grid, NT, 0, s>>>(g);
+        vec ? gemm_kernel<false, 1><<<grid, NT, 0, s>>>(g) : gemm_kernel<false, 0><<<grid, NT, 0, s>>>(g);
     return cudaGetLastError();
 }
 
-cudaError_t sno_features(const float *u0, const float *r, const float *bl, const float *br, float *f, int batch, int n,
-                         cudaStream_t s)
+cudaError_t sno_features(const float *u0, const float *r, const float *bl, const float *br, void *f, int batch, int n,
+                         int bf16, cudaStream_t s)
 {
-    features_kernel<<<grid_for((long long)batch * n), 256, 0, s>>>(u0, r, bl, br, f, batch, n);
+    features_kernel<<<grid_for((long long)batch * n), 256, 0, s>>>(u0, r, bl, br, f, batch, n, bf16);
     return cudaGetLastError();
 }
 
-cudaError_t sno_spec_assemble(const float *rr, const float *ri, float *w, int modes, int c, cudaStream_t s)
+cudaError_t sno_spec_assemble(const float *rr, const float *ri, void *w, int modes, int c, int bf16, cudaStream_t s)
 {
-    spec_assemble_kernel<<<grid_for(4LL * modes * c * c), 256, 0, s>>>(rr, ri, w, modes, c);
+    spec_assemble_kernel<<<grid_for(4LL * modes * c * c), 256, 0, s>>>(rr, ri, w, modes, c, bf16);
     return cudaGetLastError();
 }
 
@@ -607,15 +799,16 @@ cudaError_t sno_spec_reduce(const float *dw, float *drr, float *dri, int modes, 
     return cudaGetLastError();
 }
 
-cudaError_t sno_colsum(const float *x, float *out, long long rows, int cols, cudaStream_t s)
+cudaError_t sno_colsum(const void *x, float *out, long long rows, int cols, int bf16, cudaStream_t s)
 {
-    colsum_kernel<<<cols, 256, 0, s>>>(x, out, rows, cols);
+    colsum_kernel<<<cols, 256, 0, s>>>(x, out, rows, cols, bf16);
     return cudaGetLastError();
 }
 
-cudaError_t sno_rel_l2(const float *pred, const float *target, float *dpred, float *loss, int n, int batch, cudaStream_t s)
+cudaError_t sno_rel_l2(const float *pred, const float *target, void *dpred, float *loss, int n, int batch, int bf16,
+                       cudaStream_t s)
 {
-    rel_l2_kernel<<<batch, 256, 0, s>>>(pred, target, dpred, loss, n, batch);
+    rel_l2_kernel<<<batch, 256, 0, s>>>(pred, target, dpred, loss, n, batch, bf16);
     return cudaGetLastError();
 }
 
@@ -626,9 +819,9 @@ cudaError_t sno_adam(float *p, const float *g, float *m, float *v, long long n, 
     return cudaGetLastError();
 }
 
-cudaError_t sno_round_bf16(const float *x, float *y, long long n, cudaStream_t s)
+cudaError_t sno_round_bf16(const float *x, float *y, void *y16, long long n, cudaStream_t s)
 {
-    round_bf16_kernel<<<grid_for(n), 256, 0, s>>>(x, y, n);
+    round_bf16_kernel<<<grid_for(n), 256, 0, s>>>(x, y, static_cast<__nv_bfloat16 *>(y16), n);
     return cudaGetLastError();
 }
 
