@@ -459,7 +459,9 @@ def sno_flops_per_problem(n=SNO_N, C=64, M=16, L=4, H=128):
 
 
 def sno_launches_per_forward(L=4):
-    return 3 + 4 * L + 2
+    """Inference: weight rounding, lift, per layer (spectral weights, DFT,
+    mode mixing, fused layer GEMM), output init, fused projection."""
+    return 2 + 4 * L + 2
 
 
 def launches_per_solve(kernel, depth):

@@ -169,13 +169,12 @@ ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float
     const float *P = s->pw;  // FP32 rounded weights: biases and the spectral matrices' source
     const void *F = bf ? s->F16 : static_cast<const void *>(s->F);
     const void *G = bf ? s->G16 : static_cast<const void *>(s->G);
-    const int ldf = bf ? 8 : 4;
     SNO_TRY(ge::sno_round_bf16(s->params, s->pw, bf ? s->pw16 : nullptr, s->n_params, st));
-    SNO_TRY(ge::sno_features(u0, r, bl, br, s->feat, B, n, bf ? 1 : 0, st));
-    // lift
-    ge::GemmArgs g = gemm(s->feat, ldf, 1, weight(s, s->off_w0), C, 1, s->v[0], C, (int)R, C, 4);
-    g.bias = P + s->off_b0;
-    SNO_TRY(ge::sno_gemm(act_fmt(g, bf), 1, s->split, st));
+    // lift (K = 4: no GEMM); the features themselves only for the backward pass
+    if (keep)
+        SNO_TRY(ge::sno_features(u0, r, bl, br, s->feat, B, n, bf ? 1 : 0, st));
+    SNO_TRY(ge::sno_lift(u0, r, bl, br, weight(s, s->off_w0), P + s->off_b0, s->v[0], B, n, C, bf ? 1 : 0, st));
+    ge::GemmArgs g;
     for (int l = 0; l < s->L; ++l) {
         const LayerOff &o = s->lay[l];
         void *ws = at(s->wspec, (long long)l * M * 4 * C * C, bf);
@@ -215,12 +214,26 @@ ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float
         }
         SNO_TRY(ge::sno_gemm(act_fmt(g, bf), B, s->split, st));
     }
-    // projection
-    g = gemm(s->v[s->L], C, 1, weight(s, s->off_q1), H, 1, keep ? s->hpre : nullptr, H, (int)R, H, C);
+    // projection; the residual output (FP32) predicts the change of u over the jump
+    if (!keep) {
+        // inference: h never leaves the chip: the first projection's epilogue
+        // writes per-row partial sums of GELU(.)_j Q2[j] (one per 32 hidden
+        // columns, into the gradient scratch dA), summed in a fixed order
+        // into out = u0 + q2 + sum
+        const int slots = (H + 31) / 32;
+        g = gemm(s->v[s->L], C, 1, weight(s, s->off_q1), H, 1, nullptr, H, (int)R, H, C);
+        g.bias = P + s->off_qb1;
+        g.dot_w = P + s->off_q2;
+        g.dot_out = s->dA;
+        g.dot_slots = slots;
+        SNO_TRY(ge::sno_gemm(act_fmt(g, bf), 1, s->split, st));
+        SNO_TRY(ge::sno_dot_finish(u0, P + s->off_qb2, s->dA, slots, out, R, st));
+        return GE_OK;
+    }
+    g = gemm(s->v[s->L], C, 1, weight(s, s->off_q1), H, 1, s->hpre, H, (int)R, H, C);
     g.bias = P + s->off_qb1;
     g.act = s->h;
     SNO_TRY(ge::sno_gemm(act_fmt(g, bf), 1, s->split, st));
-    // residual output (FP32): the network predicts the change of u over the jump
     g = gemm(s->h, H, 1, weight(s, s->off_q2), 1, 1, out, 1, (int)R, 1, H);
     g.bias = P + s->off_qb2;
     g.C0 = u0;

@@ -43,6 +43,14 @@ struct GemmArgs {
     void *act;
     long long sAct;
     int in_bf16, out_bf16, dg_bf16;
+    // dot_w set (FP32, N entries): instead of storing, each output row i
+    // writes its partial sums of GELU(value_ij) dot_w[j], one per 32-column
+    // group of the tile columns, to dot_out[i * dot_slots + group] (no
+    // atomics, so the result is deterministic); dot_slots >= ceil(N / 32).
+    // No C, act or ksplit with it.
+    const float *dot_w;
+    float *dot_out;
+    int dot_slots;
     // set by sno_gemm: vector staging allowed for A, B, A2, B2 (float4 for
     // FP32, 16-byte cp.async chunks of 8 elements for BF16); paired epilogue
     int vec[4];
@@ -60,5 +68,12 @@ cudaError_t sno_rel_l2(const float *pred, const float *target, void *dpred, floa
 cudaError_t sno_adam(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
                      float eps, float c1, float c2, cudaStream_t s);
 cudaError_t sno_round_bf16(const float *x, float *y, void *y16, long long n, cudaStream_t s);
+// v0[b n + j][c] = b0[c] + sum_k feature_k(b, j) W0[k][c] (features as in
+// sno_features, rounded to BF16 when bf16); W0 BF16 or FP32 as v0.
+cudaError_t sno_lift(const float *u0, const float *r, const float *bl, const float *br, const void *w0,
+                     const float *b0, void *v0, int batch, int n, int c, int bf16, cudaStream_t s);
+// out[i] = u0[i] + q2[0] + sum_k part[i * slots + k], summed in a fixed order
+cudaError_t sno_dot_finish(const float *u0, const float *q2, const float *part, int slots, float *out, long long n,
+                           cudaStream_t s);
 
 }  // namespace ge

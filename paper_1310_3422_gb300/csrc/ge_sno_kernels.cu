@@ -474,6 +474,34 @@ __device__ __forceinline__ void epilogue(const GemmArgs &g, int bz, int ks_n, in
     const float *C0 = g.C0 ? g.C0 + (long long)bz * g.sC0 : nullptr;
     const void *Dg = g.dgelu_pre ? static_cast<const char *>(g.dgelu_pre) + (long long)bz * g.sDg * des : nullptr;
     void *act = g.act ? static_cast<char *>(g.act) + (long long)bz * g.sAct * oes : nullptr;
+    if (g.dot_w) {
+        // per row: sum over this CTA's columns of GELU(value) * dot_w[j]
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int i = i0 + wm + mi * 16 + grp + hh * 8;
+                float part = 0.0f;
+#pragma unroll
+                for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const int j = j0 + wn + ni * 8 + tig * 2 + c;
+                        if (i < g.M && j < g.N) {
+                            float w = g.alpha * acc[mi][ni][2 * hh + c];
+                            if (g.bias)
+                                w += g.bias[j];
+                            part += gelu<SPLIT>(w) * g.dot_w[j];
+                        }
+                    }
+                // the four lanes of a row group (tig) hold the warp's 32 columns
+                part += __shfl_xor_sync(0xffffffffu, part, 1);
+                part += __shfl_xor_sync(0xffffffffu, part, 2);
+                if (tig == 0 && i < g.M && j0 + wn < g.N)
+                    g.dot_out[((long long)bz * g.M + i) * g.dot_slots + (j0 + wn) / 32] = part;
+            }
+        return;
+    }
 #pragma unroll
     for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
@@ -725,6 +753,51 @@ __global__ void round_bf16_kernel(const float *__restrict__ x, float *__restrict
     }
 }
 
+// Lift without a GEMM (K = 4): one thread per point and 8 channels.
+template <typename T>
+__global__ void lift_kernel(const float *__restrict__ u0, const float *__restrict__ r, const float *__restrict__ bl,
+                            const float *__restrict__ br, const T *__restrict__ w0, const float *__restrict__ b0,
+                            T *__restrict__ v0, int batch, int n, int c, int bf16)
+{
+    const int cg = (c + 7) / 8;
+    const long long total = (long long)batch * n * cg;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / cg;
+        const int c0 = (int)(e % cg) * 8;
+        const int b = (int)(i / n), j = (int)(i % n);
+        const float x = (float)(j + 1) / (float)(n + 1);
+        float f[4] = {u0[i], x, r[b], bl[b] + (br[b] - bl[b]) * x};
+        if (bf16) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                f[k] = __bfloat162float(__float2bfloat16_rn(f[k]));
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int ch = c0 + q;
+            if (ch >= c)
+                break;
+            float v = b0[ch];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                v = fmaf(f[k], (float)w0[k * c + ch], v);
+            v0[i * c + ch] = (T)v;
+        }
+    }
+}
+
+__global__ void dot_finish_kernel(const float *__restrict__ u0, const float *__restrict__ q2,
+                                  const float *__restrict__ part, int slots, float *__restrict__ out, long long n)
+{
+    const float b = q2[0];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float acc = 0.0f;
+        for (int k = 0; k < slots; ++k)
+            acc += part[i * slots + k];
+        out[i] = u0[i] + (b + acc);
+    }
+}
+
 int grid_for(long long n)
 {
     long long b = (n + 255) / 256;
@@ -757,7 +830,9 @@ cudaError_t sno_gemm(const GemmArgs &g0, int batch, bool split, cudaStream_t s)
         return cudaSuccess;
     GemmArgs g = g0;
     const int ks = g.ksplit > 1 ? g.ksplit : 1;
-    if (ks > 1 && (g.A2 || g.C0 || g.bias || g.dgelu_pre || g.act || !g.C || g.out_bf16))
+    if (ks > 1 && (g.A2 || g.C0 || g.bias || g.dgelu_pre || g.act || !g.C || g.out_bf16 || g.dot_w))
+        return cudaErrorInvalidValue;
+    if (g.dot_w && (g.C || g.act || g.C0 || g.dgelu_pre || !g.dot_out || g.dot_slots < (g.N + 31) / 32))
         return cudaErrorInvalidValue;
     if (g.in_bf16 && split)
         return cudaErrorInvalidValue;
@@ -816,6 +891,26 @@ cudaError_t sno_adam(float *p, const float *g, float *m, float *v, long long n, 
                      float c1, float c2, cudaStream_t s)
 {
     adam_kernel<<<grid_for(n), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t sno_lift(const float *u0, const float *r, const float *bl, const float *br, const void *w0,
+                     const float *b0, void *v0, int batch, int n, int c, int bf16, cudaStream_t s)
+{
+    const long long total = (long long)batch * n * ((c + 7) / 8);
+    if (bf16)
+        lift_kernel<__nv_bfloat16><<<grid_for(total), 256, 0, s>>>(u0, r, bl, br, static_cast<const __nv_bfloat16 *>(w0),
+                                                                  b0, static_cast<__nv_bfloat16 *>(v0), batch, n, c, 1);
+    else
+        lift_kernel<float><<<grid_for(total), 256, 0, s>>>(u0, r, bl, br, static_cast<const float *>(w0), b0,
+                                                          static_cast<float *>(v0), batch, n, c, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t sno_dot_finish(const float *u0, const float *q2, const float *part, int slots, float *out, long long n,
+                           cudaStream_t s)
+{
+    dot_finish_kernel<<<grid_for(n), 256, 0, s>>>(u0, q2, part, slots, out, n);
     return cudaGetLastError();
 }
 
