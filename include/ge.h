@@ -66,7 +66,7 @@ typedef enum {
                                 evaluation in that order); GE_F64/GE_F32 only */
     GE_KERNEL_ONESTEP = 2,   /* one launch per step on the group systems'
                                 right-hand sides (see GE_KERNEL_TEMPORAL)     */
-    GE_KERNEL_TEMPORAL = 3   /* `depth` steps per launch: a tile plus a halo
+    GE_KERNEL_TEMPORAL = 3,  /* `depth` steps per launch: a tile plus a halo
                                 of depth+1 points per side is staged in shared
                                 memory by TMA and advanced on chip.  Between
                                 steps it carries the right-hand side of each
@@ -74,6 +74,22 @@ typedef enum {
                                 terms, so one step is the block map
                                 (I - r G)(I + r G)^{-1} = [[1,2r],[2r,1]]/(1+2r)
                                 on each group: the same scheme, reassociated */
+    GE_KERNEL_TEMPORAL_DF = 4 /* GE_KERNEL_TEMPORAL for GE_F64 contexts with
+                                the steps evaluated on the FP32 pipes in
+                                double-float arithmetic: every value an
+                                unevaluated sum of two floats (about 48
+                                significant bits), each step built from
+                                error-free transformations (TwoProd by FMA,
+                                TwoSum, Fast2Sum).  Storage, API and HBM bytes
+                                stay FP64; each call prescales by the power of
+                                two that brings max |u| and the wall values
+                                below 1, so any double data are in range.
+                                Rounding is about 2^-48 per step instead of
+                                2^-53: within 1e-12 of a serial FP64
+                                evaluation at moderate r, but at very large r
+                                (where FP64 itself loses digits to
+                                conditioning) some 30x further off than FP64.
+                                GE_F64 only; r <= 2^20; width k = 1 */
 } ge_kernel;
 
 typedef struct ge_ctx ge_ctx;  /* opaque; owned by the library */
@@ -99,9 +115,11 @@ ge_status ge_create(ge_ctx **out, int64_t n, double r, double beta_l, double bet
                     ge_precision prec, const void *u0_dev, void *stream);
 
 /* Select the kernel used by later ge_step_n calls.  depth: steps per launch
- * for GE_KERNEL_TEMPORAL, 1..1023 (0 = built-in default); ignored otherwise.
+ * for GE_KERNEL_TEMPORAL and GE_KERNEL_TEMPORAL_DF, 1..1023 (0 = built-in
+ * default); ignored otherwise.
  * Errors: GE_EINVAL (NULL ctx, unknown kernel, depth out of range,
- * GE_KERNEL_CANONICAL with GE_F32_COMP). */
+ * GE_KERNEL_CANONICAL with GE_F32_COMP, GE_KERNEL_TEMPORAL_DF with a
+ * precision other than GE_F64 or with r > 2^20). */
 ge_status ge_set_kernel(ge_ctx *ctx, ge_kernel kernel, int32_t depth);
 
 /* The kernel in use and the tiled kernel's steps per launch (the default
@@ -110,7 +128,7 @@ ge_status ge_get_kernel(const ge_ctx *ctx, ge_kernel *kernel, int32_t *depth);
 
 /* Autotune the tiled kernel's steps per launch: times `steps` steps from the
  * current state at each candidate depth (FP64: 24, 32, 48, 64, 96; FP32:
- * 64 ... 256), keeps the fastest (returned in *best_depth, may be NULL) and
+ * 64 ... 256; double-float: 32 ... 128), keeps the fastest (returned in *best_depth, may be NULL) and
  * leaves the state and the step counter as they were.  A context on the
  * canonical, one-step or width-k path keeps its setting.  Synchronous;
  * allocates one scratch copy of the state.  Errors: GE_EINVAL, GE_ENOMEM,

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(PKG, "libge.so")
 
 GE_OK, GE_EINVAL, GE_ENOMEM, GE_ECUDA, GE_ETIMEOUT, GE_ENONFINITE = range(6)
 GE_F64, GE_F32, GE_F32_COMP = 0, 1, 2
-GE_KERNEL_AUTO, GE_KERNEL_CANONICAL, GE_KERNEL_ONESTEP, GE_KERNEL_TEMPORAL = 0, 1, 2, 3
+GE_KERNEL_AUTO, GE_KERNEL_CANONICAL, GE_KERNEL_ONESTEP, GE_KERNEL_TEMPORAL, GE_KERNEL_TEMPORAL_DF = 0, 1, 2, 3, 4
 
 # Every symbol include/ge.h and include/ge_sno.h declare.
 EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", "ge_read_state", "ge_write_state",

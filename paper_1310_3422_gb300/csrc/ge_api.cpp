@@ -40,6 +40,10 @@ ge_status cuda_fail(cudaError_t e, const char *what)
 
 constexpr int kDefaultDepthF64 = 48;
 constexpr int kDefaultDepthF32 = 128;
+constexpr int kDefaultDepthDf = 96;
+// Largest r the double-float kernel takes: the right-hand side reaches about
+// (1 + 3r) times the data and must stay far inside the FP32 exponent range.
+constexpr double kDfMaxR = 1048576.0;
 constexpr int kMaxDepth = 1023;
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
@@ -84,6 +88,7 @@ struct ge_ctx {
     int *err_dev = nullptr;
     int num_sms = 0;
     int tb_blocks_per_sm = 0;
+    int tb_df_blocks_per_sm = 0;  // double-float kernel (GE_F64 contexts)
     ge::CanonCoef canon{};
     ge::TbParams tb{};   // launch-independent fields filled at creation
 };
@@ -163,7 +168,47 @@ bool valid_prec(int p) { return p == GE_F64 || p == GE_F32 || p == GE_F32_COMP; 
 bool valid_kernel(int k)
 {
     return k == GE_KERNEL_AUTO || k == GE_KERNEL_CANONICAL || k == GE_KERNEL_ONESTEP ||
-           k == GE_KERNEL_TEMPORAL;
+           k == GE_KERNEL_TEMPORAL || k == GE_KERNEL_TEMPORAL_DF;
+}
+
+// (hi, lo) float pair of a double: hi = fl32(x), lo = fl32(x - hi).
+void df_split(double x, float *pair)
+{
+    pair[0] = (float)x;
+    pair[1] = (float)(x - (double)pair[0]);
+}
+
+// Prescale code of one value (see ge::kDfCodeBias); 0 for zero.
+int df_code_of(double x)
+{
+    if (x == 0.0)
+        return 0;
+    int e = 0;
+    std::frexp(x, &e);  // |x| = m 2^e with 0.5 <= m < 1: the smallest e with |x| < 2^e
+    return e + ge::kDfCodeBias;
+}
+
+// Launch-independent fields of the double-float kernel.  The scaled map's
+// growth per step is exactly 1 + g with g = g_hi + g_lo the pair the kernel
+// holds; the host's scale mirror (growth_lo) and the singleton factor use
+// that g.  Rescalings keep the FP32 headroom.
+ge::TbParams df_params(const ge_ctx *c, double *growth_lo)
+{
+    ge::TbParams p = c->tb;
+    const double r = c->r;
+    df_split(2.0 * r, p.dfc[0]);
+    p.df_gl = p.dfc[0][1] != 0.0f;
+    const double g = (double)p.dfc[0][0] + (double)p.dfc[0][1];
+    p.onepg = 1.0 + g;
+    const double bb = p.onepg - 1.0;  // TwoSum: onepg + lo == 1 + g exactly
+    *growth_lo = (1.0 - (p.onepg - bb)) + (g - bb);
+    df_split((1.0 + g) * ((1.0 - r) / (1.0 + r)), p.dfc[1]);
+    df_split(r, p.dfc[2]);
+    df_split(1.0 - r, p.dfc[3]);
+    const int every = (int)std::floor(GE_F32_HEADROOM / std::log2(1.0 + 2.0 * r));
+    p.rescale_every = every < 1 ? 1 : every;
+    p.df_code = c->err_dev + 32;
+    return p;
 }
 
 // Depth of the tiled kernel from the tuning table named by GE_TUNE_TABLE
@@ -196,27 +241,41 @@ int table_depth(ge_precision prec, int64_t n)
 
 int effective_depth(const ge_ctx *c)
 {
-    return c->depth ? c->depth : ((c->prec == GE_F64) ? kDefaultDepthF64 : kDefaultDepthF32);
+    if (c->depth)
+        return c->depth;
+    if (c->kernel == GE_KERNEL_TEMPORAL_DF)
+        return kDefaultDepthDf;
+    return (c->prec == GE_F64) ? kDefaultDepthF64 : kDefaultDepthF32;
 }
 
-// Advance `steps` steps with the tiled kernel, `depth` steps per launch.
-// The host mirrors the kernel's scale recurrence (see TbParams): sigma starts
-// at 1 after the entry conversion, is multiplied by (1+2r) per block step and
-// by 2^-e at each rescaling, where e brings it back into [1, 2).
-ge_status run_tiled(ge_ctx *c, int64_t steps, int depth)
+// Advance `steps` steps with the tiled kernel, `depth` steps per launch
+// (df: the double-float kernel).  The host mirrors the kernel's scale
+// recurrence (see TbParams): sigma starts at 1 after the entry conversion, is
+// multiplied by (1+2r) per block step and by 2^-e at each rescaling, where e
+// brings it back into [1, 2).
+ge_status run_tiled(ge_ctx *c, int64_t steps, int depth, bool df = false)
 {
-    const int every = c->tb.rescale_every;
+    double growth_lo = c->onepg_lo;
+    const ge::TbParams base = df ? df_params(c, &growth_lo) : c->tb;
+    const int every = base.rescale_every;
     if (every > 0 && depth > (ge::kMaxRescale - 1) * every)
         depth = (ge::kMaxRescale - 1) * every;
     if (depth > ge::kMaxTableSteps)
         depth = ge::kMaxTableSteps;
     const int prec = c->prec == GE_F64 ? 0 : (c->prec == GE_F32 ? 1 : 2);
+    if (df) {
+        // the prescale 2^-e0 of this call: data and walls below 1 in magnitude
+        const int wl = df_code_of(c->beta_l), wr = df_code_of(c->beta_r);
+        cudaError_t e = ge::df_prescale(c->buf[c->cur], c->n, wl > wr ? wl : wr, c->err_dev + 32, c->stream);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "double-float prescale launch");
+    }
     double sigma = 1.0, sigma_lo = 0.0;  // double-double scale
     int until = every;
     int64_t n0 = 0;
     while (n0 < steps) {
         const int64_t L = (steps - n0 < depth) ? steps - n0 : depth;
-        ge::TbParams p = c->tb;
+        ge::TbParams p = base;
         const bool last = (n0 + L == steps);
         p.do_entry = (n0 == 0) ? 1 : 0;
         p.n_mid = (int)(last ? L - 1 : L);
@@ -227,7 +286,7 @@ ge_status run_tiled(ge_ctx *c, int64_t steps, int depth)
         if (every > 0) {
             int ev = 0;
             for (int m = 0; m < p.n_mid; ++m) {
-                ge::dd_mul(sigma, sigma_lo, p.onepg, c->onepg_lo);
+                ge::dd_mul(sigma, sigma_lo, p.onepg, growth_lo);
                 if (--until == 0) {
                     until = every;
                     int e2 = 0;
@@ -243,21 +302,27 @@ ge_status run_tiled(ge_ctx *c, int64_t steps, int depth)
             p.x1 = ge::dd_div(c->tb.x1, sigma, sigma_lo);
             p.x2 = ge::dd_div(c->tb.x2, sigma, sigma_lo);
             p.xs = ge::dd_div(c->tb.xs, sigma, sigma_lo);
+            df_split(p.x1, p.dfc[4]);
+            df_split(p.x2, p.dfc[5]);
+            df_split(p.xs, p.dfc[6]);
         }
+        p.df_in = p.do_entry;
+        p.df_out = p.do_exit;
         const int reach = p.do_entry + p.n_mid + p.do_exit;
-        if (!ge::tb_geometry(prec, reach, &p.H, &p.U))
+        if (!(df ? ge::tb_df_geometry(reach, &p.H, &p.U) : ge::tb_geometry(prec, reach, &p.H, &p.U)))
             return fail(GE_EINVAL, "depth %d does not fit a tile", depth);
         p.n = c->n;
         p.n_rows = c->n_rows;
         p.n_tiles = (c->n + p.U - 1) / p.U;
         p.out = c->buf[c->cur ^ 1];
         p.err = c->err_dev;
-        long long grid = (long long)c->num_sms * c->tb_blocks_per_sm;
+        long long grid = (long long)c->num_sms * (df ? c->tb_df_blocks_per_sm : c->tb_blocks_per_sm);
         if (grid > p.n_tiles)
             grid = p.n_tiles;
         if (grid < 1)
             grid = 1;
-        cudaError_t e = ge::launch_tb(prec, &c->tmap[c->cur], p, (int)grid, c->stream);
+        cudaError_t e = df ? ge::launch_tb_df(&c->tmap[c->cur], p, (int)grid, c->stream)
+                           : ge::launch_tb(prec, &c->tmap[c->cur], p, (int)grid, c->stream);
         if (e != cudaSuccess)
             return cuda_fail(e, "tiled GE kernel launch");
         c->cur ^= 1;
@@ -405,6 +470,11 @@ ge_status ge_create(ge_ctx **out, int64_t n, double r, double beta_l, double bet
     }
     const int prec_idx = prec == GE_F64 ? 0 : (prec == GE_F32 ? 1 : 2);
     e = ge::tb_occupancy(prec_idx, &c->tb_blocks_per_sm);
+    if (e == cudaSuccess && prec == GE_F64) {
+        e = ge::tb_df_occupancy(&c->tb_df_blocks_per_sm);
+        if (e == cudaSuccess && c->tb_df_blocks_per_sm < 1)
+            e = cudaErrorInvalidConfiguration;
+    }
     if (e != cudaSuccess || c->tb_blocks_per_sm < 1) {
         release(c);
         return cuda_fail(e == cudaSuccess ? cudaErrorInvalidConfiguration : e,
@@ -424,6 +494,10 @@ ge_status ge_set_kernel(ge_ctx *c, ge_kernel kernel, int32_t depth)
         return fail(GE_EINVAL, "ge_set_kernel: depth %d outside 0..%d", (int)depth, kMaxDepth);
     if (kernel == GE_KERNEL_CANONICAL && c->prec == GE_F32_COMP)
         return fail(GE_EINVAL, "ge_set_kernel: the canonical kernel has no compensated variant");
+    if (kernel == GE_KERNEL_TEMPORAL_DF && c->prec != GE_F64)
+        return fail(GE_EINVAL, "ge_set_kernel: the double-float kernel needs a GE_F64 context");
+    if (kernel == GE_KERNEL_TEMPORAL_DF && c->r > kDfMaxR)
+        return fail(GE_EINVAL, "ge_set_kernel: the double-float kernel takes r <= 2^20 (r = %g)", c->r);
     c->kernel = kernel;
     c->depth = depth;
     return GE_OK;
@@ -450,7 +524,9 @@ ge_status ge_tune(ge_ctx *c, int64_t steps, int32_t *best_depth)
     ge::NvtxRange nvtx("ge_tune");
     static const int cand64[] = {24, 32, 48, 64, 96};
     static const int cand32[] = {64, 96, 128, 192, 256};
-    const int *cand = c->prec == GE_F64 ? cand64 : cand32;
+    static const int cand_df[] = {32, 48, 64, 96, 128};
+    const bool df = c->kernel == GE_KERNEL_TEMPORAL_DF;
+    const int *cand = df ? cand_df : (c->prec == GE_F64 ? cand64 : cand32);
     const size_t bytes = (size_t)c->n * elem_size(c->prec);
     void *saved = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -474,7 +550,7 @@ ge_status ge_tune(ge_ctx *c, int64_t steps, int32_t *best_depth)
             if (e == cudaSuccess && rep == 1)
                 e = cudaEventRecord(e0, c->stream);
             if (e == cudaSuccess)
-                st = run_tiled(c, steps, cand[i]);
+                st = run_tiled(c, steps, cand[i], df);
             if (e == cudaSuccess && st == GE_OK && rep == 1)
                 e = cudaEventRecord(e1, c->stream);
         }
@@ -544,6 +620,9 @@ ge_status ge_step_n(ge_ctx *c, int64_t steps)
         break;
     case GE_KERNEL_ONESTEP:
         st = run_tiled(c, steps, 1);
+        break;
+    case GE_KERNEL_TEMPORAL_DF:
+        st = run_tiled(c, steps, effective_depth(c), true);
         break;
     default:
         st = run_tiled(c, steps, effective_depth(c));

@@ -88,7 +88,23 @@ struct TbParams {
     double f_l, f_r;      // wall terms r*beta_l, r*beta_r (unscaled)
     double x1, x2, xs;    // exit: (1+r)/(1+2r), r/(1+2r), 1/(1+r), each / sigma_end
     short rs_exp[kMaxRescale];  // exponents of this launch's rescalings
+    // double-float kernel (ge_tb_df.cu) only
+    int df_in;            // the source holds doubles (split on load), else (hi, lo) float pairs
+    int df_out;           // write doubles, else (hi, lo) float pairs
+    int df_gl;            // the pair of g = 2r has a nonzero low part
+    const int *df_code;   // prescale exponent word written by df_prescale
+    float dfc[7][2];      // (hi, lo) of g, kappa, r, 1 - r, x1, x2, xs
 };
+
+// Prescale exponent word of the double-float kernel: for the smallest e with
+// |x| < 2^e over the data and the walls, code = e + kDfCodeBias (e >= -1073,
+// subnormals included); 0 when every value is zero.
+constexpr int kDfCodeBias = 2048;
+// Zero the word, then raise it to the data's code and walls_code.
+cudaError_t df_prescale(const void *u, long long n, int walls_code, int *code, cudaStream_t s);
+bool tb_df_geometry(int reach, int *H, int *U);
+cudaError_t tb_df_occupancy(int *blocks_per_sm);
+cudaError_t launch_tb_df(const void *tmap, const TbParams &p, int grid, cudaStream_t s);
 
 // One problem of a batch (device table, one entry per problem).  The batch
 // kernel uses the normalised block map x <- x + d (x_p - x), so every value
