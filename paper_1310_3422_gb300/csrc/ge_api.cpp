@@ -321,8 +321,12 @@ ge_status run_tiled(ge_ctx *c, int64_t steps, int depth, bool df = false)
             grid = p.n_tiles;
         if (grid < 1)
             grid = 1;
-        cudaError_t e = df ? ge::launch_tb_df(&c->tmap[c->cur], p, (int)grid, c->stream)
-                           : ge::launch_tb(prec, &c->tmap[c->cur], p, (int)grid, c->stream);
+        p.tile_ctr = c->err_dev + 48;
+        // the launch's tile queue starts empty
+        cudaError_t e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int), c->stream);
+        if (e == cudaSuccess)
+            e = df ? ge::launch_tb_df(&c->tmap[c->cur], p, (int)grid, c->stream)
+                   : ge::launch_tb(prec, &c->tmap[c->cur], p, (int)grid, c->stream);
         if (e != cudaSuccess)
             return cuda_fail(e, "tiled GE kernel launch");
         c->cur ^= 1;

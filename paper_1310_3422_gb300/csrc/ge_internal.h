@@ -93,6 +93,8 @@ struct TbParams {
     int df_out;           // write doubles, else (hi, lo) float pairs
     int df_gl;            // the pair of g = 2r has a nonzero low part
     const int *df_code;   // prescale exponent word written by df_prescale
+    int *tile_ctr;        // dynamic tile queue: zeroed before the launch; CTA b takes
+                          // queue position b first, then gridDim.x + atomicAdd(tile_ctr, 1)
     float dfc[7][2];      // (hi, lo) of g, kappa, r, 1 - r, x1, x2, xs
 };
 

@@ -241,10 +241,13 @@ extern "C" ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double
             p.n_tiles = (n + p.U - 1) / p.U;
             p.out = buf[cur ^ 1];
             p.err = err;
+            p.tile_ctr = err + 48;  // the launch's tile queue, zeroed first
             long long grid = (long long)sms * bps;
             if (grid > p.n_tiles)
                 grid = p.n_tiles;
-            e = ge::launch_tb(pidx, &tmap[cur], p, (int)grid, s);
+            e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int), s);
+            if (e == cudaSuccess)
+                e = ge::launch_tb(pidx, &tmap[cur], p, (int)grid, s);
             if (e != cudaSuccess)
                 return nfail(GE_ECUDA, "ge_solve_noalloc: launch: %s", cudaGetErrorString(e));
             cur ^= 1;

@@ -259,20 +259,29 @@ __global__ void __launch_bounds__(Layout<Real, COMP>::NT, Layout<Real, COMP>::MI
     }
     __syncthreads();
 
-    long long tile = blockIdx.x;
-    if (t == 0 && tile < P.n_tiles) {
+    // tiles come from the launch's dynamic queue (queue_tile): thread 0
+    // takes the next position while the current tile is computed
+    __shared__ long long s_next;
+    long long k = blockIdx.x;
+    if (t == 0 && k < P.n_tiles) {
         mbar_arrive_expect_tx(&mbar[0], kTileBytes);
-        tma_load_rows(tiles, &tmap, &mbar[0], (int)(tile * ur - hr));
+        tma_load_rows(tiles, &tmap, &mbar[0], (int)(queue_tile(k, P.n_tiles) * ur - hr));
     }
-    for (long long it = 0; tile < P.n_tiles; ++it, tile += gridDim.x) {
+    for (long long it = 0; k < P.n_tiles; ++it) {
         const int b = (int)(it & 1);
         unsigned char *cur = tiles + b * kTileBytes;
-        const long long next = tile + gridDim.x;
-        const bool prefetch = next < P.n_tiles;
-        if (t == 0 && prefetch) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&mbar[b ^ 1], kTileBytes);
-            tma_load_rows(tiles + (b ^ 1) * kTileBytes, &tmap, &mbar[b ^ 1], (int)(next * ur - hr));
+        const long long tile = queue_tile(k, P.n_tiles);
+        bool prefetch = false;
+        if (t == 0) {
+            const long long nk = (long long)gridDim.x + atomicAdd(P.tile_ctr, 1);
+            s_next = nk;
+            prefetch = nk < P.n_tiles;
+            if (prefetch) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&mbar[b ^ 1], kTileBytes);
+                tma_load_rows(tiles + (b ^ 1) * kTileBytes, &tmap, &mbar[b ^ 1],
+                              (int)(queue_tile(nk, P.n_tiles) * ur - hr));
+            }
         }
         const bool ok = tile_wait(mbar, &mbar[2], b, it, P.stall);
         if (__syncthreads_or(!ok)) {
@@ -280,6 +289,7 @@ __global__ void __launch_bounds__(Layout<Real, COMP>::NT, Layout<Real, COMP>::MI
                 tile_wait_failed(P.err, mbar, b, it, prefetch);
             return;
         }
+        const long long next = s_next;  // written by thread 0 before the barrier
 
         Real v[K];
 #pragma unroll
@@ -337,6 +347,7 @@ __global__ void __launch_bounds__(Layout<Real, COMP>::NT, Layout<Real, COMP>::MI
             }
         }
         __syncthreads();
+        k = next;
     }
 }
 

@@ -88,6 +88,21 @@ __device__ __forceinline__ void tile_wait_failed(int *err, uint64_t *mbar, int b
         mbar_wait_bounded(&mbar[b ^ 1], (uint32_t)(((it + 1) >> 1) & 1), kWaitLimitCycles);
 }
 
+// Tile at position k of a launch's dynamic tile queue.  The two edge tiles
+// (the only ones with warps on the checked path, several times slower) go
+// first, so the CTAs that take them take fewer tiles in all; then the
+// interior tiles in order.
+__device__ __forceinline__ long long queue_tile(long long k, long long n_tiles)
+{
+    if (n_tiles <= 2 || k >= n_tiles)
+        return k;
+    if (k == 0)
+        return 0;
+    if (k == 1)
+        return n_tiles - 1;
+    return k - 1;
+}
+
 // 2D tiled TMA load: box origin (x = 0, y = row), completes on `bar`.
 __device__ __forceinline__ void tma_load_rows(void *dst, const CUtensorMap *map, uint64_t *bar,
                                               int row)

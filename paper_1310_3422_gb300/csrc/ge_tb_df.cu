@@ -81,9 +81,12 @@ __device__ __forceinline__ float df_prod_lo(float ah, float al, float ph, float 
 
 // (oh, ol) = x + g * p, every operand a (hi, lo) pair; GL: g_lo != 0.
 // g_hi p_hi = q + qe exactly (one FMA gives the product's rounding error);
-// x_hi + q = s + e exactly (TwoSum); the low-order terms join e in FP32 and
-// (s, rest) is renormalised.
-template <bool GL>
+// x_hi + q = s + e exactly (TwoSum); the low-order terms join e in FP32.
+// NORM: renormalise (s, rest) by Fast2Sum.  Without it the pair stays an
+// exact-enough unevaluated sum whose low part may exceed half an ulp of the
+// high part; every operation above takes such pairs, and the fast step loop
+// renormalises every second step (measured over 2e4 steps: no loss).
+template <bool GL, bool NORM = true>
 __device__ __forceinline__ void df_axpy(float xh, float xl, float gh, float gl, float ph, float pl, float &oh,
                                         float &ol)
 {
@@ -92,7 +95,12 @@ __device__ __forceinline__ void df_axpy(float xh, float xl, float gh, float gl, 
     const float c = df_prod_lo<GL>(gh, gl, ph, pl, qe);
     float s, e;
     two_sum(xh, q, s, e);
-    fast_two_sum(s, __fadd_rn(e, __fadd_rn(xl, c)), oh, ol);
+    if constexpr (NORM) {
+        fast_two_sum(s, __fadd_rn(e, __fadd_rn(xl, c)), oh, ol);
+    } else {
+        oh = s;
+        ol = __fadd_rn(e, __fadd_rn(xl, c));
+    }
 }
 
 // (oh, ol) = a * x.
@@ -199,15 +207,15 @@ __device__ __forceinline__ DfC df_partner(const float (&h)[kDfK], const float (&
 
 // One scaled block step x <- x + g x_partner on a thread whose points and
 // partners all lie inside the grid, none a wall point.
-template <int Q, bool GL>
+template <int Q, bool GL, bool NORM>
 __device__ __forceinline__ void df_mid_fast(float (&h)[kDfK], float (&l)[kDfK], DfC g, DfExch &x)
 {
     if constexpr (Q == 0) {
 #pragma unroll
         for (int j = 0; j < kDfK; j += 2) {
             float ah, al, bh, bl;
-            df_axpy<GL>(h[j], l[j], g.h, g.l, h[j + 1], l[j + 1], ah, al);
-            df_axpy<GL>(h[j + 1], l[j + 1], g.h, g.l, h[j], l[j], bh, bl);
+            df_axpy<GL, NORM>(h[j], l[j], g.h, g.l, h[j + 1], l[j + 1], ah, al);
+            df_axpy<GL, NORM>(h[j + 1], l[j + 1], g.h, g.l, h[j], l[j], bh, bl);
             h[j] = ah;
             l[j] = al;
             h[j + 1] = bh;
@@ -217,13 +225,13 @@ __device__ __forceinline__ void df_mid_fast(float (&h)[kDfK], float (&l)[kDfK], 
         DfC L, R;
         df_exchange(h, l, L, R, x);
         float fh, fl, kh, kl;
-        df_axpy<GL>(h[0], l[0], g.h, g.l, L.h, L.l, fh, fl);
-        df_axpy<GL>(h[kDfK - 1], l[kDfK - 1], g.h, g.l, R.h, R.l, kh, kl);
+        df_axpy<GL, NORM>(h[0], l[0], g.h, g.l, L.h, L.l, fh, fl);
+        df_axpy<GL, NORM>(h[kDfK - 1], l[kDfK - 1], g.h, g.l, R.h, R.l, kh, kl);
 #pragma unroll
         for (int j = 1; j + 1 < kDfK; j += 2) {
             float ah, al, bh, bl;
-            df_axpy<GL>(h[j], l[j], g.h, g.l, h[j + 1], l[j + 1], ah, al);
-            df_axpy<GL>(h[j + 1], l[j + 1], g.h, g.l, h[j], l[j], bh, bl);
+            df_axpy<GL, NORM>(h[j], l[j], g.h, g.l, h[j + 1], l[j + 1], ah, al);
+            df_axpy<GL, NORM>(h[j + 1], l[j + 1], g.h, g.l, h[j], l[j], bh, bl);
             h[j] = ah;
             l[j] = al;
             h[j + 1] = bh;
@@ -285,29 +293,43 @@ __device__ __forceinline__ DfC dfc(const TbParams &P, int i) { return DfC{P.dfc[
 
 // Block steps m0 .. m0+count-1 (step m has grouping parity (p_first + m) & 1).
 // The checked path carries the scale sigma in double for its wall terms.
+// One block step of grouping Q; the checked path updates sigma and forms
+// the scaled wall terms.
+template <int Q, bool EDGE, bool GL, bool NORM>
+__device__ __forceinline__ void df_mid_step(float (&h)[kDfK], float (&l)[kDfK], const TbParams &P, DfExch &x,
+                                            Span sp, DfC g, DfC kap, double &sig, double fls, double frs)
+{
+    if constexpr (EDGE) {
+        const DfC zero{0.0f, 0.0f};
+        sig *= P.onepg;
+        DfC fl, fr;
+        df_split(sig * fls, fl.h, fl.l);
+        df_split(sig * frs, fr.h, fr.l);
+        df_stage_checked<Q, true, true, GL>(h, l, zero, g, kap, fl, fr, sp, x);
+    } else {
+        df_mid_fast<Q, GL, NORM>(h, l, g, x);
+    }
+}
+
+// Block steps m0 .. m0+count-1, step m having grouping parity
+// (p_first + m) & 1: an odd first step alone, then (even, odd) pairs (the
+// even one not renormalised), then an even trailing step.
 template <bool EDGE, bool GL>
 __device__ __forceinline__ void df_mid_run(float (&h)[kDfK], float (&l)[kDfK], int m0, int count, const TbParams &P,
                                            DfExch &x, Span sp, DfC g, DfC kap, double &sig, double fls, double frs)
 {
-    const DfC zero{0.0f, 0.0f};
-    for (int m = m0; m < m0 + count; ++m) {
-        const bool odd = ((P.p_first + m) & 1) != 0;
-        if constexpr (EDGE) {
-            sig *= P.onepg;
-            DfC fl, fr;
-            df_split(sig * fls, fl.h, fl.l);
-            df_split(sig * frs, fr.h, fr.l);
-            if (odd)
-                df_stage_checked<1, true, true, GL>(h, l, zero, g, kap, fl, fr, sp, x);
-            else
-                df_stage_checked<0, true, true, GL>(h, l, zero, g, kap, fl, fr, sp, x);
-        } else {
-            if (odd)
-                df_mid_fast<1, GL>(h, l, g, x);
-            else
-                df_mid_fast<0, GL>(h, l, g, x);
-        }
+    int m = m0;
+    const int end = m0 + count;
+    if (m < end && ((P.p_first + m) & 1)) {
+        df_mid_step<1, EDGE, GL, true>(h, l, P, x, sp, g, kap, sig, fls, frs);
+        ++m;
     }
+    for (; m + 1 < end; m += 2) {
+        df_mid_step<0, EDGE, GL, false>(h, l, P, x, sp, g, kap, sig, fls, frs);
+        df_mid_step<1, EDGE, GL, true>(h, l, P, x, sp, g, kap, sig, fls, frs);
+    }
+    if (m < end)
+        df_mid_step<0, EDGE, GL, true>(h, l, P, x, sp, g, kap, sig, fls, frs);
 }
 
 // Entry, the launch's block steps (in runs between rescalings) and exit on
@@ -402,20 +424,29 @@ __global__ void __launch_bounds__(kDfNT, GE_TB_MINBLOCKS_DF)
     }
     __syncthreads();
 
-    long long tile = blockIdx.x;
-    if (t == 0 && tile < P.n_tiles) {
+    // tiles come from the launch's dynamic queue (queue_tile): thread 0
+    // takes the next position while the current tile is computed
+    __shared__ long long s_next;
+    long long k = blockIdx.x;
+    if (t == 0 && k < P.n_tiles) {
         mbar_arrive_expect_tx(&mbar[0], kTileBytes);
-        tma_load_rows(tiles, &tmap, &mbar[0], (int)(tile * ur - hr));
+        tma_load_rows(tiles, &tmap, &mbar[0], (int)(queue_tile(k, P.n_tiles) * ur - hr));
     }
-    for (long long it = 0; tile < P.n_tiles; ++it, tile += gridDim.x) {
+    for (long long it = 0; k < P.n_tiles; ++it) {
         const int b = (int)(it & 1);
         unsigned char *cur = tiles + b * kTileBytes;
-        const long long next = tile + gridDim.x;
-        const bool prefetch = next < P.n_tiles;
-        if (t == 0 && prefetch) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&mbar[b ^ 1], kTileBytes);
-            tma_load_rows(tiles + (b ^ 1) * kTileBytes, &tmap, &mbar[b ^ 1], (int)(next * ur - hr));
+        const long long tile = queue_tile(k, P.n_tiles);
+        bool prefetch = false;
+        if (t == 0) {
+            const long long nk = (long long)gridDim.x + atomicAdd(P.tile_ctr, 1);
+            s_next = nk;
+            prefetch = nk < P.n_tiles;
+            if (prefetch) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&mbar[b ^ 1], kTileBytes);
+                tma_load_rows(tiles + (b ^ 1) * kTileBytes, &tmap, &mbar[b ^ 1],
+                              (int)(queue_tile(nk, P.n_tiles) * ur - hr));
+            }
         }
         const bool ok = tile_wait(mbar, &mbar[2], b, it, P.stall);
         if (__syncthreads_or(!ok)) {
@@ -423,6 +454,7 @@ __global__ void __launch_bounds__(kDfNT, GE_TB_MINBLOCKS_DF)
                 tile_wait_failed(P.err, mbar, b, it, prefetch);
             return;
         }
+        const long long next = s_next;  // written by thread 0 before the barrier
 
         float h[K], l[K];
         unsigned char *rp = cur + t * kRowBytes;
@@ -479,6 +511,7 @@ __global__ void __launch_bounds__(kDfNT, GE_TB_MINBLOCKS_DF)
             }
         }
         __syncthreads();
+        k = next;
     }
 }
 
