@@ -4,7 +4,7 @@ sine modes.  One benchmark step = one full solve (reset the state, advance
 10000 steps) through the C ABI.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision f64|f32|f32c] [--kernel temporal|onestep|canonical]
+                    [--precision f64|f32|f32c] [--kernel temporal|temporal_df|onestep|canonical]
                     [--depth D] [--no-variants] [--no-cpu]
 
 Prints one JSON line (rank 0).  Under torchrun every rank solves its own
@@ -37,21 +37,23 @@ REF_SAMPLE_STEPS = 10      # --impl reference: 10 GE steps over the full grid pe
 N_SAMPLES = 12             # oracle-checked sample points
 
 
-def tb_source_digest() -> str:
-    """sha256 over the tiled kernel's sources (ge_tb.cu + ge_tb_dev.cuh)."""
+def tb_source_digest(kernel_name: str = "tb_kernel") -> str:
+    """sha256 over a tiled kernel's sources: ge_tb.cu (or ge_tb_df.cu for the
+    double-float kernel) + ge_tb_dev.cuh."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("ge_tb.cu", "ge_tb_dev.cuh"):
+    main = "ge_tb_df.cu" if kernel_name.startswith("tb_df_kernel") else "ge_tb.cu"
+    for f in (main, "ge_tb_dev.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1310_3422_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
 
 def measured_traffic(kernel_name: str):
     """Per-launch DRAM bytes of `kernel_name` from profiles/traffic.txt, or None
-    when absent or when the kernel source (ge_tb.cu and the device helpers of
-    ge_tb_dev.cuh) changed since the capture."""
+    when absent or when the kernel source (its .cu file and the device helpers
+    of ge_tb_dev.cuh) changed since the capture."""
     try:
-        digest = tb_source_digest()
+        digest = tb_source_digest(kernel_name)
         for line in open(os.path.join(ROOT, "profiles", "traffic.txt")):
             if line.startswith("#") or not line.strip():
                 continue
@@ -76,6 +78,16 @@ def load_peaks():
 # nominal at 2.07 GHz is 2 FMA/clk/SM; FP32 is 128 FMA/clk/SM.
 SMS = 152
 FMA_PER_CLK = {"f64": 2.0, "f32": 128.0, "f32c": 128.0}
+# Double-float kernel: FP32-pipe instructions (FADD, FMUL, FFMA alike, one
+# issue each) per point and step of its fast path, renormalised every second
+# step: 11 + 3/2 (renormalised every second step) when 2r is an FP32 number,
+# 21 + 3 otherwise (the exact low-order product sum, renormalised every
+# step).  Its peak is 128 such instructions/clk/SM.
+DF_OPS_PER_UPDATE = {True: 12.5, False: 24.0}
+
+
+def two_r_is_fp32(r: float) -> bool:
+    return float(np.float32(2.0 * r)) == 2.0 * r
 
 
 class ClockSampler:
@@ -393,6 +405,11 @@ def measure_surrogate(B, torch, inputs, train_steps):
     pred = sur.rollout(u0, r, bl, br, SNO_JUMPS)
     sync()
     t_sur = time.perf_counter() - t0
+    # untimed warm-up of the whole pipeline on a slice: the first use of the
+    # framework's own reductions (the non-finite row check, nonzero) loads
+    # their kernels, which took seconds inside the timed region
+    SG.solve_with_fallback(sur, u0[:256], r[:256], bl[:256], br[:256], 1, tol=SNO_TOL, sample_frac=0.01)
+    sync()
     t0 = time.perf_counter()
     out, rep = SG.solve_with_fallback(sur, u0, r, bl, br, SNO_JUMPS, tol=SNO_TOL, sample_frac=0.01)
     sync()
@@ -460,15 +477,17 @@ def sno_flops_per_problem(n=SNO_N, C=64, M=16, L=4, H=128):
 
 def sno_launches_per_forward(L=4):
     """Inference: weight rounding, lift, per layer (spectral weights, DFT,
-    mode mixing, fused layer GEMM), output init, fused projection."""
+    mode mixing, fused layer GEMM), fused projection, fixed-order row sum."""
     return 2 + 4 * L + 2
 
 
 def launches_per_solve(kernel, depth):
+    """Kernel launches of one solve (the tiled kernels' tile-queue resets are
+    memsets, not kernels; the double-float kernel adds its prescale)."""
     if kernel in ("canonical", "subdomain16"):
         return GE_STEPS
     d = 1 if kernel == "onestep" else depth
-    return (GE_STEPS + d - 1) // d
+    return (GE_STEPS + d - 1) // d + (1 if kernel == "temporal_df" else 0)
 
 
 def main():
@@ -478,7 +497,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="f64", choices=["f64", "f32", "f32c"])
-    ap.add_argument("--kernel", default="temporal", choices=["temporal", "onestep", "canonical"])
+    ap.add_argument("--kernel", default="temporal", choices=["temporal", "temporal_df", "onestep", "canonical"])
     ap.add_argument("--depth", type=int, default=0)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -520,10 +539,12 @@ def main():
         print(json.dumps({"surrogate_forward": measure_sno_forward(torch, inputs, args.steps, args.warmup)}),
               flush=True)
         return 0
+    if args.kernel == "temporal_df" and args.precision != "f64":
+        ap.error("--kernel temporal_df runs FP64 contexts only")
     prec = {"f64": B.GE_F64, "f32": B.GE_F32, "f32c": B.GE_F32_COMP}[args.precision]
-    kern = {"temporal": B.GE_KERNEL_TEMPORAL, "onestep": B.GE_KERNEL_ONESTEP,
-            "canonical": B.GE_KERNEL_CANONICAL}[args.kernel]
-    depth = args.depth or (48 if args.precision == "f64" else 128)
+    kern = {"temporal": B.GE_KERNEL_TEMPORAL, "temporal_df": B.GE_KERNEL_TEMPORAL_DF,
+            "onestep": B.GE_KERNEL_ONESTEP, "canonical": B.GE_KERNEL_CANONICAL}[args.kernel]
+    depth = args.depth or (96 if args.kernel == "temporal_df" else (48 if args.precision == "f64" else 128))
     hbm_gbs, sm_max_mhz, peak_src = load_peaks()
 
     u0 = inputs.sine_modes_state(N_POINTS, seed=inputs.SEED_BASE + 1 + rank)
@@ -571,7 +592,8 @@ def main():
     updates = float(N_POINTS) * GE_STEPS
     value = updates * world / (ms_per_step / 1e3)
     n_launch = launches_per_solve(args.kernel, depth)
-    launch_ms = ms_per_step / n_launch
+    n_tiled = (GE_STEPS + depth - 1) // depth if args.kernel in ("temporal", "temporal_df") else n_launch
+    launch_ms = ms_per_step / n_tiled  # the dominant kernel's average launch (prescale time included for DF)
 
     if rank != 0:
         B.ge_destroy(ctx)
@@ -588,7 +610,19 @@ def main():
     else:
         flops_per_update = 2.0    # one multiply-add per point and step (right-hand-side form)
     alu_peak = 2.0 * FMA_PER_CLK[args.precision] * SMS * sm_max_mhz * 1e6  # flop/s
-    if args.kernel == "temporal":
+    if args.kernel == "temporal_df":
+        ops = DF_OPS_PER_UPDATE[two_r_is_fp32(R)]
+        peak_ops = 128.0 * SMS * sm_max_mhz * 1e6
+        achieved = ops * N_POINTS * (GE_STEPS / n_tiled) / (launch_ms / 1e3)
+        kname = "tb_df_kernel<%s>" % ("false" if two_r_is_fp32(R) else "true")
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                    "unit": "T FP32-pipe instructions/s", "frac": achieved / peak_ops,
+                    "traffic": measured_traffic(kname),
+                    "algorithmic_bytes_per_launch": 2 * bytes_per_update * N_POINTS,
+                    "ops_per_update": ops,
+                    "peak_source": "derived: 128 FP32 instructions/clk/SM x %d SMs x %.0f MHz" % (SMS, sm_max_mhz),
+                    "kernel": kname}
+    elif args.kernel == "temporal":
         achieved = flops_per_update * N_POINTS * (GE_STEPS / n_launch) / (launch_ms / 1e3)
         kname = "tb_kernel<%s>" % ("double" if prec == B.GE_F64 else "float")
         traffic = measured_traffic(kname) if (prec == B.GE_F64 and depth == 48) else None
@@ -609,7 +643,7 @@ def main():
     # HBM fraction from the bytes the dominant kernel actually moves (ncu DRAM counters per launch)
     hbm_actual = None
     if roofline.get("traffic"):
-        steps_per_launch = GE_STEPS / n_launch
+        steps_per_launch = GE_STEPS / n_tiled
         gbs = roofline["traffic"] / (launch_ms / 1e3) / 1e9
         hbm_actual = {"bytes_per_launch": roofline["traffic"], "steps_per_launch": steps_per_launch,
                       "bytes_per_step": roofline["traffic"] / steps_per_launch, "achieved_gbs": gbs,
@@ -640,14 +674,16 @@ def main():
 
         def flush():
             flush_buf.fill_(1)
-        for vp, vk, vd in (("f64", "onestep", 1), ("f64", "canonical", 1), ("f32", "temporal", 128),
-                           ("f32c", "temporal", 64), ("f32", "onestep", 1), ("f64", "subdomain16", 1)):
+        for vp, vk, vd in (("f64", "temporal_df", 96), ("f64", "onestep", 1), ("f64", "canonical", 1),
+                           ("f32", "temporal", 128), ("f32c", "temporal", 64), ("f32", "onestep", 1),
+                           ("f64", "subdomain16", 1)):
             if (vp, vk) == (args.precision, args.kernel):
                 continue
             p2 = {"f64": B.GE_F64, "f32": B.GE_F32, "f32c": B.GE_F32_COMP}[vp]
             width = 16 if vk == "subdomain16" else 1
-            k2 = {"temporal": B.GE_KERNEL_TEMPORAL, "onestep": B.GE_KERNEL_ONESTEP,
-                  "canonical": B.GE_KERNEL_CANONICAL, "subdomain16": B.GE_KERNEL_CANONICAL}[vk]
+            k2 = {"temporal": B.GE_KERNEL_TEMPORAL, "temporal_df": B.GE_KERNEL_TEMPORAL_DF,
+                  "onestep": B.GE_KERNEL_ONESTEP, "canonical": B.GE_KERNEL_CANONICAL,
+                  "subdomain16": B.GE_KERNEL_CANONICAL}[vk]
             x2 = torch.from_numpy(u0).to(dev, dtype=B.dtype_of(p2))
             with torch.cuda.stream(stream):
                 c2 = B.ge_create(N_POINTS, R, 0.0, 0.0, p2, x2, stream=stream)
@@ -667,7 +703,13 @@ def main():
                 ent.update(errors(o2.cpu().numpy().astype(np.float64)[idx], want, scale))
             else:
                 ent["scheme"] = "sub-domain width k = 16 (the paper's 32-node sub-domain couples)"
-            variants[f"{vp}_{vk}" + (f"_d{vd}" if vk == "temporal" else "")] = ent
+            if vk == "temporal_df":
+                ops = DF_OPS_PER_UPDATE[two_r_is_fp32(R)]
+                ent.update({"arithmetic": "double-float on the FP32 pipes (FP64 storage and API)",
+                            "ops_per_update": ops,
+                            "alu_frac": ops * upd_s / (128.0 * SMS * sm_max_mhz * 1e6),
+                            "vs_f64_temporal": upd_s / value if args.kernel == "temporal" else None})
+            variants[f"{vp}_{vk}" + (f"_d{vd}" if vk.startswith("temporal") else "")] = ent
             del x2, o2
         del flush_buf
 

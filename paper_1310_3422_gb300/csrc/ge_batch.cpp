@@ -171,10 +171,13 @@ ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int *result_buf)
             }
         }
         p.out = b->buf[cur ^ 1];
+        p.tile_ctr = b->err + 48;  // the launch's tile queue, zeroed first
         long long grid = (long long)b->num_sms * b->blocks_per_sm;
         if (grid > p.n_tiles)
             grid = p.n_tiles;
-        cudaError_t e = ge::launch_tbb(pidx, &b->tmap[cur], p, (int)grid, b->stream);
+        cudaError_t e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int), b->stream);
+        if (e == cudaSuccess)
+            e = ge::launch_tbb(pidx, &b->tmap[cur], p, (int)grid, b->stream);
         if (e != cudaSuccess)
             return bcuda(e, "ge_batch: kernel launch");
         cur ^= 1;

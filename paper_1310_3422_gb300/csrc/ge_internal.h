@@ -135,6 +135,7 @@ struct TbbParams {
     const BatchDesc *desc;     // per-problem constants
     long long n_rows, n_tiles;
     long long stall;           // diagnostic, as in TbParams
+    int *tile_ctr;             // dynamic tile queue, as in TbParams (zeroed before the launch)
     int U, H;
     int p_first, do_entry, n_mid, do_exit;
     // scaled form (scaled != 0): after every R block steps the data of

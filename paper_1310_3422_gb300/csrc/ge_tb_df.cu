@@ -83,9 +83,13 @@ __device__ __forceinline__ float df_prod_lo(float ah, float al, float ph, float 
 // g_hi p_hi = q + qe exactly (one FMA gives the product's rounding error);
 // x_hi + q = s + e exactly (TwoSum); the low-order terms join e in FP32.
 // NORM: renormalise (s, rest) by Fast2Sum.  Without it the pair stays an
-// exact-enough unevaluated sum whose low part may exceed half an ulp of the
-// high part; every operation above takes such pairs, and the fast step loop
-// renormalises every second step (measured over 2e4 steps: no loss).
+// unevaluated sum whose low part may exceed half an ulp of the high part;
+// every operation above takes such pairs.  With g_lo = 0 the fast step loop
+// renormalises every second step only (over 2e4 smooth steps no loss:
+// 2-3e-14 for r = 0.125 ... 3).  With g_lo != 0 it renormalises every step:
+// skipping it there brought the systematic error back (2.0e-12 at r = 0.3
+// against 1.4e-13), the unnormalised high parts feeding the same fixed-
+// pattern products.
 template <bool GL, bool NORM = true>
 __device__ __forceinline__ void df_axpy(float xh, float xl, float gh, float gl, float ph, float pl, float &oh,
                                         float &ol)
@@ -312,8 +316,8 @@ __device__ __forceinline__ void df_mid_step(float (&h)[kDfK], float (&l)[kDfK], 
 }
 
 // Block steps m0 .. m0+count-1, step m having grouping parity
-// (p_first + m) & 1: an odd first step alone, then (even, odd) pairs (the
-// even one not renormalised), then an even trailing step.
+// (p_first + m) & 1: an odd first step alone, then (even, odd) pairs (with
+// g_lo = 0 the even one not renormalised), then an even trailing step.
 template <bool EDGE, bool GL>
 __device__ __forceinline__ void df_mid_run(float (&h)[kDfK], float (&l)[kDfK], int m0, int count, const TbParams &P,
                                            DfExch &x, Span sp, DfC g, DfC kap, double &sig, double fls, double frs)
@@ -325,7 +329,7 @@ __device__ __forceinline__ void df_mid_run(float (&h)[kDfK], float (&l)[kDfK], i
         ++m;
     }
     for (; m + 1 < end; m += 2) {
-        df_mid_step<0, EDGE, GL, false>(h, l, P, x, sp, g, kap, sig, fls, frs);
+        df_mid_step<0, EDGE, GL, GL>(h, l, P, x, sp, g, kap, sig, fls, frs);
         df_mid_step<1, EDGE, GL, true>(h, l, P, x, sp, g, kap, sig, fls, frs);
     }
     if (m < end)

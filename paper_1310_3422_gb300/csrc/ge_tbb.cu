@@ -237,20 +237,28 @@ __global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
     }
     __syncthreads();
 
+    // tiles come from the launch's dynamic queue in order (tiles with checked
+    // warps are everywhere in a batch): thread 0 takes the next one while the
+    // current tile is computed
+    __shared__ long long s_next;
     long long tile = blockIdx.x;
     if (t == 0 && tile < P.n_tiles) {
         mbar_arrive_expect_tx(&mbar[0], kTileBytes);
         tma_load_rows(tiles, &tmap, &mbar[0], (int)(tile * ur - hr));
     }
-    for (long long it = 0; tile < P.n_tiles; ++it, tile += gridDim.x) {
+    for (long long it = 0; tile < P.n_tiles; ++it) {
         const int b = (int)(it & 1);
         unsigned char *cur = tiles + b * kTileBytes;
-        const long long next = tile + gridDim.x;
-        const bool prefetch = next < P.n_tiles;
-        if (t == 0 && prefetch) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&mbar[b ^ 1], kTileBytes);
-            tma_load_rows(tiles + (b ^ 1) * kTileBytes, &tmap, &mbar[b ^ 1], (int)(next * ur - hr));
+        bool prefetch = false;
+        if (t == 0) {
+            const long long next = (long long)gridDim.x + atomicAdd(P.tile_ctr, 1);
+            s_next = next;
+            prefetch = next < P.n_tiles;
+            if (prefetch) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&mbar[b ^ 1], kTileBytes);
+                tma_load_rows(tiles + (b ^ 1) * kTileBytes, &tmap, &mbar[b ^ 1], (int)(next * ur - hr));
+            }
         }
         const bool ok = tile_wait(mbar, &mbar[2], b, it, P.stall);
         if (__syncthreads_or(!ok)) {
@@ -258,6 +266,7 @@ __global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
                 tile_wait_failed(P.err, mbar, b, it, prefetch);
             return;
         }
+        const long long next_tile = s_next;  // written by thread 0 before the barrier
 
         Real v[K];
         {
@@ -320,6 +329,7 @@ __global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
             }
         }
         __syncthreads();
+        tile = next_tile;
     }
 }
 

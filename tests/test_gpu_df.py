@@ -152,6 +152,19 @@ def test_df_long_run_against_extended_precision(r):
     assert e_df <= tol64(r), (e_df, e_64)
 
 
+@pytest.mark.parametrize("r", [0.3, 0.7])
+def test_df_long_run_fast_path(r):
+    """As above with n = 4096: here the interior warps run the fast path
+    (renormalised every second step, exact low-order product sum) and only
+    the two wall warps the checked one."""
+    n, steps = 4096, 20000
+    u0 = inputs.sine_state(n)
+    ref = ext_precision_run(u0, r, 0.0, 0.0, steps).astype(np.float64)
+    e_df = rel_max(df_run(u0, r, 0.0, 0.0, steps), ref)
+    print(f"fast path r={r}: double-float {e_df:.3e}")
+    assert e_df <= tol64(r), e_df
+
+
 def test_df_full_size_sampled():
     """N = 2^24, r = 2, 10000 steps, eight seeded sine modes: the single large
     solve the benchmark times, sampled points against the oracle on their
