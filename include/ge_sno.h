@@ -97,6 +97,28 @@ ge_status ge_sno_train_step(ge_sno *model, int32_t batch, const float *u0_dev, c
                             const float *beta_l_dev, const float *beta_r_dev, const float *target_dev,
                             float lr, float *loss_dev);
 
+/* Fallback arbiter helpers.  GE recomputes a sample of the problems and
+ * replaces any problem the surrogate fails on; these move and compare rows
+ * of the model's n FP32 values on the model's stream, so that no step of
+ * that check runs outside the library.  Row indices are device int64
+ * arrays; an index outside [0, rows) is skipped on the device (gather and
+ * scatter leave that destination row untouched, rel_err writes NaN).
+ *   rows_nonfinite: flags_dev[i] = 1 if row i of u_dev ([rows][n]) holds a
+ *                   NaN or an infinity, else 0.
+ *   rows_gather:    dst_dev row i <- src_dev row idx[i] (src has src_rows rows).
+ *   rows_scatter:   dst_dev row idx[i] <- src_dev row i (dst has dst_rows rows).
+ *   rows_rel_err:   err_dev[i] = ||a row idx[i] - ref row i||_2 / ||ref row i||_2,
+ *                   sums in FP64; +inf when not finite or when ref is zero
+ *                   and the rows differ.
+ * Errors: GE_EINVAL (NULL model or pointer, negative counts), GE_ECUDA. */
+ge_status ge_sno_rows_nonfinite(ge_sno *model, const float *u_dev, int64_t rows, int32_t *flags_dev);
+ge_status ge_sno_rows_gather(ge_sno *model, const float *src_dev, int64_t src_rows, const int64_t *idx_dev,
+                             int64_t count, float *dst_dev);
+ge_status ge_sno_rows_scatter(ge_sno *model, float *dst_dev, int64_t dst_rows, const int64_t *idx_dev,
+                              const float *src_dev, int64_t count);
+ge_status ge_sno_rows_rel_err(ge_sno *model, const float *a_dev, int64_t a_rows, const int64_t *idx_dev,
+                              const float *ref_dev, int64_t count, float *err_dev);
+
 /* Free the model (waits for its stream first).  NULL is a no-op. */
 void ge_sno_destroy(ge_sno *model);
 

@@ -30,7 +30,8 @@ EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", 
            "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune",
            "ge_sno_create", "ge_sno_num_params", "ge_sno_get_params", "ge_sno_set_params",
            "ge_sno_set_precision", "ge_sno_forward", "ge_sno_loss_grad", "ge_sno_adam_step",
-           "ge_sno_train_step", "ge_sno_destroy")
+           "ge_sno_train_step", "ge_sno_rows_nonfinite", "ge_sno_rows_gather", "ge_sno_rows_scatter",
+           "ge_sno_rows_rel_err", "ge_sno_destroy")
 
 _lock = threading.Lock()
 _lib = None
@@ -118,6 +119,12 @@ def load(path: str | None = None):
         lib.ge_sno_train_step.restype = ctypes.c_int
         lib.ge_sno_destroy.argtypes = [_VP]
         lib.ge_sno_destroy.restype = None
+        lib.ge_sno_rows_nonfinite.argtypes = [_VP, _VP, _I64, _VP]
+        lib.ge_sno_rows_gather.argtypes = [_VP, _VP, _I64, _VP, _I64, _VP]
+        lib.ge_sno_rows_scatter.argtypes = [_VP, _VP, _I64, _VP, _VP, _I64]
+        lib.ge_sno_rows_rel_err.argtypes = [_VP, _VP, _I64, _VP, _VP, _I64, _VP]
+        for fn in ("ge_sno_rows_nonfinite", "ge_sno_rows_gather", "ge_sno_rows_scatter", "ge_sno_rows_rel_err"):
+            getattr(lib, fn).restype = ctypes.c_int
         lib.ge_get_kernel.argtypes = [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I32)]
         lib.ge_get_kernel.restype = ctypes.c_int
         lib.ge_tune.argtypes = [_VP, _I64, ctypes.POINTER(_I32)]
@@ -403,6 +410,61 @@ def _f32_dev(x, count: int, what: str):
     if x is None or x.dtype != torch.float32 or x.numel() < count:
         raise ValueError(f"{what} must be a CUDA float32 tensor of at least {count} elements")
     return _dptr(x)
+
+
+def _rows(model: "Sno", x, what: str, dtype=None) -> int:
+    """Row count of a contiguous CUDA [rows, n] (or flat) tensor of the model's row length."""
+    import torch
+    dtype = dtype or torch.float32
+    if x is None or not x.is_cuda or x.dtype != dtype or not x.is_contiguous() or x.numel() % model.n:
+        raise ValueError(f"{what} must be a contiguous CUDA {dtype} tensor of whole rows of {model.n}")
+    return x.numel() // model.n
+
+
+def _idx(idx, what: str = "idx") -> int:
+    import torch
+    if idx is None or not idx.is_cuda or idx.dtype != torch.int64 or not idx.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous CUDA int64 tensor")
+    return idx.numel()
+
+
+def ge_sno_rows_nonfinite(model: "Sno", u, flags):
+    """flags (CUDA int32, one per row) <- 1 where the row of u holds NaN/Inf."""
+    import torch
+    rows = _rows(model, u, "u")
+    if flags.dtype != torch.int32 or flags.numel() < rows or not flags.is_cuda:
+        raise ValueError("flags must be a CUDA int32 tensor with one entry per row")
+    _check(load().ge_sno_rows_nonfinite(model.handle, _dptr(u), rows, _dptr(flags)), "ge_sno_rows_nonfinite")
+
+
+def ge_sno_rows_gather(model: "Sno", src, idx, dst):
+    """dst row i <- src row idx[i]."""
+    count = _idx(idx)
+    if _rows(model, dst, "dst") < count:
+        raise ValueError("dst holds fewer rows than idx")
+    _check(load().ge_sno_rows_gather(model.handle, _dptr(src), _rows(model, src, "src"), _dptr(idx), count,
+                                     _dptr(dst)), "ge_sno_rows_gather")
+
+
+def ge_sno_rows_scatter(model: "Sno", dst, idx, src):
+    """dst row idx[i] <- src row i."""
+    count = _idx(idx)
+    if _rows(model, src, "src") < count:
+        raise ValueError("src holds fewer rows than idx")
+    _check(load().ge_sno_rows_scatter(model.handle, _dptr(dst), _rows(model, dst, "dst"), _dptr(idx), _dptr(src),
+                                      count), "ge_sno_rows_scatter")
+
+
+def ge_sno_rows_rel_err(model: "Sno", a, idx, ref, err):
+    """err[i] (CUDA float32) <- ||a row idx[i] - ref row i|| / ||ref row i||."""
+    import torch
+    count = _idx(idx)
+    if _rows(model, ref, "ref") < count:
+        raise ValueError("ref holds fewer rows than idx")
+    if err.dtype != torch.float32 or err.numel() < count or not err.is_cuda:
+        raise ValueError("err must be a CUDA float32 tensor with one entry per index")
+    _check(load().ge_sno_rows_rel_err(model.handle, _dptr(a), _rows(model, a, "a"), _dptr(idx), _dptr(ref), count,
+                                      _dptr(err)), "ge_sno_rows_rel_err")
 
 
 def ge_sno_create(n: int, width: int, modes: int, layers: int, hidden: int, max_batch: int, seed: int = 0,

@@ -556,6 +556,46 @@ ge_status ge_sno_forward(ge_sno *s, int32_t batch, const float *u0, const float 
     return forward(s, batch, u0, r, bl, br, pred, false);
 }
 
+ge_status ge_sno_rows_nonfinite(ge_sno *s, const float *u, int64_t rows, int32_t *flags)
+{
+    if (!s || !u || !flags || rows < 0)
+        return sfail(GE_EINVAL, "ge_sno_rows_nonfinite: NULL argument or rows < 0");
+    static_assert(sizeof(int32_t) == sizeof(int), "int32 flags");
+    cudaError_t e = ge::sno_rows_nonfinite(u, rows, s->n, reinterpret_cast<int *>(flags), s->stream);
+    return e == cudaSuccess ? GE_OK : scuda(e, "ge_sno_rows_nonfinite");
+}
+
+ge_status ge_sno_rows_gather(ge_sno *s, const float *src, int64_t src_rows, const int64_t *idx, int64_t count,
+                             float *dst)
+{
+    if (!s || !src || !idx || !dst || src_rows < 0 || count < 0)
+        return sfail(GE_EINVAL, "ge_sno_rows_gather: NULL argument or negative count");
+    static_assert(sizeof(int64_t) == sizeof(long long), "int64 indices");
+    cudaError_t e = ge::sno_rows_move(src, dst, reinterpret_cast<const long long *>(idx), count, s->n, src_rows,
+                                      false, s->stream);
+    return e == cudaSuccess ? GE_OK : scuda(e, "ge_sno_rows_gather");
+}
+
+ge_status ge_sno_rows_scatter(ge_sno *s, float *dst, int64_t dst_rows, const int64_t *idx, const float *src,
+                              int64_t count)
+{
+    if (!s || !src || !idx || !dst || dst_rows < 0 || count < 0)
+        return sfail(GE_EINVAL, "ge_sno_rows_scatter: NULL argument or negative count");
+    cudaError_t e = ge::sno_rows_move(src, dst, reinterpret_cast<const long long *>(idx), count, s->n, dst_rows,
+                                      true, s->stream);
+    return e == cudaSuccess ? GE_OK : scuda(e, "ge_sno_rows_scatter");
+}
+
+ge_status ge_sno_rows_rel_err(ge_sno *s, const float *a, int64_t a_rows, const int64_t *idx, const float *ref,
+                              int64_t count, float *err)
+{
+    if (!s || !a || !idx || !ref || !err || a_rows < 0 || count < 0)
+        return sfail(GE_EINVAL, "ge_sno_rows_rel_err: NULL argument or negative count");
+    cudaError_t e = ge::sno_rows_rel_err(a, a_rows, reinterpret_cast<const long long *>(idx), ref, count, s->n, err,
+                                         s->stream);
+    return e == cudaSuccess ? GE_OK : scuda(e, "ge_sno_rows_rel_err");
+}
+
 ge_status ge_sno_loss_grad(ge_sno *s, int32_t batch, const float *u0, const float *r, const float *bl,
                            const float *br, const float *target, float *loss_dev, float *grads_dev)
 {

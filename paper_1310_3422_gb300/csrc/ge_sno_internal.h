@@ -73,6 +73,13 @@ cudaError_t sno_round_bf16(const float *x, float *y, void *y16, long long n, cud
 cudaError_t sno_lift(const float *u0, const float *r, const float *bl, const float *br, const void *w0,
                      const float *b0, void *v0, int batch, int n, int c, int bf16, cudaStream_t s);
 // out[i] = u0[i] + q2[0] + sum_k part[i * slots + k], summed in a fixed order
+// Fallback arbiter helpers on rows of n FP32 values (row indices outside
+// [0, rows) are skipped; rel_err gives NaN for them).
+cudaError_t sno_rows_nonfinite(const float *u, long long rows, int n, int *flags, cudaStream_t s);
+cudaError_t sno_rows_move(const float *src, float *dst, const long long *idx, long long count, int n, long long rows,
+                          bool scatter, cudaStream_t s);
+cudaError_t sno_rows_rel_err(const float *a, long long a_rows, const long long *idx, const float *ref, long long count,
+                             int n, float *err, cudaStream_t s);
 cudaError_t sno_dot_finish(const float *u0, const float *q2, const float *part, int slots, float *out, long long n,
                            cudaStream_t s);
 

@@ -58,13 +58,6 @@ __device__ __forceinline__ float gelu_grad(float x)
     return 0.5f * (1.0f + th) + 0.5f * x * (1.0f - th * th) * du;
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi)
-{
-    const uint16_t a = *reinterpret_cast<const uint16_t *>(&lo);
-    const uint16_t b = *reinterpret_cast<const uint16_t *>(&hi);
-    return (uint32_t)a | ((uint32_t)b << 16);
-}
-
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
 {
     asm volatile(
@@ -798,6 +791,96 @@ __global__ void dot_finish_kernel(const float *__restrict__ u0, const float *__r
     }
 }
 
+// --- fallback arbiter helpers: rows of n FP32 values -----------------------
+
+// Block-wide sum of a double (blockDim.x = 256); valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// flags[i] = 1 when row i holds a NaN or an infinity (one block per row).
+__global__ void rows_nonfinite_kernel(const float *__restrict__ u, long long rows, int n, int *__restrict__ flags)
+{
+    for (long long i = blockIdx.x; i < rows; i += gridDim.x) {
+        const float *row = u + i * (long long)n;
+        int bad = 0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x)
+            bad |= !isfinite(row[j]);
+        const int any = __syncthreads_or(bad);
+        if (threadIdx.x == 0)
+            flags[i] = any;
+    }
+}
+
+// dst row i <- src row idx[i] (gather) or dst row idx[i] <- src row i
+// (scatter); an index outside [0, rows) is skipped.
+__global__ void rows_move_kernel(const float *__restrict__ src, float *__restrict__ dst, const long long *__restrict__ idx,
+                                 long long count, int n, long long rows, int scatter)
+{
+    const long long total = count * (long long)n;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / n;
+        const int j = (int)(e % n);
+        const long long k = idx[i];
+        if (k < 0 || k >= rows)
+            continue;
+        if (scatter)
+            dst[k * n + j] = src[e];
+        else
+            dst[e] = src[k * n + j];
+    }
+}
+
+// err[i] = ||a[idx[i]] - ref[i]|| / ||ref[i]|| (sums in FP64; +inf when the
+// result is not finite or ref is zero with a difference; NaN for an index
+// outside [0, a_rows)).  One block per row.
+__global__ void rows_rel_err_kernel(const float *__restrict__ a, long long a_rows, const long long *__restrict__ idx,
+                                    const float *__restrict__ ref, long long count, int n, float *__restrict__ err)
+{
+    __shared__ double red[32];
+    for (long long i = blockIdx.x; i < count; i += gridDim.x) {
+        const long long k = idx[i];
+        if (k < 0 || k >= a_rows) {
+            if (threadIdx.x == 0)
+                err[i] = __int_as_float(0x7fc00000);
+            continue;  // uniform across the block
+        }
+        const float *ar = a + k * (long long)n;
+        const float *rr = ref + i * (long long)n;
+        double d2 = 0.0, r2 = 0.0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            const double d = (double)ar[j] - (double)rr[j];
+            d2 += d * d;
+            r2 += (double)rr[j] * (double)rr[j];
+        }
+        d2 = block_sum(d2, red);
+        r2 = block_sum(r2, red);
+        if (threadIdx.x == 0) {
+            double e;
+            if (!isfinite(d2) || !isfinite(r2))
+                e = INFINITY;
+            else if (r2 == 0.0)
+                e = d2 == 0.0 ? 0.0 : INFINITY;
+            else
+                e = sqrt(d2 / r2);
+            err[i] = (float)e;
+        }
+    }
+}
+
 int grid_for(long long n)
 {
     long long b = (n + 255) / 256;
@@ -917,6 +1000,34 @@ cudaError_t sno_dot_finish(const float *u0, const float *q2, const float *part, 
 cudaError_t sno_round_bf16(const float *x, float *y, void *y16, long long n, cudaStream_t s)
 {
     round_bf16_kernel<<<grid_for(n), 256, 0, s>>>(x, y, static_cast<__nv_bfloat16 *>(y16), n);
+    return cudaGetLastError();
+}
+
+cudaError_t sno_rows_nonfinite(const float *u, long long rows, int n, int *flags, cudaStream_t s)
+{
+    if (rows <= 0)
+        return cudaSuccess;
+    const int grid = (int)(rows < 8192 ? rows : 8192);
+    rows_nonfinite_kernel<<<grid, 256, 0, s>>>(u, rows, n, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t sno_rows_move(const float *src, float *dst, const long long *idx, long long count, int n, long long rows,
+                          bool scatter, cudaStream_t s)
+{
+    if (count <= 0)
+        return cudaSuccess;
+    rows_move_kernel<<<grid_for(count * (long long)n), 256, 0, s>>>(src, dst, idx, count, n, rows, scatter ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t sno_rows_rel_err(const float *a, long long a_rows, const long long *idx, const float *ref, long long count,
+                             int n, float *err, cudaStream_t s)
+{
+    if (count <= 0)
+        return cudaSuccess;
+    const int grid = (int)(count < 8192 ? count : 8192);
+    rows_rel_err_kernel<<<grid, 256, 0, s>>>(a, a_rows, idx, ref, count, n, err);
     return cudaGetLastError();
 }
 

@@ -203,34 +203,45 @@ def solve_with_fallback(sur: Surrogate, u0, r, beta_l, beta_r, jumps: int, tol: 
     torch = _torch()
     P, n = u0.shape
     steps = jumps * sur.K
+    dev = u0.device
+    u0 = u0.contiguous()
     u = sur.rollout(u0, r, beta_l, beta_r, jumps)
-    flagged = (~torch.isfinite(u).all(dim=1)) | (r < r_range[0]) | (r > r_range[1])
-    flagged_idx = torch.nonzero(flagged).flatten().cpu().numpy()
+    # flag, gather, compare and scatter rows with the library's own kernels;
+    # the host only draws the sample and takes the decisions
+    bad = torch.empty(P, dtype=torch.int32, device=dev)
+    B.ge_sno_rows_nonfinite(sur.model, u, bad)
+    r_h, bl_h, br_h = (x.double().cpu().numpy() for x in (r, beta_l, beta_r))
+    flagged = (bad.cpu().numpy() != 0) | (r_h < r_range[0]) | (r_h > r_range[1])
+    flagged_idx = np.nonzero(flagged)[0]
     rng = np.random.default_rng(seed)
     n_sample = min(P, max(1, int(math.ceil(sample_frac * P))))
     sample = np.sort(rng.choice(P, n_sample, replace=False))
     check = np.union1d(sample, flagged_idx)
-    ci = torch.tensor(check, device=u0.device)
-    r_h, bl_h, br_h = (x.double().cpu().numpy() for x in (r, beta_l, beta_r))
-    ref_dtype = torch.float64 if ge_prec == B.GE_F64 else torch.float32
-    ref = u0[ci].to(ref_dtype).contiguous()
+    ci = torch.tensor(check, dtype=torch.int64, device=dev)
+    ref = torch.empty(check.size, n, dtype=torch.float32, device=dev)
+    B.ge_sno_rows_gather(sur.model, u0, ci, ref)
     ge = GEBatch(r_h[check], bl_h[check], br_h[check], n, ge_prec)
-    ge.run(ref, steps)
-    ref = ref.float()
-    is_sample = torch.tensor(np.isin(check, sample), device=u0.device)
-    err = torch.linalg.vector_norm(u[ci] - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)
-    err = torch.where(torch.isfinite(err), err, torch.full_like(err, float("inf")))
-    se = err[is_sample & ~flagged[ci]]
-    n_over = int((se > tol).sum())
-    u[ci] = ref
+    if ge_prec == B.GE_F64:
+        ref64 = ref.double()
+        ge.run(ref64, steps)
+        ref = ref64.float()
+    else:
+        ge.run(ref, steps)
     ge.close()
+    err = torch.empty(check.size, dtype=torch.float32, device=dev)
+    B.ge_sno_rows_rel_err(sur.model, u, ci, ref, err)
+    err_h = err.cpu().numpy()
+    se = err_h[np.isin(check, sample) & ~flagged[check]]
+    n_over = int((se > tol).sum())
+    B.ge_sno_rows_scatter(sur.model, u, ci, ref)
     fell_back = n_over > 0
     if fell_back:
-        full = u0.to(ref_dtype, copy=True).contiguous()
+        ref_dtype = torch.float64 if ge_prec == B.GE_F64 else torch.float32
+        full = u0.to(ref_dtype, copy=True)
         ge = GEBatch(r_h, bl_h, br_h, n, ge_prec)
         ge.run(full, steps)
-        u = full.float()
+        u = full.float() if ge_prec == B.GE_F64 else full
         ge.close()
-    rep = FallbackReport(P, n_sample, int(flagged_idx.size), float(se.max()) if se.numel() else 0.0,
-                         float(se.mean()) if se.numel() else 0.0, n_over, fell_back, sample)
+    rep = FallbackReport(P, n_sample, int(flagged_idx.size), float(se.max()) if se.size else 0.0,
+                         float(se.mean()) if se.size else 0.0, n_over, fell_back, sample)
     return u, rep

@@ -132,6 +132,10 @@ def test_sno_calls_on_null_model(lib):
     assert lib.ge_sno_loss_grad(None, 1, 1, 1, 1, 1, 1, None, None) == B.GE_EINVAL
     assert lib.ge_sno_adam_step(None, 1e-3) == B.GE_EINVAL
     assert lib.ge_sno_train_step(None, 1, 1, 1, 1, 1, 1, 1e-3, None) == B.GE_EINVAL
+    assert lib.ge_sno_rows_nonfinite(None, 1, 1, 1) == B.GE_EINVAL
+    assert lib.ge_sno_rows_gather(None, 1, 1, 1, 1, 1) == B.GE_EINVAL
+    assert lib.ge_sno_rows_scatter(None, 1, 1, 1, 1, 1) == B.GE_EINVAL
+    assert lib.ge_sno_rows_rel_err(None, 1, 1, 1, 1, 1, 1) == B.GE_EINVAL
     lib.ge_sno_destroy(None)
 
 

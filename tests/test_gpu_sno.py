@@ -203,3 +203,64 @@ def test_non_finite_predictions_are_flagged():
     assert rep.n_flagged == 40 and not rep.fell_back_all
     assert torch.equal(out, ge_reference(u0, r, bl, br, 256))
     sur.close()
+
+
+def test_arbiter_row_helpers_match_numpy():
+    """The fallback arbiter's row kernels: non-finite flags, gather, scatter
+    (indices outside the rows skipped) and the per-row relative L2 error
+    (FP64 sums; inf for non-finite rows or a zero reference that differs,
+    NaN for an index outside the rows)."""
+    a = SMALL
+    m = make_model(a, 8, split=1)
+    rng = np.random.default_rng(41)
+    P = 37
+    u = rng.standard_normal((P, a.n)).astype(np.float32)
+    u[3, 5] = np.nan
+    u[10, 0] = np.inf
+    u[36, a.n - 1] = -np.inf
+    ud = torch.tensor(u, device=DEV)
+    flags = torch.empty(P, dtype=torch.int32, device=DEV)
+    B.ge_sno_rows_nonfinite(m, ud, flags)
+    assert np.array_equal(flags.cpu().numpy(), (~np.isfinite(u).all(axis=1)).astype(np.int32))
+
+    idx = np.array([0, 7, 36, -1, P, 12, 7], dtype=np.int64)
+    idd = torch.tensor(idx, device=DEV)
+    dst = torch.full((idx.size, a.n), 5.0, device=DEV)
+    B.ge_sno_rows_gather(m, ud, idd, dst)
+    got = dst.cpu().numpy()
+    for i, k in enumerate(idx):
+        want = u[k] if 0 <= k < P else np.full(a.n, 5.0, np.float32)
+        assert np.array_equal(got[i], want, equal_nan=True)
+
+    tgt = torch.zeros(P, a.n, device=DEV)
+    src = torch.tensor(rng.standard_normal((idx.size, a.n)).astype(np.float32), device=DEV)
+    sidx = torch.tensor(np.array([4, 9, -3, 40, 30], dtype=np.int64), device=DEV)
+    B.ge_sno_rows_scatter(m, tgt, sidx, src)
+    want = np.zeros((P, a.n), np.float32)
+    sh = src.cpu().numpy()
+    for i, k in enumerate([4, 9, -3, 40, 30]):
+        if 0 <= k < P:
+            want[k] = sh[i]
+    assert np.array_equal(tgt.cpu().numpy(), want)
+
+    ref = rng.standard_normal((idx.size, a.n)).astype(np.float32)
+    ref[5] = 0.0
+    a_rows = u.copy()
+    a_rows[12] = 0.0   # row 12 against the zero reference row 5: error 0
+    ad = torch.tensor(a_rows, device=DEV)
+    err = torch.empty(idx.size, dtype=torch.float32, device=DEV)
+    B.ge_sno_rows_rel_err(m, ad, idd, torch.tensor(ref, device=DEV), err)
+    got = err.cpu().numpy()
+    for i, k in enumerate(idx):
+        if not 0 <= k < P:
+            assert np.isnan(got[i])
+            continue
+        d = a_rows[k].astype(np.float64) - ref[i]
+        if not np.all(np.isfinite(d)):
+            assert got[i] == np.inf
+        elif not np.any(ref[i]):
+            assert got[i] == (0.0 if not np.any(d) else np.inf)
+        else:
+            w = np.linalg.norm(d) / np.linalg.norm(ref[i].astype(np.float64))
+            assert abs(got[i] - w) <= 1e-6 * w
+    B.ge_sno_destroy(m)
