@@ -48,7 +48,10 @@ class GeError(RuntimeError):
 
 
 def load(path: str | None = None):
-    """Load libge.so and declare the C signatures (idempotent)."""
+    """Load libge.so and declare the C signatures (idempotent).  `path`
+    loads another build of the library (a variant compiled with other
+    tuning macros) and makes it the one every later call of this binding
+    uses."""
     global _lib
     with _lock:
         if _lib is not None and path is None:
@@ -139,8 +142,7 @@ def load(path: str | None = None):
         lib.ge_status_str.restype = ctypes.c_char_p
         lib.ge_last_error.argtypes = []
         lib.ge_last_error.restype = ctypes.c_char_p
-        if path is None:
-            _lib = lib
+        _lib = lib
         return lib
 
 
