@@ -604,7 +604,9 @@ def main():
     # ---- roofline of the dominant kernel ----------------------------------
     bytes_per_update = 8 if prec == B.GE_F64 else 4
     if args.kernel == "canonical":
-        flops_per_update = 8.0    # four multiply-adds, Eqs. (cc)/(dd)
+        flops_per_update = 7.0    # one multiply and three multiply-adds, Eqs. (cc)/(dd)
+    elif args.kernel == "onestep":
+        flops_per_update = 4.0    # entry and exit multiply-adds (a one-step launch has no block step)
     elif prec == B.GE_F32_COMP:
         flops_per_update = 6.0    # normalised block map + Kahan sum, FP32
     else:
@@ -633,12 +635,23 @@ def main():
                     % (FMA_PER_CLK[args.precision], SMS, sm_max_mhz),
                     "kernel": "tb_kernel<%s>" % ("double" if prec == B.GE_F64 else "float")}
     else:
+        # one step per launch: report the roofline that binds (HBM bytes or
+        # the ALU), with the other fraction beside it
         byt = 2.0 * bytes_per_update * N_POINTS
         achieved = byt / (launch_ms / 1e3)
-        roofline = {"bound": "hbm", "achieved": achieved / 1e9, "peak": hbm_gbs, "unit": "GB/s",
-                    "frac": achieved / (hbm_gbs * 1e9), "traffic": None,
-                    "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
-                    "kernel": "canon_kernel" if args.kernel == "canonical" else "tb_kernel (1 step/launch)"}
+        hbm_frac = achieved / (hbm_gbs * 1e9)
+        flops = flops_per_update * N_POINTS / (launch_ms / 1e3)
+        alu_frac = flops / alu_peak
+        kname = "canon_kernel" if args.kernel == "canonical" else "tb_kernel (1 step/launch)"
+        if alu_frac >= hbm_frac:
+            roofline = {"bound": "alu", "achieved": flops / 1e12, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
+                        "frac": alu_frac, "traffic": None, "hbm_frac": hbm_frac,
+                        "peak_source": "derived: %g FMA/clk/SM x %d SMs x %.0f MHz"
+                        % (FMA_PER_CLK[args.precision], SMS, sm_max_mhz), "kernel": kname}
+        else:
+            roofline = {"bound": "hbm", "achieved": achieved / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                        "frac": hbm_frac, "traffic": None, "alu_frac": alu_frac,
+                        "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)", "kernel": kname}
     hbm_roof_updates = hbm_gbs * 1e9 / (2.0 * bytes_per_update)
     # HBM fraction from the bytes the dominant kernel actually moves (ncu DRAM counters per launch)
     hbm_actual = None

@@ -2,14 +2,14 @@
 // literally (arXiv:1310.3422 Sec. 2, Eqs. (aa), (bb), (cc), (dd), sub-domain
 // width 1).
 //
-// Every point is one thread.  Its role follows from the parity p of the
-// global step counter: with partner = i+1 if (i+p) is even else i-1, a point
-// whose partner lies inside [0, n) is a member of the 2-point group
-// (min, max); otherwise it is a singleton at a wall.  Group members use the
-// closed forms (cc) (left) and (dd) (right) with prefactor 1/(1+2r); a left
-// singleton uses Saul'yev A with beta_l as the new-level neighbour, a right
-// singleton Saul'yev B with beta_r.  Old-level values outside the grid are
-// the wall values.
+// The role of a point follows from the parity p of the global step counter:
+// with partner = i+1 if (i+p) is even else i-1, a point whose partner lies
+// inside [0, n) is a member of the 2-point group (min, max); otherwise it is
+// a singleton at a wall.  One thread evaluates one group (or singleton).
+// Group members use the closed forms (cc) (left) and (dd) (right) with
+// prefactor 1/(1+2r); a left singleton uses Saul'yev A with beta_l as the
+// new-level neighbour, a right singleton Saul'yev B with beta_r.  Old-level
+// values outside the grid are the wall values.
 //
 // Rounding: each sum of products is a chain of fused multiply-adds in the
 // order the equation prints its terms (first product rounded on its own), so
@@ -40,39 +40,39 @@ struct Coef {
     Real c1, c2, c3, c4, s0, s1, bl, br;
 };
 
+// One thread per unit of the step's grouping: unit u holds the points
+// s = 2u - parity and s + 1.  Both inside: the group (s, s+1), Eqs. (cc)
+// and (dd) from the shared old values a = u_{s-1}, b, c, d = u_{s+2} (the
+// wall values beyond the grid); s = -1: point 0 alone (Saul'yev A); s + 1 = n:
+// point n - 1 alone (Saul'yev B).  Only the two wall units branch, so a warp
+// runs one FMA chain per group member (one thread per point had neighbouring
+// lanes on the two different chains of (cc) and (dd)).
 template <typename Real>
 __global__ void __launch_bounds__(256) canon_kernel(const Real *__restrict__ in, Real *__restrict__ out,
                                                     long long n, int parity, Coef<Real> k)
 {
+    const long long units = (n + parity + 1) / 2;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const long long partner = (((i + parity) & 1) == 0) ? i + 1 : i - 1;
-        Real res;
-        if (partner == i + 1 && partner < n) {
-            // left member of group (i, i+1): Eq. (cc)
-            const Real a = (i == 0) ? k.bl : in[i - 1];
-            const Real b = in[i];
-            const Real c = in[i + 1];
-            const Real d = (i + 2 == n) ? k.br : in[i + 2];
-            res = fma_rn(k.c4, d, fma_rn(k.c3, c, fma_rn(k.c2, b, mul_rn(k.c1, a))));
-        } else if (partner == i - 1 && partner >= 0) {
-            // right member of group (i-1, i): Eq. (dd)
-            const long long lo = i - 1;
-            const Real a = (lo == 0) ? k.bl : in[lo - 1];
-            const Real b = in[lo];
-            const Real c = in[i];
-            const Real d = (i + 1 == n) ? k.br : in[i + 1];
-            res = fma_rn(k.c1, d, fma_rn(k.c2, c, fma_rn(k.c3, b, mul_rn(k.c4, a))));
-        } else if (partner < 0) {
+    for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < units; u += stride) {
+        const long long s = 2 * u - parity;
+        if (s >= 0 && s + 1 < n) {
+            const Real a = (s == 0) ? k.bl : in[s - 1];
+            const Real b = in[s];
+            const Real c = in[s + 1];
+            const Real d = (s + 2 == n) ? k.br : in[s + 2];
+            // Eq. (cc), left member, terms in printed order
+            out[s] = fma_rn(k.c4, d, fma_rn(k.c3, c, fma_rn(k.c2, b, mul_rn(k.c1, a))));
+            // Eq. (dd), right member
+            out[s + 1] = fma_rn(k.c1, d, fma_rn(k.c2, c, fma_rn(k.c3, b, mul_rn(k.c4, a))));
+        } else if (s < 0) {
             // left singleton: Saul'yev A, Eq. (aa), new-level neighbour = beta_l
             const Real far = (n == 1) ? k.br : in[1];
-            res = fma_rn(k.s0, far, fma_rn(k.s1, in[0], mul_rn(k.s0, k.bl)));
+            out[0] = fma_rn(k.s0, far, fma_rn(k.s1, in[0], mul_rn(k.s0, k.bl)));
         } else {
             // right singleton: Saul'yev B, Eq. (bb), new-level neighbour = beta_r
             const Real far = (n == 1) ? k.bl : in[n - 2];
-            res = fma_rn(k.s0, far, fma_rn(k.s1, in[n - 1], mul_rn(k.s0, k.br)));
+            out[n - 1] = fma_rn(k.s0, far, fma_rn(k.s1, in[n - 1], mul_rn(k.s0, k.br)));
         }
-        out[i] = res;
     }
 }
 
@@ -90,7 +90,8 @@ cudaError_t launch(const Real *in, Real *out, long long n, int parity, const Can
     k.bl = (Real)c.beta_l;
     k.br = (Real)c.beta_r;
     const int threads = 256;
-    long long blocks = (n + threads - 1) / threads;
+    const long long units = (n + parity + 1) / 2;
+    long long blocks = (units + threads - 1) / threads;
     if (blocks > (1LL << 20))
         blocks = 1LL << 20;  // grid-stride loop covers the rest
     canon_kernel<Real><<<(unsigned)blocks, threads, 0, s>>>(in, out, n, parity, k);
