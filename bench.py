@@ -484,7 +484,7 @@ def sno_launches_per_forward(L=4):
 def launches_per_solve(kernel, depth):
     """Kernel launches of one solve (the tiled kernels' tile-queue resets are
     memsets, not kernels; the double-float kernel adds its prescale)."""
-    if kernel in ("canonical", "subdomain16"):
+    if kernel in ("canonical", "subdomain16_onestep"):
         return GE_STEPS
     d = 1 if kernel == "onestep" else depth
     return (GE_STEPS + d - 1) // d + (1 if kernel == "temporal_df" else 0)
@@ -509,7 +509,8 @@ def main():
     ap.add_argument("--sno-forward-only", action="store_true",
                     help="time only surrogate forward passes (untrained weights; profiling)")
     ap.add_argument("--subdomain", type=int, default=1,
-                    help="sub-domain width k of the main solve (k > 1 needs --kernel canonical)")
+                    help="sub-domain width k of the main solve (k > 1: --kernel temporal runs --depth steps "
+                         "per launch, --kernel canonical one launch per step)")
     ap.add_argument("--only-batched", default=None, choices=["f32", "f32c", "f64"],
                     help="run only the batched workload in this precision (profiling)")
     args = ap.parse_args()
@@ -689,14 +690,15 @@ def main():
             flush_buf.fill_(1)
         for vp, vk, vd in (("f64", "temporal_df", 96), ("f64", "onestep", 1), ("f64", "canonical", 1),
                            ("f32", "temporal", 128), ("f32c", "temporal", 64), ("f32", "onestep", 1),
-                           ("f64", "subdomain16", 1)):
+                           ("f64", "subdomain16", 8), ("f64", "subdomain16_onestep", 1)):
             if (vp, vk) == (args.precision, args.kernel):
                 continue
             p2 = {"f64": B.GE_F64, "f32": B.GE_F32, "f32c": B.GE_F32_COMP}[vp]
-            width = 16 if vk == "subdomain16" else 1
+            width = 16 if vk.startswith("subdomain16") else 1
+            # width 16: `depth` steps per launch on a tile in shared memory, or one launch per step
             k2 = {"temporal": B.GE_KERNEL_TEMPORAL, "temporal_df": B.GE_KERNEL_TEMPORAL_DF,
                   "onestep": B.GE_KERNEL_ONESTEP, "canonical": B.GE_KERNEL_CANONICAL,
-                  "subdomain16": B.GE_KERNEL_CANONICAL}[vk]
+                  "subdomain16": B.GE_KERNEL_TEMPORAL, "subdomain16_onestep": B.GE_KERNEL_CANONICAL}[vk]
             x2 = torch.from_numpy(u0).to(dev, dtype=B.dtype_of(p2))
             with torch.cuda.stream(stream):
                 c2 = B.ge_create(N_POINTS, R, 0.0, 0.0, p2, x2, stream=stream)
@@ -722,7 +724,7 @@ def main():
                             "ops_per_update": ops,
                             "alu_frac": ops * upd_s / (128.0 * SMS * sm_max_mhz * 1e6),
                             "vs_f64_temporal": upd_s / value if args.kernel == "temporal" else None})
-            variants[f"{vp}_{vk}" + (f"_d{vd}" if vk.startswith("temporal") else "")] = ent
+            variants[f"{vp}_{vk}" + (f"_d{vd}" if vk.startswith("temporal") or vk == "subdomain16" else "")] = ent
             del x2, o2
         del flush_buf
 

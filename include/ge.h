@@ -141,8 +141,12 @@ ge_status ge_tune(ge_ctx *ctx, int64_t steps, int32_t *best_depth);
  * For k > 1 each step couples the two wall nodes of every confluence of a B
  * sub-domain with the A sub-domain to its right by Eqs. (cc)/(dd) and sweeps
  * Saul'yev A runs to the right and B runs to the left (paper node j uses A
- * at parity p iff floor(j/k) + p is even); ge_step_n then runs one launch per
- * step with one thread per confluence unit, whatever ge_set_kernel chose.
+ * at parity p iff floor(j/k) + p is even), one thread per confluence unit.
+ * With GE_KERNEL_AUTO / GE_KERNEL_TEMPORAL ge_step_n then runs `depth` steps
+ * per launch (ge_set_kernel; default 8) on tiles kept in shared memory,
+ * falling back to one launch per step when fewer than 64 units of 2k nodes
+ * fit a CTA's shared memory; GE_KERNEL_CANONICAL / GE_KERNEL_ONESTEP run one
+ * launch per step.  Both are bit-identical to a serial FP64 evaluation.
  * Errors: GE_EINVAL (NULL ctx, k < 1, k > 1 with GE_F32_COMP). */
 ge_status ge_set_subdomain_width(ge_ctx *ctx, int64_t k);
 

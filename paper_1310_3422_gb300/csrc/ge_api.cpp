@@ -41,6 +41,7 @@ ge_status cuda_fail(cudaError_t e, const char *what)
 constexpr int kDefaultDepthF64 = 48;
 constexpr int kDefaultDepthF32 = 128;
 constexpr int kDefaultDepthDf = 96;
+constexpr int kDefaultDepthSweep = 8;  // width-k steps per launch (k = 16, N = 2^24: 1.41e11 updates/s)
 // Largest r the double-float kernel takes: the right-hand side reaches about
 // (1 + 3r) times the data and must stay far inside the FP32 exponent range.
 constexpr double kDfMaxR = 1048576.0;
@@ -335,12 +336,33 @@ ge_status run_tiled(ge_ctx *c, int64_t steps, int depth, bool df = false)
     return GE_OK;
 }
 
-// General sub-domain width k: one launch per step (ge_sweep.cu).
-ge_status run_sweep(ge_ctx *c, int64_t steps)
+// General sub-domain width k (ge_sweep.cu): up to `depth` steps per launch on
+// a tile in shared memory (multi), else, or where the width leaves too few
+// units per tile, one launch per step.
+ge_status run_sweep(ge_ctx *c, int64_t steps, bool multi, int depth)
 {
-    for (int64_t s = 0; s < steps; ++s) {
+    for (int64_t s = 0; s < steps;) {
         const int parity = (int)((c->step + s) & 1);
         cudaError_t e;
+        if (multi) {
+            const int want = (int)((steps - s) < depth ? (steps - s) : depth);
+            int done = 0;
+            if (c->prec == GE_F64)
+                e = ge::launch_sweep_tb_f64(static_cast<const double *>(c->buf[c->cur]),
+                                            static_cast<double *>(c->buf[c->cur ^ 1]), c->n, parity, c->width,
+                                            want, c->canon, &done, c->stream);
+            else
+                e = ge::launch_sweep_tb_f32(static_cast<const float *>(c->buf[c->cur]),
+                                            static_cast<float *>(c->buf[c->cur ^ 1]), c->n, parity, c->width,
+                                            want, c->canon, &done, c->stream);
+            if (e != cudaSuccess)
+                return cuda_fail(e, "sub-domain sweep kernel launch");
+            if (done > 0) {
+                c->cur ^= 1;
+                s += done;
+                continue;
+            }
+        }
         if (c->prec == GE_F64)
             e = ge::launch_sweep_f64(static_cast<const double *>(c->buf[c->cur]),
                                      static_cast<double *>(c->buf[c->cur ^ 1]), c->n, parity, c->width,
@@ -352,6 +374,7 @@ ge_status run_sweep(ge_ctx *c, int64_t steps)
         if (e != cudaSuccess)
             return cuda_fail(e, "sub-domain sweep kernel launch");
         c->cur ^= 1;
+        ++s;
     }
     return GE_OK;
 }
@@ -613,7 +636,8 @@ ge_status ge_step_n(ge_ctx *c, int64_t steps)
         return GE_OK;
     ge_status st;
     if (c->width > 1) {
-        st = run_sweep(c, steps);
+        const bool multi = c->kernel != GE_KERNEL_CANONICAL && c->kernel != GE_KERNEL_ONESTEP;
+        st = run_sweep(c, steps, multi, c->depth ? c->depth : kDefaultDepthSweep);
         if (st == GE_OK)
             c->step += steps;
         return st;

@@ -196,6 +196,12 @@ cudaError_t launch_sweep_f64(const double *in, double *out, long long n, int par
                              const CanonCoef &c, cudaStream_t s);
 cudaError_t launch_sweep_f32(const float *in, float *out, long long n, int parity, long long k,
                              const CanonCoef &c, cudaStream_t s);
+// Up to `steps` width-k steps in one launch (tile in shared memory);
+// *done = steps taken, 0 when the width does not fit (use the one-step launch).
+cudaError_t launch_sweep_tb_f64(const double *in, double *out, long long n, int parity, long long k, int steps,
+                                const CanonCoef &c, int *done, cudaStream_t s);
+cudaError_t launch_sweep_tb_f32(const float *in, float *out, long long n, int parity, long long k, int steps,
+                                const CanonCoef &c, int *done, cudaStream_t s);
 
 // prec: 0 = FP64, 1 = FP32, 2 = FP32 compensated.  tmap: 128-byte-aligned
 // CUtensorMap (opaque here) describing the source buffer.

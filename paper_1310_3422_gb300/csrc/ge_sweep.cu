@@ -190,6 +190,129 @@ __global__ void __launch_bounds__(256) sweep_smem_kernel(const Real *__restrict_
     }
 }
 
+// D steps per launch on a tile kept in shared memory.  A tile covers NU
+// units of the first step's grouping (nodes [T0, T0 + 2k NU)); nodes are
+// stored with one pad slot after every 2k, so the threads' units (2k nodes,
+// shifted by k on alternate steps) fall in different banks.  One step
+// changes a unit from the old values of the unit and one node on each side,
+// so the valid part of the tile shrinks by at most 2k + 1 nodes per side per
+// step: the tile writes back its inner NU - 2 HU units, HU = D + 1 +
+// ceil(D / 2k).  Each step every thread reads the two old values just
+// outside its unit, the CTA synchronises, and the unit is updated in place
+// with the arithmetic of sweep_smem_kernel, in the same order.
+template <typename Real>
+__global__ void __launch_bounds__(256) sweep_tb_kernel(const Real *__restrict__ in, Real *__restrict__ out, long long n,
+                                                       int parity, int k, int steps, int NU, int HU,
+                                                       long long n_tiles, SweepCoef<Real> c)
+{
+    extern __shared__ unsigned char sweep_smem[];
+    Real *sm = reinterpret_cast<Real *>(sweep_smem);
+    const int t = threadIdx.x;
+    const int w = 2 * k;
+    const int span = NU * w;  // tile nodes
+    const long long out_units = NU - 2 * HU;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        // first node of the tile: unit (tile * out_units - HU) of the first step's grouping
+        const long long T0 = ((long long)(parity - 1) + 2 * (tile * out_units - HU)) * k;
+        for (int e = t; e < span; e += blockDim.x) {
+            const long long j = T0 + e;
+            if (j >= 1 && j <= n)
+                sm[e + e / w] = in[j - 1];
+        }
+        __syncthreads();
+        for (int st = 0; st < steps; ++st) {
+            // this step's units start at local node e0 = off + w * i (off = 0 on
+            // the first step's grouping, k on the other); the partial ones at
+            // the tile's ends are skipped
+            const int off = (st & 1) ? k : 0;
+            const int nu = (st & 1) ? NU - 1 : NU;
+            const bool active = t < nu;
+            const int e0 = off + w * t;
+            const long long ub = T0 + e0;  // first node of this thread's unit
+            const int base = e0 + e0 / w;
+            const int split = w - (e0 % w);  // nodes of the unit before the next pad slot
+            auto addr = [&](long long jj) -> int {
+                const int i = (int)(jj - ub);
+                return base + i + (i >= split ? 1 : 0);
+            };
+            Real left = (Real)0, right = (Real)0;  // old values of nodes ub - 1 and ub + w
+            if (active) {
+                const long long jl = ub - 1, jr = ub + w;
+                if (e0 >= 1 && jl >= 1 && jl <= n)
+                    left = sm[(e0 - 1) + (e0 - 1) / w];
+                if (e0 + w < span && jr >= 1 && jr <= n)
+                    right = sm[(e0 + w) + (e0 + w) / w];
+            }
+            __syncthreads();
+            if (active) {
+                auto old = [&](long long j) -> Real {
+                    if (j == 0)
+                        return c.bl;
+                    if (j == n + 1)
+                        return c.br;
+                    if (j < ub)
+                        return left;
+                    if (j >= ub + w)
+                        return right;
+                    return sm[addr(j)];
+                };
+                auto saulyev = [&](Real nb, long long j, long long far) -> Real {
+                    return f_fma(c.s0, old(far), f_fma(c.s1, sm[addr(j)], f_mul(c.s0, nb)));
+                };
+                const long long bA = ub / k + 1;  // the unit's A sub-domain
+                const long long a_lo = bA * k < 1 ? 1 : bA * k;
+                const long long a_hi = bA * k + k - 1 > n ? n : bA * k + k - 1;
+                const long long b_lo = (bA - 1) * k < 1 ? 1 : (bA - 1) * k;
+                const long long b_hi = bA * k - 1 > n ? n : bA * k - 1;
+                const bool has_a = a_lo <= a_hi, has_b = b_lo <= b_hi;
+                if (has_a && has_b) {
+                    const long long j = bA * k - 1;
+                    const Real a = old(j - 1), b = old(j), cc = old(j + 1), d = old(j + 2);
+                    const Real y = f_fma(c.c4, d, f_fma(c.c3, cc, f_fma(c.c2, b, f_mul(c.c1, a))));
+                    const Real z = f_fma(c.c1, d, f_fma(c.c2, cc, f_fma(c.c3, b, f_mul(c.c4, a))));
+                    Real prev = z;
+                    for (long long m = j + 2; m <= a_hi; ++m) {  // A run to the right
+                        const Real nv = saulyev(prev, m, m + 1);
+                        sm[addr(m)] = nv;
+                        prev = nv;
+                    }
+                    prev = y;
+                    for (long long m = j - 1; m >= b_lo; --m) {  // B run to the left
+                        const Real nv = saulyev(prev, m, m - 1);
+                        sm[addr(m)] = nv;
+                        prev = nv;
+                    }
+                    sm[addr(j)] = y;
+                    sm[addr(j + 1)] = z;
+                } else if (has_a) {
+                    Real prev = c.bl;
+                    for (long long m = a_lo; m <= a_hi; ++m) {
+                        const Real nv = saulyev(prev, m, m + 1);
+                        sm[addr(m)] = nv;
+                        prev = nv;
+                    }
+                } else if (has_b) {
+                    Real prev = c.br;
+                    for (long long m = b_hi; m >= b_lo; --m) {
+                        const Real nv = saulyev(prev, m, m - 1);
+                        sm[addr(m)] = nv;
+                        prev = nv;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        // write back the tile's inner units
+        const int o_lo = HU * w, o_hi = (NU - HU) * w;
+        for (int e = o_lo + t; e < o_hi; e += blockDim.x) {
+            const long long j = T0 + e;
+            if (j >= 1 && j <= n)
+                out[j - 1] = sm[e + e / w];
+        }
+        __syncthreads();
+    }
+}
+
 template <typename Real>
 cudaError_t launch_sweep_t(const Real *in, Real *out, long long n, int parity, long long k, const CanonCoef &cf,
                            cudaStream_t s)
@@ -224,7 +347,71 @@ cudaError_t launch_sweep_t(const Real *in, Real *out, long long n, int parity, l
     return cudaGetLastError();
 }
 
+// Up to `steps` steps in one launch of sweep_tb_kernel; *done receives the
+// steps taken.  0 when the width leaves too few units per tile (the caller
+// then runs one step with launch_sweep_t).
+template <typename Real>
+cudaError_t launch_sweep_tb_t(const Real *in, Real *out, long long n, int parity, long long k, int steps,
+                              const CanonCoef &cf, int *done, cudaStream_t s)
+{
+    *done = 0;
+    if (k < 2 || steps < 1)
+        return cudaSuccess;
+    SweepCoef<Real> c{(Real)cf.c1, (Real)cf.c2, (Real)cf.c3, (Real)cf.c4,
+                      (Real)cf.s0, (Real)cf.s1, (Real)cf.beta_l, (Real)cf.beta_r};
+    const long long w = 2 * k;
+    const long long max_smem = 227 * 1024;
+    long long NU = max_smem / ((w + 1) * (long long)sizeof(Real));
+    if (NU > 256)
+        NU = 256;
+    // steps per launch: the halo HU = D + 1 + ceil(D / 2k) units per side
+    // leaves at least half of the tile's units as output
+    int D = steps;
+    auto halo = [&](int d) { return (long long)d + 1 + (d + w - 1) / w; };
+    while (D > 1 && NU - 2 * halo(D) < NU / 2)
+        --D;
+    if (NU < 64 || NU - 2 * halo(D) < 1)
+        return cudaSuccess;
+    const int HU = (int)halo(D);
+    const long long out_units = NU - 2 * HU;
+    // tiles cover nodes from (parity - 1) k up to n
+    const long long first = (long long)(parity - 1) * k;
+    const long long n_tiles = (n + 1 - first + out_units * w - 1) / (out_units * w);
+    const int smem = (int)(NU * (w + 1) * (long long)sizeof(Real));
+    cudaError_t e = cudaFuncSetAttribute(sweep_tb_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess)
+        return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_tb_kernel<Real>, 256, smem);
+    if (e != cudaSuccess)
+        return e;
+    long long grid = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (grid > n_tiles)
+        grid = n_tiles;
+    sweep_tb_kernel<Real><<<(unsigned)grid, 256, smem, s>>>(in, out, n, parity, (int)k, D, (int)NU, HU, n_tiles, c);
+    e = cudaGetLastError();
+    if (e == cudaSuccess)
+        *done = D;
+    return e;
+}
+
 }  // namespace
+
+cudaError_t launch_sweep_tb_f64(const double *in, double *out, long long n, int parity, long long k, int steps,
+                                const CanonCoef &c, int *done, cudaStream_t s)
+{
+    return launch_sweep_tb_t<double>(in, out, n, parity, k, steps, c, done, s);
+}
+
+cudaError_t launch_sweep_tb_f32(const float *in, float *out, long long n, int parity, long long k, int steps,
+                                const CanonCoef &c, int *done, cudaStream_t s)
+{
+    return launch_sweep_tb_t<float>(in, out, n, parity, k, steps, c, done, s);
+}
 
 cudaError_t launch_sweep_f64(const double *in, double *out, long long n, int parity, long long k,
                              const CanonCoef &c, cudaStream_t s)
