@@ -301,7 +301,7 @@ def measure_batch(B, torch, inputs, dev, steps, warmup, only=None):
     picks = list(rng.choice(len(bt.n), 6, replace=False)) + [int(np.argmin(bt.n)), int(np.argmax(bt.n))]
     want = {i: oracle.run(bt.u0[bt.offsets[i]:bt.offsets[i] + bt.n[i]], bt.r[i], bt.beta_l[i], bt.beta_r[i], 2000)
             for i in picks}
-    for name, prec in (("f32", B.GE_F32), ("f32c", B.GE_F32_COMP), ("f64", B.GE_F64)):
+    for name, prec in (("f32", B.GE_F32), ("f32c", B.GE_F32_COMP), ("f64", B.GE_F64), ("f64_df", B.GE_F64)):
         if only is not None and name != only:
             continue
         s = torch.cuda.Stream(device=dev)
@@ -309,6 +309,8 @@ def measure_batch(B, torch, inputs, dev, steps, warmup, only=None):
             u0 = torch.from_numpy(bt.u0).to(dev, B.dtype_of(prec))
             u = u0.clone()
             plan = B.ge_batch_create(bt.n, bt.r, bt.beta_l, bt.beta_r, bt.offsets, bt.total, prec, stream=s)
+            if name == "f64_df":  # FP64 storage, double-float arithmetic on the FP32 pipes
+                B.ge_batch_set_kernel(plan, B.GE_KERNEL_TEMPORAL_DF)
             depth = B.ge_batch_tune(plan, u0, 256)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=s):
@@ -334,7 +336,7 @@ def measure_batch(B, torch, inputs, dev, steps, warmup, only=None):
                 errs.append(float(np.max(np.abs(got[o:o + n] - w)) / np.max(np.abs(w))))
             B.ge_batch_destroy(plan)
         out[name] = {"updates_per_s": upd / (ms / 1e3), "ms_per_solve": ms, "depth": depth,
-                     "launches_per_solve": (2000 + depth - 1) // depth,
+                     "launches_per_solve": (2000 + depth - 1) // depth + (2 if name == "f64_df" else 0),
                      "max_rel_err_sampled": max(errs), "problems_checked": len(picks)}
     return out
 
@@ -511,7 +513,7 @@ def main():
     ap.add_argument("--subdomain", type=int, default=1,
                     help="sub-domain width k of the main solve (k > 1: --kernel temporal runs --depth steps "
                          "per launch, --kernel canonical one launch per step)")
-    ap.add_argument("--only-batched", default=None, choices=["f32", "f32c", "f64"],
+    ap.add_argument("--only-batched", default=None, choices=["f32", "f32c", "f64", "f64_df"],
                     help="run only the batched workload in this precision (profiling)")
     args = ap.parse_args()
 

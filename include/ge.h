@@ -227,6 +227,17 @@ ge_status ge_batch_create(ge_batch **out, int32_t n_problems, const int64_t *n, 
 
 /* Steps per launch (1..512, 0 = built-in default).  Errors: GE_EINVAL. */
 ge_status ge_batch_set_depth(ge_batch *plan, int32_t depth);
+
+/* Kernel of later ge_batch_run calls: GE_KERNEL_AUTO / GE_KERNEL_TEMPORAL
+ * (the default), or for a GE_F64 plan GE_KERNEL_TEMPORAL_DF.  The
+ * double-float kernel keeps the plan's FP64 storage and evaluates the steps
+ * as pairs of floats (see GE_KERNEL_TEMPORAL_DF): each call prescales every
+ * problem by the power of two above its largest |u| and wall value, and
+ * padding between problems comes back bit for bit.  Synchronous (waits for
+ * the plan's stream, recomputes the rescaling table).
+ * Errors: GE_EINVAL (NULL plan, another kernel, GE_KERNEL_TEMPORAL_DF on a
+ * GE_F32 / GE_F32_COMP plan or with some r > 2^20), GE_ENOMEM, GE_ECUDA. */
+ge_status ge_batch_set_kernel(ge_batch *plan, ge_kernel kernel);
 ge_status ge_batch_get_depth(const ge_batch *plan, int32_t *depth);
 
 /* Autotune the depth: times each candidate depth on `steps` steps of the data

@@ -25,7 +25,8 @@ GE_KERNEL_AUTO, GE_KERNEL_CANONICAL, GE_KERNEL_ONESTEP, GE_KERNEL_TEMPORAL, GE_K
 # Every symbol include/ge.h and include/ge_sno.h declare.
 EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", "ge_read_state", "ge_write_state",
            "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_batch_create", "ge_batch_set_depth",
-           "ge_batch_get_depth", "ge_batch_tune", "ge_batch_run", "ge_batch_sync", "ge_batch_destroy",
+           "ge_batch_get_depth", "ge_batch_set_kernel", "ge_batch_tune", "ge_batch_run", "ge_batch_sync",
+           "ge_batch_destroy",
            "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error", "ge_debug_stall",
            "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune",
            "ge_sno_create", "ge_sno_num_params", "ge_sno_get_params", "ge_sno_set_params",
@@ -88,6 +89,8 @@ def load(path: str | None = None):
         lib.ge_batch_create.restype = ctypes.c_int
         lib.ge_batch_set_depth.argtypes = [_VP, _I32]
         lib.ge_batch_set_depth.restype = ctypes.c_int
+        lib.ge_batch_set_kernel.argtypes = [_VP, ctypes.c_int]
+        lib.ge_batch_set_kernel.restype = ctypes.c_int
         lib.ge_batch_get_depth.argtypes = [_VP, ctypes.POINTER(_I32)]
         lib.ge_batch_get_depth.restype = ctypes.c_int
         lib.ge_batch_tune.argtypes = [_VP, _VP, _I64, ctypes.POINTER(_I32)]
@@ -316,6 +319,10 @@ def ge_batch_create(n, r, beta_l, beta_r, offsets, total: int, prec: int, stream
 
 def ge_batch_set_depth(plan: Batch, depth: int):
     _check(load().ge_batch_set_depth(plan.handle, int(depth)), "ge_batch_set_depth")
+
+
+def ge_batch_set_kernel(plan: Batch, kernel: int):
+    _check(load().ge_batch_set_kernel(plan.handle, int(kernel)), "ge_batch_set_kernel")
 
 
 def ge_batch_get_depth(plan: Batch) -> int:

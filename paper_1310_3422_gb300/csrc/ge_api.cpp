@@ -172,22 +172,8 @@ bool valid_kernel(int k)
            k == GE_KERNEL_TEMPORAL || k == GE_KERNEL_TEMPORAL_DF;
 }
 
-// (hi, lo) float pair of a double: hi = fl32(x), lo = fl32(x - hi).
-void df_split(double x, float *pair)
-{
-    pair[0] = (float)x;
-    pair[1] = (float)(x - (double)pair[0]);
-}
-
-// Prescale code of one value (see ge::kDfCodeBias); 0 for zero.
-int df_code_of(double x)
-{
-    if (x == 0.0)
-        return 0;
-    int e = 0;
-    std::frexp(x, &e);  // |x| = m 2^e with 0.5 <= m < 1: the smallest e with |x| < 2^e
-    return e + ge::kDfCodeBias;
-}
+void df_split(double x, float *pair) { ge::df_split_host(x, pair); }
+int df_code_of(double x) { return ge::df_code_host(x); }
 
 // Launch-independent fields of the double-float kernel.  The scaled map's
 // growth per step is exactly 1 + g with g = g_hi + g_lo the pair the kernel

@@ -73,6 +73,11 @@ struct ge_batch {
     long long stall = 0;  // diagnostic (ge_batch_debug_stall)
     std::vector<int> slot_nmid;
     std::vector<char> slot_ready;
+    // double-float kernel (FP64 plans, ge_batch_set_kernel)
+    bool df = false;
+    double r_max = 0.0;
+    int *df_codes = nullptr;  // per-problem prescale codes of the current call
+    int df_blocks_per_sm = 0;
 };
 
 namespace {
@@ -94,6 +99,8 @@ void release_batch(ge_batch *b)
         cudaFree(b->exps);
     if (b->endf)
         cudaFree(b->endf);
+    if (b->df_codes)
+        cudaFree(b->df_codes);
     delete b;
 }
 
@@ -106,9 +113,11 @@ constexpr int kEndfSlots = 64;
 // filled inside a capture is not marked ready: the next direct run fills it
 // again, since the captured graph may never be launched.  -1 when all slots
 // are taken (that launch then uses the normalised form).
+// Coefficient mode of the scaled form's tables (see ge::batch_exps).
+int scale_mode(const ge_batch *b) { return b->df ? 2 : (b->prec == GE_F32 ? 1 : 0); }
+
 int endf_slot(ge_batch *b, int n_mid, cudaError_t *err)
 {
-    const bool f32 = b->prec == GE_F32;
     size_t i = 0;
     while (i < b->slot_nmid.size() && b->slot_nmid[i] != n_mid)
         ++i;
@@ -120,7 +129,7 @@ int endf_slot(ge_batch *b, int n_mid, cudaError_t *err)
     }
     if (!b->slot_ready[i]) {
         void *dst = static_cast<char *>(b->endf) + i * (size_t)b->n_problems * 8;
-        *err = ge::batch_endf(b->desc, b->exps, b->n_problems, b->R, b->Q, n_mid, f32 ? 1 : 0, dst, b->stream);
+        *err = ge::batch_endf(b->desc, b->exps, b->n_problems, b->R, b->Q, n_mid, scale_mode(b), dst, b->stream);
         if (*err != cudaSuccess)
             return -1;
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -140,6 +149,14 @@ ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int *result_buf)
     const int dmax = ge::tbb_max_depth(pidx);
     if (depth > dmax)
         depth = dmax;
+    if (b->df) {
+        // the call's prescale: per problem, the power of two just above its
+        // largest |u| and wall value
+        cudaError_t e = ge::batch_df_prescale(static_cast<const double *>(b->buf[0]), b->row_pid, b->desc,
+                                              b->n_rows, b->n_problems, b->df_codes, b->stream);
+        if (e != cudaSuccess)
+            return bcuda(e, "ge_batch: double-float prescale");
+    }
     while (n0 < steps) {
         const int64_t L = (steps - n0 < depth) ? steps - n0 : depth;
         ge::TbbParams p{};
@@ -170,14 +187,21 @@ ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int *result_buf)
                 p.endf = static_cast<const char *>(b->endf) + (size_t)slot * b->n_problems * 8;
             }
         }
+        if (b->df && !p.scaled)
+            return bfail(GE_EINVAL, "ge_batch: the double-float kernel needs an end-factor slot (at most 64 "
+                                    "launch lengths per plan)");
+        p.df_in = n0 == 0 ? 1 : 0;
+        p.df_out = last ? 1 : 0;
+        p.df_codes = b->df_codes;
         p.out = b->buf[cur ^ 1];
         p.tile_ctr = b->err + 48;  // the launch's tile queue, zeroed first
-        long long grid = (long long)b->num_sms * b->blocks_per_sm;
+        long long grid = (long long)b->num_sms * (b->df ? b->df_blocks_per_sm : b->blocks_per_sm);
         if (grid > p.n_tiles)
             grid = p.n_tiles;
         cudaError_t e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int), b->stream);
         if (e == cudaSuccess)
-            e = ge::launch_tbb(pidx, &b->tmap[cur], p, (int)grid, b->stream);
+            e = b->df ? ge::launch_tbb_df(&b->tmap[cur], p, (int)grid, b->stream)
+                      : ge::launch_tbb(pidx, &b->tmap[cur], p, (int)grid, b->stream);
         if (e != cudaSuccess)
             return bcuda(e, "ge_batch: kernel launch");
         cur ^= 1;
@@ -241,11 +265,23 @@ ge_status ge_batch_create(ge_batch **out, int32_t n_problems, const int64_t *n, 
         d.kap_s = (1.0 + g_used) * (1.0 - ri) / (1.0 + ri);
         d.ustar_a = beta_l[i];
         d.ustar_b = (beta_r[i] - beta_l[i]) / (double)(n[i] + 1);
+        // double-float pairs: the scaled map's growth is 1 + (g_hi + g_lo)
+        ge::df_split_host(2.0 * ri, d.dfc[0]);
+        const double g_df = (double)d.dfc[0][0] + (double)d.dfc[0][1];
+        ge::df_split_host((1.0 + g_df) * ((1.0 - ri) / (1.0 + ri)), d.dfc[1]);
+        ge::df_split_host(ri, d.dfc[2]);
+        ge::df_split_host(1.0 - ri, d.dfc[3]);
+        ge::df_split_host(d.x1, d.dfc[4]);
+        ge::df_split_host(d.x2, d.dfc[5]);
+        ge::df_split_host(d.xs, d.dfc[6]);
+        const int wl = ge::df_code_host(beta_l[i]), wr = ge::df_code_host(beta_r[i]);
+        d.walls_code = wl > wr ? wl : wr;
         r_max = ri > r_max ? ri : r_max;
     }
     ge_batch *b = new (std::nothrow) ge_batch();
     if (!b)
         return bfail(GE_ENOMEM, "ge_batch_create: host allocation failed");
+    b->r_max = r_max;
     b->prec = prec;
     b->stream = static_cast<cudaStream_t>(stream);
     b->n_problems = n_problems;
@@ -287,7 +323,7 @@ ge_status ge_batch_create(ge_batch **out, int32_t n_problems, const int64_t *n, 
         if (e == cudaSuccess)
             e = cudaMalloc(&b->endf, (size_t)kEndfSlots * n_problems * 8);
         if (e == cudaSuccess)
-            e = ge::batch_exps(b->desc, n_problems, b->R, b->Q, prec == GE_F32 ? 1 : 0, b->exps, b->stream);
+            e = ge::batch_exps(b->desc, n_problems, b->R, b->Q, scale_mode(b), b->exps, b->stream);
     }
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(b->stream);
@@ -318,6 +354,51 @@ ge_status ge_batch_create(ge_batch **out, int32_t n_problems, const int64_t *n, 
     }
     *out = b;
     return GE_OK;
+}
+
+ge_status ge_batch_set_kernel(ge_batch *b, ge_kernel kernel)
+{
+    if (!b)
+        return bfail(GE_EINVAL, "ge_batch_set_kernel: plan is NULL");
+    const bool df = kernel == GE_KERNEL_TEMPORAL_DF;
+    if (!df && kernel != GE_KERNEL_AUTO && kernel != GE_KERNEL_TEMPORAL)
+        return bfail(GE_EINVAL, "ge_batch_set_kernel: batches run GE_KERNEL_TEMPORAL or GE_KERNEL_TEMPORAL_DF");
+    if (df && b->prec != GE_F64)
+        return bfail(GE_EINVAL, "ge_batch_set_kernel: the double-float kernel needs a GE_F64 plan");
+    if (df && b->r_max > 1048576.0)
+        return bfail(GE_EINVAL, "ge_batch_set_kernel: the double-float kernel takes r <= 2^20");
+    if (df == b->df)
+        return GE_OK;
+    // launches in flight still read the scaled form's tables
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess && df && !b->df_codes)
+        e = cudaMalloc(reinterpret_cast<void **>(&b->df_codes), (size_t)b->n_problems * sizeof(int));
+    if (e == cudaSuccess && df && b->df_blocks_per_sm < 1)
+        e = ge::tbb_df_occupancy(&b->df_blocks_per_sm);
+    if (e != cudaSuccess)
+        return bcuda(e, "ge_batch_set_kernel");
+    // the scaled form's rescalings and end factors for the new arithmetic:
+    // FP32 headroom for the double-float pairs, the FP64 one otherwise
+    const double headroom = df ? GE_F32_HEADROOM : 256.0;
+    int R = (int)std::floor(headroom / std::log2(1.0 + 2.0 * b->r_max));
+    R = R < 1 ? 1 : (R > ge::kMaxTableSteps ? ge::kMaxTableSteps : R);
+    const int Q = (ge::kMaxTableSteps + R - 1) / R;
+    if (Q > b->Q) {
+        cudaFree(b->exps);
+        b->exps = nullptr;
+        e = cudaMalloc(reinterpret_cast<void **>(&b->exps), (size_t)b->n_problems * Q * sizeof(short));
+        if (e != cudaSuccess)
+            return bcuda(e, "ge_batch_set_kernel: rescale table");
+    }
+    b->df = df;
+    b->R = R;
+    b->Q = Q;
+    b->slot_nmid.clear();
+    b->slot_ready.clear();
+    e = ge::batch_exps(b->desc, b->n_problems, b->R, b->Q, scale_mode(b), b->exps, b->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(b->stream);
+    return e == cudaSuccess ? GE_OK : bcuda(e, "ge_batch_set_kernel: rescale exponents");
 }
 
 ge_status ge_batch_set_depth(ge_batch *b, int32_t depth)

@@ -102,6 +102,15 @@ struct TbParams {
 // |x| < 2^e over the data and the walls, code = e + kDfCodeBias (e >= -1073,
 // subnormals included); 0 when every value is zero.
 constexpr int kDfCodeBias = 2048;
+// Prescale code of one value on the host; 0 for zero.
+inline int df_code_host(double x)
+{
+    if (x == 0.0)
+        return 0;
+    int e = 0;
+    std::frexp(x, &e);  // |x| = m 2^e with 0.5 <= m < 1: the smallest e with |x| < 2^e
+    return e + kDfCodeBias;
+}
 // Zero the word, then raise it to the data's code and walls_code.
 cudaError_t df_prescale(const void *u, long long n, int walls_code, int *code, cudaStream_t s);
 bool tb_df_geometry(int reach, int *H, int *U);
@@ -125,6 +134,11 @@ struct BatchDesc {
     double g;             // 2r
     double kap_s;         // singleton factor (1 + g)(1-r)/(1+r)
     double ustar_a, ustar_b;
+    // double-float kernel (FP64 plans): (hi, lo) pairs of g = 2r, the
+    // singleton factor (1 + g_hi + g_lo)(1-r)/(1+r), r, 1 - r, x1, x2, xs,
+    // and the prescale code of the wall values (see kDfCodeBias)
+    float dfc[7][2];
+    int walls_code;
 };
 
 // One launch of the batched tiled kernel over the packed buffer.
@@ -145,16 +159,29 @@ struct TbbParams {
     int scaled, R, Q;
     const short *exps;
     const void *endf;
+    // double-float kernel only: the source holds doubles (converted on load),
+    // the launch writes doubles, per-problem prescale codes
+    int df_in, df_out;
+    const int *df_codes;
 };
+
+// Host (hi, lo) float pair of a double, hi = fl32(x), lo = fl32(x - hi).
+inline void df_split_host(double x, float *pair)
+{
+    pair[0] = (float)x;
+    pair[1] = (float)(x - (double)pair[0]);
+}
 
 // Per-problem non-finite scan of a packed buffer (status zeroed first).
 cudaError_t batch_check(int prec, const void *u, const int *row_pid, const BatchDesc *desc, long long n_rows,
                         int *status, cudaStream_t s);
 
 // Rescale exponents of the batched scaled form (one row of Q per problem) and
-// the end factor of a launch with n_mid block steps (kernels in ge_tb.cu).
-cudaError_t batch_exps(const BatchDesc *desc, int n_problems, int R, int Q, int f32, short *exps, cudaStream_t s);
-cudaError_t batch_endf(const BatchDesc *desc, const short *exps, int n_problems, int R, int Q, int n_mid, int f32,
+// the end factor of a launch with n_mid block steps (kernels in ge_tbb.cu).
+// mode: the coefficient the kernel holds for g = 2r: 0 FP64 (end factor
+// double), 1 FP32, 2 the double-float pair (end factors float2 hi, lo).
+cudaError_t batch_exps(const BatchDesc *desc, int n_problems, int R, int Q, int mode, short *exps, cudaStream_t s);
+cudaError_t batch_endf(const BatchDesc *desc, const short *exps, int n_problems, int R, int Q, int n_mid, int mode,
                        void *endf, cudaStream_t s);
 
 // Host-side scale bookkeeping of the scaled block map x <- x + g x_partner
@@ -207,6 +234,12 @@ cudaError_t launch_sweep_tb_f32(const float *in, float *out, long long n, int pa
 // CUtensorMap (opaque here) describing the source buffer.
 cudaError_t launch_tb(int prec, const void *tmap, const TbParams &p, int grid, cudaStream_t s);
 cudaError_t launch_tbb(int prec, const void *tmap, const TbbParams &p, int grid, cudaStream_t s);
+// Batched double-float kernel (ge_tbb_df.cu) for FP64 plans; its per-call
+// prescale: codes[b] = max(desc[b].walls_code, code of the problem's values).
+cudaError_t launch_tbb_df(const void *tmap, const TbbParams &p, int grid, cudaStream_t s);
+cudaError_t tbb_df_occupancy(int *blocks_per_sm);
+cudaError_t batch_df_prescale(const double *u, const int *row_pid, const BatchDesc *desc, long long n_rows,
+                              int n_problems, int *codes, cudaStream_t s);
 cudaError_t tbb_occupancy(int prec, int *blocks_per_sm);
 bool tbb_geometry(int prec, int reach, int *H, int *U);
 // Largest steps per launch whose reach (steps + 2 stages) fits the batched

@@ -463,23 +463,26 @@ __device__ __forceinline__ void dd_mul_dev(double &h, double &l, double bh, doub
     l = __dsub_rn(t, __dsub_rn(h, p));
 }
 
-__device__ __forceinline__ void growth_dev(const BatchDesc &d, int f32, double &gh, double &gl)
+// 1 + g as a double-double, g the coefficient the kernel holds: FP64
+// (mode 0), rounded to FP32 (1), the double-float pair (2).
+__device__ __forceinline__ void growth_dev(const BatchDesc &d, int mode, double &gh, double &gl)
 {
-    const double g = f32 ? (double)__double2float_rn(d.g) : d.g;
+    const double g = mode == 1 ? (double)__double2float_rn(d.g)
+                               : (mode == 2 ? __dadd_rn((double)d.dfc[0][0], (double)d.dfc[0][1]) : d.g);
     gh = __dadd_rn(1.0, g);
     gl = __dadd_rn(__dsub_rn(1.0, gh), g);  // exact: 1 + g == gh + gl
 }
 
 // exps[b][q]: after block q of R steps (scale starting at 1) the scale is
 // brought back into [1, 2) by 2^-exps[b][q].
-__global__ void batch_exps_kernel(const BatchDesc *__restrict__ desc, int np, int R, int Q, int f32,
+__global__ void batch_exps_kernel(const BatchDesc *__restrict__ desc, int np, int R, int Q, int mode,
                                   short *__restrict__ exps)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= np)
         return;
     double gh, gl, sh = 1.0, sl = 0.0;
-    growth_dev(desc[b], f32, gh, gl);
+    growth_dev(desc[b], mode, gh, gl);
     for (int q = 0; q < Q; ++q) {
         for (int i = 0; i < R; ++i)
             dd_mul_dev(sh, sl, gh, gl);
@@ -493,15 +496,15 @@ __global__ void batch_exps_kernel(const BatchDesc *__restrict__ desc, int np, in
 }
 
 // endf[b] = 1 / (scale after n_mid block steps with the rescalings above):
-// float2 (hi, lo) on the FP32 path, double on the FP64 path.
+// float2 (hi, lo) on the FP32 and double-float paths, double on the FP64 path.
 __global__ void batch_endf_kernel(const BatchDesc *__restrict__ desc, const short *__restrict__ exps, int np, int R,
-                                  int Q, int n_mid, int f32, void *endf)
+                                  int Q, int n_mid, int mode, void *endf)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= np)
         return;
     double gh, gl, sh = 1.0, sl = 0.0;
-    growth_dev(desc[b], f32, gh, gl);
+    growth_dev(desc[b], mode, gh, gl);
     for (int m = 0; m < n_mid; ++m) {
         dd_mul_dev(sh, sl, gh, gl);
         if ((m + 1) % R == 0) {
@@ -512,7 +515,7 @@ __global__ void batch_endf_kernel(const BatchDesc *__restrict__ desc, const shor
     }
     const double ih = __ddiv_rn(1.0, sh);
     const double inv = __dsub_rn(ih, __dmul_rn(ih, __ddiv_rn(sl, sh)));
-    if (f32) {
+    if (mode != 0) {
         const float hi = __double2float_rn(inv);
         reinterpret_cast<float2 *>(endf)[b] = make_float2(hi, __double2float_rn(__dsub_rn(inv, (double)hi)));
     } else {
@@ -562,16 +565,16 @@ cudaError_t batch_check(int prec, const void *u, const int *row_pid, const Batch
     return cudaGetLastError();
 }
 
-cudaError_t batch_exps(const BatchDesc *desc, int n_problems, int R, int Q, int f32, short *exps, cudaStream_t s)
+cudaError_t batch_exps(const BatchDesc *desc, int n_problems, int R, int Q, int mode, short *exps, cudaStream_t s)
 {
-    batch_exps_kernel<<<(n_problems + 127) / 128, 128, 0, s>>>(desc, n_problems, R, Q, f32, exps);
+    batch_exps_kernel<<<(n_problems + 127) / 128, 128, 0, s>>>(desc, n_problems, R, Q, mode, exps);
     return cudaGetLastError();
 }
 
-cudaError_t batch_endf(const BatchDesc *desc, const short *exps, int n_problems, int R, int Q, int n_mid, int f32,
+cudaError_t batch_endf(const BatchDesc *desc, const short *exps, int n_problems, int R, int Q, int n_mid, int mode,
                        void *endf, cudaStream_t s)
 {
-    batch_endf_kernel<<<(n_problems + 127) / 128, 128, 0, s>>>(desc, exps, n_problems, R, Q, n_mid, f32, endf);
+    batch_endf_kernel<<<(n_problems + 127) / 128, 128, 0, s>>>(desc, exps, n_problems, R, Q, n_mid, mode, endf);
     return cudaGetLastError();
 }
 
