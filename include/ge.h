@@ -233,7 +233,10 @@ ge_status ge_batch_set_depth(ge_batch *plan, int32_t depth);
  * double-float kernel keeps the plan's FP64 storage and evaluates the steps
  * as pairs of floats (see GE_KERNEL_TEMPORAL_DF): each call prescales every
  * problem by the power of two above its largest |u| and wall value, and
- * padding between problems comes back bit for bit.  Synchronous (waits for
+ * padding between problems comes back bit for bit.  Every distinct launch
+ * length of a plan takes one of its 64 end-factor slots; the FP64 kernel
+ * falls back to its normalised form past them, the double-float kernel has
+ * none, so there ge_batch_run fails with GE_EINVAL.  Synchronous (waits for
  * the plan's stream, recomputes the rescaling table).
  * Errors: GE_EINVAL (NULL plan, another kernel, GE_KERNEL_TEMPORAL_DF on a
  * GE_F32 / GE_F32_COMP plan or with some r > 2^20), GE_ENOMEM, GE_ECUDA. */

@@ -171,3 +171,52 @@ def test_batch_df_settings_rejected():
     with pytest.raises(B.GeError):
         B.ge_batch_set_kernel(plan, B.GE_KERNEL_CANONICAL)
     B.ge_batch_destroy(plan)
+
+
+def test_batch_df_full_size_sampled():
+    """The batched workload (4096 problems, N log-uniform in [256, 65536],
+    r in [0.25, 4], 2000 steps) on the double-float kernel; eight problems
+    checked against the oracle at the FP64 tolerance."""
+    bt = inputs.uneven_batch()
+    x = torch.from_numpy(bt.u0).to(DEV)
+    plan = B.ge_batch_create(bt.n, bt.r, bt.beta_l, bt.beta_r, bt.offsets, bt.total, B.GE_F64)
+    B.ge_batch_set_kernel(plan, DF)
+    B.ge_batch_run(plan, x, 2000)
+    B.ge_batch_sync(plan)
+    B.ge_batch_destroy(plan)
+    got = x.cpu().numpy()
+    rng = np.random.default_rng(7)
+    picks = list(rng.choice(len(bt.n), 6, replace=False)) + [int(np.argmin(bt.n)), int(np.argmax(bt.n))]
+    for i in picks:
+        o, n = bt.offsets[i], bt.n[i]
+        want = oracle.run(bt.u0[o:o + n], bt.r[i], bt.beta_l[i], bt.beta_r[i], 2000)
+        assert rel(got[o:o + n], want) <= tol64(bt.r[i]), (i, n, bt.r[i])
+
+
+def test_batch_df_end_factor_slots_are_bounded():
+    """Every distinct launch length takes one of the plan's 64 end-factor
+    slots; the double-float kernel has no normalised form to fall back to, so
+    a run that needs a 65th length fails with GE_EINVAL and leaves the plan
+    usable for the lengths it has."""
+    n, r, bl, br, offs, total, u = make_batch([37, 200, 64, 5], seed=11)
+    plan = B.ge_batch_create(n, r, bl, br, offs, total, B.GE_F64)
+    B.ge_batch_set_kernel(plan, DF)
+    B.ge_batch_set_depth(plan, 128)
+    x = torch.from_numpy(u).to(DEV)
+    failed_at = None
+    for steps in range(1, 80):
+        try:
+            B.ge_batch_run(plan, x, steps)
+        except B.GeError as err:
+            assert err.status == B.GE_EINVAL
+            failed_at = steps
+            break
+    assert failed_at is not None and failed_at > 60
+    x = torch.from_numpy(u).to(DEV)
+    B.ge_batch_run(plan, x, 10)
+    B.ge_batch_sync(plan)
+    got = x.cpu().numpy()
+    B.ge_batch_destroy(plan)
+    for i in range(len(n)):
+        want = oracle.run(u[offs[i]:offs[i] + n[i]], r[i], bl[i], br[i], 10)
+        assert rel(got[offs[i]:offs[i] + n[i]], want) <= tol64(r[i])
