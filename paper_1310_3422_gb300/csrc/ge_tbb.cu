@@ -108,10 +108,12 @@ __device__ __forceinline__ void run_batch_comp(float (&v)[K], const TbbParams &P
 // so a thread's row is a whole interior run, the problem's first row, its
 // last row (followed by padding), or padding of no problem.  Hence at most
 // two of its points are singletons (register 0 under grouping 1 in a first
-// row, register jhi - 1 whose partner jhi lies past the end), and the
-// points from `keep` on (padding) keep their values.
+// row, register jhi - 1 whose partner jhi lies past the end).  The padding
+// registers (from `keep` on) run the update like the others: no point of a
+// problem reads them (both singletons replace the value computed from their
+// outside partner), and the write-back leaves padding as the tile loaded it.
 struct BatchFix {
-    int keep;       // registers keep .. K-1 keep their values (K: none)
+    int keep;       // registers keep .. K-1 are padding (K: none)
     int tail;       // jhi - 1: the last point of the problem in this row (-1: none)
     bool head;      // register 0 is the problem's first point
 };
@@ -134,18 +136,12 @@ __device__ __forceinline__ BatchFix batch_fix(int pid, Span sp)
 
 // One scaled block step x <- x + g x_partner on a warp that holds problem
 // boundaries: every lane runs the one-FMA update, then the lanes that need
-// it turn their singletons into x <- kap_s x and restore their padding
-// (switches on the two runtime register indices).  Against the generic
-// checked stage this took the FP64 batch from 4.3e11 to 5.6e11 updates/s;
-// the FP32 batch stayed at 9.1e12.
+// it turn their singletons into x <- kap_s x (a switch on the runtime
+// register index of the tail).
 #define GE_TBB_SINGLE(J) \
     case J:              \
         if constexpr ((J) < K) nv[J] = kap * v[J]; \
         break;
-#define GE_TBB_KEEP(J) \
-    case J:            \
-        if constexpr ((J) < K) nv[J] = v[J]; \
-        [[fallthrough]];
 template <int Q, typename Real, int K>
 __device__ __forceinline__ void batch_mid_fixed(Real (&v)[K], Real L, Real R, const BatchFix &f, Real g, Real kap)
 {
@@ -168,24 +164,11 @@ __device__ __forceinline__ void batch_mid_fixed(Real (&v)[K], Real L, Real R, co
             break;
         }
     }
-    if (f.keep < K) {
-        switch (f.keep) {
-            GE_TBB_KEEP(0) GE_TBB_KEEP(1) GE_TBB_KEEP(2) GE_TBB_KEEP(3) GE_TBB_KEEP(4) GE_TBB_KEEP(5) GE_TBB_KEEP(6)
-            GE_TBB_KEEP(7) GE_TBB_KEEP(8) GE_TBB_KEEP(9) GE_TBB_KEEP(10) GE_TBB_KEEP(11) GE_TBB_KEEP(12)
-            GE_TBB_KEEP(13) GE_TBB_KEEP(14) GE_TBB_KEEP(15) GE_TBB_KEEP(16) GE_TBB_KEEP(17) GE_TBB_KEEP(18)
-            GE_TBB_KEEP(19) GE_TBB_KEEP(20) GE_TBB_KEEP(21) GE_TBB_KEEP(22) GE_TBB_KEEP(23) GE_TBB_KEEP(24)
-            GE_TBB_KEEP(25) GE_TBB_KEEP(26) GE_TBB_KEEP(27) GE_TBB_KEEP(28) GE_TBB_KEEP(29) GE_TBB_KEEP(30)
-            GE_TBB_KEEP(31)
-        default:
-            break;
-        }
-    }
 #pragma unroll
     for (int j = 0; j < K; ++j)
         v[j] = nv[j];
 }
 #undef GE_TBB_SINGLE
-#undef GE_TBB_KEEP
 
 // One scaled block step: the fast stage inside a problem, the fixed-up one
 // on warps that hold boundaries.
@@ -207,7 +190,7 @@ __device__ __forceinline__ void batch_mid(Real (&v)[K], Real L, Real R, Span sp,
 // problem's power of two 2^-e after every R block steps, and brought back to
 // the normalised state at the launch end by the factor endf (the inverse of
 // the accumulated scale, computed in double-double by batch_endf_kernel).
-// Only points inside the problem change: padding keeps its values.
+// Only points inside the problem are written back: padding keeps its values.
 template <bool EDGE, typename Real, int K, int NW, bool WT>
 __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &P, const BatchDesc &bd, int pid,
                                                  long long g0, Exch<Real, NW, WT> &x, Span sp)
@@ -407,9 +390,25 @@ __global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
 
         if (writes) {
             unsigned char *rp = cur + my_row * kRowBytes;
+            if (!edge_thr) {
 #pragma unroll
-            for (int c = 0; c < CH; ++c)
-                regs_to_chunk<K>(rp + ((c ^ (my_row & 7)) << 4), v, c);
+                for (int c = 0; c < CH; ++c)
+                    regs_to_chunk<K>(rp + ((c ^ (my_row & 7)) << 4), v, c);
+            } else {
+                // only the points of the thread's problem: padding and rows of
+                // no problem keep the values the tile loaded
+                constexpr int PER = 16 / (int)sizeof(Real);
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    Real *q = reinterpret_cast<Real *>(rp + ((c ^ (my_row & 7)) << 4));
+#pragma unroll
+                    for (int i = 0; i < PER; ++i) {
+                        const int j = c * PER + i;
+                        if (pid >= 0 && j >= sp.jlo && j < sp.jhi)
+                            q[i] = v[j];
+                    }
+                }
+            }
         }
         __syncthreads();
         {
