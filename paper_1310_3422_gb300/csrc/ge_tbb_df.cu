@@ -15,9 +15,9 @@
 // Storage: the plan's buffers hold doubles between calls.  The first launch
 // of a call converts each point of a problem, shifted by u* and prescaled by
 // 2^-e0 of its problem (e0 from a per-problem reduction at the start of the
-// call), to a pair; points of no problem (padding) keep their raw 64 bits in
-// the pair's registers, untouched by every stage, so they come back exactly.
-// The last launch joins the pairs, scales back and adds u*.
+// call), to a pair; points of no problem (padding) are never written back,
+// so the tile passes on the raw 64 bits it loaded and they come back
+// exactly.  The last launch joins the pairs, scales back and adds u*.
 #include <cuda.h>
 #include <cstdint>
 
@@ -66,9 +66,9 @@ __global__ void df_codes_rows_kernel(const double *__restrict__ u, const int *__
     }
 }
 
-// Boundary fix-ups of one thread (as BatchFix in ge_tbb.cu): points from
-// `keep` on keep their values, `tail` is the problem's last point in this
-// row (-1: none), `head` marks the problem's first point at register 0.
+// Boundary fix-ups of one thread (as BatchFix in ge_tbb.cu): registers from
+// `keep` on are padding, `tail` is the problem's last point in this row
+// (-1: none), `head` marks the problem's first point at register 0.
 struct DfFix {
     int keep, tail;
     bool head;
@@ -90,8 +90,8 @@ __device__ __forceinline__ DfFix df_fix(int pid, Span sp)
 }
 
 // One scaled block step on a warp that holds problem boundaries: every lane
-// runs the update, then singletons become x <- kap_s x and padding keeps
-// its raw bits.
+// runs the update (padding registers too: no point of a problem reads them,
+// and the write-back skips them), then singletons become x <- kap_s x.
 template <int Q>
 __device__ __forceinline__ void df_batch_fixed(float (&h)[K], float (&l)[K], DfC g, DfC kap, const DfFix &f,
                                                DfExch &x)
@@ -113,14 +113,6 @@ __device__ __forceinline__ void df_batch_fixed(float (&h)[K], float (&l)[K], DfC
         for (int j = 0; j < K; ++j)
             if (j == f.tail)
                 df_mul(kap.h, kap.l, h[j], l[j], nh[j], nl[j]);
-    }
-    if (f.keep < K) {
-#pragma unroll
-        for (int j = 0; j < K; ++j)
-            if (j >= f.keep) {
-                nh[j] = h[j];
-                nl[j] = l[j];
-            }
     }
 #pragma unroll
     for (int j = 0; j < K; ++j) {
@@ -201,17 +193,13 @@ __device__ __forceinline__ void df_batch_run(float (&h)[K], float (&l)[K], const
     }
 }
 
-// Raw 64 bits of a double in a pair's registers, and back.
+// Raw 64 bits of a double in a pair's registers (padding: never used in
+// arithmetic that reaches a problem's points, never written back).
 __device__ __forceinline__ void raw_to_pair(double x, float &h, float &l)
 {
     const long long b = __double_as_longlong(x);
     h = __int_as_float((int)(b & 0xffffffffLL));
     l = __int_as_float((int)(b >> 32));
-}
-__device__ __forceinline__ double pair_to_raw(float h, float l)
-{
-    const unsigned long long lo = (unsigned int)__float_as_int(h), hi = (unsigned int)__float_as_int(l);
-    return __longlong_as_double((long long)(lo | (hi << 32)));
 }
 
 __global__ void __launch_bounds__(kDfNT, 2)
@@ -314,24 +302,22 @@ __global__ void __launch_bounds__(kDfNT, 2)
         else
             df_batch_run<false>(h, l, P, bd, pid, fx, sp, x);
 
-        // write back every row, then copy the output rows out with coalesced stores
+        // write back the points of the thread's problem (padding and rows of
+        // no problem keep the raw bits the tile loaded), then copy the output
+        // rows out with coalesced stores
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             unsigned char *p = rp + ((c ^ (t & 7)) << 4);
-            if (P.df_out) {
-                double v2[2];
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int j = 2 * c + i;
-                    if (j >= sp.jlo && j < sp.jhi)
-                        v2[i] = ldexp((double)h[j] + (double)l[j], e0) +
-                                (bd.ustar_a + bd.ustar_b * (double)(g0 + j + 1));
+            for (int i = 0; i < 2; ++i) {
+                const int j = 2 * c + i;
+                if (j >= sp.jlo && j < sp.jhi) {
+                    if (P.df_out)
+                        reinterpret_cast<double *>(p)[i] = ldexp((double)h[j] + (double)l[j], e0) +
+                                                           (bd.ustar_a + bd.ustar_b * (double)(g0 + j + 1));
                     else
-                        v2[i] = pair_to_raw(h[j], l[j]);
+                        reinterpret_cast<float2 *>(p)[i] = make_float2(h[j], l[j]);
                 }
-                *reinterpret_cast<double2 *>(p) = make_double2(v2[0], v2[1]);
-            } else {
-                *reinterpret_cast<float4 *>(p) = make_float4(h[2 * c], l[2 * c], h[2 * c + 1], l[2 * c + 1]);
             }
         }
         __syncthreads();
