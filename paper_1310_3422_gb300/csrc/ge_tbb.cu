@@ -197,11 +197,14 @@ __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &
 {
     Real L = 0, R = 0;
     const Real ua = (Real)bd.ustar_a, ub = (Real)bd.ustar_b;
+    // grid position j + 1 of register 0: one 64-bit conversion (the FP64 pipe)
+    // per thread, the registers' positions by exact small additions
+    const Real p1 = (Real)(g0 + 1);
     if (P.do_entry) {
 #pragma unroll
         for (int j = 0; j < K; ++j)
             if (!EDGE || (j >= sp.jlo && j < sp.jhi))
-                v[j] -= ua + ub * (Real)(g0 + j + 1);
+                v[j] -= ua + ub * (p1 + (Real)j);
         const StageC<Real> c{(Real)bd.r, (Real)bd.omr, (Real)0, (Real)0, (Real)0};
         if (((1 - P.p_first) & 1) == 1) {
             exchange(v, L, R, x);
@@ -263,7 +266,7 @@ __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &
 #pragma unroll
         for (int j = 0; j < K; ++j)
             if (!EDGE || (j >= sp.jlo && j < sp.jhi))
-                v[j] += ua + ub * (Real)(g0 + j + 1);
+                v[j] += ua + ub * (p1 + (Real)j);
     }
 }
 
@@ -427,6 +430,174 @@ __global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
         }
         __syncthreads();
         tile = next_tile;
+    }
+}
+
+// Plain FP32 batches, warp-specialised: one producer warp takes tiles from
+// the launch's queue and loads them by TMA into two shared buffers; eight
+// consumer warps each advance their window of the tile (warp windows carry
+// their own halo, so the steps need no CTA barrier) and write their output
+// rows out through their own staging rows.  The warps meet only at the
+// buffers: `full` (the tile landed) and `empty` (all eight consumers have
+// read it), so a warp that holds problem boundaries and runs longer holds
+// back the reuse of a buffer, a tile later, not the other warps' next tile.
+// (With one CTA barrier per tile the FP32 batch spent most stalls there.)
+constexpr int kWsConsumers = kTileRows / 32;      // consumer warps
+constexpr int kWsThreads = kTileRows + 32;         // plus the producer warp
+constexpr int kWsStageBytes = 32 * kRowBytes;      // staging rows of one consumer warp
+int ws_smem_bytes() { return 2 * kTileRows * kRowBytes + kWsConsumers * kWsStageBytes + 1024; }
+
+__global__ void __launch_bounds__(kWsThreads, 2)
+    tbb_ws_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TbbParams P)
+{
+    using Real = float;
+    constexpr bool WT = true;
+    constexpr int K = kRowBytes / (int)sizeof(Real);
+    constexpr int NW = kWsConsumers;
+    constexpr int CH = kRowBytes / 16;
+    constexpr uint32_t kTileBytes = kTileRows * kRowBytes;
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *tiles = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char *stage_all = tiles + 2 * kTileBytes;
+    __shared__ __align__(8) uint64_t full[2], empty[2], never;
+    __shared__ long long tile_of[2];
+    __shared__ Real slot[2][NW][2];  // unused with warp windows (Exch needs the type)
+
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int hr = P.H / K, ur = P.U / K;
+    const long long limit = P.stall > 0 ? P.stall : kWaitLimitCycles;
+
+    if (t == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], NW);
+        mbar_init(&empty[1], NW);
+        mbar_init(&never, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (warp == NW) {
+        // producer: lane 0 issues, the other lanes leave
+        if (lane != 0)
+            return;
+        long long issued[2] = {-1, -1};  // iteration of the last copy into each buffer
+        for (long long it = 0;; ++it) {
+            const int b = (int)(it & 1);
+            if (it >= 2 && !mbar_wait_bounded(&empty[b], (uint32_t)(((it - 2) >> 1) & 1), limit)) {
+                atomicExch(P.err, kDevTimeout);
+                // let this CTA's own copies in flight land before it leaves
+                for (int q = 0; q < 2; ++q)
+                    if (issued[q] >= 0)
+                        mbar_wait_bounded(&full[q], (uint32_t)((issued[q] >> 1) & 1), kWaitLimitCycles);
+                return;
+            }
+            const long long tile = it == 0 ? (long long)blockIdx.x : (long long)gridDim.x + atomicAdd(P.tile_ctr, 1);
+            if (tile >= P.n_tiles) {
+                tile_of[b] = -1;  // no more tiles: the consumers leave
+                mbar_arrive(&full[b]);
+                return;
+            }
+            tile_of[b] = tile;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&full[b], kTileBytes);
+            tma_load_rows(tiles + b * kTileBytes, &tmap, &full[b], (int)(tile * ur - hr));
+            issued[b] = it;
+        }
+    }
+
+    // consumers: warp w owns the window of rows w (32 - 2 hr) .. + 31
+    const int my_row = warp * (32 - 2 * hr) + lane;
+    const bool writes = lane >= hr && lane < 32 - hr;
+    const int out_rows = 32 - 2 * hr;      // this warp's output rows
+    const int row_local = lane - hr;       // this lane's output row in the staging rows
+    unsigned char *stage = stage_all + warp * kWsStageBytes;
+    Exch<Real, NW, WT> x{slot, 0, lane, warp};
+    for (long long it = 0;; ++it) {
+        const int b = (int)(it & 1);
+        if (!tile_wait(full, &never, b, it, P.stall)) {
+            if (lane == 0)
+                atomicExch(P.err, kDevTimeout);
+            return;
+        }
+        const long long tile = tile_of[b];
+        if (tile < 0)
+            return;
+        const unsigned char *cur = tiles + b * kTileBytes;
+        Real v[K];
+        {
+            const unsigned char *rp = cur + my_row * kRowBytes;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const unsigned char *src = rp + ((c ^ (my_row & 7)) << 4);
+                chunk_to_regs<K>(src, v, c);
+                // the loaded row, so that padding goes back unchanged
+                if (writes)
+                    *reinterpret_cast<uint4 *>(stage + row_local * kRowBytes + ((c ^ (row_local & 7)) << 4)) =
+                        *reinterpret_cast<const uint4 *>(src);
+            }
+        }
+        __syncwarp();
+        if (lane == 0)
+            mbar_arrive(&empty[b]);  // this warp is done with the buffer
+
+        const long long grow = tile * ur - hr + my_row;
+        const int pid = (grow >= 0 && grow < P.n_rows) ? __ldg(P.row_pid + grow) : -1;
+        BatchDesc bd{};
+        Span sp{K + 1, K + 1};
+        if (pid >= 0) {
+            bd = P.desc[pid];
+            sp = make_span<K>(grow * K - bd.off, bd.n);
+        }
+        const bool edge_thr = !(sp.jlo <= -1 && sp.jhi >= K + 1);
+        const bool edge_warp = __any_sync(0xffffffffu, edge_thr);
+        const long long g0 = pid >= 0 ? grow * K - bd.off : 0;
+        if (P.scaled) {
+            if (edge_warp)
+                run_batch_scaled<true>(v, P, bd, pid, g0, x, sp);
+            else
+                run_batch_scaled<false>(v, P, bd, pid, g0, x, sp);
+        } else if (edge_warp) {
+            run_batch<true>(v, P, bd, x, sp);
+        } else {
+            run_batch<false>(v, P, bd, x, sp);
+        }
+
+        if (writes) {
+            unsigned char *rp = stage + row_local * kRowBytes;
+            if (!edge_thr) {
+#pragma unroll
+                for (int c = 0; c < CH; ++c)
+                    regs_to_chunk<K>(rp + ((c ^ (row_local & 7)) << 4), v, c);
+            } else {
+                // only the points of the thread's problem
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    Real *q = reinterpret_cast<Real *>(rp + ((c ^ (row_local & 7)) << 4));
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int j = c * 4 + i;
+                        if (pid >= 0 && j >= sp.jlo && j < sp.jhi)
+                            q[i] = v[j];
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        {
+            const long long grow0 = tile * ur + (long long)warp * out_rows;
+            unsigned char *out = static_cast<unsigned char *>(P.out);
+            for (int ch = lane; ch < out_rows * CH; ch += 32) {
+                const int lr = ch / CH, c = ch % CH;
+                const long long gr = grow0 + lr;
+                if (gr < P.n_rows && warp * out_rows + lr < ur)
+                    *reinterpret_cast<uint4 *>(out + gr * kRowBytes + c * 16) =
+                        *reinterpret_cast<const uint4 *>(stage + lr * kRowBytes + ((c ^ (lr & 7)) << 4));
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -605,8 +776,13 @@ cudaError_t tbb_occupancy(int prec, int *blocks)
 {
     if (prec == 0)
         return batch_attr_and_occupancy<double, false>(blocks);
-    if (prec == 1)
-        return batch_attr_and_occupancy<float, false>(blocks);
+    if (prec == 1) {
+        cudaError_t e = cudaFuncSetAttribute(tbb_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             ws_smem_bytes());
+        if (e != cudaSuccess)
+            return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tbb_ws_kernel, kWsThreads, ws_smem_bytes());
+    }
     return batch_attr_and_occupancy<float, true>(blocks);
 }
 
@@ -614,8 +790,11 @@ cudaError_t launch_tbb(int prec, const void *tmap, const TbbParams &p, int grid,
 {
     if (prec == 0)
         return launch_batch_one<double, false>(tmap, p, grid, s);
-    if (prec == 1)
-        return launch_batch_one<float, false>(tmap, p, grid, s);
+    if (prec == 1) {
+        const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
+        tbb_ws_kernel<<<grid, kWsThreads, ws_smem_bytes(), s>>>(*m, p);
+        return cudaGetLastError();
+    }
     return launch_batch_one<float, true>(tmap, p, grid, s);
 }
 
