@@ -73,6 +73,37 @@ def test_batch_matches_oracle(prec, depth):
     assert np.all(got[mask] == np.float32(7.25))
 
 
+@pytest.mark.parametrize("prec", [B.GE_F64, B.GE_F32])
+@pytest.mark.parametrize("shape", ["one_tile", "more_tiles_than_ctas"])
+def test_batch_tile_queue_extremes(prec, shape):
+    """The launch's tile queue at its ends: a batch that is one tile (grid of
+    one CTA), and one with more tiles than the persistent grid has CTAs
+    (every CTA takes several from the queue).  97 steps at depth 96: a launch
+    with the entry and 95 mid steps, then one with the last mid step and the
+    exit."""
+    ns = [5] if shape == "one_tile" else [8190] * 300  # 2.46e6 points: > 304 tiles of 6656 FP32 points
+    n, r, bl, br, offs, total, u = make_batch(ns, seed=31)
+    x = torch.from_numpy(u).to(DEV, B.dtype_of(prec))
+    plan = B.ge_batch_create(n, r, bl, br, offs, total, prec)
+    B.ge_batch_set_depth(plan, 96)
+    B.ge_batch_run(plan, x, 97)
+    B.ge_batch_sync(plan)
+    B.ge_batch_destroy(plan)
+    got = x.double().cpu().numpy()
+    picks = sorted({0, len(ns) - 1, len(ns) // 2, len(ns) // 3, 2 * len(ns) // 3})
+    for i in picks:
+        want = oracle.run(u[offs[i]:offs[i] + n[i]], r[i], bl[i], br[i], 97)
+        e = rel(got[offs[i]:offs[i] + n[i]], want)
+        assert e <= tol(prec, r[i]), (i, e)
+    # every problem moved (none was skipped by the queue), and padding is untouched
+    for i in range(len(ns)):
+        assert not np.array_equal(got[offs[i]:offs[i] + n[i]], u[offs[i]:offs[i] + n[i]].astype(got.dtype)), i
+    mask = np.ones(total, bool)
+    for i in range(len(n)):
+        mask[offs[i]:offs[i] + n[i]] = False
+    assert np.all(got[mask] == np.float32(7.25))
+
+
 def test_one_shot_equals_plan_and_zero_steps():
     n, r, bl, br, offs, total, u = make_batch([300, 5000, 777], seed=3)
     a = torch.from_numpy(u).to(DEV)
