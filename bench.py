@@ -702,10 +702,11 @@ def main():
 
         def flush():
             flush_buf.fill_(1)
-        for vp, vk, vd in (("f64", "temporal_df", 96), ("f64", "onestep", 1), ("f64", "canonical", 1),
+        for vp, vk, vd in (("f64", "temporal_df", 96), ("f64", "temporal_df", 1), ("f64", "onestep", 1),
+                           ("f64", "canonical", 1),
                            ("f32", "temporal", 128), ("f32c", "temporal", 64), ("f32", "onestep", 1),
                            ("f64", "subdomain16", 8), ("f64", "subdomain16_onestep", 1)):
-            if (vp, vk) == (args.precision, args.kernel):
+            if (vp, vk) == (args.precision, args.kernel) and (vd == depth or vk not in ("temporal", "temporal_df")):
                 continue
             p2 = {"f64": B.GE_F64, "f32": B.GE_F32, "f32c": B.GE_F32_COMP}[vp]
             width = 16 if vk.startswith("subdomain16") else 1

@@ -270,29 +270,14 @@ __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &
     }
 }
 
-// Layout of the batched kernel: GE_TBB_WT_F32 = 1 gives plain FP32 warp
-// windows (no barrier in the step loop; 9.2e12 against 8.6e12 updates/s for
-// CTA rows at 3 CTAs/SM on the 4096-problem batch); FP64 and compensated
-// FP32 use CTA rows.
-#ifndef GE_TBB_WT_F32
-#define GE_TBB_WT_F32 1
-#endif
-
-#ifndef GE_TBB_MINB_F32
-#define GE_TBB_MINB_F32 2
-#endif
-
+// Batched kernel for FP64 and compensated FP32: CTA rows (thread t holds
+// tile row t; warp edges exchange through shared memory), 2 CTAs per SM.
+// Plain FP32 runs the warp-specialised warp-window kernel below.
 template <typename Real, bool COMP>
-struct BatchLayout {
-    static constexpr bool WT = sizeof(Real) == 4 && !COMP && GE_TBB_WT_F32 != 0;
-    static constexpr int MINB = (sizeof(Real) == 4 && !COMP) ? GE_TBB_MINB_F32 : 2;
-};
-
-template <typename Real, bool COMP>
-__global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
+__global__ void __launch_bounds__(kTileRows, 2)
     tbb_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TbbParams P)
 {
-    constexpr bool WT = BatchLayout<Real, COMP>::WT;
+    constexpr bool WT = false;
     constexpr int NT = kTileRows;
     constexpr int K = kRowBytes / (int)sizeof(Real);
     constexpr int NW = NT / 32;
@@ -307,10 +292,7 @@ __global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int hr = P.H / K, ur = P.U / K;
-    // tile row of this thread: CTA rows -> row t; warp windows -> warp w
-    // starts where warp w-1's output ends (windows overlap by 2 halos)
-    const int my_row = WT ? warp * (32 - 2 * hr) + lane : t;
-    const bool writes = WT ? (lane >= hr && lane < 32 - hr) : true;
+    const int my_row = t;  // CTA rows: thread t holds tile row t
     Exch<Real, NW, WT> x{slot, 0, lane, warp};
 
     if (t == 0) {
@@ -359,8 +341,6 @@ __global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
             for (int c = 0; c < CH; ++c)
                 chunk_to_regs<K>(rp + ((c ^ (my_row & 7)) << 4), v, c);
         }
-        if constexpr (WT)
-            __syncthreads();  // windows overlap: every load before any write-back
         // this thread's problem: rows outside the buffer or in padding have none
         const long long grow = tile * ur - hr + my_row;
         const int pid = (grow >= 0 && grow < P.n_rows) ? __ldg(P.row_pid + grow) : -1;
@@ -391,7 +371,7 @@ __global__ void __launch_bounds__(kTileRows, BatchLayout<Real, COMP>::MINB)
                 run_batch_comp<false>(v, P, bd, x, sp);
         }
 
-        if (writes) {
+        {
             unsigned char *rp = cur + my_row * kRowBytes;
             if (!edge_thr) {
 #pragma unroll
@@ -752,7 +732,7 @@ bool tbb_geometry(int prec, int reach, int *H, int *U)
 {
     const int K = kRowBytes / (prec == 0 ? 8 : 4);
     const int ht = (reach + K - 1) / K;
-    const bool wt = prec == 1 ? BatchLayout<float, false>::WT : false;
+    const bool wt = prec == 1;  // plain FP32: tbb_ws_kernel's warp windows
     *H = ht * K;
     if (wt) {
         if (2 * ht >= 32)
