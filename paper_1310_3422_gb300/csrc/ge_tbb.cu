@@ -56,52 +56,6 @@ __device__ __forceinline__ void run_batch(Real (&v)[K], const TbbParams &P, cons
     }
 }
 
-template <bool EDGE, int K, int NW, bool WT>
-__device__ __forceinline__ void run_batch_comp(float (&v)[K], const TbbParams &P, const BatchDesc &bd,
-                                               Exch<float, NW, WT> &x, Span sp)
-{
-    float L = 0.0f, R = 0.0f;
-    if (P.do_entry) {
-        const StageC<float> c{(float)bd.r, (float)bd.omr, 0.0f, (float)bd.f_l, (float)bd.f_r};
-        if (((1 - P.p_first) & 1) == 1) {
-            exchange(v, L, R, x);
-            stage<1, kEntry, EDGE>(v, L, R, sp, c);
-        } else {
-            stage<0, kEntry, EDGE>(v, L, R, sp, c);
-        }
-    }
-    float lo[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j)
-        lo[j] = 0.0f;
-    const float d = (float)bd.d, km1 = (float)(bd.kappa - 1.0);
-    const float fl = (float)bd.f_l, fr = (float)bd.f_r;
-    TbParams dummy{};
-    dummy.n = 0;
-    int m = 0;
-    if (P.n_mid > 0 && (P.p_first & 1)) {
-        mid_comp<1, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp);
-        m = 1;
-    }
-    for (; m + 1 < P.n_mid; m += 2) {
-        mid_comp<0, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp);
-        mid_comp<1, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp);
-    }
-    if (m < P.n_mid)
-        mid_comp<0, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp);
-#pragma unroll
-    for (int j = 0; j < K; ++j)
-        v[j] += lo[j];
-    if (P.do_exit) {
-        const StageC<float> c{(float)bd.x1, (float)bd.x2, (float)bd.xs, 0.0f, 0.0f};
-        if (((P.p_first + P.n_mid) & 1) == 1) {
-            exchange(v, L, R, x);
-            stage<1, kExit, EDGE>(v, L, R, sp, c);
-        } else {
-            stage<0, kExit, EDGE>(v, L, R, sp, c);
-        }
-    }
-}
 
 // Boundary fix-ups of one thread in the batched scaled form, set once per
 // tile.  A problem starts on a row boundary and its walls are shifted out,
@@ -180,6 +134,135 @@ __device__ __forceinline__ void batch_mid(Real (&v)[K], Real L, Real R, Span sp,
         batch_mid_fixed<Q>(v, L, R, f, cm.a, cm.s);
     else
         stage<Q, kMid, false>(v, L, R, sp, cm);
+}
+
+// Compensated block step on a warp that holds problem boundaries (the
+// normalised form keeps the walls, so wall terms stay): the interior deltas
+// d (x_p - x) on every register, then the thread's (at most two) boundary
+// points fixed: a singleton takes (kappa - 1)(x + lo), then the wall terms
+// fl at the problem's first point and fr at its last, in the order of the
+// checked step; then the Kahan sums.  A problem's points get exactly the
+// checked step's deltas; padding registers take garbage and are never
+// written back.
+#define GE_TBB_COMP_TAIL(J)                                                 \
+    case J:                                                                 \
+        if constexpr ((J) < K) {                                            \
+            if (single)                                                     \
+                t[J] = km1 * (v[J] + lo[J]);                                \
+            if ((J) == 0 && f.head)                                         \
+                t[J] += fl;                                                 \
+            t[J] += fr;                                                     \
+        }                                                                   \
+        break;
+template <int Q, int K, int NW, bool WT>
+__device__ __forceinline__ void comp_batch_fixed(float (&v)[K], float (&lo)[K], float d, float km1, float fl,
+                                                 float fr, Exch<float, NW, WT> &x, const BatchFix &f)
+{
+    float L = 0.0f, R = 0.0f;
+    if (Q == 1)
+        exchange(v, L, R, x);
+    float t[K];
+    if (Q == 0) {
+#pragma unroll
+        for (int j = 0; j < K; j += 2) {
+            const float a = d * (v[j + 1] - v[j]);
+            t[j] = a;
+            t[j + 1] = -a;
+        }
+    } else {
+        t[0] = d * (L - v[0]);
+        t[K - 1] = d * (R - v[K - 1]);
+#pragma unroll
+        for (int j = 1; j + 1 < K; j += 2) {
+            const float a = d * (v[j + 1] - v[j]);
+            t[j] = a;
+            t[j + 1] = -a;
+        }
+    }
+    // register 0 is the first point: a singleton under grouping 1 (its
+    // partner -1 is outside); a one-point problem is the tail too
+    if (Q == 1 && f.head)
+        t[0] = km1 * (v[0] + lo[0]);
+    if (f.tail >= 0) {
+        const bool single = ((f.tail + Q) & 1) == 0;  // partner tail + 1 is outside
+        switch (f.tail) {
+            GE_TBB_COMP_TAIL(0) GE_TBB_COMP_TAIL(1) GE_TBB_COMP_TAIL(2) GE_TBB_COMP_TAIL(3)
+            GE_TBB_COMP_TAIL(4) GE_TBB_COMP_TAIL(5) GE_TBB_COMP_TAIL(6) GE_TBB_COMP_TAIL(7)
+            GE_TBB_COMP_TAIL(8) GE_TBB_COMP_TAIL(9) GE_TBB_COMP_TAIL(10) GE_TBB_COMP_TAIL(11)
+            GE_TBB_COMP_TAIL(12) GE_TBB_COMP_TAIL(13) GE_TBB_COMP_TAIL(14) GE_TBB_COMP_TAIL(15)
+            GE_TBB_COMP_TAIL(16) GE_TBB_COMP_TAIL(17) GE_TBB_COMP_TAIL(18) GE_TBB_COMP_TAIL(19)
+            GE_TBB_COMP_TAIL(20) GE_TBB_COMP_TAIL(21) GE_TBB_COMP_TAIL(22) GE_TBB_COMP_TAIL(23)
+            GE_TBB_COMP_TAIL(24) GE_TBB_COMP_TAIL(25) GE_TBB_COMP_TAIL(26) GE_TBB_COMP_TAIL(27)
+            GE_TBB_COMP_TAIL(28) GE_TBB_COMP_TAIL(29) GE_TBB_COMP_TAIL(30) GE_TBB_COMP_TAIL(31)
+        default:
+            break;
+        }
+    }
+    if (f.head && f.tail != 0)
+        t[0] += fl;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        kahan_add(v[j], lo[j], t[j]);
+}
+#undef GE_TBB_COMP_TAIL
+
+template <int Q, bool EDGE, int K, int NW, bool WT>
+__device__ __forceinline__ void comp_batch_step(float (&v)[K], float (&lo)[K], const TbParams &dummy, float d,
+                                                float km1, float fl, float fr, Exch<float, NW, WT> &x, Span sp,
+                                                const BatchFix &f)
+{
+    if constexpr (EDGE)
+        comp_batch_fixed<Q>(v, lo, d, km1, fl, fr, x, f);
+    else
+        mid_comp<Q, false>(v, lo, dummy, d, km1, fl, fr, x, sp);
+}
+
+template <bool EDGE, int K, int NW, bool WT>
+__device__ __forceinline__ void run_batch_comp(float (&v)[K], const TbbParams &P, const BatchDesc &bd, int pid,
+                                               Exch<float, NW, WT> &x, Span sp)
+{
+    float L = 0.0f, R = 0.0f;
+    if (P.do_entry) {
+        const StageC<float> c{(float)bd.r, (float)bd.omr, 0.0f, (float)bd.f_l, (float)bd.f_r};
+        if (((1 - P.p_first) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kEntry, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kEntry, EDGE>(v, L, R, sp, c);
+        }
+    }
+    float lo[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        lo[j] = 0.0f;
+    const float d = (float)bd.d, km1 = (float)(bd.kappa - 1.0);
+    const float fl = (float)bd.f_l, fr = (float)bd.f_r;
+    TbParams dummy{};
+    dummy.n = 0;
+    const BatchFix fx = batch_fix<K>(pid, sp);
+    int m = 0;
+    if (P.n_mid > 0 && (P.p_first & 1)) {
+        comp_batch_step<1, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp, fx);
+        m = 1;
+    }
+    for (; m + 1 < P.n_mid; m += 2) {
+        comp_batch_step<0, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp, fx);
+        comp_batch_step<1, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp, fx);
+    }
+    if (m < P.n_mid)
+        comp_batch_step<0, EDGE>(v, lo, dummy, d, km1, fl, fr, x, sp, fx);
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        v[j] += lo[j];
+    if (P.do_exit) {
+        const StageC<float> c{(float)bd.x1, (float)bd.x2, (float)bd.xs, 0.0f, 0.0f};
+        if (((P.p_first + P.n_mid) & 1) == 1) {
+            exchange(v, L, R, x);
+            stage<1, kExit, EDGE>(v, L, R, sp, c);
+        } else {
+            stage<0, kExit, EDGE>(v, L, R, sp, c);
+        }
+    }
 }
 
 // Scaled batched form (FP64 and plain FP32).  The thread's problem is
@@ -366,9 +449,9 @@ __global__ void __launch_bounds__(kTileRows, 2)
             }
         } else {
             if (edge_warp)
-                run_batch_comp<true>(v, P, bd, x, sp);
+                run_batch_comp<true>(v, P, bd, pid, x, sp);
             else
-                run_batch_comp<false>(v, P, bd, x, sp);
+                run_batch_comp<false>(v, P, bd, pid, x, sp);
         }
 
         {
