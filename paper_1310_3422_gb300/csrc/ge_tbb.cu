@@ -14,7 +14,9 @@ namespace {
 // run_batch_scaled) and the normalised one x <- x + d (x_partner - x) with
 // per-problem walls (run_batch, run_batch_comp; the compensated path, and
 // any launch whose end factor has no table slot).  Every launch starts and
-// ends with the normalised state in the buffer.
+// ends with the normalised state in the buffer.  Two kernels: tbb_kernel
+// (CTA rows; FP64 and compensated FP32) and tbb_ws_kernel (plain FP32:
+// warp windows fed by a TMA producer warp).
 
 // Entry, block steps and exit of one tile, normalised form.
 template <bool EDGE, typename Real, int K, int NW, bool WT>
