@@ -287,18 +287,34 @@ ge_status ge_solve_batch(int32_t n_problems, const int64_t *n, const double *r, 
  *               step counter 0 (device, caller-owned; may alias u0_dev).
  *   depth       steps per launch, 0 = built-in default, up to 1023.
  * It allocates nothing: its working memory (two padded state buffers and the
- * device error word) is one static device array of 16 MiB + 256 bytes that
- * every GPU loading the library holds until exit, so n is limited to
- * 1,048,576 points (GE_EINVAL beyond).  The first call on a device looks the
- * array's address up (with that device current); make it before any stream
- * capture.  Every call on a device shares the array: calls whose GPU work
- * overlaps (other streams, other host threads) race, so serialise them.
- * Synchronous: returns once u_out_dev holds the result.
+ * device error word) is one static device array of 16 MiB + 256 bytes, held
+ * on a device from its creation until exit, so n is limited to 1,048,576
+ * points (GE_EINVAL beyond).  The first call on a device does the set-up,
+ * with that device current: it looks the array's address up, and under
+ * CUDA's default lazy module loading the driver then loads the library's
+ * modules and creates the array -- driver allocations.  A caller that must
+ * not allocate later therefore makes one warm-up call at start-up on each
+ * device, for each precision it uses, with steps >= 1 (or sets
+ * CUDA_MODULE_LOADING=EAGER); make it before any stream capture.  Every call
+ * on a device shares the array: calls whose GPU work overlaps (other
+ * streams, other host threads) race, so serialise them.
+ * Synchronous: returns once u_out_dev holds the result (it synchronises the
+ * stream).
  * Errors: GE_EINVAL (n out of range, bad r, beta, prec, depth, steps, NULL
  * buffer), GE_ECUDA, GE_ETIMEOUT (a bounded device wait gave up). */
 ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double beta_r, ge_precision prec,
                            int32_t depth, int64_t steps, const void *u0_dev, void *u_out_dev,
                            void *stream);
+
+/* Diagnostic: register-only fused multiply-add throughput probe, the
+ * measured ALU ceiling the tiled kernels are read against (the paper has no
+ * counterpart).  Launches `blocks` CTAs of 256 threads on `stream`; every
+ * thread runs 16 independent chains x <- x * a + b for `iters` iterations in
+ * registers (prec GE_F64: DFMA, GE_F32: FFMA), then stores one value to
+ * sink_dev (device, caller-owned, blocks * 256 elements of the precision's
+ * type).  Multiply-adds done: blocks * 256 * 16 * iters.  Asynchronous;
+ * the caller times it on the stream.  Errors: GE_EINVAL, GE_ECUDA. */
+ge_status ge_probe_fma(int32_t prec, int32_t blocks, int64_t iters, void *sink_dev, void *stream);
 
 /* Name of a status code (static string). */
 const char *ge_status_str(ge_status status);

@@ -28,7 +28,7 @@ EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", 
            "ge_batch_get_depth", "ge_batch_set_kernel", "ge_batch_tune", "ge_batch_run", "ge_batch_sync",
            "ge_batch_destroy",
            "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error", "ge_debug_stall",
-           "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune",
+           "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune", "ge_probe_fma",
            "ge_sno_create", "ge_sno_num_params", "ge_sno_get_params", "ge_sno_set_params",
            "ge_sno_set_precision", "ge_sno_forward", "ge_sno_loss_grad", "ge_sno_adam_step",
            "ge_sno_train_step", "ge_sno_rows_nonfinite", "ge_sno_rows_gather", "ge_sno_rows_scatter",
@@ -105,6 +105,8 @@ def load(path: str | None = None):
         lib.ge_solve_batch.restype = ctypes.c_int
         lib.ge_solve_noalloc.argtypes = [_I64, _D, _D, _D, ctypes.c_int, _I32, _I64, _VP, _VP, _VP]
         lib.ge_solve_noalloc.restype = ctypes.c_int
+        lib.ge_probe_fma.argtypes = [_I32, _I32, _I64, _VP, _VP]
+        lib.ge_probe_fma.restype = ctypes.c_int
         lib.ge_sno_create.argtypes = [ctypes.POINTER(_VP), _I32, _I32, _I32, _I32, _I32, _I32, ctypes.c_uint64, _VP]
         lib.ge_sno_create.restype = ctypes.c_int
         lib.ge_sno_num_params.argtypes = [_VP, ctypes.POINTER(_I64)]
@@ -396,6 +398,20 @@ def ge_solve_noalloc(n: int, r: float, beta_l: float, beta_r: float, prec: int, 
     _check(load().ge_solve_noalloc(int(n), float(r), float(beta_l), float(beta_r), int(prec), int(depth),
                                    int(steps), _dptr(u0), _dptr(u_out), _stream_handle(stream)),
            "ge_solve_noalloc")
+
+
+PROBE_THREADS, PROBE_CHAINS = 256, 16
+
+
+def ge_probe_fma(prec: int, blocks: int, iters: int, sink, stream=None) -> int:
+    """Register-only multiply-add throughput probe (GE_F64: DFMA, GE_F32:
+    FFMA); sink: CUDA tensor of blocks * 256 elements of the precision's
+    dtype.  Returns the multiply-adds the launch does."""
+    if sink.numel() < blocks * PROBE_THREADS or sink.dtype != dtype_of(prec):
+        raise ValueError("sink must hold blocks * 256 elements of the precision's dtype")
+    _check(load().ge_probe_fma(int(prec), int(blocks), int(iters), _dptr(sink), _stream_handle(stream)),
+           "ge_probe_fma")
+    return int(blocks) * PROBE_THREADS * PROBE_CHAINS * int(iters)
 
 
 class Sno:

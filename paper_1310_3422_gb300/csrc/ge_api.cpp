@@ -38,9 +38,9 @@ ge_status cuda_fail(cudaError_t e, const char *what)
     return fail(GE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-constexpr int kDefaultDepthF64 = 48;
-constexpr int kDefaultDepthF32 = 128;
-constexpr int kDefaultDepthDf = 96;
+using ge::kDefaultDepthDf;
+using ge::kDefaultDepthF32;
+using ge::kDefaultDepthF64;
 constexpr int kDefaultDepthSweep = 8;  // width-k steps per launch (k = 16, N = 2^24: 1.41e11 updates/s)
 // Largest r the double-float kernel takes: the right-hand side reaches about
 // (1 + 3r) times the data and must stay far inside the FP32 exponent range.
@@ -112,35 +112,8 @@ void fill_coefficients(ge_ctx *c)
     c->canon.beta_l = c->beta_l;
     c->canon.beta_r = c->beta_r;
 
-    ge::TbParams &p = c->tb;
-    p.g = 2.0 * r;
-    // The scaled block map x <- x + g x_partner multiplies the symmetric part
-    // of every pair by exactly 1 + g, with g the coefficient the kernel holds
-    // (rounded to FP32 on the FP32 path).  The host's scale mirror uses that
-    // factor, carried as a double-double (onepg + onepg_lo == 1 + g exactly),
-    // so no systematic scale error builds up over many steps.
-    ge::scaled_growth(r, c->prec == GE_F32, &p.onepg, &c->onepg_lo);
-    p.stall = 0;
-    p.r = r;
-    p.omr = 1.0 - r;
-    p.d = 2.0 * r / det;
-    p.f_l = r * c->beta_l;
-    p.f_r = r * c->beta_r;
-    p.x1 = (1.0 + r) / det;
-    p.x2 = r / det;
-    p.xs = 1.0 / (1.0 + r);
-    if (c->prec == GE_F32_COMP) {
-        p.kappa = (1.0 - r) / (1.0 + r);
-        p.rescale_every = 0;
-    } else {
-        p.kappa = det * (1.0 - r) / (1.0 + r);
-        // block steps between rescalings: the scale grows by (1+2r) per step
-        // and stays below 2^headroom (data magnitudes up to 2^(max_exp -
-        // headroom - 1) are safe)
-        const double headroom = (c->prec == GE_F64) ? 256.0 : GE_F32_HEADROOM;
-        int every = (int)std::floor(headroom / std::log2(1.0 + 2.0 * r));
-        p.rescale_every = every < 1 ? 1 : every;
-    }
+    ge::tb_fill_base(r, c->beta_l, c->beta_r, c->prec == GE_F64 ? 0 : (c->prec == GE_F32 ? 1 : 2), &c->tb,
+                     &c->onepg_lo);
 }
 
 ge_status make_tensor_maps(ge_ctx *c)
@@ -236,19 +209,12 @@ int effective_depth(const ge_ctx *c)
 }
 
 // Advance `steps` steps with the tiled kernel, `depth` steps per launch
-// (df: the double-float kernel).  The host mirrors the kernel's scale
-// recurrence (see TbParams): sigma starts at 1 after the entry conversion, is
-// multiplied by (1+2r) per block step and by 2^-e at each rescaling, where e
-// brings it back into [1, 2).
+// (df: the double-float kernel, after its per-call prescale); the launches
+// and the scale mirror are planned by ge::tb_run.
 ge_status run_tiled(ge_ctx *c, int64_t steps, int depth, bool df = false)
 {
     double growth_lo = c->onepg_lo;
     const ge::TbParams base = df ? df_params(c, &growth_lo) : c->tb;
-    const int every = base.rescale_every;
-    if (every > 0 && depth > (ge::kMaxRescale - 1) * every)
-        depth = (ge::kMaxRescale - 1) * every;
-    if (depth > ge::kMaxTableSteps)
-        depth = ge::kMaxTableSteps;
     const int prec = c->prec == GE_F64 ? 0 : (c->prec == GE_F32 ? 1 : 2);
     if (df) {
         // the prescale 2^-e0 of this call: data and walls below 1 in magnitude
@@ -257,68 +223,21 @@ ge_status run_tiled(ge_ctx *c, int64_t steps, int depth, bool df = false)
         if (e != cudaSuccess)
             return cuda_fail(e, "double-float prescale launch");
     }
-    double sigma = 1.0, sigma_lo = 0.0;  // double-double scale
-    int until = every;
-    int64_t n0 = 0;
-    while (n0 < steps) {
-        const int64_t L = (steps - n0 < depth) ? steps - n0 : depth;
-        ge::TbParams p = base;
-        const bool last = (n0 + L == steps);
-        p.do_entry = (n0 == 0) ? 1 : 0;
-        p.n_mid = (int)(last ? L - 1 : L);
-        p.do_exit = last ? 1 : 0;
-        p.p_first = (int)((c->step + n0) & 1);
-        p.sigma_in = sigma;
-        p.rescale_phase = until;
-        if (every > 0) {
-            int ev = 0;
-            for (int m = 0; m < p.n_mid; ++m) {
-                ge::dd_mul(sigma, sigma_lo, p.onepg, growth_lo);
-                if (--until == 0) {
-                    until = every;
-                    int e2 = 0;
-                    std::frexp(sigma, &e2);
-                    const int e = e2 - 1;  // sigma * 2^-e in [1, 2)
-                    p.rs_exp[ev++] = (short)e;
-                    sigma = std::ldexp(sigma, -e);
-                    sigma_lo = std::ldexp(sigma_lo, -e);
-                }
-            }
-        }
-        if (p.do_exit) {
-            p.x1 = ge::dd_div(c->tb.x1, sigma, sigma_lo);
-            p.x2 = ge::dd_div(c->tb.x2, sigma, sigma_lo);
-            p.xs = ge::dd_div(c->tb.xs, sigma, sigma_lo);
-            df_split(p.x1, p.dfc[4]);
-            df_split(p.x2, p.dfc[5]);
-            df_split(p.xs, p.dfc[6]);
-        }
-        p.df_in = p.do_entry;
-        p.df_out = p.do_exit;
-        const int reach = p.do_entry + p.n_mid + p.do_exit;
-        if (!(df ? ge::tb_df_geometry(reach, &p.H, &p.U) : ge::tb_geometry(prec, reach, &p.H, &p.U)))
-            return fail(GE_EINVAL, "depth %d does not fit a tile", depth);
-        p.n = c->n;
-        p.n_rows = c->n_rows;
-        p.n_tiles = (c->n + p.U - 1) / p.U;
-        p.out = c->buf[c->cur ^ 1];
-        p.err = c->err_dev;
-        long long grid = (long long)c->num_sms * (df ? c->tb_df_blocks_per_sm : c->tb_blocks_per_sm);
-        if (grid > p.n_tiles)
-            grid = p.n_tiles;
-        if (grid < 1)
-            grid = 1;
-        p.tile_ctr = c->err_dev + 48;
-        // the launch's tile queue starts empty
-        cudaError_t e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int), c->stream);
-        if (e == cudaSuccess)
-            e = df ? ge::launch_tb_df(&c->tmap[c->cur], p, (int)grid, c->stream)
-                   : ge::launch_tb(prec, &c->tmap[c->cur], p, (int)grid, c->stream);
-        if (e != cudaSuccess)
-            return cuda_fail(e, "tiled GE kernel launch");
-        c->cur ^= 1;
-        n0 += L;
-    }
+    ge::TbTarget t{};
+    t.tmap[0] = &c->tmap[0];
+    t.tmap[1] = &c->tmap[1];
+    t.buf[0] = c->buf[0];
+    t.buf[1] = c->buf[1];
+    t.n = c->n;
+    t.n_rows = c->n_rows;
+    t.err = c->err_dev;
+    t.tile_ctr = c->err_dev + 48;
+    t.grid_cap = (long long)c->num_sms * (df ? c->tb_df_blocks_per_sm : c->tb_blocks_per_sm);
+    const cudaError_t e = ge::tb_run(t, base, growth_lo, df, prec, &c->cur, c->step, steps, depth, c->stream);
+    if (e == cudaErrorInvalidValue)
+        return fail(GE_EINVAL, "depth %d does not fit a tile", depth);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "tiled GE kernel launch");
     return GE_OK;
 }
 

@@ -31,6 +31,13 @@ struct NvtxRange {
 #ifndef GE_F32_HEADROOM
 #define GE_F32_HEADROOM 64.0
 #endif
+constexpr double kF64Headroom = 256.0;
+
+// Built-in steps per launch of the tiled kernels (FP64, FP32 and compensated
+// FP32, double-float), measured best on N = 2^24, r = 2.
+constexpr int kDefaultDepthF64 = 48;
+constexpr int kDefaultDepthF32 = 128;
+constexpr int kDefaultDepthDf = 96;
 
 // Device error codes written to the context's error word.
 enum DevErr : int { kDevOk = 0, kDevTimeout = 1 };
@@ -251,6 +258,37 @@ int tb_smem_bytes();
 // Tile geometry of a launch whose stages reach `reach` points: halo H and
 // output elements U per tile.  False if the reach does not fit a tile.
 bool tb_geometry(int prec, int reach, int *H, int *U);
+
+// Host-side planning of tiled solves (ge_tb_plan.cpp), shared by the context
+// API and ge_solve_noalloc.
+//
+// Launch-independent fields of the tiled right-hand-side kernel for mesh
+// ratio r and wall values beta_l, beta_r (prec: 0 FP64, 1 FP32, 2 FP32
+// compensated); *growth_lo receives the low part of the scaled map's growth
+// factor (onepg + growth_lo == 1 + g exactly).
+void tb_fill_base(double r, double beta_l, double beta_r, int prec, TbParams *p, double *growth_lo);
+// A depth clamped to what one launch's rescaling and step tables hold.
+int tb_clamp_depth(const TbParams &base, int depth);
+// Where a tiled solve runs: two state buffers of n_rows 128-byte rows with a
+// tensor map each, the device error word and the tile-queue word.
+struct TbTarget {
+    const void *tmap[2];  // 64-byte aligned CUtensorMap of each buffer (opaque here)
+    void *buf[2];
+    long long n, n_rows;
+    int *err;
+    int *tile_ctr;
+    long long grid_cap;   // SMs x co-resident CTAs per SM
+};
+// Issue the launches of `steps` steps from global step `step0`, `depth` steps
+// per launch (df: the double-float kernel; its prescale is the caller's).
+// *cur names the buffer holding the state and is updated.  The host mirrors
+// the kernel's scale recurrence (see TbParams): sigma starts at 1 after the
+// entry conversion, is multiplied by (1+2r) per block step and by 2^-e at
+// each rescaling, where e brings it back into [1, 2).  Returns
+// cudaErrorInvalidValue when the depth does not fit a tile, else the first
+// launch error.
+cudaError_t tb_run(const TbTarget &t, const TbParams &base, double growth_lo, bool df, int prec, int *cur,
+                   long long step0, long long steps, int depth, cudaStream_t s);
 
 // Record the calling thread's last-failure text (read by ge_last_error()).
 void set_last_error(const char *msg);

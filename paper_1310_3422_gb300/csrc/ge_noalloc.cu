@@ -11,13 +11,21 @@
 //
 // The working buffers the tiled kernel needs (two ping-pong states padded
 // to whole 128-byte rows, and the device error word) live in one file-scope
-// static device array of fixed size.  Every GPU that loads this library
-// holds it (16 MiB + 256 bytes) until the process exits.
+// static device array of fixed size (16 MiB + 256 bytes).  Once created on a
+// device it stays there until the process exits.
 //
 // Set-up: the first call on a device, with that device current, looks the
 // array's device address up with cudaGetSymbolAddress (host code cannot use
 // the array's name as a device address) and remembers it for that device.
-// Make that first call before any stream capture.
+// With CUDA's default lazy module loading, that first call is also where the
+// driver loads this file's module and the tiled kernel's module on the
+// device and creates the array in device memory: those are driver
+// allocations, with the synchronisation they imply.  So a caller that must
+// not allocate later makes one warm-up call at start-up, on each device and
+// for each precision it will use, with steps >= 1 (or runs the process with
+// CUDA_MODULE_LOADING=EAGER, which loads every module when the context is
+// created).  Make that first call before any stream capture.  After it,
+// calls allocate nothing.
 //
 // Sharing: every call on a device uses the same array, which keeps the last
 // call's contents.  A call clears what must start at zero (the error word
@@ -164,36 +172,13 @@ extern "C" ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double
             if (cr != CUDA_SUCCESS)
                 return nfail(GE_ECUDA, "ge_solve_noalloc: cuTensorMapEncodeTiled failed (%d)", (int)cr);
         }
-        // coefficients of the tiled kernel (right-hand-side form, Sec. 2)
-        const double det = 1.0 + 2.0 * r;
-        ge::TbParams base_p{};
-        base_p.g = 2.0 * r;
-        double onepg_lo = 0.0;
-        ge::scaled_growth(r, prec == GE_F32, &base_p.onepg, &onepg_lo);
-        base_p.r = r;
-        base_p.omr = 1.0 - r;
-        base_p.d = 2.0 * r / det;
-        base_p.f_l = r * beta_l;
-        base_p.f_r = r * beta_r;
-        const double x1 = (1.0 + r) / det, x2 = r / det, xs = 1.0 / (1.0 + r);
-        int every = 0;
-        if (prec == GE_F32_COMP) {
-            base_p.kappa = (1.0 - r) / (1.0 + r);
-        } else {
-            base_p.kappa = det * (1.0 - r) / (1.0 + r);
-            const double headroom = prec == GE_F64 ? 256.0 : 64.0;
-            every = (int)std::floor(headroom / std::log2(1.0 + 2.0 * r));
-            if (every < 1)
-                every = 1;
-        }
-        base_p.rescale_every = every;
-        base_p.stall = 0;
-        int d = depth > 0 ? depth : (prec == GE_F64 ? 48 : 128);
-        if (every > 0 && d > (ge::kMaxRescale - 1) * every)
-            d = (ge::kMaxRescale - 1) * every;
-        if (d > ge::kMaxTableSteps)
-            d = ge::kMaxTableSteps;
+        // coefficients of the tiled kernel (right-hand-side form, Sec. 2) and
+        // its launches, planned by the same code as the context API's
         const int pidx = prec == GE_F64 ? 0 : (prec == GE_F32 ? 1 : 2);
+        ge::TbParams base_p{};
+        double growth_lo = 0.0;
+        ge::tb_fill_base(r, beta_l, beta_r, pidx, &base_p, &growth_lo);
+        const int d = depth > 0 ? depth : (prec == GE_F64 ? ge::kDefaultDepthF64 : ge::kDefaultDepthF32);
         int bps = 0, sms = 0, dev = 0;
         e = ge::tb_occupancy(pidx, &bps);
         if (e == cudaSuccess)
@@ -202,67 +187,32 @@ extern "C" ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess || bps < 1)
             return nfail(GE_ECUDA, "ge_solve_noalloc: occupancy query failed");
-
-        double sigma = 1.0, sigma_lo = 0.0;  // double-double scale
-        int until = every;
-        long long n0 = 0;
-        while (n0 < steps) {
-            const long long L = (steps - n0 < d) ? steps - n0 : d;
-            ge::TbParams p = base_p;
-            const bool last = (n0 + L == steps);
-            p.do_entry = (n0 == 0) ? 1 : 0;
-            p.n_mid = (int)(last ? L - 1 : L);
-            p.do_exit = last ? 1 : 0;
-            p.p_first = (int)(n0 & 1);
-            p.sigma_in = sigma;
-            p.rescale_phase = until;
-            if (every > 0) {
-                int ev = 0;
-                for (int m = 0; m < p.n_mid; ++m) {
-                    ge::dd_mul(sigma, sigma_lo, p.onepg, onepg_lo);
-                    if (--until == 0) {
-                        until = every;
-                        int e2 = 0;
-                        std::frexp(sigma, &e2);
-                        p.rs_exp[ev++] = (short)(e2 - 1);
-                        sigma = std::ldexp(sigma, -(e2 - 1));
-                        sigma_lo = std::ldexp(sigma_lo, -(e2 - 1));
-                    }
-                }
-            }
-            p.x1 = ge::dd_div(x1, sigma, sigma_lo);
-            p.x2 = ge::dd_div(x2, sigma, sigma_lo);
-            p.xs = ge::dd_div(xs, sigma, sigma_lo);
-            const int reach = p.do_entry + p.n_mid + p.do_exit;
-            if (!ge::tb_geometry(pidx, reach, &p.H, &p.U))
-                return nfail(GE_EINVAL, "ge_solve_noalloc: depth %d does not fit a tile", d);
-            p.n = n;
-            p.n_rows = n_rows;
-            p.n_tiles = (n + p.U - 1) / p.U;
-            p.out = buf[cur ^ 1];
-            p.err = err;
-            p.tile_ctr = err + 48;  // the launch's tile queue, zeroed first
-            long long grid = (long long)sms * bps;
-            if (grid > p.n_tiles)
-                grid = p.n_tiles;
-            e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int), s);
-            if (e == cudaSuccess)
-                e = ge::launch_tb(pidx, &tmap[cur], p, (int)grid, s);
-            if (e != cudaSuccess)
-                return nfail(GE_ECUDA, "ge_solve_noalloc: launch: %s", cudaGetErrorString(e));
-            cur ^= 1;
-            n0 += L;
-        }
+        ge::TbTarget t{};
+        t.tmap[0] = &tmap[0];
+        t.tmap[1] = &tmap[1];
+        t.buf[0] = buf[0];
+        t.buf[1] = buf[1];
+        t.n = n;
+        t.n_rows = n_rows;
+        t.err = err;
+        t.tile_ctr = err + 48;  // the launch's tile queue, zeroed before each launch
+        t.grid_cap = (long long)sms * bps;
+        e = ge::tb_run(t, base_p, growth_lo, false, pidx, &cur, 0, steps, d, s);
+        if (e == cudaErrorInvalidValue)
+            return nfail(GE_EINVAL, "ge_solve_noalloc: depth %d does not fit a tile", d);
+        if (e != cudaSuccess)
+            return nfail(GE_ECUDA, "ge_solve_noalloc: launch: %s", cudaGetErrorString(e));
     }
+    // the result and the error word travel on the caller's stream; one
+    // synchronisation of that stream ends the call
+    int word = 0;
     e = cudaMemcpyAsync(u_out_dev, buf[cur], used, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(s);
     if (e != cudaSuccess)
         return nfail(GE_ECUDA, "ge_solve_noalloc: %s", cudaGetErrorString(e));
-    int word = 0;
-    e = cudaMemcpy(&word, err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess)
-        return nfail(GE_ECUDA, "ge_solve_noalloc: reading the error word: %s", cudaGetErrorString(e));
     if (word == ge::kDevTimeout)
         return nfail(GE_ETIMEOUT, "ge_solve_noalloc: a tile load did not complete within the wait limit");
     return GE_OK;

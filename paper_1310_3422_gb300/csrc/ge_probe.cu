@@ -1,0 +1,61 @@
+// ge_probe.cu -- register-only fused multiply-add throughput probe (FP64 and
+// FP32), the measured ALU ceiling that the tiled kernels' roofline is read
+// against.  The paper has no counterpart.
+//
+// Every thread runs kChains independent multiply-add chains x <- x * a + b
+// for `iters` iterations, entirely in registers (no memory traffic in the
+// loop), and stores its chain sum once at the end so that nothing is
+// eliminated.  With a <= 1 and b small the values stay finite and normal.
+// The caller times the launch (CUDA events on the same stream); the
+// multiply-adds done are blocks * kThreads * kChains * iters.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ge.h"
+#include "ge_internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChains = 16;
+
+template <typename Real>
+__global__ void __launch_bounds__(kThreads) fma_probe_kernel(long long iters, Real a, Real b, Real *sink)
+{
+    Real x[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+        x[c] = (Real)(threadIdx.x + c) * (Real)1e-3;
+    for (long long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kChains; ++c)
+            x[c] = fma(x[c], a, b);
+    }
+    Real s = 0;
+#pragma unroll
+    for (int c = 0; c < kChains; ++c)
+        s += x[c];
+    sink[(size_t)blockIdx.x * kThreads + threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" ge_status ge_probe_fma(int32_t prec, int32_t blocks, int64_t iters, void *sink_dev, void *stream)
+{
+    if ((prec != GE_F64 && prec != GE_F32) || blocks < 1 || iters < 1 || !sink_dev) {
+        ge::set_last_error("ge_probe_fma: need prec GE_F64 or GE_F32, blocks >= 1, iters >= 1, a sink");
+        return GE_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (prec == GE_F64)
+        fma_probe_kernel<double><<<blocks, kThreads, 0, s>>>(iters, 0.999999, 1e-7, static_cast<double *>(sink_dev));
+    else
+        fma_probe_kernel<float><<<blocks, kThreads, 0, s>>>(iters, 0.9999f, 1e-5f, static_cast<float *>(sink_dev));
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        ge::set_last_error(cudaGetErrorString(e));
+        return GE_ECUDA;
+    }
+    return GE_OK;
+}

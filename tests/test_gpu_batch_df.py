@@ -8,6 +8,7 @@ import torch
 
 import oracle
 from ext_reference import ext_precision_run
+from tolerances import tol64
 from paper_1310_3422_gb300 import binding as B
 from paper_1310_3422_gb300 import inputs
 
@@ -16,8 +17,6 @@ DEV = torch.device("cuda:0")
 DF = B.GE_KERNEL_TEMPORAL_DF
 
 
-def tol64(r):
-    return 1e-12 * max(1.0, 2.0 * r - 1.0)
 
 
 def rel(got, want):

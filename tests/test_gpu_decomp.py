@@ -13,6 +13,7 @@ import torch.distributed as dist
 import torch.multiprocessing as mp
 
 import oracle
+from tolerances import tol64
 
 pytestmark = pytest.mark.gpu
 
@@ -64,4 +65,4 @@ def test_decomposed_gpu_stepper_matches_oracle(world, n, steps, depth, step0):
         got[a:b] = own
         covered[a:b] = True
     assert covered.all()
-    assert np.max(np.abs(got - want)) <= 1e-12 * max(1.0, 2 * r - 1) * np.max(np.abs(want))
+    assert np.max(np.abs(got - want)) <= tol64(r) * np.max(np.abs(want))

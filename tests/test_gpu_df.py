@@ -2,8 +2,8 @@
 storage, steps evaluated as unevaluated sums of two floats on the FP32 pipes)
 with the CPU oracle, through the C ABI.
 
-Tolerance: the FP64 one, 1e-12 * max(1, 2r - 1) relative max-norm, at the
-moderate r the kernel is meant for.  Its rounding unit is about 2^-48
+Tolerance: the FP64 one (tests/tolerances.py: 1e-12 relative max-norm for
+r <= 4), at the moderate r the kernel is meant for.  Its rounding unit is about 2^-48
 instead of 2^-53.  Over s steps the rounding errors of a non-expansive map
 add up like a random walk, about sqrt(s) * 2^-48 ~ 3.6e-13 at s = 10000.  At
 very large r the conditioning of the scheme amplifies every evaluation's
@@ -17,6 +17,7 @@ import torch
 
 import oracle
 from ext_reference import ext_precision_run
+from tolerances import tol64
 from paper_1310_3422_gb300 import binding as B
 from paper_1310_3422_gb300 import inputs
 
@@ -26,8 +27,6 @@ DEV = torch.device("cuda:0")
 DF = B.GE_KERNEL_TEMPORAL_DF
 
 
-def tol64(r):
-    return 1e-12 * max(1.0, 2.0 * r - 1.0)
 
 
 def rel_max(got, want):

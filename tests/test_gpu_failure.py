@@ -9,6 +9,7 @@ import pytest
 import torch
 
 import oracle
+from tolerances import tol64
 from paper_1310_3422_gb300 import binding as B
 from paper_1310_3422_gb300 import inputs
 
@@ -51,7 +52,7 @@ def test_tiled_timeout_is_reported_and_the_context_recovers(prec, kernel):
     want = oracle.sample(u0 if prec == B.GE_F64 else u0.astype(np.float32).astype(np.float64), r, 0.2, -0.1,
                          steps, idx)
     got = out.double().cpu().numpy()[idx]
-    tol = 1e-12 * (2 * r - 1) if prec == B.GE_F64 else 1e-5
+    tol = tol64(r) if prec == B.GE_F64 else 1e-5
     assert np.max(np.abs(got - want)) <= tol * np.max(np.abs(want))
 
 

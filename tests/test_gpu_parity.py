@@ -2,15 +2,13 @@
 
 Tolerances:
   * GE_KERNEL_CANONICAL, FP64: bit-identical (same operations, same order).
-  * FP64 tiled kernels: 1e-12 * kappa(r) relative max-norm, kappa(r) =
-    max(1, 2r - 1).  They reassociate the step, so rounding differs; two
-    FP64 evaluations of the same steps differ by up to the round-off each one
-    carries, which scales with the step's max-norm 2r - 1 (the sum of the
-    magnitudes of the coefficients of Eqs. (cc)/(dd)).  For r <= 1 this is the
-    plain 1e-12 target.  At very large r on rough data (r = 1e4) any FP64
-    evaluation is off by ~1e-6 (the bound grows like steps * kappa^2 * eps);
-    there test_large_r_error_is_conditioning checks that the kernel is as
-    close to an extended-precision evaluation as the oracle is.
+  * FP64 tiled kernels: 1e-12 relative max-norm for r <= 4 (every r of
+    the benchmark workloads); above r = 4 widened by kappa(r) = 2r - 1
+    (tests/tolerances.py says why).  They reassociate the step, so rounding
+    differs from the oracle's.  At very large r on rough data (r = 1e4) any
+    FP64 evaluation is off by ~1e-6 (the bound grows like steps * kappa^2 *
+    eps); there test_large_r_error_is_conditioning checks that the kernel is
+    as close to an extended-precision evaluation as the oracle is.
   * FP32 / FP32 compensated: 1e-5 relative max-norm against the FP64 oracle
     (the accuracy target for the FP32 path) at the step counts used here.
 """
@@ -20,18 +18,14 @@ import torch
 
 import oracle
 from ext_reference import ext_precision_run
+from tolerances import TOL64, tol64
 from paper_1310_3422_gb300 import binding as B
 from paper_1310_3422_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
 DEV = torch.device("cuda:0")
-TOL64 = 1e-12
 TOL32 = 1e-5
-
-
-def tol64(r):
-    return TOL64 * max(1.0, 2.0 * r - 1.0)
 
 
 def rel_max(got, want):
