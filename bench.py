@@ -74,9 +74,9 @@ def load_peaks():
         return 6800.0, 2070.0, "fallback"
 
 
-# FP64 / FP32 FMA lanes per SM per clock on GB300 (152 SMs): FP64 1.25 TFLOP/s
-# nominal at 2.07 GHz is 2 FMA/clk/SM; FP32 is 128 FMA/clk/SM.
-SMS = 152
+# FP64 / FP32 FMA lanes per SM per clock on GB300: FP64 1.25 TFLOP/s nominal
+# over 152 SMs at 2.07 GHz is 2 FMA/clk/SM; FP32 is 128 FMA/clk/SM.  The SM
+# count is read from the device.
 FMA_PER_CLK = {"f64": 2.0, "f32": 128.0, "f32c": 128.0}
 # Double-float kernel: FP32-pipe instructions (FADD, FMUL, FFMA alike, one
 # issue each) per point and step of its fast path, renormalised every second
@@ -84,6 +84,39 @@ FMA_PER_CLK = {"f64": 2.0, "f32": 128.0, "f32c": 128.0}
 # 21 + 3 otherwise (the exact low-order product sum, renormalised every
 # step).  Its peak is 128 such instructions/clk/SM.
 DF_OPS_PER_UPDATE = {True: 12.5, False: 24.0}
+
+
+# The method's own work per point and step (Eqs. (cc)/(dd) as printed): one
+# multiply and three multiply-adds, and one FP64 value read and one written.
+METHOD_FLOPS_PER_UPDATE = 7
+METHOD_BYTES_PER_UPDATE = 16
+
+
+def fma_probe(B, torch, dev, stream, prec, sms):
+    """Measured multiply-add throughput of the register-only probe
+    (ge_probe_fma), timed with CUDA events on `stream`: the best rate over
+    1, 2 and 4 CTAs of 256 threads per SM and 8, 16 and 32 independent
+    chains per thread (each timed twice after a warm-up launch).  Returns
+    (multiply-adds per second, CTAs per SM, chains) of the best."""
+    best = (0.0, 0, 0)
+    fmas_per_launch = 6e9 if prec == B.GE_F64 else 2e11   # about 10 ms each
+    sink = torch.empty(4 * sms * B.PROBE_THREADS, dtype=B.dtype_of(prec), device=dev)
+    with torch.cuda.stream(stream):
+        for cps in (1, 2, 4):
+            for chains in (8, 16, 32):
+                blocks = cps * sms
+                iters = max(1, int(fmas_per_launch / (blocks * B.PROBE_THREADS * chains)))
+                B.ge_probe_fma(prec, blocks, chains, iters, sink, stream=stream)
+                for _ in range(2):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fmas = B.ge_probe_fma(prec, blocks, chains, iters, sink, stream=stream)
+                    e1.record(stream)
+                    e1.synchronize()
+                    rate = fmas / (e0.elapsed_time(e1) / 1e3)
+                    if rate > best[0]:
+                        best = (rate, cps, chains)
+    return best
 
 
 def two_r_is_fp32(r: float) -> bool:
@@ -506,6 +539,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-probe", action="store_true", help="skip the FMA throughput probe")
     ap.add_argument("--only-surrogate", action="store_true", help="run only the surrogate workload")
     ap.add_argument("--sno-train-steps", type=int, default=3000)
     ap.add_argument("--sno-forward-only", action="store_true",
@@ -549,6 +583,7 @@ def main():
             "onestep": B.GE_KERNEL_ONESTEP, "canonical": B.GE_KERNEL_CANONICAL}[args.kernel]
     depth = args.depth or (96 if args.kernel == "temporal_df" else (48 if args.precision == "f64" else 128))
     hbm_gbs, sm_max_mhz, peak_src = load_peaks()
+    SMS = torch.cuda.get_device_properties(dev).multi_processor_count
 
     u0 = inputs.sine_modes_state(N_POINTS, seed=inputs.SEED_BASE + 1 + rank)
     dt = B.dtype_of(prec)
@@ -590,6 +625,19 @@ def main():
         B.ge_read_state(ctx, out)
         B.ge_sync(ctx)
     got = out.cpu().numpy()
+    clocks = sampler.summary()
+    # measured ALU ceiling of the main line's precision, right after the timed region
+    probe = None
+    if not args.no_probe and args.kernel != "temporal_df":
+        p_prec = B.GE_F64 if prec == B.GE_F64 else B.GE_F32
+        fma_s, cps, chains = fma_probe(B, torch, dev, stream, p_prec, SMS)
+        mhz = clocks.get("sm_mhz") or sm_max_mhz
+        probe = {"fma_per_s": fma_s, "flops_per_s": 2.0 * fma_s,
+                 "fma_per_clk_per_sm": fma_s / (SMS * mhz * 1e6), "sm_mhz": mhz, "sms": SMS,
+                 "best_ctas_per_sm": cps, "best_chains": chains,
+                 "how": "ge_probe_fma: %s chains in registers, CTAs of 256 threads; best over 1, 2, 4 CTAs per SM "
+                        "and 8, 16, 32 chains per thread; CUDA events; per-SM rate at the median SM clock of the "
+                        "timed region" % ("DFMA" if p_prec == B.GE_F64 else "FFMA")}
 
     ms_per_step = elapsed_ms / args.steps
     updates = float(N_POINTS) * GE_STEPS
@@ -638,15 +686,28 @@ def main():
                     "peak_source": "derived: 128 FP32 instructions/clk/SM x %d SMs x %.0f MHz" % (SMS, sm_max_mhz),
                     "kernel": kname}
     elif args.kernel == "temporal":
-        achieved = flops_per_update * N_POINTS * (GE_STEPS / n_launch) / (launch_ms / 1e3)
+        updates_per_launch = N_POINTS * (GE_STEPS / n_launch)
+        achieved = flops_per_update * updates_per_launch / (launch_ms / 1e3)
         kname = "tb_kernel<%s>" % ("double" if prec == B.GE_F64 else "float")
         traffic = measured_traffic(kname) if (prec == B.GE_F64 and depth == 48) else None
         roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
                     "unit": "TFLOP/s", "frac": achieved / alu_peak,
                     "traffic": traffic, "algorithmic_bytes_per_launch": 2 * bytes_per_update * N_POINTS,
-                    "peak_source": "derived: %g FMA/clk/SM x %d SMs x %.0f MHz"
-                    % (FMA_PER_CLK[args.precision], SMS, sm_max_mhz),
-                    "kernel": "tb_kernel<%s>" % ("double" if prec == B.GE_F64 else "float")}
+                    "kernel": kname,
+                    # achieved = executed_flops_per_update x updates_per_launch / launch_ms
+                    "executed_flops_per_update": flops_per_update,
+                    "executed_work": ("one multiply-add per point and step (right-hand-side form)"
+                                      if prec != B.GE_F32_COMP else "normalised block map + Kahan sum"),
+                    "updates_per_launch": updates_per_launch, "launch_ms": launch_ms,
+                    # peak = 2 flops x FMA/clk/SM x SMs x max SM clock
+                    "peak_source": "derived: 2 flops x %g FMA/clk/SM x %d SMs (device attribute) x %.0f MHz "
+                                   "(max SM clock); the probe below measures the same ceiling in this run"
+                                   % (FMA_PER_CLK[args.precision], SMS, sm_max_mhz),
+                    "method_flops_per_update": METHOD_FLOPS_PER_UPDATE if prec == B.GE_F64 else None,
+                    "method_bytes_per_update": 2 * bytes_per_update}
+        if probe is not None:
+            roofline["peak_probe"] = probe["flops_per_s"] / 1e12
+            roofline["frac_of_probe"] = achieved / probe["flops_per_s"]
     else:
         # one step per launch: report the roofline that binds (HBM bytes or
         # the ALU), with the other fraction beside it
@@ -666,6 +727,9 @@ def main():
                         "frac": hbm_frac, "traffic": None, "alu_frac": alu_frac,
                         "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)", "kernel": kname}
     hbm_roof_updates = hbm_gbs * 1e9 / (2.0 * bytes_per_update)
+    # effective HBM fraction: the updates/s over the one-step HBM roofline
+    # (method bytes per update over the measured copy bandwidth)
+    roofline["hbm_effective_frac"] = value / world / hbm_roof_updates
     # HBM fraction from the bytes the dominant kernel actually moves (ncu DRAM counters per launch)
     hbm_actual = None
     if roofline.get("traffic"):
@@ -793,7 +857,8 @@ def main():
         "e2e": e2e,
         "gpu_launches": n_launch * args.steps,
         "kernel_ms_per_launch": launch_ms,
-        "clocks": sampler.summary(),
+        "clocks": clocks,
+        "alu_probe": probe,
         "accuracy": acc,
         "variants": variants,
         "batched": batched,

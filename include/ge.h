@@ -309,12 +309,14 @@ ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double beta_r, ge
 /* Diagnostic: register-only fused multiply-add throughput probe, the
  * measured ALU ceiling the tiled kernels are read against (the paper has no
  * counterpart).  Launches `blocks` CTAs of 256 threads on `stream`; every
- * thread runs 16 independent chains x <- x * a + b for `iters` iterations in
- * registers (prec GE_F64: DFMA, GE_F32: FFMA), then stores one value to
- * sink_dev (device, caller-owned, blocks * 256 elements of the precision's
- * type).  Multiply-adds done: blocks * 256 * 16 * iters.  Asynchronous;
- * the caller times it on the stream.  Errors: GE_EINVAL, GE_ECUDA. */
-ge_status ge_probe_fma(int32_t prec, int32_t blocks, int64_t iters, void *sink_dev, void *stream);
+ * thread runs `chains` (4, 8, 16 or 32) independent chains x <- x * a + b
+ * for `iters` iterations in registers (prec GE_F64: DFMA, GE_F32: FFMA),
+ * then stores one value to sink_dev (device, caller-owned, blocks * 256
+ * elements of the precision's type).  Multiply-adds done:
+ * blocks * 256 * chains * iters.  Asynchronous; the caller times it on the
+ * stream.  Errors: GE_EINVAL, GE_ECUDA. */
+ge_status ge_probe_fma(int32_t prec, int32_t blocks, int32_t chains, int64_t iters, void *sink_dev,
+                       void *stream);
 
 /* Name of a status code (static string). */
 const char *ge_status_str(ge_status status);

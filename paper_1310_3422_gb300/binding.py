@@ -105,7 +105,7 @@ def load(path: str | None = None):
         lib.ge_solve_batch.restype = ctypes.c_int
         lib.ge_solve_noalloc.argtypes = [_I64, _D, _D, _D, ctypes.c_int, _I32, _I64, _VP, _VP, _VP]
         lib.ge_solve_noalloc.restype = ctypes.c_int
-        lib.ge_probe_fma.argtypes = [_I32, _I32, _I64, _VP, _VP]
+        lib.ge_probe_fma.argtypes = [_I32, _I32, _I32, _I64, _VP, _VP]
         lib.ge_probe_fma.restype = ctypes.c_int
         lib.ge_sno_create.argtypes = [ctypes.POINTER(_VP), _I32, _I32, _I32, _I32, _I32, _I32, ctypes.c_uint64, _VP]
         lib.ge_sno_create.restype = ctypes.c_int
@@ -400,18 +400,19 @@ def ge_solve_noalloc(n: int, r: float, beta_l: float, beta_r: float, prec: int, 
            "ge_solve_noalloc")
 
 
-PROBE_THREADS, PROBE_CHAINS = 256, 16
+PROBE_THREADS = 256
 
 
-def ge_probe_fma(prec: int, blocks: int, iters: int, sink, stream=None) -> int:
+def ge_probe_fma(prec: int, blocks: int, chains: int, iters: int, sink, stream=None) -> int:
     """Register-only multiply-add throughput probe (GE_F64: DFMA, GE_F32:
-    FFMA); sink: CUDA tensor of blocks * 256 elements of the precision's
-    dtype.  Returns the multiply-adds the launch does."""
+    FFMA), `chains` (4, 8, 16, 32) independent chains per thread; sink: CUDA
+    tensor of blocks * 256 elements of the precision's dtype.  Returns the
+    multiply-adds the launch does."""
     if sink.numel() < blocks * PROBE_THREADS or sink.dtype != dtype_of(prec):
         raise ValueError("sink must hold blocks * 256 elements of the precision's dtype")
-    _check(load().ge_probe_fma(int(prec), int(blocks), int(iters), _dptr(sink), _stream_handle(stream)),
-           "ge_probe_fma")
-    return int(blocks) * PROBE_THREADS * PROBE_CHAINS * int(iters)
+    _check(load().ge_probe_fma(int(prec), int(blocks), int(chains), int(iters), _dptr(sink),
+                               _stream_handle(stream)), "ge_probe_fma")
+    return int(blocks) * PROBE_THREADS * int(chains) * int(iters)
 
 
 class Sno:
