@@ -374,6 +374,135 @@ def measure_batch(B, torch, inputs, dev, steps, warmup, only=None):
     return out
 
 
+def shard_problems(n, world: int):
+    """Contiguous blocks of problems, one per rank, balanced by points: rank
+    q takes problems [cuts[q], cuts[q + 1]) (at least one each)."""
+    cum = np.cumsum(np.asarray(n, dtype=np.float64))
+    cuts = [0]
+    for q in range(1, world):
+        c = int(np.searchsorted(cum, cum[-1] * q / world))
+        cuts.append(min(max(c, cuts[-1] + 1), len(n) - (world - q)))
+    cuts.append(len(n))
+    return cuts
+
+
+def measure_batch_sharded(B, torch, inputs, dev, dist, rank, world, steps, warmup):
+    """The batched workload (config 3) sharded by problem over the ranks:
+    rank q solves its block of problems (balanced by points) on its own GPU,
+    with no collective on the data path.  One CUDA-graph replay per solve
+    (reset + ge_batch_run of 2000 steps), depth autotuned per rank; timed
+    with a barrier and a device synchronisation on both sides, the max over
+    ranks.  updates_per_s counts every problem of the batch."""
+    import oracle
+    bt = inputs.uneven_batch()
+    cuts = shard_problems(bt.n, world)
+    i0, i1 = cuts[rank], cuts[rank + 1]
+    ns = bt.n[i0:i1]
+    offs = np.zeros(len(ns), dtype=np.int64)
+    pos = 0
+    for k, n in enumerate(ns):
+        offs[k] = pos
+        pos += ((int(n) + 31) // 32) * 32
+    u_host = np.zeros(pos)
+    for k in range(len(ns)):
+        o = bt.offsets[i0 + k]
+        u_host[offs[k]:offs[k] + ns[k]] = bt.u0[o:o + ns[k]]
+    upd_all = float(bt.n.sum()) * 2000
+    out = {"ranks": world, "problems_per_rank": [cuts[q + 1] - cuts[q] for q in range(world)],
+           "points_per_rank": [int(bt.n[cuts[q]:cuts[q + 1]].sum()) for q in range(world)],
+           "updates_per_solve": upd_all}
+    for name, prec in (("f32", B.GE_F32), ("f64", B.GE_F64)):
+        s = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(s):
+            u0 = torch.from_numpy(u_host).to(dev, B.dtype_of(prec))
+            u = u0.clone()
+            plan = B.ge_batch_create(ns, bt.r[i0:i1], bt.beta_l[i0:i1], bt.beta_r[i0:i1], offs, pos, prec,
+                                     stream=s)
+            depth = B.ge_batch_tune(plan, u0, 256)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                u.copy_(u0)
+                B.ge_batch_run(plan, u, 2000)
+            for _ in range(warmup):
+                g.replay()
+            torch.cuda.synchronize()
+            dist.barrier()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(steps):
+                g.replay()
+            e1.record(s)
+            e1.synchronize()
+            t = torch.tensor([e0.elapsed_time(e1) / steps], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            B.ge_batch_sync(plan)
+            got = u.double().cpu().numpy()
+            B.ge_batch_destroy(plan)
+        # two of this rank's problems against the oracle
+        errs = []
+        for k in (0, len(ns) - 1):
+            start = u_host[offs[k]:offs[k] + ns[k]]
+            if prec == B.GE_F32:
+                start = start.astype(np.float32).astype(np.float64)
+            w = oracle.run(start, bt.r[i0 + k], bt.beta_l[i0 + k], bt.beta_r[i0 + k], 2000)
+            errs.append(float(np.max(np.abs(got[offs[k]:offs[k] + ns[k]] - w)) / np.max(np.abs(w))))
+        e = torch.tensor([max(errs)], device=dev)
+        dist.all_reduce(e, op=dist.ReduceOp.MAX)
+        out[name] = {"updates_per_s": upd_all / (ms / 1e3), "ms_per_solve_max_over_ranks": ms,
+                     "depth_rank0": depth if rank == 0 else None,
+                     "max_rel_err_sampled": float(e.item()), "problems_checked": 2 * world}
+    return out
+
+
+def measure_split_solve(B, torch, inputs, dev, dist, rank, world, depth=48):
+    """Config 2 (N = 2^24, r = 2, 10000 steps) as ONE solve split over the
+    ranks: each rank keeps a device-resident GE context over its owned range
+    plus depth + 1 halo points per side and exchanges halos with its
+    neighbours every `depth` steps (NCCL point-to-point; no collective).
+    Strong scaling: the work is fixed, and updates_per_s counts the whole
+    grid.  One warm-up solve, one timed solve (barrier + device sync on both
+    sides, max over ranks); eight owned points checked against the oracle."""
+    import oracle
+    from paper_1310_3422_gb300 import decomp
+    u0 = inputs.sine_modes_state(N_POINTS)
+    p = decomp.partition(N_POINTS, world, rank, depth + 1)
+    bl = br = 0.0
+
+    def solve():
+        st = decomp.DeviceState(u0[p.lo:p.hi], R, bl, br, 0, depth)
+        done = 0
+        while done < GE_STEPS:
+            L = min(depth, GE_STEPS - done)
+            st.step_n(L)
+            done += L
+            if done < GE_STEPS:
+                decomp.exchange_halos(st, p, dist)
+        return st
+
+    solve().close()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = solve()
+    torch.cuda.synchronize()
+    dt = torch.tensor([time.perf_counter() - t0], device=dev)
+    dist.all_reduce(dt, op=dist.ReduceOp.MAX)
+    own = st.result(p.a - p.lo, p.b - p.a)
+    st.close()
+    idx = np.linspace(p.a, p.b - 1, 8).astype(np.int64)
+    want = oracle.sample(u0, R, 0.0, 0.0, GE_STEPS, list(idx))
+    err = torch.tensor([float(np.max(np.abs(own[idx - p.a] - want)) / np.max(np.abs(u0)))], device=dev)
+    dist.all_reduce(err, op=dist.ReduceOp.MAX)
+    return {"workload": WORKLOAD + ", one solve split over the ranks", "ranks": world, "depth": depth,
+            "halo_points_per_side": p.halo, "owned_points_rank0": p.b - p.a if rank == 0 else None,
+            "updates_per_s": float(N_POINTS) * GE_STEPS / float(dt.item()), "seconds_max_over_ranks": float(dt.item()),
+            "scaling": "strong", "max_rel_err_sampled": float(err.item()),
+            "timer": "host wall clock around the solve, device synchronised, max over ranks"}
+
+
 SNO_PROBLEMS, SNO_N, SNO_K, SNO_JUMPS, SNO_TOL = 65536, 1024, 256, 8, 1e-3
 
 
@@ -646,6 +775,13 @@ def main():
     n_tiled = (GE_STEPS + depth - 1) // depth if args.kernel in ("temporal", "temporal_df") else n_launch
     launch_ms = ms_per_step / n_tiled  # the dominant kernel's average launch (prescale time included for DF)
 
+    # ---- under torchrun: the batch sharded by problem, and config 2 as one
+    # solve split over the ranks (every rank takes part) ---------------------
+    batched_sharded = split_solve = None
+    if dist is not None and not args.no_variants:
+        batched_sharded = measure_batch_sharded(B, torch, inputs, dev, dist, rank, world, 3, 2)
+        split_solve = measure_split_solve(B, torch, inputs, dev, dist, rank, world)
+
     if rank != 0:
         B.ge_destroy(ctx)
         if dist is not None:
@@ -862,6 +998,8 @@ def main():
         "accuracy": acc,
         "variants": variants,
         "batched": batched,
+        "batched_sharded": batched_sharded,
+        "split_solve": split_solve,
         "surrogate": surrogate,
     }
     B.ge_destroy(ctx)

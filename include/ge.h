@@ -166,6 +166,17 @@ ge_status ge_read_state(ge_ctx *ctx, void *out_dev);
  * Errors: GE_EINVAL, GE_ECUDA. */
 ge_status ge_write_state(ge_ctx *ctx, const void *in_dev, int64_t step_count);
 
+/* Copy points [offset, offset + count) of the current state to out_dev
+ * (device, count elements of the context's type, caller-owned), or replace
+ * them by in_dev.  The step counter and any recorded device failure stay as
+ * they are.  These move the halos of a solve split over ranks: after S steps
+ * a point depends only on the points within S + 1 of it (the dependency cone
+ * of the step of Sec. 2), so refreshing a range's halos every S steps keeps
+ * its inner points exact.  Asynchronous on the context's stream.
+ * Errors: GE_EINVAL (NULL buffer, range outside 0..n), GE_ECUDA. */
+ge_status ge_read_range(ge_ctx *ctx, int64_t offset, int64_t count, void *out_dev);
+ge_status ge_write_range(ge_ctx *ctx, int64_t offset, int64_t count, const void *in_dev);
+
 /* Query the step counter.  Errors: GE_EINVAL. */
 ge_status ge_get_step(const ge_ctx *ctx, int64_t *step_count);
 

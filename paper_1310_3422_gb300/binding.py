@@ -24,6 +24,7 @@ GE_KERNEL_AUTO, GE_KERNEL_CANONICAL, GE_KERNEL_ONESTEP, GE_KERNEL_TEMPORAL, GE_K
 
 # Every symbol include/ge.h and include/ge_sno.h declare.
 EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", "ge_read_state", "ge_write_state",
+           "ge_read_range", "ge_write_range",
            "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_batch_create", "ge_batch_set_depth",
            "ge_batch_get_depth", "ge_batch_set_kernel", "ge_batch_tune", "ge_batch_run", "ge_batch_sync",
            "ge_batch_destroy",
@@ -74,6 +75,10 @@ def load(path: str | None = None):
         lib.ge_read_state.restype = ctypes.c_int
         lib.ge_write_state.argtypes = [_VP, _VP, _I64]
         lib.ge_write_state.restype = ctypes.c_int
+        lib.ge_read_range.argtypes = [_VP, _I64, _I64, _VP]
+        lib.ge_read_range.restype = ctypes.c_int
+        lib.ge_write_range.argtypes = [_VP, _I64, _I64, _VP]
+        lib.ge_write_range.restype = ctypes.c_int
         lib.ge_get_step.argtypes = [_VP, ctypes.POINTER(_I64)]
         lib.ge_get_step.restype = ctypes.c_int
         lib.ge_sync.argtypes = [_VP]
@@ -242,6 +247,20 @@ def ge_write_state(ctx: Ctx, src, step_count: int):
     if src.numel() < ctx.n or src.dtype != dtype_of(ctx.prec):
         raise ValueError("state tensor too small or of the wrong dtype")
     _check(load().ge_write_state(ctx.handle, _dptr(src), int(step_count)), "ge_write_state")
+
+
+def ge_read_range(ctx: Ctx, offset: int, count: int, dst):
+    """dst (CUDA tensor of at least `count` elements) <- points [offset, offset + count)."""
+    if dst.numel() < count or dst.dtype != dtype_of(ctx.prec):
+        raise ValueError("destination too small or of the wrong dtype")
+    _check(load().ge_read_range(ctx.handle, int(offset), int(count), _dptr(dst)), "ge_read_range")
+
+
+def ge_write_range(ctx: Ctx, offset: int, count: int, src):
+    """Points [offset, offset + count) <- src (CUDA tensor); the step counter stays."""
+    if src.numel() < count or src.dtype != dtype_of(ctx.prec):
+        raise ValueError("source too small or of the wrong dtype")
+    _check(load().ge_write_range(ctx.handle, int(offset), int(count), _dptr(src)), "ge_write_range")
 
 
 def ge_get_step(ctx: Ctx) -> int:

@@ -590,6 +590,36 @@ ge_status ge_write_state(ge_ctx *c, const void *in_dev, int64_t step_count)
     return GE_OK;
 }
 
+ge_status ge_read_range(ge_ctx *c, int64_t offset, int64_t count, void *out_dev)
+{
+    if (!c || (!out_dev && count > 0))
+        return fail(GE_EINVAL, "ge_read_range: NULL argument");
+    if (offset < 0 || count < 0 || offset > c->n - count)
+        return fail(GE_EINVAL, "ge_read_range: points [%lld, %lld) outside 0..%lld", (long long)offset,
+                    (long long)(offset + count), (long long)c->n);
+    if (count == 0)
+        return GE_OK;
+    const size_t es = elem_size(c->prec);
+    cudaError_t e = cudaMemcpyAsync(out_dev, static_cast<const char *>(c->buf[c->cur]) + offset * es,
+                                    (size_t)count * es, cudaMemcpyDeviceToDevice, c->stream);
+    return e == cudaSuccess ? GE_OK : cuda_fail(e, "ge_read_range");
+}
+
+ge_status ge_write_range(ge_ctx *c, int64_t offset, int64_t count, const void *in_dev)
+{
+    if (!c || (!in_dev && count > 0))
+        return fail(GE_EINVAL, "ge_write_range: NULL argument");
+    if (offset < 0 || count < 0 || offset > c->n - count)
+        return fail(GE_EINVAL, "ge_write_range: points [%lld, %lld) outside 0..%lld", (long long)offset,
+                    (long long)(offset + count), (long long)c->n);
+    if (count == 0)
+        return GE_OK;
+    const size_t es = elem_size(c->prec);
+    cudaError_t e = cudaMemcpyAsync(static_cast<char *>(c->buf[c->cur]) + offset * es, in_dev, (size_t)count * es,
+                                    cudaMemcpyDeviceToDevice, c->stream);
+    return e == cudaSuccess ? GE_OK : cuda_fail(e, "ge_write_range");
+}
+
 ge_status ge_debug_stall(ge_ctx *c, int64_t cycles)
 {
     if (!c || cycles < 0)

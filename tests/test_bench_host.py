@@ -77,3 +77,21 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+
+
+def test_shard_problems_balances_points():
+    """Config 3 sharded by problem: contiguous blocks covering every problem
+    once, at least one per rank, points within one problem's size of an
+    equal share."""
+    from paper_1310_3422_gb300 import inputs
+    bt = inputs.uneven_batch()
+    for world in (1, 2, 3, 4, 8):
+        cuts = bench.shard_problems(bt.n, world)
+        assert cuts[0] == 0 and cuts[-1] == len(bt.n) and len(cuts) == world + 1
+        assert all(cuts[q + 1] > cuts[q] for q in range(world))
+        share = bt.n.sum() / world
+        for q in range(world):
+            pts = bt.n[cuts[q]:cuts[q + 1]].sum()
+            assert abs(pts - share) <= bt.n.max() + 1
+    # more ranks than would balance: still one problem each
+    assert bench.shard_problems([1000, 1, 1, 1], 4) == [0, 1, 2, 3, 4]

@@ -1,8 +1,9 @@
-"""Domain decomposition with the library's tiled FP64 kernel as the local
-stepper: two gloo ranks in separate processes share the one GPU (their
-launches never wait on one another; halos travel between launches through
-the host), and the assembled result matches the monolithic oracle to the
-FP64 parity tolerance."""
+"""Domain decomposition with a device-resident GE context of the library
+(tiled FP64 kernel) per rank for the whole solve, halos read and written as
+device ranges: two gloo ranks in separate processes share the one GPU (their
+launches never wait on one another; under gloo the halos are staged through
+the host between launches), and the assembled result matches the monolithic
+oracle to the FP64 parity tolerance."""
 import os
 import socket
 
@@ -35,7 +36,7 @@ def _worker(rank, world, port, n, r, bl, br, steps, depth, step0, q):
     try:
         u0 = np.random.default_rng(43).standard_normal(n)
         part = decomp.partition(n, world, rank, depth + 1)
-        own = decomp.solve_decomposed(u0, r, bl, br, steps, depth, dist, stepper=decomp.gpu_stepper, step0=step0)
+        own = decomp.solve_decomposed(u0, r, bl, br, steps, depth, dist, step0=step0)
         q.put((rank, part.a, part.b, own))
     finally:
         dist.destroy_process_group()

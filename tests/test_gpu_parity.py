@@ -343,3 +343,36 @@ def test_tuning_table_sets_the_default_depth(tmp_path, monkeypatch):
     ctx = B.ge_create(500, 1.0, 0.0, 0.0, B.GE_F64)
     assert B.ge_get_kernel(ctx)[1] == 48  # built-in default
     B.ge_destroy(ctx)
+
+
+def test_range_read_write_keep_the_step_counter():
+    """ge_read_range / ge_write_range move points of the current state (the
+    halos of a split solve) and leave the step counter alone."""
+    n = 3001
+    u0 = inputs.random_state(n, seed=14)
+    x = torch.from_numpy(u0).to(DEV)
+    ctx = B.ge_create(n, 1.3, 0.2, -0.1, B.GE_F64, x)
+    B.ge_step_n(ctx, 5)
+    mid = torch.empty(100, dtype=torch.float64, device=DEV)
+    B.ge_read_range(ctx, 1000, 100, mid)
+    full = torch.empty_like(x)
+    B.ge_read_state(ctx, full)
+    B.ge_sync(ctx)
+    assert torch.equal(mid, full[1000:1100])
+    patch = torch.arange(50, dtype=torch.float64, device=DEV)
+    B.ge_write_range(ctx, n - 50, 50, patch)
+    B.ge_read_state(ctx, full)
+    B.ge_sync(ctx)
+    assert torch.equal(full[n - 50:], patch) and B.ge_get_step(ctx) == 5
+    with pytest.raises(B.GeError):
+        B.ge_read_range(ctx, n - 10, 11, mid)
+    with pytest.raises(B.GeError):
+        B.ge_write_range(ctx, -1, 5, patch)
+    # continue from the patched state: same as the oracle from it, at step 5
+    B.ge_step_n(ctx, 40)
+    B.ge_read_state(ctx, x)
+    B.ge_sync(ctx)
+    B.ge_destroy(ctx)
+    start = full.cpu().numpy()
+    want = oracle.run(start, 1.3, 0.2, -0.1, 40, step0=5)
+    assert rel_max(x.cpu().numpy(), want) <= tol64(1.3)
