@@ -254,9 +254,24 @@ ge_status ge_batch_set_depth(ge_batch *plan, int32_t depth);
 ge_status ge_batch_set_kernel(ge_batch *plan, ge_kernel kernel);
 ge_status ge_batch_get_depth(const ge_batch *plan, int32_t *depth);
 
-/* Autotune the depth: times each candidate depth on `steps` steps of the data
- * in u_dev (which is not modified), keeps the fastest and returns it in
- * *best_depth (may be NULL).  Synchronous.  Errors: GE_EINVAL, GE_ECUDA. */
+/* Tile geometry of later ge_batch_run calls: rows per tile (256, the
+ * default, or 128: the tile width W of the 2D TMA box; 0 = 256) and CTAs per
+ * SM of the persistent grid (1 .. what fits, 0 = as many as fit; 256-row
+ * tiles fit 2 per SM, 128-row tiles 4).  The double-float kernel has
+ * 256-row tiles only.  Errors: GE_EINVAL (NULL plan, other values). */
+ge_status ge_batch_set_geometry(ge_batch *plan, int32_t tile_rows, int32_t ctas_per_sm);
+/* The geometry in use (0 values resolved).  Errors: GE_EINVAL. */
+ge_status ge_batch_get_geometry(const ge_batch *plan, int32_t *tile_rows, int32_t *ctas_per_sm);
+
+/* Autotune the launches on the caller's data: times `steps` steps of the
+ * data in u_dev (which is not modified) for each candidate, by coordinate
+ * search: the depth T (16, 32, 48, 64, 96, 128, 192, 256 steps per launch)
+ * at the plan's geometry, then the geometry (rows per tile W in {256, 128}
+ * x CTAs per SM) at that depth, then the depth again.  Keeps the fastest
+ * (see ge_batch_get_depth, ge_batch_get_geometry) and returns its depth in
+ * *best_depth (may be NULL).  This is the counterpart of the paper's tuning
+ * of its block count (Sec. 4) for the batched kernel.  Synchronous.
+ * Errors: GE_EINVAL, GE_ECUDA. */
 ge_status ge_batch_tune(ge_batch *plan, const void *u_dev, int64_t steps, int32_t *best_depth);
 
 /* Advance every problem of the batch by `steps` steps, in place in u_dev.

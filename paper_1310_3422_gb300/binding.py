@@ -26,7 +26,8 @@ GE_KERNEL_AUTO, GE_KERNEL_CANONICAL, GE_KERNEL_ONESTEP, GE_KERNEL_TEMPORAL, GE_K
 EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", "ge_read_state", "ge_write_state",
            "ge_read_range", "ge_write_range",
            "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_batch_create", "ge_batch_set_depth",
-           "ge_batch_get_depth", "ge_batch_set_kernel", "ge_batch_tune", "ge_batch_run", "ge_batch_sync",
+           "ge_batch_get_depth", "ge_batch_set_kernel", "ge_batch_tune", "ge_batch_set_geometry",
+           "ge_batch_get_geometry", "ge_batch_run", "ge_batch_sync",
            "ge_batch_destroy",
            "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error", "ge_debug_stall",
            "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune", "ge_probe_fma",
@@ -98,6 +99,10 @@ def load(path: str | None = None):
         lib.ge_batch_set_kernel.restype = ctypes.c_int
         lib.ge_batch_get_depth.argtypes = [_VP, ctypes.POINTER(_I32)]
         lib.ge_batch_get_depth.restype = ctypes.c_int
+        lib.ge_batch_set_geometry.argtypes = [_VP, _I32, _I32]
+        lib.ge_batch_set_geometry.restype = ctypes.c_int
+        lib.ge_batch_get_geometry.argtypes = [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]
+        lib.ge_batch_get_geometry.restype = ctypes.c_int
         lib.ge_batch_tune.argtypes = [_VP, _VP, _I64, ctypes.POINTER(_I32)]
         lib.ge_batch_tune.restype = ctypes.c_int
         lib.ge_batch_run.argtypes = [_VP, _VP, _I64]
@@ -344,6 +349,18 @@ def ge_batch_set_depth(plan: Batch, depth: int):
 
 def ge_batch_set_kernel(plan: Batch, kernel: int):
     _check(load().ge_batch_set_kernel(plan.handle, int(kernel)), "ge_batch_set_kernel")
+
+
+def ge_batch_set_geometry(plan: Batch, tile_rows: int, ctas_per_sm: int):
+    """Rows per tile (256 or 128; 0 = 256) and CTAs per SM (0 = as many as fit)."""
+    _check(load().ge_batch_set_geometry(plan.handle, int(tile_rows), int(ctas_per_sm)), "ge_batch_set_geometry")
+
+
+def ge_batch_get_geometry(plan: Batch):
+    """(rows per tile, CTAs per SM) of the plan's launches."""
+    tr, c = _I32(), _I32()
+    _check(load().ge_batch_get_geometry(plan.handle, ctypes.byref(tr), ctypes.byref(c)), "ge_batch_get_geometry")
+    return int(tr.value), int(c.value)
 
 
 def ge_batch_get_depth(plan: Batch) -> int:

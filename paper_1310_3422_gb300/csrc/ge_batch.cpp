@@ -53,7 +53,8 @@ constexpr int kBatchDefaultDepthF32 = 64;
 }  // namespace
 
 struct ge_batch {
-    CUtensorMap tmap[2];
+    CUtensorMap tmap[2];      // box of 256 rows, one per working buffer
+    CUtensorMap tmap128[2];   // box of 128 rows (the 128-row tile geometry)
     ge_precision prec = GE_F32;
     cudaStream_t stream = nullptr;
     int n_problems = 0;
@@ -65,6 +66,10 @@ struct ge_batch {
     int *err = nullptr;
     int depth = 0;
     int num_sms = 0, blocks_per_sm = 0;
+    // tile geometry of the launches (ge_batch_set_geometry, ge_batch_tune):
+    // rows per tile (256 or 128) and co-resident CTAs per SM (0: as many as fit)
+    int tile_rows = 256, ctas_per_sm = 0;
+    int blocks_per_sm_128 = 0;
     // scaled form (FP64, plain FP32): rescale exponents [n_problems][Q] and
     // end-factor slots, one per launch length n_mid met so far
     short *exps = nullptr;
@@ -139,14 +144,28 @@ int endf_slot(ge_batch *b, int n_mid, cudaError_t *err)
     return (int)i;
 }
 
-// Enqueue `steps` steps on the working buffers (state in buf[0] on entry);
+// Largest co-resident CTAs per SM of the plan's kernel at a tile geometry.
+int max_ctas(const ge_batch *b, int tile_rows)
+{
+    if (b->df)
+        return b->df_blocks_per_sm;
+    return tile_rows == 128 ? b->blocks_per_sm_128 : b->blocks_per_sm;
+}
+
+// Enqueue `steps` steps on the working buffers (state in buf[0] on entry)
+// at the given depth and tile geometry (ctas 0: as many per SM as fit);
 // returns the index of the buffer holding the result.
-ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int *result_buf)
+ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int tile_rows, int ctas, int *result_buf)
 {
     const int pidx = prec_index(b->prec);
+    if (b->df)
+        tile_rows = 256;  // the double-float kernel has the 256-row tile only
+    const int cmax = max_ctas(b, tile_rows);
+    if (ctas < 1 || ctas > cmax)
+        ctas = cmax;
     int cur = 0;
     int64_t n0 = 0;
-    const int dmax = ge::tbb_max_depth(pidx);
+    const int dmax = ge::tbb_max_depth(pidx, tile_rows);
     if (depth > dmax)
         depth = dmax;
     if (b->df) {
@@ -166,7 +185,7 @@ ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int *result_buf)
         p.do_exit = last ? 1 : 0;
         p.p_first = (int)(n0 & 1);
         const int reach = p.do_entry + p.n_mid + p.do_exit;
-        if (!ge::tbb_geometry(pidx, reach, &p.H, &p.U))
+        if (!ge::tbb_geometry(pidx, tile_rows, reach, &p.H, &p.U))
             return bfail(GE_EINVAL, "ge_batch: depth does not fit a tile");
         p.n_rows = b->n_rows;
         p.n_tiles = (b->n_rows * (ge::kRowBytes / (b->prec == GE_F64 ? 8 : 4)) + p.U - 1) / p.U;
@@ -195,13 +214,14 @@ ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int *result_buf)
         p.df_codes = b->df_codes;
         p.out = b->buf[cur ^ 1];
         p.tile_ctr = b->err + 48;  // the launch's tile queue, zeroed first
-        long long grid = (long long)b->num_sms * (b->df ? b->df_blocks_per_sm : b->blocks_per_sm);
+        long long grid = (long long)b->num_sms * ctas;
         if (grid > p.n_tiles)
             grid = p.n_tiles;
         cudaError_t e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int), b->stream);
         if (e == cudaSuccess)
             e = b->df ? ge::launch_tbb_df(&b->tmap[cur], p, (int)grid, b->stream)
-                      : ge::launch_tbb(pidx, &b->tmap[cur], p, (int)grid, b->stream);
+                      : ge::launch_tbb(pidx, tile_rows, tile_rows == 128 ? &b->tmap128[cur] : &b->tmap[cur], p,
+                                       (int)grid, b->stream);
         if (e != cudaSuccess)
             return bcuda(e, "ge_batch: kernel launch");
         cur ^= 1;
@@ -328,8 +348,10 @@ ge_status ge_batch_create(ge_batch **out, int32_t n_problems, const int64_t *n, 
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(b->stream);
     if (e == cudaSuccess)
-        e = ge::tbb_occupancy(prec_index(prec), &b->blocks_per_sm);
-    if (e != cudaSuccess || b->blocks_per_sm < 1) {
+        e = ge::tbb_occupancy(prec_index(prec), 256, &b->blocks_per_sm);
+    if (e == cudaSuccess)
+        e = ge::tbb_occupancy(prec_index(prec), 128, &b->blocks_per_sm_128);
+    if (e != cudaSuccess || b->blocks_per_sm < 1 || b->blocks_per_sm_128 < 1) {
         release_batch(b);
         return bcuda(e == cudaSuccess ? cudaErrorInvalidConfiguration : e, "ge_batch_create");
     }
@@ -338,13 +360,14 @@ ge_status ge_batch_create(ge_batch **out, int32_t n_problems, const int64_t *n, 
         release_batch(b);
         return bfail(GE_ECUDA, "ge_batch_create: cuTensorMapEncodeTiled is not available");
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 4; ++i) {
         cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)n_rows};
         cuuint64_t strides[1] = {(cuuint64_t)ge::kRowBytes};
-        cuuint32_t box[2] = {(cuuint32_t)K, (cuuint32_t)ge::kTileRows};
+        cuuint32_t box[2] = {(cuuint32_t)K, (cuuint32_t)(i < 2 ? 256 : 128)};
         cuuint32_t estr[2] = {1, 1};
-        CUresult cr = enc(&b->tmap[i], prec == GE_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                          2, b->buf[i], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+        CUresult cr = enc(i < 2 ? &b->tmap[i] : &b->tmap128[i - 2],
+                          prec == GE_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                          2, b->buf[i & 1], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (cr != CUDA_SUCCESS) {
@@ -391,6 +414,8 @@ ge_status ge_batch_set_kernel(ge_batch *b, ge_kernel kernel)
             return bcuda(e, "ge_batch_set_kernel: rescale table");
     }
     b->df = df;
+    if (df)
+        b->tile_rows = 256;  // the double-float kernel has the 256-row tile only
     b->R = R;
     b->Q = Q;
     b->slot_nmid.clear();
@@ -429,11 +454,39 @@ ge_status ge_batch_run(ge_batch *b, void *u_dev, int64_t steps)
     if (e != cudaSuccess)
         return bcuda(e, "ge_batch_run: copy in");
     int res = 0;
-    ge_status st = batch_steps(b, steps, b->depth, &res);
+    ge_status st = batch_steps(b, steps, b->depth, b->tile_rows, b->ctas_per_sm, &res);
     if (st != GE_OK)
         return st;
     e = cudaMemcpyAsync(u_dev, b->buf[res], bytes, cudaMemcpyDeviceToDevice, b->stream);
     return e == cudaSuccess ? GE_OK : bcuda(e, "ge_batch_run: copy out");
+}
+
+ge_status ge_batch_set_geometry(ge_batch *b, int32_t tile_rows, int32_t ctas_per_sm)
+{
+    if (!b)
+        return bfail(GE_EINVAL, "ge_batch_set_geometry: plan is NULL");
+    if (tile_rows == 0)
+        tile_rows = 256;
+    if (tile_rows != 256 && tile_rows != 128)
+        return bfail(GE_EINVAL, "ge_batch_set_geometry: tile_rows must be 0, 128 or 256");
+    if (b->df && tile_rows != 256)
+        return bfail(GE_EINVAL, "ge_batch_set_geometry: the double-float kernel has 256-row tiles only");
+    if (ctas_per_sm < 0 || ctas_per_sm > max_ctas(b, tile_rows))
+        return bfail(GE_EINVAL, "ge_batch_set_geometry: ctas_per_sm beyond what fits on an SM");
+    b->tile_rows = tile_rows;
+    b->ctas_per_sm = ctas_per_sm;
+    return GE_OK;
+}
+
+ge_status ge_batch_get_geometry(const ge_batch *b, int32_t *tile_rows, int32_t *ctas_per_sm)
+{
+    if (!b || !tile_rows || !ctas_per_sm)
+        return bfail(GE_EINVAL, "ge_batch_get_geometry: NULL argument");
+    const int tr = b->df ? 256 : b->tile_rows;
+    const int cmax = max_ctas(b, tr);
+    *tile_rows = tr;
+    *ctas_per_sm = (b->ctas_per_sm < 1 || b->ctas_per_sm > cmax) ? cmax : b->ctas_per_sm;
+    return GE_OK;
 }
 
 ge_status ge_batch_tune(ge_batch *b, const void *u_dev, int64_t steps, int32_t *best_depth)
@@ -447,45 +500,80 @@ ge_status ge_batch_tune(ge_batch *b, const void *u_dev, int64_t steps, int32_t *
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess)
         e = cudaEventCreate(&e1);
-    double best = 1e300;
-    int best_d = b->depth;
-    for (int d : cand) {
+    // time one configuration on `steps` steps of the caller's data: one
+    // untimed run (first use of this launch shape), then a timed one
+    auto timed = [&](int d, int tr, int ctas, float *ms) -> ge_status {
         int res = 0;
-        // one untimed run (first use of this launch shape), then a timed one
         for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
             e = cudaMemcpyAsync(b->buf[0], u_dev, bytes, cudaMemcpyDeviceToDevice, b->stream);
             if (e == cudaSuccess && rep == 1)
                 e = cudaEventRecord(e0, b->stream);
             if (e != cudaSuccess)
                 break;
-            ge_status st = batch_steps(b, steps, d, &res);
-            if (st != GE_OK) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
+            ge_status st = batch_steps(b, steps, d, tr, ctas, &res);
+            if (st != GE_OK)
                 return st;
-            }
             if (rep == 1)
                 e = cudaEventRecord(e1, b->stream);
         }
         if (e == cudaSuccess)
             e = cudaEventSynchronize(e1);
-        float ms = 0.0f;
         if (e == cudaSuccess)
-            e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess)
-            break;
-        if (ms < best) {
-            best = ms;
-            best_d = d;
+            e = cudaEventElapsedTime(ms, e0, e1);
+        return GE_OK;
+    };
+    // coordinate search: the depth at the plan's geometry, then the geometry
+    // (rows per tile x CTAs per SM) at that depth, then the depth again
+    double best = 1e300;
+    int best_d = b->depth, best_tr = b->df ? 256 : b->tile_rows;
+    int best_c = max_ctas(b, best_tr);
+    if (b->ctas_per_sm >= 1 && b->ctas_per_sm < best_c)
+        best_c = b->ctas_per_sm;
+    ge_status st = GE_OK;
+    for (int pass = 0; pass < 3 && st == GE_OK && e == cudaSuccess; ++pass) {
+        if (pass == 1) {
+            const int tr0 = best_tr, c0 = best_c;
+            for (int tr : {256, 128}) {
+                if (b->df && tr != 256)
+                    continue;
+                for (int c = 1; c <= max_ctas(b, tr) && st == GE_OK && e == cudaSuccess; ++c) {
+                    if (tr == tr0 && c == c0)
+                        continue;
+                    float ms = 0.0f;
+                    st = timed(best_d, tr, c, &ms);
+                    if (st == GE_OK && e == cudaSuccess && ms < best) {
+                        best = ms;
+                        best_tr = tr;
+                        best_c = c;
+                    }
+                }
+            }
+        } else {
+            for (int d : cand) {
+                if (pass == 2 && d == best_d)
+                    continue;
+                float ms = 0.0f;
+                st = timed(d, best_tr, best_c, &ms);
+                if (st != GE_OK || e != cudaSuccess)
+                    break;
+                if (ms < best) {
+                    best = ms;
+                    best_d = d;
+                }
+            }
         }
     }
     if (e0)
         cudaEventDestroy(e0);
     if (e1)
         cudaEventDestroy(e1);
+    if (st != GE_OK)
+        return st;
     if (e != cudaSuccess)
         return bcuda(e, "ge_batch_tune");
     b->depth = best_d;
+    b->tile_rows = best_tr;
+    b->ctas_per_sm = best_c;
     if (best_depth)
         *best_depth = best_d;
     return GE_OK;

@@ -240,18 +240,20 @@ cudaError_t launch_sweep_tb_f32(const float *in, float *out, long long n, int pa
 // prec: 0 = FP64, 1 = FP32, 2 = FP32 compensated.  tmap: 128-byte-aligned
 // CUtensorMap (opaque here) describing the source buffer.
 cudaError_t launch_tb(int prec, const void *tmap, const TbParams &p, int grid, cudaStream_t s);
-cudaError_t launch_tbb(int prec, const void *tmap, const TbbParams &p, int grid, cudaStream_t s);
+// tile_rows: 256 or 128 (the tile geometry of the plan; the tensor map's box
+// must have as many rows).
+cudaError_t launch_tbb(int prec, int tile_rows, const void *tmap, const TbbParams &p, int grid, cudaStream_t s);
 // Batched double-float kernel (ge_tbb_df.cu) for FP64 plans; its per-call
 // prescale: codes[b] = max(desc[b].walls_code, code of the problem's values).
 cudaError_t launch_tbb_df(const void *tmap, const TbbParams &p, int grid, cudaStream_t s);
 cudaError_t tbb_df_occupancy(int *blocks_per_sm);
 cudaError_t batch_df_prescale(const double *u, const int *row_pid, const BatchDesc *desc, long long n_rows,
                               int n_problems, int *codes, cudaStream_t s);
-cudaError_t tbb_occupancy(int prec, int *blocks_per_sm);
-bool tbb_geometry(int prec, int reach, int *H, int *U);
+cudaError_t tbb_occupancy(int prec, int tile_rows, int *blocks_per_sm);
+bool tbb_geometry(int prec, int tile_rows, int reach, int *H, int *U);
 // Largest steps per launch whose reach (steps + 2 stages) fits the batched
 // kernel's tile for this precision.
-int tbb_max_depth(int prec);
+int tbb_max_depth(int prec, int tile_rows);
 // Largest co-resident CTAs per SM for the tiled kernel of this precision.
 cudaError_t tb_occupancy(int prec, int *blocks_per_sm);
 int tb_smem_bytes();

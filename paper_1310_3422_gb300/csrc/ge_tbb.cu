@@ -356,18 +356,19 @@ __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &
 }
 
 // Batched kernel for FP64 and compensated FP32: CTA rows (thread t holds
-// tile row t; warp edges exchange through shared memory), 2 CTAs per SM.
-// Plain FP32 runs the warp-specialised warp-window kernel below.
-template <typename Real, bool COMP>
-__global__ void __launch_bounds__(kTileRows, 2)
+// tile row t; warp edges exchange through shared memory).  TR: rows per tile
+// (= threads), a geometry the plan's autotuner picks (256: 2 CTAs per SM,
+// 128: 4).  Plain FP32 runs the warp-specialised warp-window kernel below.
+template <typename Real, bool COMP, int TR>
+__global__ void __launch_bounds__(TR, TR == 256 ? 2 : 4)
     tbb_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TbbParams P)
 {
     constexpr bool WT = false;
-    constexpr int NT = kTileRows;
+    constexpr int NT = TR;
     constexpr int K = kRowBytes / (int)sizeof(Real);
     constexpr int NW = NT / 32;
     constexpr int CH = kRowBytes / 16;
-    constexpr uint32_t kTileBytes = kTileRows * kRowBytes;
+    constexpr uint32_t kTileBytes = TR * kRowBytes;
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char *tiles = reinterpret_cast<unsigned char *>(
@@ -507,20 +508,27 @@ __global__ void __launch_bounds__(kTileRows, 2)
 // read it), so a warp that holds problem boundaries and runs longer holds
 // back the reuse of a buffer, a tile later, not the other warps' next tile.
 // (With one CTA barrier per tile the FP32 batch spent most stalls there.)
-constexpr int kWsConsumers = kTileRows / 32;      // consumer warps
-constexpr int kWsThreads = kTileRows + 32;         // plus the producer warp
+// TR: rows per tile, a geometry the plan's autotuner picks (256: eight
+// consumer warps, 2 CTAs per SM; 128: four, 4 CTAs per SM).
 constexpr int kWsStageBytes = 32 * kRowBytes;      // staging rows of one consumer warp
-int ws_smem_bytes() { return 2 * kTileRows * kRowBytes + kWsConsumers * kWsStageBytes + 1024; }
+template <int TR>
+struct Ws {
+    static constexpr int kConsumers = TR / 32;     // consumer warps
+    static constexpr int kThreads = TR + 32;       // plus the producer warp
+    static constexpr int kMinBlocks = TR == 256 ? 2 : 4;
+    static int smem_bytes() { return 2 * TR * kRowBytes + kConsumers * kWsStageBytes + 1024; }
+};
 
-__global__ void __launch_bounds__(kWsThreads, 2)
+template <int TR>
+__global__ void __launch_bounds__(Ws<TR>::kThreads, Ws<TR>::kMinBlocks)
     tbb_ws_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TbbParams P)
 {
     using Real = float;
     constexpr bool WT = true;
     constexpr int K = kRowBytes / (int)sizeof(Real);
-    constexpr int NW = kWsConsumers;
+    constexpr int NW = Ws<TR>::kConsumers;
     constexpr int CH = kRowBytes / 16;
-    constexpr uint32_t kTileBytes = kTileRows * kRowBytes;
+    constexpr uint32_t kTileBytes = TR * kRowBytes;
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char *tiles = reinterpret_cast<unsigned char *>(
@@ -666,23 +674,44 @@ __global__ void __launch_bounds__(kWsThreads, 2)
     }
 }
 
-template <typename Real, bool COMP>
+constexpr int rows_smem_bytes(int tr) { return 2 * tr * kRowBytes + 1024; }
+
+template <typename Real, bool COMP, int TR>
 cudaError_t launch_batch_one(const void *tmap, const TbbParams &p, int grid, cudaStream_t s)
 {
     const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
-    tbb_kernel<Real, COMP><<<grid, kTileRows, tb_smem_bytes(), s>>>(*m, p);
+    tbb_kernel<Real, COMP, TR><<<grid, TR, rows_smem_bytes(TR), s>>>(*m, p);
     return cudaGetLastError();
 }
 
-template <typename Real, bool COMP>
+template <typename Real, bool COMP, int TR>
 cudaError_t batch_attr_and_occupancy(int *blocks)
 {
-    cudaError_t e = cudaFuncSetAttribute(tbb_kernel<Real, COMP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, tb_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute(tbb_kernel<Real, COMP, TR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem_bytes(TR));
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tbb_kernel<Real, COMP>, kTileRows,
-                                                         tb_smem_bytes());
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tbb_kernel<Real, COMP, TR>, TR,
+                                                         rows_smem_bytes(TR));
+}
+
+template <int TR>
+cudaError_t ws_attr_and_occupancy(int *blocks)
+{
+    cudaError_t e = cudaFuncSetAttribute(tbb_ws_kernel<TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Ws<TR>::smem_bytes());
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tbb_ws_kernel<TR>, Ws<TR>::kThreads,
+                                                         Ws<TR>::smem_bytes());
+}
+
+template <int TR>
+cudaError_t launch_ws(const void *tmap, const TbbParams &p, int grid, cudaStream_t s)
+{
+    const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
+    tbb_ws_kernel<TR><<<grid, Ws<TR>::kThreads, Ws<TR>::smem_bytes(), s>>>(*m, p);
+    return cudaGetLastError();
 }
 
 // Scale bookkeeping of the batched scaled form, one thread per problem, in
@@ -813,54 +842,52 @@ cudaError_t batch_endf(const BatchDesc *desc, const short *exps, int n_problems,
     return cudaGetLastError();
 }
 
-bool tbb_geometry(int prec, int reach, int *H, int *U)
+bool tbb_geometry(int prec, int tile_rows, int reach, int *H, int *U)
 {
     const int K = kRowBytes / (prec == 0 ? 8 : 4);
     const int ht = (reach + K - 1) / K;
     const bool wt = prec == 1;  // plain FP32: tbb_ws_kernel's warp windows
+    if (tile_rows != 128 && tile_rows != 256)
+        return false;
     *H = ht * K;
     if (wt) {
         if (2 * ht >= 32)
             return false;
-        *U = (kTileRows / 32) * (32 - 2 * ht) * K;
+        *U = (tile_rows / 32) * (32 - 2 * ht) * K;
         return true;
     }
-    *U = kTileRows * K - 2 * *H;
+    *U = tile_rows * K - 2 * *H;
     return *U > 0;
 }
 
-int tbb_max_depth(int prec)
+int tbb_max_depth(int prec, int tile_rows)
 {
     int H, U, d = kMaxTableSteps;
-    while (d > 1 && !tbb_geometry(prec, d + 2, &H, &U))
+    while (d > 1 && !tbb_geometry(prec, tile_rows, d + 2, &H, &U))
         --d;
     return d;
 }
 
-cudaError_t tbb_occupancy(int prec, int *blocks)
+cudaError_t tbb_occupancy(int prec, int tile_rows, int *blocks)
 {
+    if (prec == 1)
+        return tile_rows == 128 ? ws_attr_and_occupancy<128>(blocks) : ws_attr_and_occupancy<256>(blocks);
     if (prec == 0)
-        return batch_attr_and_occupancy<double, false>(blocks);
-    if (prec == 1) {
-        cudaError_t e = cudaFuncSetAttribute(tbb_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             ws_smem_bytes());
-        if (e != cudaSuccess)
-            return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tbb_ws_kernel, kWsThreads, ws_smem_bytes());
-    }
-    return batch_attr_and_occupancy<float, true>(blocks);
+        return tile_rows == 128 ? batch_attr_and_occupancy<double, false, 128>(blocks)
+                                : batch_attr_and_occupancy<double, false, 256>(blocks);
+    return tile_rows == 128 ? batch_attr_and_occupancy<float, true, 128>(blocks)
+                            : batch_attr_and_occupancy<float, true, 256>(blocks);
 }
 
-cudaError_t launch_tbb(int prec, const void *tmap, const TbbParams &p, int grid, cudaStream_t s)
+cudaError_t launch_tbb(int prec, int tile_rows, const void *tmap, const TbbParams &p, int grid, cudaStream_t s)
 {
+    if (prec == 1)
+        return tile_rows == 128 ? launch_ws<128>(tmap, p, grid, s) : launch_ws<256>(tmap, p, grid, s);
     if (prec == 0)
-        return launch_batch_one<double, false>(tmap, p, grid, s);
-    if (prec == 1) {
-        const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
-        tbb_ws_kernel<<<grid, kWsThreads, ws_smem_bytes(), s>>>(*m, p);
-        return cudaGetLastError();
-    }
-    return launch_batch_one<float, true>(tmap, p, grid, s);
+        return tile_rows == 128 ? launch_batch_one<double, false, 128>(tmap, p, grid, s)
+                                : launch_batch_one<double, false, 256>(tmap, p, grid, s);
+    return tile_rows == 128 ? launch_batch_one<float, true, 128>(tmap, p, grid, s)
+                            : launch_batch_one<float, true, 256>(tmap, p, grid, s);
 }
 
 }  // namespace ge

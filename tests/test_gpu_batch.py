@@ -247,3 +247,59 @@ def test_batch_check_flags_non_finite_problems(prec):
     for i in (0, 1, 3):  # the other problems are untouched by their neighbours' NaN / Inf
         want = oracle.run(u[offs[i]:offs[i] + n[i]], r[i], bl[i], br[i], 20)
         assert rel(got[offs[i]:offs[i] + n[i]], want) <= tol(prec, r[i])
+
+
+@pytest.mark.parametrize("prec", [B.GE_F64, B.GE_F32, B.GE_F32_COMP])
+def test_every_tile_geometry_gives_the_same_result(prec):
+    """Rows per tile (256, 128) and CTAs per SM change where the tiles are
+    cut and who computes them, not the arithmetic of any point: every
+    geometry gives the same bits, and they match the oracle problem by
+    problem."""
+    n, r, bl, br, offs, total, u = make_batch(MIXED, seed=41, gap=32)
+    outs = {}
+    for tr in (256, 128):
+        plan = B.ge_batch_create(n, r, bl, br, offs, total, prec)
+        B.ge_batch_set_geometry(plan, tr, 0)
+        got_tr, cmax = B.ge_batch_get_geometry(plan)
+        assert got_tr == tr and cmax >= 1
+        for c in sorted({1, cmax}):
+            for depth in (5, 48):
+                B.ge_batch_set_geometry(plan, tr, c)
+                B.ge_batch_set_depth(plan, depth)
+                x = torch.from_numpy(u).to(DEV, B.dtype_of(prec))
+                B.ge_batch_run(plan, x, 101)
+                B.ge_batch_sync(plan)
+                outs[(tr, c, depth)] = x.double().cpu().numpy()
+        with pytest.raises(B.GeError):
+            B.ge_batch_set_geometry(plan, tr, cmax + 1)
+        B.ge_batch_destroy(plan)
+    ref = outs[(256, 1, 48)]
+    for key, got in outs.items():
+        if key[2] == 48:
+            assert np.array_equal(got, ref), key
+    for key in ((256, 1, 5), (128, 1, 5)):
+        for i in range(len(n)):
+            want = oracle.run(u[offs[i]:offs[i] + n[i]], r[i], bl[i], br[i], 101)
+            assert rel(outs[key][offs[i]:offs[i] + n[i]], want) <= tol(prec, r[i]), (key, i)
+
+
+def test_tune_picks_a_geometry_on_the_callers_data():
+    """The autotuner searches depth and geometry on the caller's data, leaves
+    the data alone, and the plan then runs at what it picked, matching the
+    oracle."""
+    n, r, bl, br, offs, total, u = make_batch(MIXED * 4, seed=42)
+    x = torch.from_numpy(u).to(DEV, torch.float32)
+    before = x.clone()
+    plan = B.ge_batch_create(n, r, bl, br, offs, total, B.GE_F32)
+    best = B.ge_batch_tune(plan, x, 96)
+    assert torch.equal(x, before)
+    tr, c = B.ge_batch_get_geometry(plan)
+    assert best == B.ge_batch_get_depth(plan) and tr in (128, 256) and c >= 1
+    B.ge_batch_run(plan, x, 60)
+    B.ge_batch_sync(plan)
+    got = x.double().cpu().numpy()
+    B.ge_batch_destroy(plan)
+    for i in range(len(n)):
+        start = u[offs[i]:offs[i] + n[i]].astype(np.float32).astype(np.float64)
+        want = oracle.run(start, r[i], bl[i], br[i], 60)
+        assert rel(got[offs[i]:offs[i] + n[i]], want) <= tol(B.GE_F32, r[i]), i
