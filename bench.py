@@ -319,11 +319,12 @@ def measure_e2e(B, torch, u0, prec, kern, depth, steps, world):
             "ms_per_step": t_e2e * 1e3, "timer": "host wall clock around ge_solve (synchronous)"}
 
 
-def measure_batch(B, torch, inputs, dev, steps, warmup, only=None):
+def measure_batch(B, torch, inputs, dev, steps, warmup, only=None, fixed=None):
     """Batched workload: 4096 problems, N log-uniform in [256, 65536], r in
     [0.25, 4], 2000 steps.  One CUDA-graph replay per solve (reset from u0 +
-    ge_batch_run); depth autotuned; sampled problems checked against the
-    oracle."""
+    ge_batch_run); depth and tile geometry autotuned (or `fixed` = (depth,
+    rows per tile, CTAs per SM), for profiling one launch shape); sampled
+    problems checked against the oracle."""
     import oracle
     bt = inputs.uneven_batch()
     upd = float(bt.n.sum()) * 2000
@@ -344,7 +345,13 @@ def measure_batch(B, torch, inputs, dev, steps, warmup, only=None):
             plan = B.ge_batch_create(bt.n, bt.r, bt.beta_l, bt.beta_r, bt.offsets, bt.total, prec, stream=s)
             if name == "f64_df":  # FP64 storage, double-float arithmetic on the FP32 pipes
                 B.ge_batch_set_kernel(plan, B.GE_KERNEL_TEMPORAL_DF)
-            depth = B.ge_batch_tune(plan, u0, 256)
+            if fixed is None:
+                depth = B.ge_batch_tune(plan, u0, 256)
+            else:
+                depth = fixed[0]
+                B.ge_batch_set_depth(plan, depth)
+                B.ge_batch_set_geometry(plan, fixed[1], fixed[2])
+            tile_rows, ctas = B.ge_batch_get_geometry(plan)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=s):
                 u.copy_(u0)
@@ -352,14 +359,21 @@ def measure_batch(B, torch, inputs, dev, steps, warmup, only=None):
             for _ in range(warmup):
                 g.replay()
             torch.cuda.synchronize()
+            # enough replays for the clock sampler to see the region (>= 1 s)
+            t0 = time.perf_counter()
+            g.replay()
+            torch.cuda.synchronize()
+            reps = max(steps, int(np.ceil(1.0 / max(1e-4, time.perf_counter() - t0))))
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(s)
-            for _ in range(steps):
-                g.replay()
-            e1.record(s)
-            e1.synchronize()
-            ms = e0.elapsed_time(e1) / steps
+            sampler = ClockSampler(dev.index or 0)
+            with sampler:
+                e0.record(s)
+                for _ in range(reps):
+                    g.replay()
+                e1.record(s)
+                e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
             B.ge_batch_sync(plan)
             got = u.double().cpu().numpy()
             errs = []
@@ -369,6 +383,9 @@ def measure_batch(B, torch, inputs, dev, steps, warmup, only=None):
                 errs.append(float(np.max(np.abs(got[o:o + n] - w)) / np.max(np.abs(w))))
             B.ge_batch_destroy(plan)
         out[name] = {"updates_per_s": upd / (ms / 1e3), "ms_per_solve": ms, "depth": depth,
+                     "geometry": {"tile_rows": tile_rows, "ctas_per_sm": ctas,
+                                  "tuned": fixed is None},
+                     "replays_timed": reps, "clocks": sampler.summary(),
                      "launches_per_solve": (2000 + depth - 1) // depth + (2 if name == "f64_df" else 0),
                      "max_rel_err_sampled": max(errs), "problems_checked": len(picks)}
     return out
@@ -418,7 +435,13 @@ def measure_batch_sharded(B, torch, inputs, dev, dist, rank, world, steps, warmu
             u = u0.clone()
             plan = B.ge_batch_create(ns, bt.r[i0:i1], bt.beta_l[i0:i1], bt.beta_r[i0:i1], offs, pos, prec,
                                      stream=s)
-            depth = B.ge_batch_tune(plan, u0, 256)
+            if fixed is None:
+                depth = B.ge_batch_tune(plan, u0, 256)
+            else:
+                depth = fixed[0]
+                B.ge_batch_set_depth(plan, depth)
+                B.ge_batch_set_geometry(plan, fixed[1], fixed[2])
+            tile_rows, ctas = B.ge_batch_get_geometry(plan)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=s):
                 u.copy_(u0)
@@ -678,6 +701,9 @@ def main():
                          "per launch, --kernel canonical one launch per step)")
     ap.add_argument("--only-batched", default=None, choices=["f32", "f32c", "f64", "f64_df"],
                     help="run only the batched workload in this precision (profiling)")
+    ap.add_argument("--batch-launch", default=None,
+                    help="with --only-batched: a fixed launch shape DEPTH,TILE_ROWS,CTAS_PER_SM instead of the "
+                         "autotuner (profiling)")
     args = ap.parse_args()
 
     world, rank, local, dist = dist_setup(args)
@@ -695,7 +721,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if args.only_batched:
-        res = measure_batch(B, torch, inputs, dev, args.steps, args.warmup, only=args.only_batched)
+        fixed = tuple(int(v) for v in args.batch_launch.split(",")) if args.batch_launch else None
+        res = measure_batch(B, torch, inputs, dev, args.steps, args.warmup, only=args.only_batched, fixed=fixed)
         print(json.dumps({"batched": res}), flush=True)
         return 0
     if args.only_surrogate:

@@ -290,7 +290,10 @@ __device__ __forceinline__ float pow2neg<float>(int e)
     return __int_as_float((127 - e) << 23);
 }
 
-// Kahan sum of an update into (hi, lo).
+// Kahan sum of an update into (hi, lo).  The updates that reach it are
+// explicitly rounded products (__fmul_rn), so the compiler can never fuse a
+// product into the sum: every kernel instantiation and tile geometry then
+// gives the same bits.
 __device__ __forceinline__ void kahan_add(float &hi, float &lo, float delta)
 {
     const float y = delta + lo;
@@ -309,7 +312,7 @@ __device__ __forceinline__ float comp_delta(int j, float self, float lself, floa
     const int pj = partner_reg<Q>(j);
     const bool inside = (j >= sp.jlo) && (j < sp.jhi);
     const bool paired = (pj >= sp.jlo) && (pj < sp.jhi);
-    float val = paired ? d * (partner - self) : km1 * (self + lself);
+    float val = paired ? __fmul_rn(d, partner - self) : __fmul_rn(km1, self + lself);
     if (j == sp.jlo)
         val += fl;
     if (j == sp.jhi - 1)
@@ -331,16 +334,16 @@ __device__ __forceinline__ void mid_comp(float (&v)[K], float (&lo)[K], const Tb
         if (Q == 0) {
 #pragma unroll
             for (int j = 0; j < K; j += 2) {
-                const float t = d * (v[j + 1] - v[j]);
+                const float t = __fmul_rn(d, v[j + 1] - v[j]);
                 kahan_add(v[j], lo[j], t);
                 kahan_add(v[j + 1], lo[j + 1], -t);
             }
         } else {
-            const float t0 = d * (L - v[0]);
-            const float tk = d * (R - v[K - 1]);
+            const float t0 = __fmul_rn(d, L - v[0]);
+            const float tk = __fmul_rn(d, R - v[K - 1]);
 #pragma unroll
             for (int j = 1; j + 1 < K; j += 2) {
-                const float t = d * (v[j + 1] - v[j]);
+                const float t = __fmul_rn(d, v[j + 1] - v[j]);
                 kahan_add(v[j], lo[j], t);
                 kahan_add(v[j + 1], lo[j + 1], -t);
             }

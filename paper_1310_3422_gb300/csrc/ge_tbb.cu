@@ -150,7 +150,7 @@ __device__ __forceinline__ void batch_mid(Real (&v)[K], Real L, Real R, Span sp,
     case J:                                                                 \
         if constexpr ((J) < K) {                                            \
             if (single)                                                     \
-                t[J] = km1 * (v[J] + lo[J]);                                \
+                t[J] = __fmul_rn(km1, v[J] + lo[J]);                        \
             if ((J) == 0 && f.head)                                         \
                 t[J] += fl;                                                 \
             t[J] += fr;                                                     \
@@ -167,16 +167,16 @@ __device__ __forceinline__ void comp_batch_fixed(float (&v)[K], float (&lo)[K], 
     if (Q == 0) {
 #pragma unroll
         for (int j = 0; j < K; j += 2) {
-            const float a = d * (v[j + 1] - v[j]);
+            const float a = __fmul_rn(d, v[j + 1] - v[j]);
             t[j] = a;
             t[j + 1] = -a;
         }
     } else {
-        t[0] = d * (L - v[0]);
-        t[K - 1] = d * (R - v[K - 1]);
+        t[0] = __fmul_rn(d, L - v[0]);
+        t[K - 1] = __fmul_rn(d, R - v[K - 1]);
 #pragma unroll
         for (int j = 1; j + 1 < K; j += 2) {
-            const float a = d * (v[j + 1] - v[j]);
+            const float a = __fmul_rn(d, v[j + 1] - v[j]);
             t[j] = a;
             t[j + 1] = -a;
         }
@@ -184,7 +184,7 @@ __device__ __forceinline__ void comp_batch_fixed(float (&v)[K], float (&lo)[K], 
     // register 0 is the first point: a singleton under grouping 1 (its
     // partner -1 is outside); a one-point problem is the tail too
     if (Q == 1 && f.head)
-        t[0] = km1 * (v[0] + lo[0]);
+        t[0] = __fmul_rn(km1, v[0] + lo[0]);
     if (f.tail >= 0) {
         const bool single = ((f.tail + Q) & 1) == 0;  // partner tail + 1 is outside
         switch (f.tail) {
