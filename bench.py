@@ -608,6 +608,7 @@ def measure_surrogate(B, torch, inputs, train_steps):
     sync()
     ge64.close()
     err_pipe, err_sur, err_ge32 = rel_l2(out, ref), rel_l2(pred, ref), rel_l2(x, ref)
+    tc_used = bool(B.ge_sno_get_tensor_cores(sur.model))
     sur.close()
     chunks = -(-SNO_PROBLEMS // 1024)
     return {
@@ -627,33 +628,51 @@ def measure_surrogate(B, torch, inputs, train_steps):
                      "loss_last": float(losses[-100:].mean())},
         "surrogate_tflops": 2 * SNO_PROBLEMS * SNO_JUMPS * sno_flops_per_problem() / t_sur / 1e12,
         "gpu_launches_surrogate_only": SNO_JUMPS * chunks * sno_launches_per_forward(),
+        "tensor_core_path": tc_used,
     }
 
 
 def measure_sno_forward(torch, inputs, steps, warmup, problems=4096):
     """Forward passes of the surrogate (untrained, BF16 mode) over `problems`
     problems of N = 1024 in chunks of 1024: time per problem and tensor
-    throughput.  For profiling the network's kernels alone."""
+    throughput, on the tensor-core (tcgen05) inference path and on the
+    mma.sync path.  For profiling the network's kernels alone."""
+    from paper_1310_3422_gb300 import binding as B
     from paper_1310_3422_gb300 import surrogate as SG
     pr = inputs.surrogate_problems(problems, SNO_N, seed=inputs.SEED_BASE + 6)
     u0 = torch.tensor(pr.u0, dtype=torch.float32, device="cuda")
     r, bl, br = (torch.tensor(x, dtype=torch.float32, device="cuda") for x in (pr.r, pr.beta_l, pr.beta_r))
     sur = SG.Surrogate(max_batch=1024, seed=0)
     out = torch.empty_like(u0)
-    for _ in range(warmup):
-        sur.predict(u0, r, bl, br, out=out)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        sur.predict(u0, r, bl, br, out=out)
-    e1.record()
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / steps
+    res = {"problems": problems}
+    ref = None
+    for name, on in (("tcgen05", 1), ("mma_sync", 0)):
+        B.ge_sno_set_tensor_cores(sur.model, on)
+        tc = B.ge_sno_get_tensor_cores(sur.model) == 1
+        for _ in range(warmup):
+            sur.predict(u0, r, bl, br, out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            sur.predict(u0, r, bl, br, out=out)
+        e1.record()
+        e1.synchronize()
+        B.ge_sno_sync(sur.model)
+        ms = e0.elapsed_time(e1) / steps
+        net = (out - u0).double()
+        if ref is None:
+            ref = net.clone()
+            agree = 0.0
+        else:
+            agree = float((torch.linalg.vector_norm(net - ref, dim=1) / torch.linalg.vector_norm(ref, dim=1)).max())
+        res[name] = {"tensor_core_path": tc, "ms_per_forward_pass": ms, "us_per_problem": ms * 1e3 / problems,
+                     "tflops": 2 * problems * sno_flops_per_problem() / (ms / 1e3) / 1e12,
+                     "launches": -(-problems // 1024) * sno_launches_per_forward(tc=tc),
+                     "max_rel_diff_of_network_part_vs_tcgen05": agree}
+    B.ge_sno_set_tensor_cores(sur.model, 1)
     sur.close()
-    return {"problems": problems, "ms_per_forward_pass": ms, "us_per_problem": ms * 1e3 / problems,
-            "tflops": 2 * problems * sno_flops_per_problem() / (ms / 1e3) / 1e12,
-            "launches": -(-problems // 1024) * sno_launches_per_forward()}
+    return res
 
 
 def sno_flops_per_problem(n=SNO_N, C=64, M=16, L=4, H=128):
@@ -662,10 +681,13 @@ def sno_flops_per_problem(n=SNO_N, C=64, M=16, L=4, H=128):
     return n * 4 * C + L * per_layer + n * C * H + n * H
 
 
-def sno_launches_per_forward(L=4):
-    """Inference: weight rounding, lift, per layer (spectral weights, DFT,
-    mode mixing, fused layer GEMM), fused projection, fixed-order row sum."""
-    return 2 + 4 * L + 2
+def sno_launches_per_forward(L=4, tc=True):
+    """Inference launches per chunk.  mma.sync path: weight rounding, lift,
+    per layer (spectral weights, DFT, mode mixing, fused layer GEMM), fused
+    projection, fixed-order row sum.  tcgen05 path: weight rounding, L + 1
+    weight transposes, lift, per layer (spectral weights, DFT, mode mixing,
+    spectrum transpose, tensor-core layer), tensor-core projection."""
+    return (1 + (L + 1) + 1 + 5 * L + 1) if tc else (2 + 4 * L + 2)
 
 
 def launches_per_solve(kernel, depth):

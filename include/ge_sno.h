@@ -75,6 +75,26 @@ ge_status ge_sno_set_params(ge_sno *model, const float *src_dev);
 /* split = 0: BF16 operands (default); split = 1: two-part BF16 operands. */
 ge_status ge_sno_set_precision(ge_sno *model, int32_t split);
 
+/* Inference on the fifth-generation tensor cores (on = 1, the default):
+ * with BF16 operands (split = 0) and the shape its kernels are built for
+ * (width 64, 16 modes, hidden 128, n a multiple of 128), forward passes that
+ * keep no training state (ge_sno_forward) run each fused layer (inverse DFT
+ * + pointwise path + bias + GELU) and the projection (hidden layer + GELU +
+ * output dot product + residual) as tcgen05 MMAs with TMEM accumulators and
+ * TMA-loaded operands; the truncated DFT and the mode mixing stay on the
+ * mma.sync GEMM.  Same model and operands as the other path; results differ
+ * only by FP32 accumulation order (and the BF16 rounding that follows it).
+ * on = 0 uses the mma.sync GEMM throughout.  Errors: GE_EINVAL. */
+ge_status ge_sno_set_tensor_cores(ge_sno *model, int32_t on);
+/* *active = 1 when forward passes take the tensor-core path.  Errors: GE_EINVAL. */
+ge_status ge_sno_get_tensor_cores(const ge_sno *model, int32_t *active);
+
+/* Wait for the model's stream and report a deferred device failure: a
+ * bounded wait of a tensor-core kernel that gave up (GE_ETIMEOUT; the
+ * outputs of that pass are not valid; reported once).  Errors: GE_EINVAL,
+ * GE_ECUDA, GE_ETIMEOUT. */
+ge_status ge_sno_sync(ge_sno *model);
+
 /* Prediction for `batch` problems (1 <= batch <= max_batch): pred_dev
  * [batch][n] receives the approximate state after K steps. */
 ge_status ge_sno_forward(ge_sno *model, int32_t batch, const float *u0_dev, const float *r_dev,

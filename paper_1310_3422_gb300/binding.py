@@ -32,7 +32,7 @@ EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", 
            "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error", "ge_debug_stall",
            "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune", "ge_probe_fma",
            "ge_sno_create", "ge_sno_num_params", "ge_sno_get_params", "ge_sno_set_params",
-           "ge_sno_set_precision", "ge_sno_forward", "ge_sno_loss_grad", "ge_sno_adam_step",
+           "ge_sno_set_precision", "ge_sno_set_tensor_cores", "ge_sno_get_tensor_cores", "ge_sno_sync", "ge_sno_forward", "ge_sno_loss_grad", "ge_sno_adam_step",
            "ge_sno_train_step", "ge_sno_rows_nonfinite", "ge_sno_rows_gather", "ge_sno_rows_scatter",
            "ge_sno_rows_rel_err", "ge_sno_destroy")
 
@@ -119,6 +119,12 @@ def load(path: str | None = None):
         lib.ge_probe_fma.restype = ctypes.c_int
         lib.ge_sno_create.argtypes = [ctypes.POINTER(_VP), _I32, _I32, _I32, _I32, _I32, _I32, ctypes.c_uint64, _VP]
         lib.ge_sno_create.restype = ctypes.c_int
+        lib.ge_sno_set_tensor_cores.argtypes = [_VP, _I32]
+        lib.ge_sno_set_tensor_cores.restype = ctypes.c_int
+        lib.ge_sno_get_tensor_cores.argtypes = [_VP, ctypes.POINTER(_I32)]
+        lib.ge_sno_get_tensor_cores.restype = ctypes.c_int
+        lib.ge_sno_sync.argtypes = [_VP]
+        lib.ge_sno_sync.restype = ctypes.c_int
         lib.ge_sno_num_params.argtypes = [_VP, ctypes.POINTER(_I64)]
         lib.ge_sno_num_params.restype = ctypes.c_int
         lib.ge_sno_get_params.argtypes = [_VP, _VP]
@@ -555,6 +561,21 @@ def ge_sno_set_params(model: Sno, src):
 
 def ge_sno_set_precision(model: Sno, split: int):
     _check(load().ge_sno_set_precision(model.handle, int(split)), "ge_sno_set_precision")
+
+
+def ge_sno_set_tensor_cores(model: Sno, on: int):
+    """1: fused layers and projection of inference on tcgen05 (where the shape allows); 0: mma.sync only."""
+    _check(load().ge_sno_set_tensor_cores(model.handle, int(on)), "ge_sno_set_tensor_cores")
+
+
+def ge_sno_get_tensor_cores(model: Sno) -> int:
+    v = _I32()
+    _check(load().ge_sno_get_tensor_cores(model.handle, ctypes.byref(v)), "ge_sno_get_tensor_cores")
+    return int(v.value)
+
+
+def ge_sno_sync(model: Sno):
+    _check(load().ge_sno_sync(model.handle), "ge_sno_sync")
 
 
 def _sno_inputs(model: Sno, batch: int, u0, r, beta_l, beta_r):

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(PKG, "libge.so")
 
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["ge_canon.cu", "ge_tb.cu", "ge_tb_df.cu", "ge_tbb.cu", "ge_tbb_df.cu", "ge_sweep.cu", "ge_noalloc.cu", "ge_sno_kernels.cu", "ge_probe.cu"]
+CU_SOURCES = ["ge_canon.cu", "ge_tb.cu", "ge_tb_df.cu", "ge_tbb.cu", "ge_tbb_df.cu", "ge_sweep.cu", "ge_noalloc.cu", "ge_sno_kernels.cu", "ge_sno_tc.cu", "ge_probe.cu"]
 CPP_SOURCES = ["ge_api.cpp", "ge_tb_plan.cpp", "ge_batch.cpp", "ge_sno.cpp"]
 
 

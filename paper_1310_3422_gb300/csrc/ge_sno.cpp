@@ -20,12 +20,15 @@
 // q1 [H], Q2 [H], q2 [1].
 #include "ge_sno.h"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime_api.h>
 
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -79,6 +82,17 @@ struct ge_sno {
     float *out = nullptr, *dout = nullptr, *loss = nullptr;  // [B n], [B n], [B]
     float *dA = nullptr, *dB = nullptr;   // [B n][max(C, H)] gradient scratch
     float *dvh = nullptr;                 // [B][2M][C]
+    // tensor-core inference path (ge_sno_tc.cu; plain mode, C = 64, 2M = 32,
+    // H = 128, n a multiple of 128): transposed B operands and tensor maps
+    bool tc = true;                       // use it where the shape allows
+    bool tc_ready = false;                // tensor maps encoded
+    int num_sms = 0;
+    void *yt = nullptr;                   // [max_batch][C][2M] BF16
+    void *wt = nullptr;                   // [L][C out][C in] BF16
+    void *q1t = nullptr;                  // [H][C] BF16
+    int *err = nullptr;                   // device error word of the tensor-core kernels
+    CUtensorMap tm_g, tm_yt, tm_wt, tm_q1t;
+    std::vector<CUtensorMap> tm_v;        // one per activation buffer v[0..L]
     std::vector<void *> allocs;
 };
 
@@ -157,6 +171,50 @@ ge_status weight_grad(ge_sno *s, const void *X, int in, int ldx, const void *dY,
     return GE_OK;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2D BF16 tensor map over [rows][cols] (row pitch cols * 2 bytes) with a
+// box of box_cols x box_rows and the swizzle matching box_cols * 2 bytes.
+bool bf16_map(CUtensorMap *m, void *base, long long rows, int cols, int box_cols, int box_rows)
+{
+    auto enc = tmap_encoder();
+    if (!enc)
+        return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapSwizzle sw = box_cols * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The tensor-core inference path applies: plain mode and the shape its
+// kernels are built for.
+bool tc_shape(const ge_sno *s)
+{
+    return s->C == 64 && 2 * s->M == 32 && s->H == 128 && s->n % 128 == 0;
+}
+bool tc_active(const ge_sno *s) { return s->tc && !s->split && tc_shape(s) && s->tc_ready; }
+
+// Inference with the tensor-core kernels for the fused layers and the
+// projection (the truncated DFT and the mode mixing keep the mma.sync GEMM).
+ge_status forward_tc(ge_sno *s, int B, const float *u0, const float *r, const float *bl, const float *br,
+                     float *out);
+
 // Forward pass for B problems into out ([B n], FP32).  keep: also store the
 // pre-activations the backward pass needs (training).
 ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float *bl, const float *br, float *out,
@@ -169,6 +227,8 @@ ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float
     const float *P = s->pw;  // FP32 rounded weights: biases and the spectral matrices' source
     const void *F = bf ? s->F16 : static_cast<const void *>(s->F);
     const void *G = bf ? s->G16 : static_cast<const void *>(s->G);
+    if (!keep && tc_active(s))
+        return forward_tc(s, B, u0, r, bl, br, out);
     SNO_TRY(ge::sno_round_bf16(s->params, s->pw, bf ? s->pw16 : nullptr, s->n_params, st));
     // lift (K = 4: no GEMM); the features themselves only for the backward pass
     if (keep)
@@ -240,6 +300,61 @@ ge_status forward(ge_sno *s, int B, const float *u0, const float *r, const float
     g.beta = 1.0f;
     act_fmt(g, bf).out_bf16 = 0;
     SNO_TRY(ge::sno_gemm(g, 1, s->split, st));
+    return GE_OK;
+}
+
+ge_status forward_tc(ge_sno *s, int B, const float *u0, const float *r, const float *bl, const float *br,
+                     float *out)
+{
+    const int n = s->n, C = s->C, M = s->M, H = s->H;
+    const long long R = (long long)B * n;
+    cudaStream_t st = s->stream;
+    const float *P = s->pw;
+    SNO_TRY(ge::sno_round_bf16(s->params, s->pw, s->pw16, s->n_params, st));
+    // K-major copies of the B operands: W^T per layer, Q1^T
+    for (int l = 0; l < s->L; ++l)
+        SNO_TRY(ge::sno_transpose_rows(at(s->pw16, s->lay[l].w, true), at(s->wt, (long long)l * C * C, true), 1, C,
+                                       C, st));
+    SNO_TRY(ge::sno_transpose_rows(at(s->pw16, s->off_q1, true), s->q1t, 1, C, H, st));
+    SNO_TRY(ge::sno_lift(u0, r, bl, br, weight(s, s->off_w0), P + s->off_b0, s->v[0], B, n, C, 1, st));
+    ge::GemmArgs g;
+    ge::SnoTcArgs a{};
+    a.n_tiles = R / 128;
+    a.tiles_per_problem = n / 128;
+    a.err = s->err;
+    a.limit = ge::kWaitLimitCycles;
+    for (int l = 0; l < s->L; ++l) {
+        const LayerOff &o = s->lay[l];
+        void *ws = at(s->wspec, (long long)l * M * 4 * C * C, true);
+        SNO_TRY(ge::sno_spec_assemble(P + o.rr, P + o.ri, ws, M, C, 1, st));
+        g = gemm(s->F16, n, 1, s->v[l], C, 1, s->vh[l], C, 2 * M, C, n);
+        g.sA = 0;
+        g.sB = (long long)n * C;
+        g.sC = 2LL * M * C;
+        SNO_TRY(ge::sno_gemm(act_fmt(g, true), B, false, st));
+        g = gemm(s->vh[l], 2LL * M * C, 1, ws, 2 * C, 1, s->y, 2LL * M * C, B, 2 * C, 2 * C);
+        g.sA = 2 * C;
+        g.sB = 4LL * C * C;
+        g.sC = 2 * C;
+        SNO_TRY(ge::sno_gemm(act_fmt(g, true), M, false, st));
+        // y [B][2M][C] -> y^T [B][C][2M] (K-major B operand of G y)
+        SNO_TRY(ge::sno_transpose_rows(s->y, s->yt, B, 2 * M, C, st));
+        a.b2_row = l * C;
+        a.gelu = l < s->L - 1 ? 1 : 0;
+        a.bias = P + o.b;
+        a.out = s->v[l + 1];
+        const ge::SnoTcMaps m{&s->tm_g, &s->tm_yt, &s->tm_v[l], &s->tm_wt};
+        SNO_TRY(ge::sno_tc_layer(m, a, s->num_sms, st));
+    }
+    a.b2_row = 0;
+    a.gelu = 1;
+    a.bias = P + s->off_qb1;
+    a.q2w = P + s->off_q2;
+    a.q2b = P + s->off_qb2;
+    a.u0 = u0;
+    a.out = out;
+    const ge::SnoTcMaps m{nullptr, nullptr, &s->tm_v[s->L], &s->tm_q1t};
+    SNO_TRY(ge::sno_tc_projection(m, a, s->num_sms, st));
     return GE_OK;
 }
 
@@ -452,9 +567,31 @@ ge_status ge_sno_create(ge_sno **out, int32_t n, int32_t width, int32_t modes, i
     e = e ? e : alloc(&s->loss, max_batch);
     e = e ? e : alloc(&s->dA, R * (C > H ? C : H));
     e = e ? e : alloc(&s->dB, R * (C > H ? C : H));
+    e = e ? e : alloc_bytes(&s->yt, 2LL * max_batch * 2 * M * C);
+    e = e ? e : alloc_bytes(&s->wt, 2LL * layers * C * C);
+    e = e ? e : alloc_bytes(&s->q1t, 2LL * H * C);
+    e = e ? e : alloc_bytes(reinterpret_cast<void **>(&s->err), 256);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(s->err, 0, 256, s->stream);
+    int dev = 0;
+    if (e == cudaSuccess)
+        e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) {
         release_sno(s);
         return scuda(e, "ge_sno_create: device allocation");
+    }
+    if (tc_shape(s)) {
+        // tensor maps of the tensor-core path (BF16 views of the buffers)
+        bool ok = bf16_map(&s->tm_g, s->G16, n, 2 * modes, 2 * modes, 128) &&
+                  bf16_map(&s->tm_yt, s->yt, (long long)max_batch * C, 2 * modes, 2 * modes, 64) &&
+                  bf16_map(&s->tm_wt, s->wt, (long long)layers * C, width, width, 64) &&
+                  bf16_map(&s->tm_q1t, s->q1t, hidden, width, width, 128);
+        s->tm_v.resize(layers + 1);
+        for (int l = 0; l <= layers && ok; ++l)
+            ok = bf16_map(&s->tm_v[l], s->v[l], R, width, width, 128);
+        s->tc_ready = ok;
     }
     // DFT bases: F[2m][j] = cos(2 pi m j / n), F[2m+1][j] = -sin(...);
     // G[j][2m] = w_m cos(...), G[j][2m+1] = -w_m sin(...), w_0 = 1/n, w_m = 2/n
@@ -544,6 +681,39 @@ ge_status ge_sno_set_precision(ge_sno *s, int32_t split)
     if (!s || (split != 0 && split != 1))
         return sfail(GE_EINVAL, "ge_sno_set_precision: NULL model or mode not 0/1");
     s->split = split != 0;
+    return GE_OK;
+}
+
+ge_status ge_sno_set_tensor_cores(ge_sno *s, int32_t on)
+{
+    if (!s || (on != 0 && on != 1))
+        return sfail(GE_EINVAL, "ge_sno_set_tensor_cores: NULL model or value not 0/1");
+    s->tc = on != 0;
+    return GE_OK;
+}
+
+ge_status ge_sno_get_tensor_cores(const ge_sno *s, int32_t *active)
+{
+    if (!s || !active)
+        return sfail(GE_EINVAL, "ge_sno_get_tensor_cores: NULL argument");
+    *active = tc_active(s) ? 1 : 0;
+    return GE_OK;
+}
+
+ge_status ge_sno_sync(ge_sno *s)
+{
+    if (!s)
+        return sfail(GE_EINVAL, "ge_sno_sync: NULL model");
+    int word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, s->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess)
+        return scuda(e, "ge_sno_sync");
+    if (word == ge::kDevTimeout) {
+        cudaMemsetAsync(s->err, 0, sizeof(int), s->stream);
+        return sfail(GE_ETIMEOUT, "ge_sno: a tensor-core kernel's wait did not complete within the limit");
+    }
     return GE_OK;
 }
 

@@ -58,6 +58,36 @@ struct GemmArgs {
 };
 
 cudaError_t sno_gemm(const GemmArgs &g, int batch, bool split, cudaStream_t s);
+
+// Tensor-core (tcgen05) inference GEMMs of ge_sno_tc.cu, over 128-row tiles
+// of the activation rows (rows = batch * n, n a multiple of 128, C = 64
+// channels, 2M = 32 spectral rows, H = 128 hidden columns).  Tensor maps
+// (CUtensorMap, 64-byte aligned, opaque here), all BF16 and K-major:
+//   layer:      a1 = G [n][2M] (box 32 x 128, 64-byte swizzle), b1 = y^T
+//               [batch * C][2M] (box 32 x 64, 64-byte swizzle), a2 = v
+//               [rows][C] (box 64 x 128, 128-byte swizzle), b2 = W^T of all
+//               layers [L * C][C] (box 64 x 64, 128-byte swizzle);
+//   projection: a2 = v as above, b2 = Q1^T [H][C] (box 64 x 128).
+struct SnoTcMaps {
+    const void *a1, *b1, *a2, *b2;
+};
+struct SnoTcArgs {
+    long long n_tiles;      // rows / 128
+    int tiles_per_problem;  // n / 128
+    int b2_row;             // first row of this call's B2 block (layer * C; 0 for Q1^T)
+    int gelu;               // layer: GELU after the bias (not after the last layer)
+    const float *bias;      // layer: b [C]; projection: q1 [H]
+    const float *q2w;       // projection: Q2 [H]
+    const float *q2b;       // projection: q2 [1]
+    const float *u0;        // projection: u0 [rows]
+    void *out;              // layer: next activation, BF16 [rows][C]; projection: FP32 [rows]
+    int *err;               // device error word (GE_ETIMEOUT on a wait that gave up)
+    long long limit;        // wait limit in SM cycles
+};
+cudaError_t sno_tc_layer(const SnoTcMaps &m, const SnoTcArgs &a, int sms, cudaStream_t s);
+cudaError_t sno_tc_projection(const SnoTcMaps &m, const SnoTcArgs &a, int sms, cudaStream_t s);
+// yt[b][c][k] = y[b][k][c] for BF16 [batch][k_rows][c_cols] blocks.
+cudaError_t sno_transpose_rows(const void *y, void *yt, long long batch, int k_rows, int c_cols, cudaStream_t s);
 cudaError_t sno_features(const float *u0, const float *r, const float *bl, const float *br, void *f, int batch,
                          int n, int bf16, cudaStream_t s);
 cudaError_t sno_spec_assemble(const float *rr, const float *ri, void *w, int modes, int c, int bf16, cudaStream_t s);

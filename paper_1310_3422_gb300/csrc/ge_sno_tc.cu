@@ -1,0 +1,471 @@
+// ge_sno_tc.cu -- the surrogate's inference GEMMs on the fifth-generation
+// tensor cores: tcgen05.mma with the accumulator in tensor memory (TMEM),
+// operands staged in shared memory by 2D TMA copies, and the epilogue fused.
+// The paper has no counterpart (the surrogate is a deployment variant of the
+// GE solve; see ge_sno.h for the model).
+//
+// Two kernels of one template, each over 128-row tiles of the activation
+// rows (all problems' grid points, [rows][64] BF16, channel last):
+//   layer (MODE 0):  pre = G y + v W + b, then GELU (not after the last
+//       layer), written as the next BF16 activation.  G [n][2M] is the
+//       inverse truncated DFT, y [2M][C] the mode-mixed spectrum of the
+//       tile's problem, v the tile's activations, W [C][C] the pointwise
+//       weights.  Two products accumulate into one TMEM tile: K = 2M = 32
+//       (G y) and K = C = 64 (v W).
+//   projection (MODE 1): out = u0 + q2 + sum_h GELU(v Q1 + q1)_h Q2_h, one
+//       FP32 value per row; the hidden layer (N = H = 128) lives in TMEM
+//       only, and each thread sums its row in a fixed order.
+//
+// Operands are K-major with 128-byte (C = 64 BF16) or 64-byte (2M = 32 BF16)
+// rows, TMA-swizzled (SWIZZLE_128B / SWIZZLE_64B) as the tensor cores read
+// them: B operands are the transposed copies y^T [C][2M], W^T [C][C],
+// Q1^T [H][C], written by small kernels below.  One MMA instruction covers
+// 128 rows x N columns x 16 of K.
+//
+// Warp roles (160 threads): warp 4 lane 0 is the producer: it issues the TMA
+// loads of a stage (two stages) and, once they land, the MMAs of the tile
+// into one of two TMEM accumulators, then commits them to an mbarrier.
+// Warps 0-3 drain the accumulator of a finished tile (warp w reads TMEM
+// lanes 32w .. 32w + 31, i.e. tile rows) with tcgen05.ld, hand it back, and
+// run the epilogue.  So the loads of tile i+1 and the MMAs of tile i+1 run
+// under the epilogue of tile i.
+//
+// Every wait is bounded: on expiry the kernel records GE_ETIMEOUT in the
+// device error word, stops every role at its next wait, lets its own copies
+// and MMAs in flight finish (each wait bounded again), frees its TMEM and
+// returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ge_internal.h"
+#include "ge_sno_internal.h"
+
+namespace ge {
+namespace {
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void bar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool bar_try(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity`; false after `limit` cycles or once the CTA aborts.
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity, long long limit, volatile int *abort)
+{
+    const long long t0 = clock64();
+    while (!bar_try(bar, parity)) {
+        if (*abort || clock64() - t0 > limit)
+            return false;
+    }
+    return true;
+}
+
+// Same, ignoring the abort flag (draining this CTA's own work before exit).
+__device__ __forceinline__ void bar_drain(uint64_t *bar, uint32_t parity, long long limit)
+{
+    const long long t0 = clock64();
+    while (!bar_try(bar, parity) && clock64() - t0 <= limit) {
+    }
+}
+
+__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(saddr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
+        : "memory");
+}
+
+// ---- tcgen05 -------------------------------------------------------------
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(dst)), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] B[smem]^T, BF16 x BF16 -> FP32, one CTA.
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// Arrive on `bar` once every MMA this thread issued so far has completed.
+__device__ __forceinline__ void tc_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+                 : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand tile whose rows of
+// `row_bytes` (128 or 64) are TMA-swizzled with the same width: groups of 8
+// rows lie 8 * row_bytes apart (stride byte offset), the leading byte offset
+// is unused for a swizzled K-major tile, bits 46-47 hold the descriptor
+// version (1), bits 61-63 the swizzle (2: 128-byte, 4: 64-byte).  The tile
+// starts on a 1024-byte boundary; a K step of 16 BF16 (32 bytes) inside the
+// swizzle row advances the start address.
+__device__ __forceinline__ uint64_t smem_desc(const void *tile, uint32_t row_bytes)
+{
+    const uint64_t addr = saddr(tile);
+    const uint64_t layout = row_bytes == 128 ? 2 : 4;
+    return ((addr & 0x3FFFF) >> 4) | (1ull << 16) | ((uint64_t)((8 * row_bytes) >> 4) << 32) | (1ull << 46) |
+           (layout << 61);
+}
+
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits
+// 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ float gelu_hw(float x)
+{
+    const float k0 = 0.7978845608028654f, k1 = 0.044715f;
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(k0 * (x + k1 * x * x * x)));
+    return 0.5f * x * (1.0f + t);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half), .y = b
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+constexpr int kTcThreads = 160;
+constexpr int kTileM = 128;
+
+template <int MODE>
+struct TcShape {
+    static constexpr int N = MODE == 0 ? 64 : 128;                  // output columns (TMEM columns per stage)
+    static constexpr uint32_t kA2 = kTileM * 128;                    // v tile: 128 rows x 64 BF16
+    static constexpr uint32_t kA1 = MODE == 0 ? kTileM * 64 : 0;     // G tile: 128 rows x 32 BF16
+    static constexpr uint32_t kB1 = MODE == 0 ? 64 * 64 : 0;         // y^T: 64 rows x 32 BF16
+    static constexpr uint32_t kStage = kA2 + kA1 + kB1;              // bytes of one stage (x1024)
+    static constexpr uint32_t kB2 = N * 128;                         // W^T (64 rows) or Q1^T (128 rows)
+    static constexpr uint32_t kTmemCols = 2 * N;
+    // MODE 1 holds 256 TMEM columns: its shared memory keeps it at 2 CTAs per SM
+    static constexpr int kSmem = MODE == 0 ? (int)(2 * kStage + kB2 + 1024) : 80 * 1024;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kTcThreads) sno_tc_kernel(const __grid_constant__ CUtensorMap tmA1,
+                                                            const __grid_constant__ CUtensorMap tmB1,
+                                                            const __grid_constant__ CUtensorMap tmA2,
+                                                            const __grid_constant__ CUtensorMap tmB2,
+                                                            const __grid_constant__ SnoTcArgs P)
+{
+    using S = TcShape<MODE>;
+    constexpr int N = S::N;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    unsigned char *b2 = sm + 2 * S::kStage;
+    __shared__ __align__(8) uint64_t full[2], mma_done[2], acc_empty[2], b2_full;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ float s_bias[N], s_q2[N];
+    __shared__ volatile int s_abort;
+
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (t == 0) {
+        for (int s = 0; s < 2; ++s) {
+            bar_init(&full[s], 1);
+            bar_init(&mma_done[s], 1);
+            bar_init(&acc_empty[s], 4);
+        }
+        bar_init(&b2_full, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_base_sh, S::kTmemCols);
+        tmem_relinquish();
+    }
+    for (int i = t; i < N; i += kTcThreads) {
+        s_bias[i] = P.bias[i];
+        s_q2[i] = MODE == 1 ? P.q2w[i] : 0.0f;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tmem_base_sh;
+    const long long my_tiles =
+        P.n_tiles > (long long)blockIdx.x ? (P.n_tiles - 1 - (long long)blockIdx.x) / gridDim.x + 1 : 0;
+
+    if (warp == 4) {
+        if (lane == 0 && my_tiles > 0) {
+            // ---- producer: TMA loads and MMA issue ----------------------
+            constexpr uint32_t idesc = idesc_bf16(kTileM, N);
+            auto load_stage = [&](int s, long long i) {
+                const long long g = (long long)blockIdx.x + i * gridDim.x;
+                unsigned char *st = sm + s * S::kStage;
+                bar_expect_tx(&full[s], S::kStage);
+                tma_2d(st, &tmA2, 0, (int)(g * kTileM), &full[s]);
+                if (MODE == 0) {
+                    const long long b = g / P.tiles_per_problem, tt = g % P.tiles_per_problem;
+                    tma_2d(st + S::kA2, &tmA1, 0, (int)(tt * kTileM), &full[s]);
+                    tma_2d(st + S::kA2 + S::kA1, &tmB1, 0, (int)(b * 64), &full[s]);
+                }
+            };
+            bar_expect_tx(&b2_full, S::kB2);
+            tma_2d(b2, &tmB2, 0, P.b2_row, &b2_full);
+            load_stage(0, 0);
+            long long issued = 0, committed = 0;  // stages loaded, tiles committed
+            bool ok = bar_wait(&b2_full, 0, P.limit, &s_abort);
+            for (long long i = 0; ok && i < my_tiles; ++i) {
+                const int s = (int)(i & 1);
+                if (i + 1 < my_tiles) {
+                    const int s1 = (int)((i + 1) & 1);
+                    // stage s1 is free once the MMAs of tile i - 1 (which read it) are done
+                    if (i >= 1 && !(ok = bar_wait(&mma_done[s1], (uint32_t)(((i - 1) >> 1) & 1), P.limit, &s_abort)))
+                        break;
+                    load_stage(s1, i + 1);
+                    issued = i + 1;
+                }
+                if (!(ok = bar_wait(&full[s], (uint32_t)((i >> 1) & 1), P.limit, &s_abort)))
+                    break;
+                // accumulator s is free once the epilogue of tile i - 2 has read it
+                if (i >= 2 && !(ok = bar_wait(&acc_empty[s], (uint32_t)(((i - 2) >> 1) & 1), P.limit, &s_abort)))
+                    break;
+                tc_fence_after();
+                const uint32_t acc = tbase + (uint32_t)(s * N);
+                unsigned char *st = sm + s * S::kStage;
+                const uint64_t a2 = smem_desc(st, 128), bw = smem_desc(b2, 128);
+                if (MODE == 0) {
+                    const uint64_t a1 = smem_desc(st + S::kA2, 64), b1 = smem_desc(st + S::kA2 + S::kA1, 64);
+                    tc_mma(acc, a1, b1, idesc, 0);
+                    tc_mma(acc, a1 + 2, b1 + 2, idesc, 1);  // K step of 32 bytes = 2 in address units
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    tc_mma(acc, a2 + 2 * k, bw + 2 * k, idesc, (MODE == 0 || k > 0) ? 1u : 0u);
+                tc_commit(&mma_done[s]);
+                committed = i + 1;
+            }
+            if (!ok) {
+                atomicExch(P.err, kDevTimeout);
+                s_abort = 1;
+                // this CTA's own work in flight: the loads it issued and the
+                // MMAs it committed
+                bar_drain(&b2_full, 0, kWaitLimitCycles);
+                for (long long j = committed; j <= issued; ++j)
+                    bar_drain(&full[j & 1], (uint32_t)((j >> 1) & 1), kWaitLimitCycles);
+                if (committed > 0)
+                    bar_drain(&mma_done[(committed - 1) & 1], (uint32_t)(((committed - 1) >> 1) & 1),
+                              kWaitLimitCycles);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue warps 0-3: TMEM lanes 32 warp .. 32 warp + 31 ------
+        for (long long i = 0; i < my_tiles; ++i) {
+            const int s = (int)(i & 1);
+            const bool ok = bar_wait(&mma_done[s], (uint32_t)((i >> 1) & 1), P.limit, &s_abort);
+            if (__any_sync(0xffffffffu, !ok)) {
+                if (lane == 0 && !s_abort) {
+                    atomicExch(P.err, kDevTimeout);
+                    s_abort = 1;
+                }
+                break;
+            }
+            tc_fence_after();
+            const long long g = (long long)blockIdx.x + i * gridDim.x;
+            const long long row = g * kTileM + warp * 32 + lane;
+            const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * N);
+            if (MODE == 0) {
+                uint32_t r0[32], r1[32];
+                tmem_ld32(taddr, r0);
+                tmem_ld32(taddr + 32, r1);
+                tmem_wait_ld();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    bar_arrive(&acc_empty[s]);
+                uint4 *dst = reinterpret_cast<uint4 *>(static_cast<unsigned char *>(P.out) + row * 128);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t *r = h ? r1 : r0;
+                    uint32_t w[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        float a = __uint_as_float(r[2 * c]) + s_bias[32 * h + 2 * c];
+                        float b = __uint_as_float(r[2 * c + 1]) + s_bias[32 * h + 2 * c + 1];
+                        if (P.gelu) {
+                            a = gelu_hw(a);
+                            b = gelu_hw(b);
+                        }
+                        w[c] = pack_bf16(a, b);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        dst[4 * h + q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+                }
+            } else {
+                float sum = 0.0f;
+#pragma unroll
+                for (int h = 0; h < N / 32; ++h) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + 32 * h, r);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int c = 0; c < 32; ++c)
+                        sum += gelu_hw(__uint_as_float(r[c]) + s_bias[32 * h + c]) * s_q2[32 * h + c];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    bar_arrive(&acc_empty[s]);
+                float *out = static_cast<float *>(P.out);
+                out[row] = P.u0[row] + P.q2b[0] + sum;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        tmem_dealloc(tbase, S::kTmemCols);
+}
+
+// yT[b][c][k] = y[b][k][c]  (BF16, K = 2M rows, C columns per problem)
+__global__ void transpose_rows_kernel(const __nv_bfloat16 *__restrict__ y, __nv_bfloat16 *__restrict__ yt,
+                                      long long batch, int k_rows, int c_cols)
+{
+    const long long total = batch * k_rows * c_cols;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long b = e / ((long long)k_rows * c_cols);
+        const int rem = (int)(e - b * k_rows * c_cols);
+        const int c = rem / k_rows, k = rem % k_rows;
+        yt[e] = y[(b * k_rows + k) * c_cols + c];
+    }
+}
+
+template <int MODE>
+cudaError_t launch_tc(const SnoTcMaps &m, const SnoTcArgs &a, int sms, cudaStream_t s)
+{
+    using S = TcShape<MODE>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(sno_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             S::kSmem);
+        if (e != cudaSuccess)
+            return e;
+        attr_set = true;
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sno_tc_kernel<MODE>, kTcThreads, S::kSmem);
+    if (e != cudaSuccess)
+        return e;
+    // TMEM: at most 512 columns per SM between the co-resident CTAs
+    const int tmem_cap = 512 / (int)S::kTmemCols;
+    if (per_sm > tmem_cap)
+        per_sm = tmem_cap;
+    if (per_sm < 1)
+        return cudaErrorInvalidConfiguration;
+    long long grid = (long long)sms * per_sm;
+    if (grid > a.n_tiles)
+        grid = a.n_tiles;
+    if (grid < 1)
+        return cudaSuccess;
+    if (!m.a2 || !m.b2 || (MODE == 0 && (!m.a1 || !m.b1)))
+        return cudaErrorInvalidValue;
+    // the projection has no first product: its a1 / b1 parameters repeat a2
+    const CUtensorMap *a1 = static_cast<const CUtensorMap *>(MODE == 0 ? m.a1 : m.a2);
+    const CUtensorMap *b1 = static_cast<const CUtensorMap *>(MODE == 0 ? m.b1 : m.a2);
+    sno_tc_kernel<MODE><<<(int)grid, kTcThreads, S::kSmem, s>>>(*a1, *b1, *static_cast<const CUtensorMap *>(m.a2),
+                                                              *static_cast<const CUtensorMap *>(m.b2), a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t sno_tc_layer(const SnoTcMaps &m, const SnoTcArgs &a, int sms, cudaStream_t s)
+{
+    return launch_tc<0>(m, a, sms, s);
+}
+
+cudaError_t sno_tc_projection(const SnoTcMaps &m, const SnoTcArgs &a, int sms, cudaStream_t s)
+{
+    return launch_tc<1>(m, a, sms, s);
+}
+
+cudaError_t sno_transpose_rows(const void *y, void *yt, long long batch, int k_rows, int c_cols, cudaStream_t s)
+{
+    const long long total = batch * k_rows * c_cols;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 4096)
+        blocks = 4096;
+    if (blocks < 1)
+        return cudaSuccess;
+    transpose_rows_kernel<<<(int)blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(y),
+                                                       static_cast<__nv_bfloat16 *>(yt), batch, k_rows, c_cols);
+    return cudaGetLastError();
+}
+
+}  // namespace ge

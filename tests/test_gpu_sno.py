@@ -264,3 +264,38 @@ def test_arbiter_row_helpers_match_numpy():
             w = np.linalg.norm(d) / np.linalg.norm(ref[i].astype(np.float64))
             assert abs(got[i] - w) <= 1e-6 * w
     B.ge_sno_destroy(m)
+
+
+@pytest.mark.parametrize("batch", [1, 3, 600])
+def test_tensor_core_path_matches_the_mma_path(batch):
+    """Inference on the tcgen05 path (fused layers and projection as
+    tensor-core MMAs with TMEM accumulators) computes the same BF16 network
+    as the mma.sync path: the network's part of the prediction (pred - u0)
+    agrees to 1e-2 relative L2 per problem (only FP32 accumulation order, and
+    the BF16 roundings after it, differ), and small batches also match the
+    FP64 reference at the BF16 tolerance.  600 problems make 4800 row tiles,
+    several per CTA, so both stages and both accumulators are reused."""
+    m = make_model(FULL, batch, seed=3, split=0)
+    assert B.ge_sno_get_tensor_cores(m) == 1
+    u0, r, bl, br = problem_batch(FULL, batch, 17)
+    args = dev(u0, r, bl, br)
+    p_tc = torch.empty(batch, FULL.n, dtype=torch.float32, device=DEV)
+    B.ge_sno_forward(m, batch, *args, p_tc)
+    B.ge_sno_sync(m)
+    B.ge_sno_set_tensor_cores(m, 0)
+    assert B.ge_sno_get_tensor_cores(m) == 0
+    p_mma = torch.empty_like(p_tc)
+    B.ge_sno_forward(m, batch, *args, p_mma)
+    B.ge_sno_sync(m)
+    B.ge_sno_set_tensor_cores(m, 1)
+    B.ge_sno_set_precision(m, 1)
+    assert B.ge_sno_get_tensor_cores(m) == 0   # split mode keeps the mma.sync path
+    B.ge_sno_set_precision(m, 0)
+    a_tc, a_mma = p_tc.cpu().numpy().astype(np.float64), p_mma.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(a_tc))
+    err = rel_rows(a_tc - u0, a_mma - u0)
+    assert np.all(err <= 1e-2), err.max()
+    if batch <= 3:
+        want = S.predict(oracle_params(m), FULL, u0, r, bl, br)
+        assert np.all(rel_rows(a_tc, want) <= 3e-2)
+    B.ge_sno_destroy(m)
