@@ -632,6 +632,82 @@ def measure_surrogate(B, torch, inputs, train_steps):
     }
 
 
+SNO_SWEEP_K = (256, 1024, 4096, 16384)
+
+
+def measure_surrogate_k_sweep(B, torch, inputs, train_steps, Ks=SNO_SWEEP_K, problems=16384, jumps=2):
+    """Where the surrogate can pay: for each jump length K, a surrogate trained
+    for K (100k pairs from 12,500 FP32 GE trajectories of 8 jumps, same
+    network and schedule as the main surrogate run) advances `problems`
+    fresh problems (N = 1024, r U[0.5, 4], same u0 distribution) by `jumps`
+    jumps, alone and inside the GE fallback pipeline (1 % sample, tolerance
+    1e-3 relative L2), against plain batched FP32 GE (depth and geometry
+    autotuned) on the same problems.  rows_within_tol: the share of problems
+    whose surrogate-only result is within the tolerance of GE's (FP32 GE's
+    own error, ~1e-6, is far below it).  Times: best of 3 (GE) or one run
+    after a warm-up, device-synchronised wall clock."""
+    from paper_1310_3422_gb300 import surrogate as SG
+
+    def sync():
+        torch.cuda.synchronize()
+
+    pr = inputs.surrogate_problems(problems, SNO_N, seed=inputs.SEED_BASE + 7)
+    u0 = torch.tensor(pr.u0, dtype=torch.float32, device="cuda")
+    r, bl, br = (torch.tensor(x, dtype=torch.float32, device="cuda") for x in (pr.r, pr.beta_l, pr.beta_r))
+    points = []
+    for K in Ks:
+        t0 = time.perf_counter()
+        data = SG.make_training_set(12500, K=K, jumps=SNO_JUMPS, prec=B.GE_F32)
+        sur = SG.Surrogate(K=K, max_batch=1024, seed=0)
+        sur.train(data, steps=train_steps, batch=64, lr=2e-3, warmup=100)
+        del data
+        sync()
+        t_train = time.perf_counter() - t0
+        steps = jumps * K
+        ge = SG.GEBatch(pr.r, pr.beta_l, pr.beta_r, SNO_N, B.GE_F32)
+        B.ge_batch_tune(ge.plan, u0, min(256, K))
+        x = u0.clone()
+        ge.run(x, steps)
+        sync()
+        t_ge = 1e300
+        for _ in range(3):
+            x.copy_(u0)
+            sync()
+            t1 = time.perf_counter()
+            ge.run(x, steps)
+            sync()
+            t_ge = min(t_ge, time.perf_counter() - t1)
+        ge.close()
+        sur.rollout(u0[:1024], r[:1024], bl[:1024], br[:1024], 1)
+        sync()
+        t1 = time.perf_counter()
+        pred = sur.rollout(u0, r, bl, br, jumps)
+        sync()
+        t_sur = time.perf_counter() - t1
+        SG.solve_with_fallback(sur, u0[:256], r[:256], bl[:256], br[:256], 1, tol=SNO_TOL, sample_frac=0.01)
+        sync()
+        t1 = time.perf_counter()
+        out, rep = SG.solve_with_fallback(sur, u0, r, bl, br, jumps, tol=SNO_TOL, sample_frac=0.01)
+        sync()
+        t_pipe = time.perf_counter() - t1
+        e = (torch.linalg.vector_norm(pred - x, dim=1) / torch.linalg.vector_norm(x, dim=1)).cpu().numpy()
+        e_out = (torch.linalg.vector_norm(out - x, dim=1) / torch.linalg.vector_norm(x, dim=1)).cpu().numpy()
+        points.append({"K": K, "steps": steps, "speedup_pipeline_vs_batched_f32_ge": t_ge / t_pipe,
+                       "speedup_surrogate_only_vs_batched_f32_ge": t_ge / t_sur,
+                       "rows_within_tol": float(np.mean(e <= SNO_TOL)), "fell_back_all": rep.fell_back_all,
+                       "sample_over_tol": rep.n_sample_over_tol, "surrogate_err_median": float(np.median(e)),
+                       "surrogate_err_p99": float(np.percentile(e, 99)),
+                       "pipeline_err_max": float(np.max(e_out)),
+                       "batched_f32_ge_ms": t_ge * 1e3, "surrogate_only_ms": t_sur * 1e3,
+                       "pipeline_ms": t_pipe * 1e3, "train_seconds": t_train,
+                       "tensor_core_path": bool(B.ge_sno_get_tensor_cores(sur.model))})
+        sur.close()
+        del pred, out
+    return {"workload": f"{problems} problems N={SNO_N}, r U[0.5,4], walls U(-1,1), u0 = linear + 16-mode Fourier "
+                        f"(1/k^2) + 2 tents; {jumps} jumps of K steps; surrogate trained per K ({train_steps} steps)",
+            "tolerance_rel_l2": SNO_TOL, "points": points}
+
+
 def measure_sno_forward(torch, inputs, steps, warmup, problems=4096):
     """Forward passes of the surrogate (untrained, BF16 mode) over `problems`
     problems of N = 1024 in chunks of 1024: time per problem and tensor
@@ -716,6 +792,8 @@ def main():
     ap.add_argument("--no-probe", action="store_true", help="skip the FMA throughput probe")
     ap.add_argument("--only-surrogate", action="store_true", help="run only the surrogate workload")
     ap.add_argument("--sno-train-steps", type=int, default=3000)
+    ap.add_argument("--no-sno-sweep", action="store_true", help="skip the surrogate's jump-length sweep")
+    ap.add_argument("--only-sno-sweep", action="store_true", help="run only the surrogate's jump-length sweep")
     ap.add_argument("--sno-forward-only", action="store_true",
                     help="time only surrogate forward passes (untrained weights; profiling)")
     ap.add_argument("--subdomain", type=int, default=1,
@@ -749,6 +827,10 @@ def main():
         return 0
     if args.only_surrogate:
         print(json.dumps({"surrogate": measure_surrogate(B, torch, inputs, args.sno_train_steps)}), flush=True)
+        return 0
+    if args.only_sno_sweep:
+        print(json.dumps({"surrogate_k_sweep": measure_surrogate_k_sweep(B, torch, inputs, args.sno_train_steps)}),
+              flush=True)
         return 0
     if args.sno_forward_only:
         print(json.dumps({"surrogate_forward": measure_sno_forward(torch, inputs, args.steps, args.warmup)}),
@@ -998,9 +1080,11 @@ def main():
         batched = measure_batch(B, torch, inputs, dev, 3, 2)
 
     # ---- learned surrogate with the GE fallback ----------------------------
-    surrogate = None
+    surrogate = sweep = None
     if not args.no_surrogate and world == 1:
         surrogate = measure_surrogate(B, torch, inputs, args.sno_train_steps)
+        if not args.no_sno_sweep:
+            sweep = measure_surrogate_k_sweep(B, torch, inputs, args.sno_train_steps)
 
     # ---- CPU baseline: the oracle on a bounded sample -----------------------
     cpu = None
@@ -1050,6 +1134,7 @@ def main():
         "batched_sharded": batched_sharded,
         "split_solve": split_solve,
         "surrogate": surrogate,
+        "surrogate_k_sweep": sweep,
     }
     B.ge_destroy(ctx)
     print(json.dumps(line), flush=True)

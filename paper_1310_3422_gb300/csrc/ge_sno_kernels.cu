@@ -747,17 +747,31 @@ __global__ void round_bf16_kernel(const float *__restrict__ x, float *__restrict
 }
 
 // Lift without a GEMM (K = 4): one thread per point and 8 channels.
-template <typename T>
+constexpr int kLiftMaxC = 256;
+
+template <typename T, typename I>
 __global__ void lift_kernel(const float *__restrict__ u0, const float *__restrict__ r, const float *__restrict__ bl,
                             const float *__restrict__ br, const T *__restrict__ w0, const float *__restrict__ b0,
                             T *__restrict__ v0, int batch, int n, int c, int bf16)
 {
+    // I: index type (32-bit when every index fits: 64-bit divisions cost more
+    // than the rest of the work)
+    // the lift's weights and bias, once per CTA (c <= kLiftMaxC; else from global)
+    __shared__ float sw[4 * kLiftMaxC], sb[kLiftMaxC];
+    const bool staged = c <= kLiftMaxC;
+    if (staged) {
+        for (int k = threadIdx.x; k < 4 * c; k += blockDim.x)
+            sw[k] = (float)w0[k];
+        for (int k = threadIdx.x; k < c; k += blockDim.x)
+            sb[k] = b0[k];
+        __syncthreads();
+    }
     const int cg = (c + 7) / 8;
-    const long long total = (long long)batch * n * cg;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        const long long i = e / cg;
-        const int c0 = (int)(e % cg) * 8;
-        const int b = (int)(i / n), j = (int)(i % n);
+    const I total = (I)batch * n * cg;
+    for (I e = (I)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (I)gridDim.x * blockDim.x) {
+        const I i = e / cg;
+        const int c0 = (int)(e - i * cg) * 8;
+        const int b = (int)(i / n), j = (int)(i - (I)b * n);
         const float x = (float)(j + 1) / (float)(n + 1);
         float f[4] = {u0[i], x, r[b], bl[b] + (br[b] - bl[b]) * x};
         if (bf16) {
@@ -765,16 +779,29 @@ __global__ void lift_kernel(const float *__restrict__ u0, const float *__restric
             for (int k = 0; k < 4; ++k)
                 f[k] = __bfloat162float(__float2bfloat16_rn(f[k]));
         }
+        float v[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            const int ch = c0 + q;
-            if (ch >= c)
-                break;
-            float v = b0[ch];
+            const int ch = c0 + q < c ? c0 + q : c - 1;
+            float a = staged ? sb[ch] : b0[ch];
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                v = fmaf(f[k], (float)w0[k * c + ch], v);
-            v0[i * c + ch] = (T)v;
+                a = fmaf(f[k], staged ? sw[k * c + ch] : (float)w0[k * c + ch], a);
+            v[q] = a;
+        }
+        if (bf16 && c % 8 == 0) {
+            // eight BF16 channels in one 16-byte store
+            __nv_bfloat162 h[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                h[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+            *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(v0) + i * c + c0) =
+                *reinterpret_cast<const uint4 *>(h);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (c0 + q < c)
+                    v0[i * c + c0 + q] = (T)v[q];
         }
     }
 }
@@ -981,12 +1008,24 @@ cudaError_t sno_lift(const float *u0, const float *r, const float *bl, const flo
                      const float *b0, void *v0, int batch, int n, int c, int bf16, cudaStream_t s)
 {
     const long long total = (long long)batch * n * ((c + 7) / 8);
-    if (bf16)
-        lift_kernel<__nv_bfloat16><<<grid_for(total), 256, 0, s>>>(u0, r, bl, br, static_cast<const __nv_bfloat16 *>(w0),
-                                                                  b0, static_cast<__nv_bfloat16 *>(v0), batch, n, c, 1);
-    else
-        lift_kernel<float><<<grid_for(total), 256, 0, s>>>(u0, r, bl, br, static_cast<const float *>(w0), b0,
-                                                          static_cast<float *>(v0), batch, n, c, 0);
+    {
+        // 32-bit indices when the grid-stride loop cannot overflow them
+        const bool small = total < (1LL << 31) - 2LL * 256 * 4096;
+        if (bf16 && small)
+            lift_kernel<__nv_bfloat16, int><<<grid_for(total), 256, 0, s>>>(
+                u0, r, bl, br, static_cast<const __nv_bfloat16 *>(w0), b0, static_cast<__nv_bfloat16 *>(v0), batch, n,
+                c, 1);
+        else if (bf16)
+            lift_kernel<__nv_bfloat16, long long><<<grid_for(total), 256, 0, s>>>(
+                u0, r, bl, br, static_cast<const __nv_bfloat16 *>(w0), b0, static_cast<__nv_bfloat16 *>(v0), batch, n,
+                c, 1);
+        else if (small)
+            lift_kernel<float, int><<<grid_for(total), 256, 0, s>>>(u0, r, bl, br, static_cast<const float *>(w0), b0,
+                                                                    static_cast<float *>(v0), batch, n, c, 0);
+        else
+            lift_kernel<float, long long><<<grid_for(total), 256, 0, s>>>(
+                u0, r, bl, br, static_cast<const float *>(w0), b0, static_cast<float *>(v0), batch, n, c, 0);
+    }
     return cudaGetLastError();
 }
 

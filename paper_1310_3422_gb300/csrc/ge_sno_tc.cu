@@ -392,17 +392,18 @@ __global__ void __launch_bounds__(kTcThreads) sno_tc_kernel(const __grid_constan
         tmem_dealloc(tbase, S::kTmemCols);
 }
 
-// yT[b][c][k] = y[b][k][c]  (BF16, K = 2M rows, C columns per problem)
+// yT[b][c][k] = y[b][k][c]  (BF16, K = 2M rows, C columns per problem);
+// 32-bit indices (the caller checks that every index fits)
 __global__ void transpose_rows_kernel(const __nv_bfloat16 *__restrict__ y, __nv_bfloat16 *__restrict__ yt,
-                                      long long batch, int k_rows, int c_cols)
+                                      int batch, int k_rows, int c_cols)
 {
-    const long long total = batch * k_rows * c_cols;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long b = e / ((long long)k_rows * c_cols);
-        const int rem = (int)(e - b * k_rows * c_cols);
-        const int c = rem / k_rows, k = rem % k_rows;
-        yt[e] = y[(b * k_rows + k) * c_cols + c];
+    const int per = k_rows * c_cols;
+    const int total = batch * per;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int b = e / per;
+        const int rem = e - b * per;
+        const int c = rem / k_rows, k = rem - c * k_rows;
+        yt[e] = y[b * per + k * c_cols + c];
     }
 }
 
@@ -414,20 +415,37 @@ cudaError_t launch_tc(const SnoTcMaps &m, const SnoTcArgs &a, int sms, cudaStrea
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(sno_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              S::kSmem);
+        // the largest shared-memory carve-out, so that as many CTAs fit as
+        // TMEM allows (3 layer CTAs of 66 KB need about 200 KB)
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(sno_tc_kernel<MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess)
             return e;
         attr_set = true;
     }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sno_tc_kernel<MODE>, kTcThreads, S::kSmem);
-    if (e != cudaSuccess)
-        return e;
-    // TMEM: at most 512 columns per SM between the co-resident CTAs
-    const int tmem_cap = 512 / (int)S::kTmemCols;
-    if (per_sm > tmem_cap)
-        per_sm = tmem_cap;
-    if (per_sm < 1)
-        return cudaErrorInvalidConfiguration;
+    // co-resident CTAs per SM: what shared memory holds (the kernel's static
+    // and dynamic bytes plus the driver's reserve per CTA), capped so that
+    // their TMEM columns (at most 512 per SM) all fit
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncAttributes fa{};
+        int dev = 0, sm_bytes = 0, reserve = 0;
+        cudaError_t e = cudaFuncGetAttributes(&fa, sno_tc_kernel<MODE>);
+        if (e == cudaSuccess)
+            e = cudaGetDevice(&dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        if (e != cudaSuccess)
+            return e;
+        int fit = sm_bytes / (S::kSmem + (int)fa.sharedSizeBytes + reserve);
+        const int tmem_cap = 512 / (int)S::kTmemCols;
+        per_sm = fit < tmem_cap ? fit : tmem_cap;
+        if (per_sm < 1)
+            return cudaErrorInvalidConfiguration;
+    }
     long long grid = (long long)sms * per_sm;
     if (grid > a.n_tiles)
         grid = a.n_tiles;
@@ -458,13 +476,15 @@ cudaError_t sno_tc_projection(const SnoTcMaps &m, const SnoTcArgs &a, int sms, c
 cudaError_t sno_transpose_rows(const void *y, void *yt, long long batch, int k_rows, int c_cols, cudaStream_t s)
 {
     const long long total = batch * k_rows * c_cols;
+    if (total >= (1LL << 31) - 256LL * 4096)
+        return cudaErrorInvalidValue;
     long long blocks = (total + 255) / 256;
     if (blocks > 4096)
         blocks = 4096;
     if (blocks < 1)
         return cudaSuccess;
     transpose_rows_kernel<<<(int)blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(y),
-                                                       static_cast<__nv_bfloat16 *>(yt), batch, k_rows, c_cols);
+                                                       static_cast<__nv_bfloat16 *>(yt), (int)batch, k_rows, c_cols);
     return cudaGetLastError();
 }
 

@@ -77,18 +77,19 @@ class TrainingSet:
 
 
 def make_training_set(n_traj: int, arch: SnoArch = SnoArch(), K: int = 256, jumps: int = 8,
-                      seed: int = inputs.SEED_BASE + 4) -> TrainingSet:
-    """n_traj GE trajectories of `jumps` jumps of K steps (FP64 GE, stored as
-    FP32): n_traj * jumps training pairs."""
+                      seed: int = inputs.SEED_BASE + 4, prec: int = B.GE_F64) -> TrainingSet:
+    """n_traj GE trajectories of `jumps` jumps of K steps (GE in precision
+    `prec`, FP64 by default; stored as FP32): n_traj * jumps training pairs."""
     torch = _torch()
     probs = inputs.surrogate_problems(n_traj, arch.n, seed=seed)
-    u = torch.tensor(probs.u0, dtype=torch.float64, device="cuda")
-    ge = GEBatch(probs.r, probs.beta_l, probs.beta_r, arch.n, B.GE_F64)
+    u = torch.tensor(probs.u0, dtype=torch.float64 if prec == B.GE_F64 else torch.float32, device="cuda")
+    ge = GEBatch(probs.r, probs.beta_l, probs.beta_r, arch.n, prec)
     xs, ys = [], []
     for _ in range(jumps):
-        xs.append(u.float())
+        # copies: with FP32 GE, u.float() would be u itself, advanced in place
+        xs.append(u.to(torch.float32, copy=True))
         ge.run(u, K)
-        ys.append(u.float())
+        ys.append(u.to(torch.float32, copy=True))
     B.ge_batch_sync(ge.plan)
     ge.close()
 
