@@ -121,7 +121,7 @@ constexpr int kEndfSlots = 64;
 // Coefficient mode of the scaled form's tables (see ge::batch_exps).
 int scale_mode(const ge_batch *b) { return b->df ? 2 : (b->prec == GE_F32 ? 1 : 0); }
 
-int endf_slot(ge_batch *b, int n_mid, cudaError_t *err)
+int endf_slot(ge_batch *b, int n_mid, cudaError_t *err, std::vector<int> *filled)
 {
     size_t i = 0;
     while (i < b->slot_nmid.size() && b->slot_nmid[i] != n_mid)
@@ -132,7 +132,13 @@ int endf_slot(ge_batch *b, int n_mid, cudaError_t *err)
         b->slot_nmid.push_back(n_mid);
         b->slot_ready.push_back(0);
     }
-    if (!b->slot_ready[i]) {
+    // filled: slots this call has already enqueued (inside a capture a slot is
+    // never marked ready, and one computation per call and slot suffices)
+    bool enqueued = false;
+    for (int f : *filled)
+        enqueued = enqueued || f == (int)i;
+    if (!b->slot_ready[i] && !enqueued) {
+        filled->push_back((int)i);
         void *dst = static_cast<char *>(b->endf) + i * (size_t)b->n_problems * 8;
         *err = ge::batch_endf(b->desc, b->exps, b->n_problems, b->R, b->Q, n_mid, scale_mode(b), dst, b->stream);
         if (*err != cudaSuccess)
@@ -165,6 +171,7 @@ ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int tile_rows, int 
         ctas = cmax;
     int cur = 0;
     int64_t n0 = 0;
+    std::vector<int> filled;  // end-factor slots enqueued by this call
     const int dmax = ge::tbb_max_depth(pidx, tile_rows);
     if (depth > dmax)
         depth = dmax;
@@ -195,7 +202,7 @@ ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int tile_rows, int 
         p.stall = b->stall;
         if (b->exps) {
             cudaError_t se = cudaSuccess;
-            const int slot = endf_slot(b, p.n_mid, &se);
+            const int slot = endf_slot(b, p.n_mid, &se, &filled);
             if (se != cudaSuccess)
                 return bcuda(se, "ge_batch: end factors");
             if (slot >= 0) {

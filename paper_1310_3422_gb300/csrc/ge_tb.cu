@@ -112,10 +112,7 @@ __device__ __forceinline__ void run_scaled(Real (&v)[K], const TbParams &P, Exch
             if (until == 0) {
                 until = P.rescale_every;
                 const int e = P.rs_exp[ev++];
-                const Real s = pow2neg<Real>(e);
-#pragma unroll
-                for (int j = 0; j < K; ++j)
-                    v[j] *= s;
+                scale_pow2<true>(v, e);
                 if constexpr (EDGE)
                     sig *= pow2neg<double>(e);
             }

@@ -290,6 +290,47 @@ __device__ __forceinline__ float pow2neg<float>(int e)
     return __int_as_float((127 - e) << 23);
 }
 
+// v[j] <- v[j] * 2^-e for the registers in [jlo, jhi) (all with ALL).  In
+// double, a power-of-two scaling of a normal number whose result stays
+// normal only lowers its exponent field: when every such value of the warp
+// has an exponent field in (e, 2047), the scaling is an integer subtraction
+// on the ALU pipe instead of a multiply on the FP64 pipe (the one DFMA per
+// point and step is what bounds the FP64 kernels); the results are the same
+// bits.  Otherwise (zeros, subnormal results, infinities) the multiply.
+template <bool ALL, int K>
+__device__ __forceinline__ void scale_pow2(double (&v)[K], int e, int jlo = 0, int jhi = K)
+{
+    const long long sh = (long long)e << 52;
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int ex = (int)((__double_as_longlong(v[j]) >> 52) & 0x7FF);
+        if (ALL || (j >= jlo && j < jhi))
+            ok = ok && ex > e && ex < 2047;
+    }
+    if (__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (ALL || (j >= jlo && j < jhi))
+                v[j] = __longlong_as_double(__double_as_longlong(v[j]) - sh);
+    } else {
+        const double s = pow2neg<double>(e);
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (ALL || (j >= jlo && j < jhi))
+                v[j] *= s;
+    }
+}
+template <bool ALL, int K>
+__device__ __forceinline__ void scale_pow2(float (&v)[K], int e, int jlo = 0, int jhi = K)
+{
+    const float s = pow2neg<float>(e);
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        if (ALL || (j >= jlo && j < jhi))
+            v[j] *= s;
+}
+
 // Kahan sum of an update into (hi, lo).  The updates that reach it are
 // explicitly rounded products (__fmul_rn), so the compiler can never fuse a
 // product into the sum: every kernel instantiation and tile geometry then

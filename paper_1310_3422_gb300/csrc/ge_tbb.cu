@@ -317,12 +317,11 @@ __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &
         if (i < cnt)
             batch_mid<0, EDGE>(v, L, R, sp, fx, cm);
         m += cnt;
-        if (cnt == P.R && pid >= 0) {
-            const Real sc = pow2neg<Real>(P.exps[(long long)pid * P.Q + q]);
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-                if (!EDGE || (j >= sp.jlo && j < sp.jhi))
-                    v[j] *= sc;
+        if (cnt == P.R) {
+            // every lane takes part (the FP64 form decides warp-wide); a lane
+            // of no problem scales nothing
+            const int e = pid >= 0 ? P.exps[(long long)pid * P.Q + q] : 0;
+            scale_pow2<!EDGE>(v, e, pid >= 0 ? sp.jlo : 0, pid >= 0 ? sp.jhi : 0);
         }
         ++q;
     }
