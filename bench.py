@@ -351,7 +351,10 @@ def measure_batch(B, torch, inputs, dev, steps, warmup, only=None, fixed=None):
                 depth = fixed[0]
                 B.ge_batch_set_depth(plan, depth)
                 B.ge_batch_set_geometry(plan, fixed[1], fixed[2])
+                if len(fixed) > 3:
+                    B.ge_batch_set_persistent(plan, fixed[3])
             tile_rows, ctas = B.ge_batch_get_geometry(plan)
+            persist_flag = B.ge_batch_get_persistent(plan)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=s):
                 u.copy_(u0)
@@ -382,11 +385,14 @@ def measure_batch(B, torch, inputs, dev, steps, warmup, only=None, fixed=None):
                 w = want[i]
                 errs.append(float(np.max(np.abs(got[o:o + n] - w)) / np.max(np.abs(w))))
             B.ge_batch_destroy(plan)
+        persistent = bool(persist_flag)
         out[name] = {"updates_per_s": upd / (ms / 1e3), "ms_per_solve": ms, "depth": depth,
+                     "persistent_launch": persistent,
                      "geometry": {"tile_rows": tile_rows, "ctas_per_sm": ctas,
                                   "tuned": fixed is None},
                      "replays_timed": reps, "clocks": sampler.summary(),
-                     "launches_per_solve": (2000 + depth - 1) // depth + (2 if name == "f64_df" else 0),
+                     "launches_per_solve": (1 if persistent else (2000 + depth - 1) // depth)
+                     + (2 if name == "f64_df" else 0),
                      "max_rel_err_sampled": max(errs), "problems_checked": len(picks)}
     return out
 
@@ -435,13 +441,7 @@ def measure_batch_sharded(B, torch, inputs, dev, dist, rank, world, steps, warmu
             u = u0.clone()
             plan = B.ge_batch_create(ns, bt.r[i0:i1], bt.beta_l[i0:i1], bt.beta_r[i0:i1], offs, pos, prec,
                                      stream=s)
-            if fixed is None:
-                depth = B.ge_batch_tune(plan, u0, 256)
-            else:
-                depth = fixed[0]
-                B.ge_batch_set_depth(plan, depth)
-                B.ge_batch_set_geometry(plan, fixed[1], fixed[2])
-            tile_rows, ctas = B.ge_batch_get_geometry(plan)
+            depth = B.ge_batch_tune(plan, u0, 256)
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=s):
                 u.copy_(u0)
@@ -802,8 +802,8 @@ def main():
     ap.add_argument("--only-batched", default=None, choices=["f32", "f32c", "f64", "f64_df"],
                     help="run only the batched workload in this precision (profiling)")
     ap.add_argument("--batch-launch", default=None,
-                    help="with --only-batched: a fixed launch shape DEPTH,TILE_ROWS,CTAS_PER_SM instead of the "
-                         "autotuner (profiling)")
+                    help="with --only-batched: a fixed launch shape DEPTH,TILE_ROWS,CTAS_PER_SM[,PERSISTENT] "
+                         "instead of the autotuner (profiling)")
     args = ap.parse_args()
 
     world, rank, local, dist = dist_setup(args)

@@ -263,12 +263,27 @@ ge_status ge_batch_set_geometry(ge_batch *plan, int32_t tile_rows, int32_t ctas_
 /* The geometry in use (0 values resolved).  Errors: GE_EINVAL. */
 ge_status ge_batch_get_geometry(const ge_batch *plan, int32_t *tile_rows, int32_t *ctas_per_sm);
 
+/* Persistent launch (on = 1) for a plain FP32 plan: a ge_batch_run of more
+ * than `depth` steps runs as ONE launch that advances every tile round by
+ * round (rounds of `depth` steps, the same cut and arithmetic as one launch
+ * per round, so the same bits).  A tile of round k + 1 starts once its own
+ * and its two neighbouring tiles of round k are written: per-tile counters in
+ * device memory, acquire / release ordered, each wait bounded (GE_ETIMEOUT).
+ * There is no launch boundary, so the tail of one round overlaps the start
+ * of the next.  Other plans (FP64, compensated FP32, double-float) keep one
+ * launch per round.  on = 0 (the default): one launch per `depth` steps.
+ * Errors: GE_EINVAL, GE_ENOMEM (its counters, n_rows ints, on first use). */
+ge_status ge_batch_set_persistent(ge_batch *plan, int32_t on);
+ge_status ge_batch_get_persistent(const ge_batch *plan, int32_t *on);
+
 /* Autotune the launches on the caller's data: times `steps` steps of the
  * data in u_dev (which is not modified) for each candidate, by coordinate
  * search: the depth T (16, 32, 48, 64, 96, 128, 192, 256 steps per launch)
  * at the plan's geometry, then the geometry (rows per tile W in {256, 128}
- * x CTAs per SM) at that depth, then the depth again.  Keeps the fastest
- * (see ge_batch_get_depth, ge_batch_get_geometry) and returns its depth in
+ * x CTAs per SM) at that depth, then the depth again, and for a plain FP32
+ * plan the persistent launch against one launch per depth steps.  Keeps the
+ * fastest (see ge_batch_get_depth, ge_batch_get_geometry,
+ * ge_batch_get_persistent) and returns its depth in
  * *best_depth (may be NULL).  This is the counterpart of the paper's tuning
  * of its block count (Sec. 4) for the batched kernel.  Synchronous.
  * Errors: GE_EINVAL, GE_ECUDA. */

@@ -27,7 +27,8 @@ EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", 
            "ge_read_range", "ge_write_range",
            "ge_get_step", "ge_sync", "ge_destroy", "ge_solve", "ge_batch_create", "ge_batch_set_depth",
            "ge_batch_get_depth", "ge_batch_set_kernel", "ge_batch_tune", "ge_batch_set_geometry",
-           "ge_batch_get_geometry", "ge_batch_run", "ge_batch_sync",
+           "ge_batch_get_geometry", "ge_batch_set_persistent", "ge_batch_get_persistent", "ge_batch_run",
+           "ge_batch_sync",
            "ge_batch_destroy",
            "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error", "ge_debug_stall",
            "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune", "ge_probe_fma",
@@ -103,6 +104,10 @@ def load(path: str | None = None):
         lib.ge_batch_set_geometry.restype = ctypes.c_int
         lib.ge_batch_get_geometry.argtypes = [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I32)]
         lib.ge_batch_get_geometry.restype = ctypes.c_int
+        lib.ge_batch_set_persistent.argtypes = [_VP, _I32]
+        lib.ge_batch_set_persistent.restype = ctypes.c_int
+        lib.ge_batch_get_persistent.argtypes = [_VP, ctypes.POINTER(_I32)]
+        lib.ge_batch_get_persistent.restype = ctypes.c_int
         lib.ge_batch_tune.argtypes = [_VP, _VP, _I64, ctypes.POINTER(_I32)]
         lib.ge_batch_tune.restype = ctypes.c_int
         lib.ge_batch_run.argtypes = [_VP, _VP, _I64]
@@ -367,6 +372,17 @@ def ge_batch_get_geometry(plan: Batch):
     tr, c = _I32(), _I32()
     _check(load().ge_batch_get_geometry(plan.handle, ctypes.byref(tr), ctypes.byref(c)), "ge_batch_get_geometry")
     return int(tr.value), int(c.value)
+
+
+def ge_batch_set_persistent(plan: Batch, on: int):
+    """1: a run of more than `depth` steps as one persistent launch (plain FP32 plans)."""
+    _check(load().ge_batch_set_persistent(plan.handle, int(on)), "ge_batch_set_persistent")
+
+
+def ge_batch_get_persistent(plan: Batch) -> int:
+    v = _I32()
+    _check(load().ge_batch_get_persistent(plan.handle, ctypes.byref(v)), "ge_batch_get_persistent")
+    return int(v.value)
 
 
 def ge_batch_get_depth(plan: Batch) -> int:

@@ -70,6 +70,9 @@ struct ge_batch {
     // rows per tile (256 or 128) and co-resident CTAs per SM (0: as many as fit)
     int tile_rows = 256, ctas_per_sm = 0;
     int blocks_per_sm_128 = 0;
+    // one persistent launch per run (plain FP32 plans; ge_batch_set_persistent)
+    bool persistent = false;
+    int *done = nullptr;     // per-tile completion counters of a persistent launch (n_rows ints)
     // scaled form (FP64, plain FP32): rescale exponents [n_problems][Q] and
     // end-factor slots, one per launch length n_mid met so far
     short *exps = nullptr;
@@ -106,6 +109,8 @@ void release_batch(ge_batch *b)
         cudaFree(b->endf);
     if (b->df_codes)
         cudaFree(b->df_codes);
+    if (b->done)
+        cudaFree(b->done);
     delete b;
 }
 
@@ -182,6 +187,57 @@ ge_status batch_steps(ge_batch *b, int64_t steps, int depth, int tile_rows, int 
                                               b->n_rows, b->n_problems, b->df_codes, b->stream);
         if (e != cudaSuccess)
             return bcuda(e, "ge_batch: double-float prescale");
+    }
+    if (b->persistent && pidx == 1 && !b->df && b->exps && b->done && steps > depth) {
+        // the whole run as one persistent launch: rounds of `depth` steps
+        // (the plan's scaled FP32 form; every round's reach fits the tile)
+        const int64_t rounds = (steps + depth - 1) / depth;
+        const int64_t L_last = steps - (rounds - 1) * depth;
+        cudaError_t se = cudaSuccess;
+        const int slot_mid = endf_slot(b, depth, &se, &filled);
+        const int slot_last = se == cudaSuccess ? endf_slot(b, (int)(L_last - 1), &se, &filled) : -1;
+        if (se != cudaSuccess)
+            return bcuda(se, "ge_batch: end factors");
+        ge::TbbParams p{};
+        if (slot_mid >= 0 && slot_last >= 0 && ge::tbb_geometry(pidx, tile_rows, depth + 1, &p.H, &p.U)) {
+            p.n_rows = b->n_rows;
+            p.n_tiles = (b->n_rows * (ge::kRowBytes / 4) + p.U - 1) / p.U;
+            p.row_pid = b->row_pid;
+            p.desc = b->desc;
+            p.err = b->err;
+            p.stall = b->stall;
+            p.scaled = 1;
+            p.R = b->R;
+            p.Q = b->Q;
+            p.exps = b->exps;
+            p.endf = static_cast<const char *>(b->endf) + (size_t)slot_mid * b->n_problems * 8;
+            p.endf_last = static_cast<const char *>(b->endf) + (size_t)slot_last * b->n_problems * 8;
+            p.rounds = (int)rounds;
+            p.depth = depth;
+            p.steps = steps;
+            p.outs[0] = b->buf[1];  // round k reads buffer k & 1 and writes the other
+            p.outs[1] = b->buf[0];
+            p.done = b->done;
+            p.tile_ctr = b->err + 48;
+            // every CTA co-resident: at most what fits of the persistent kernel
+            int pmax = 0;
+            cudaError_t oe = ge::tbb_persist_occupancy(tile_rows, &pmax);
+            if (oe != cudaSuccess || pmax < 1)
+                return bcuda(oe == cudaSuccess ? cudaErrorInvalidConfiguration : oe, "ge_batch: persistent occupancy");
+            long long grid = (long long)b->num_sms * (ctas < pmax ? ctas : pmax);
+            if (grid > p.n_tiles)
+                grid = p.n_tiles;
+            cudaError_t e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int), b->stream);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(b->done, 0, sizeof(int) * (size_t)p.n_tiles, b->stream);
+            if (e == cudaSuccess)
+                e = ge::launch_tbb(pidx, tile_rows, tile_rows == 128 ? &b->tmap128[0] : &b->tmap[0], p, (int)grid,
+                                   b->stream, tile_rows == 128 ? &b->tmap128[1] : &b->tmap[1]);
+            if (e != cudaSuccess)
+                return bcuda(e, "ge_batch: persistent kernel launch");
+            *result_buf = (int)(rounds & 1);
+            return GE_OK;
+        }
     }
     while (n0 < steps) {
         const int64_t L = (steps - n0 < depth) ? steps - n0 : depth;
@@ -496,6 +552,27 @@ ge_status ge_batch_get_geometry(const ge_batch *b, int32_t *tile_rows, int32_t *
     return GE_OK;
 }
 
+ge_status ge_batch_set_persistent(ge_batch *b, int32_t on)
+{
+    if (!b || (on != 0 && on != 1))
+        return bfail(GE_EINVAL, "ge_batch_set_persistent: NULL plan or value not 0/1");
+    if (on && !b->done) {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&b->done), sizeof(int) * (size_t)(b->n_rows + 1));
+        if (e != cudaSuccess)
+            return bcuda(e, "ge_batch_set_persistent");
+    }
+    b->persistent = on != 0;
+    return GE_OK;
+}
+
+ge_status ge_batch_get_persistent(const ge_batch *b, int32_t *on)
+{
+    if (!b || !on)
+        return bfail(GE_EINVAL, "ge_batch_get_persistent: NULL argument");
+    *on = b->persistent ? 1 : 0;
+    return GE_OK;
+}
+
 ge_status ge_batch_tune(ge_batch *b, const void *u_dev, int64_t steps, int32_t *best_depth)
 {
     ge::NvtxRange nvtx("ge_batch_tune");
@@ -570,6 +647,19 @@ ge_status ge_batch_tune(ge_batch *b, const void *u_dev, int64_t steps, int32_t *
             }
         }
     }
+    // finally, for a plain FP32 plan: the run as one persistent launch
+    // against one launch per `depth` steps, at the chosen depth and geometry
+    bool best_persist = false;
+    if (st == GE_OK && e == cudaSuccess && b->prec == GE_F32 && !b->df && b->exps && steps > best_d) {
+        const bool was = b->persistent;
+        st = ge_batch_set_persistent(b, 1);
+        float ms = 0.0f;
+        if (st == GE_OK)
+            st = timed(best_d, best_tr, best_c, &ms);
+        if (st == GE_OK && e == cudaSuccess && ms < best)
+            best_persist = true;
+        b->persistent = was;
+    }
     if (e0)
         cudaEventDestroy(e0);
     if (e1)
@@ -581,6 +671,7 @@ ge_status ge_batch_tune(ge_batch *b, const void *u_dev, int64_t steps, int32_t *
     b->depth = best_d;
     b->tile_rows = best_tr;
     b->ctas_per_sm = best_c;
+    b->persistent = best_persist;
     if (best_depth)
         *best_depth = best_d;
     return GE_OK;

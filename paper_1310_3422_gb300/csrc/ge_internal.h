@@ -170,6 +170,18 @@ struct TbbParams {
     // the launch writes doubles, per-problem prescale codes
     int df_in, df_out;
     const int *df_codes;
+    // persistent launch (rounds > 1; plain FP32 kernel): the whole solve of
+    // `steps` steps as rounds of `depth` steps in one launch.  Round k reads
+    // the buffer of the launch's tensor map k & 1 and writes outs[k & 1];
+    // done[n_tiles] (zeroed first) counts the consumer warps that finished
+    // each tile; endf is the end-factor slot of the full rounds, endf_last
+    // that of the last one.  rounds <= 1: one launch (out, endf, and the
+    // per-launch fields above).
+    int rounds, depth;
+    long long steps;
+    void *outs[2];
+    int *done;
+    const void *endf_last;
 };
 
 // Host (hi, lo) float pair of a double, hi = fl32(x), lo = fl32(x - hi).
@@ -242,7 +254,8 @@ cudaError_t launch_sweep_tb_f32(const float *in, float *out, long long n, int pa
 cudaError_t launch_tb(int prec, const void *tmap, const TbParams &p, int grid, cudaStream_t s);
 // tile_rows: 256 or 128 (the tile geometry of the plan; the tensor map's box
 // must have as many rows).
-cudaError_t launch_tbb(int prec, int tile_rows, const void *tmap, const TbbParams &p, int grid, cudaStream_t s);
+cudaError_t launch_tbb(int prec, int tile_rows, const void *tmap, const TbbParams &p, int grid, cudaStream_t s,
+                       const void *tmap_other = nullptr);
 // Batched double-float kernel (ge_tbb_df.cu) for FP64 plans; its per-call
 // prescale: codes[b] = max(desc[b].walls_code, code of the problem's values).
 cudaError_t launch_tbb_df(const void *tmap, const TbbParams &p, int grid, cudaStream_t s);
@@ -250,6 +263,8 @@ cudaError_t tbb_df_occupancy(int *blocks_per_sm);
 cudaError_t batch_df_prescale(const double *u, const int *row_pid, const BatchDesc *desc, long long n_rows,
                               int n_problems, int *codes, cudaStream_t s);
 cudaError_t tbb_occupancy(int prec, int tile_rows, int *blocks_per_sm);
+// Co-resident CTAs per SM of the persistent plain FP32 kernel.
+cudaError_t tbb_persist_occupancy(int tile_rows, int *blocks_per_sm);
 bool tbb_geometry(int prec, int tile_rows, int reach, int *H, int *U);
 // Largest steps per launch whose reach (steps + 2 stages) fits the batched
 // kernel's tile for this precision.

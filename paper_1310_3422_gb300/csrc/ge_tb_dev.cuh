@@ -73,6 +73,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+// The same for a producer lane whose waits last about a tile's compute: it
+// sleeps between polls, so that it takes no issue slots from the warps that
+// compute on its SM sub-partition.
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t *bar, uint32_t parity, long long limit)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > limit)
+            return false;
+        __nanosleep(128);
+    }
+    return true;
+}
+
 // Wait for the tile in buffer b (phase from the iteration).  With the
 // diagnostic `stall` > 0 the wait polls `never`, a barrier no thread or copy
 // arrives on, and so runs out after `stall` cycles: the failure path below

@@ -18,15 +18,38 @@ namespace {
 // (CTA rows; FP64 and compensated FP32) and tbb_ws_kernel (plain FP32:
 // warp windows fed by a TMA producer warp).
 
+// The per-launch fields of a tile's steps: one launch of a graph of launches,
+// or one round of a persistent launch (round_of).
+struct BRound {
+    int p_first, do_entry, n_mid, do_exit;
+    const void *endf;  // scaled form: end factors of this launch length
+};
+
+__device__ __forceinline__ BRound launch_round(const TbbParams &P)
+{
+    return BRound{P.p_first, P.do_entry, P.n_mid, P.do_exit, P.endf};
+}
+
+// Round k of a persistent launch of P.steps steps, P.depth per round: the
+// same cut into launches as the host's graph of launches (steps n0 = k depth
+// onwards; the entry conversion in round 0, the exit in the last).
+__device__ __forceinline__ BRound round_of(const TbbParams &P, long long k)
+{
+    const long long n0 = k * P.depth;
+    const long long L = (P.steps - n0 < P.depth) ? P.steps - n0 : P.depth;
+    const bool last = k == P.rounds - 1;
+    return BRound{(int)(n0 & 1), k == 0 ? 1 : 0, (int)(last ? L - 1 : L), last ? 1 : 0, last ? P.endf_last : P.endf};
+}
+
 // Entry, block steps and exit of one tile, normalised form.
 template <bool EDGE, typename Real, int K, int NW, bool WT>
-__device__ __forceinline__ void run_batch(Real (&v)[K], const TbbParams &P, const BatchDesc &bd,
-                                          Exch<Real, NW, WT> &x, Span sp)
+__device__ __forceinline__ void run_batch(Real (&v)[K], const TbbParams &P, const BRound &rd,
+                                          const BatchDesc &bd, Exch<Real, NW, WT> &x, Span sp)
 {
     Real L = 0, R = 0;
-    if (P.do_entry) {
+    if (rd.do_entry) {
         const StageC<Real> c{(Real)bd.r, (Real)bd.omr, (Real)0, (Real)bd.f_l, (Real)bd.f_r};
-        if (((1 - P.p_first) & 1) == 1) {
+        if (((1 - rd.p_first) & 1) == 1) {
             exchange(v, L, R, x);
             stage<1, kEntry, EDGE>(v, L, R, sp, c);
         } else {
@@ -35,21 +58,21 @@ __device__ __forceinline__ void run_batch(Real (&v)[K], const TbbParams &P, cons
     }
     const StageC<Real> cm{(Real)bd.d, (Real)0, (Real)bd.kappa, (Real)bd.f_l, (Real)bd.f_r};
     int m = 0;
-    if (P.n_mid > 0 && (P.p_first & 1)) {
+    if (rd.n_mid > 0 && (rd.p_first & 1)) {
         exchange(v, L, R, x);
         stage<1, kMidN, EDGE>(v, L, R, sp, cm);
         m = 1;
     }
-    for (; m + 1 < P.n_mid; m += 2) {
+    for (; m + 1 < rd.n_mid; m += 2) {
         stage<0, kMidN, EDGE>(v, L, R, sp, cm);
         exchange(v, L, R, x);
         stage<1, kMidN, EDGE>(v, L, R, sp, cm);
     }
-    if (m < P.n_mid)
+    if (m < rd.n_mid)
         stage<0, kMidN, EDGE>(v, L, R, sp, cm);
-    if (P.do_exit) {
+    if (rd.do_exit) {
         const StageC<Real> c{(Real)bd.x1, (Real)bd.x2, (Real)bd.xs, (Real)0, (Real)0};
-        if (((P.p_first + P.n_mid) & 1) == 1) {
+        if (((rd.p_first + rd.n_mid) & 1) == 1) {
             exchange(v, L, R, x);
             stage<1, kExit, EDGE>(v, L, R, sp, c);
         } else {
@@ -277,21 +300,21 @@ __device__ __forceinline__ void run_batch_comp(float (&v)[K], const TbbParams &P
 // the accumulated scale, computed in double-double by batch_endf_kernel).
 // Only points inside the problem are written back: padding keeps its values.
 template <bool EDGE, typename Real, int K, int NW, bool WT>
-__device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &P, const BatchDesc &bd, int pid,
-                                                 long long g0, Exch<Real, NW, WT> &x, Span sp)
+__device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &P, const BRound &rd, const BatchDesc &bd,
+                                                 int pid, long long g0, Exch<Real, NW, WT> &x, Span sp)
 {
     Real L = 0, R = 0;
     const Real ua = (Real)bd.ustar_a, ub = (Real)bd.ustar_b;
     // grid position j + 1 of register 0: one 64-bit conversion (the FP64 pipe)
     // per thread, the registers' positions by exact small additions
     const Real p1 = (Real)(g0 + 1);
-    if (P.do_entry) {
+    if (rd.do_entry) {
 #pragma unroll
         for (int j = 0; j < K; ++j)
             if (!EDGE || (j >= sp.jlo && j < sp.jhi))
                 v[j] -= ua + ub * (p1 + (Real)j);
         const StageC<Real> c{(Real)bd.r, (Real)bd.omr, (Real)0, (Real)0, (Real)0};
-        if (((1 - P.p_first) & 1) == 1) {
+        if (((1 - rd.p_first) & 1) == 1) {
             exchange(v, L, R, x);
             stage<1, kEntry, EDGE>(v, L, R, sp, c);
         } else {
@@ -301,10 +324,10 @@ __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &
     const StageC<Real> cm{(Real)bd.g, (Real)0, (Real)bd.kap_s, (Real)0, (Real)0};
     const BatchFix fx = batch_fix<K>(pid, sp);
     int m = 0, q = 0;
-    while (m < P.n_mid) {
-        const int cnt = (P.n_mid - m < P.R) ? P.n_mid - m : P.R;
+    while (m < rd.n_mid) {
+        const int cnt = (rd.n_mid - m < P.R) ? rd.n_mid - m : P.R;
         int i = 0;
-        if (((P.p_first + m) & 1) == 1) {
+        if (((rd.p_first + m) & 1) == 1) {
             exchange(v, L, R, x);
             batch_mid<1, EDGE>(v, L, R, sp, fx, cm);
             i = 1;
@@ -328,10 +351,10 @@ __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &
     if (pid >= 0) {
         Real fh, fl;
         if constexpr (sizeof(Real) == 4) {
-            const float2 f = reinterpret_cast<const float2 *>(P.endf)[pid];
+            const float2 f = reinterpret_cast<const float2 *>(rd.endf)[pid];
             fh = f.x, fl = f.y;
         } else {
-            fh = reinterpret_cast<const double *>(P.endf)[pid];
+            fh = reinterpret_cast<const double *>(rd.endf)[pid];
             fl = 0;
         }
 #pragma unroll
@@ -339,9 +362,9 @@ __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &
             if (!EDGE || (j >= sp.jlo && j < sp.jhi))
                 v[j] = fma(v[j], fh, v[j] * fl);
     }
-    if (P.do_exit) {
+    if (rd.do_exit) {
         const StageC<Real> c{(Real)bd.x1, (Real)bd.x2, (Real)bd.xs, (Real)0, (Real)0};
-        if (((P.p_first + P.n_mid) & 1) == 1) {
+        if (((rd.p_first + rd.n_mid) & 1) == 1) {
             exchange(v, L, R, x);
             stage<1, kExit, EDGE>(v, L, R, sp, c);
         } else {
@@ -439,15 +462,16 @@ __global__ void __launch_bounds__(TR, TR == 256 ? 2 : 4)
         const bool edge_warp = __any_sync(0xffffffffu, edge_thr);
         if constexpr (!COMP) {
             const long long g0 = pid >= 0 ? grow * K - bd.off : 0;
+            const BRound rd = launch_round(P);
             if (P.scaled) {
                 if (edge_warp)
-                    run_batch_scaled<true>(v, P, bd, pid, g0, x, sp);
+                    run_batch_scaled<true>(v, P, rd, bd, pid, g0, x, sp);
                 else
-                    run_batch_scaled<false>(v, P, bd, pid, g0, x, sp);
+                    run_batch_scaled<false>(v, P, rd, bd, pid, g0, x, sp);
             } else if (edge_warp) {
-                run_batch<true>(v, P, bd, x, sp);
+                run_batch<true>(v, P, rd, bd, x, sp);
             } else {
-                run_batch<false>(v, P, bd, x, sp);
+                run_batch<false>(v, P, rd, bd, x, sp);
             }
         } else {
             if (edge_warp)
@@ -515,12 +539,42 @@ struct Ws {
     static constexpr int kConsumers = TR / 32;     // consumer warps
     static constexpr int kThreads = TR + 32;       // plus the producer warp
     static constexpr int kMinBlocks = TR == 256 ? 2 : 4;
+    // the persistent kernel's round bookkeeping needs more registers: with
+    // 128-row tiles it runs 3 CTAs per SM (at 4 it spilled and ran slower)
+    static constexpr int kMinBlocksPersist = TR == 256 ? 2 : 3;
     static int smem_bytes() { return 2 * TR * kRowBytes + kConsumers * kWsStageBytes + 1024; }
 };
 
-template <int TR>
-__global__ void __launch_bounds__(Ws<TR>::kThreads, Ws<TR>::kMinBlocks)
-    tbb_ws_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ TbbParams P)
+// Acquire load of a device-wide counter (another CTA's release publishes it).
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// PERSIST: the whole solve in one launch.  Work items are (round k, tile i),
+// k = 0 .. P.rounds - 1, claimed in order from the launch's queue (so every
+// item of round k is claimed before any of round k + 1).  Round k reads
+// buffer k & 1 (tensor map tmap[k & 1]) and writes P.outs[k & 1]; the
+// producer loads item (k, i) only once tiles i - 1, i, i + 1 of round k - 1
+// are done.  Completion: the consumer warps arrive on the shared barrier
+// stored[b] after their stores of the item in buffer b; the producer lane
+// (otherwise idle) waits for it, fences at GPU scope (the consumers' stores,
+// seen through the barrier, are ordered before it) and adds NW to
+// P.done[tile], so round k of tile i is done at done[i] >= (k + 1) NW.  The
+// producer posts what it owes whenever it can, and always before it blocks
+// on a dependency, so no wait of it is on its own CTA.  The dependency order
+// also keeps every write after the reads of the buffer it overwrites (round
+// k + 1 writes buffer k & 1, which round k read).  CTAs take items only once
+// running, so the smallest unfinished item always has its inputs: no wait
+// is circular.  Every wait is bounded; a timeout is recorded in P.err, which
+// every dependency wait also watches, and the producer then hands its
+// consumers the end marker.
+template <int TR, bool PERSIST>
+__global__ void __launch_bounds__(Ws<TR>::kThreads, PERSIST ? Ws<TR>::kMinBlocksPersist : Ws<TR>::kMinBlocks)
+    tbb_ws_kernel(const __grid_constant__ CUtensorMap tmap0, const __grid_constant__ CUtensorMap tmap1,
+                  const __grid_constant__ TbbParams P)
 {
     using Real = float;
     constexpr bool WT = true;
@@ -533,19 +587,22 @@ __global__ void __launch_bounds__(Ws<TR>::kThreads, Ws<TR>::kMinBlocks)
     unsigned char *tiles = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     unsigned char *stage_all = tiles + 2 * kTileBytes;
-    __shared__ __align__(8) uint64_t full[2], empty[2], never;
+    __shared__ __align__(8) uint64_t full[2], empty[2], stored[4], never;
     __shared__ long long tile_of[2];
     __shared__ Real slot[2][NW][2];  // unused with warp windows (Exch needs the type)
 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int hr = P.H / K, ur = P.U / K;
     const long long limit = P.stall > 0 ? P.stall : kWaitLimitCycles;
+    const long long items = PERSIST ? (long long)P.rounds * P.n_tiles : P.n_tiles;
 
     if (t == 0) {
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
         mbar_init(&empty[0], NW);
         mbar_init(&empty[1], NW);
+        for (int i = 0; i < 4; ++i)
+            mbar_init(&stored[i], NW);
         mbar_init(&never, 1);
         fence_mbar_init();
     }
@@ -556,9 +613,47 @@ __global__ void __launch_bounds__(Ws<TR>::kThreads, Ws<TR>::kMinBlocks)
         if (lane != 0)
             return;
         long long issued[2] = {-1, -1};  // iteration of the last copy into each buffer
+        // persistent launch: items handed out but not yet published (their
+        // iterations sig .. it - 1, tiles in sig_tile by iteration mod 4)
+        long long sig = 0;
+        int sig_tile[4] = {0, 0, 0, 0};
+        // publish iteration j: its consumers' stores (seen through
+        // stored[j & 3]) and then the tile's count, released at GPU scope
+        auto publish = [&](long long j, bool block) -> bool {
+            const int bj = (int)(j & 3);
+            const uint32_t ph = (uint32_t)((j >> 2) & 1);
+            if (block ? !mbar_wait_backoff(&stored[bj], ph, kWaitLimitCycles) : !mbar_try_wait(&stored[bj], ph))
+                return false;
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
+            atomicAdd(P.done + sig_tile[bj], NW);
+            return true;
+        };
+        bool failed = false;
         for (long long it = 0;; ++it) {
             const int b = (int)(it & 1);
-            if (it >= 2 && !mbar_wait_bounded(&empty[b], (uint32_t)(((it - 2) >> 1) & 1), limit)) {
+            if (PERSIST) {
+                // iteration it - 4 (the last one on stored[it & 3]) is
+                // published before iteration it is handed out: that barrier
+                // then never runs two phases ahead of what the producer has
+                // seen (the consumers are two items behind at most, so this
+                // hardly ever waits)
+                bool okp = true;
+                while (okp && sig <= it - 4) {
+                    okp = publish(sig, true);
+                    sig += okp ? 1 : 0;
+                }
+                if (!okp) {
+                    atomicExch(P.err, kDevTimeout);
+                    tile_of[b] = -1;
+                    mbar_arrive(&full[b]);
+                    if (issued[b ^ 1] == it - 1)
+                        mbar_wait_bounded(&full[b ^ 1], (uint32_t)(((it - 1) >> 1) & 1), kWaitLimitCycles);
+                    return;
+                }
+                while (sig < it && publish(sig, false))
+                    ++sig;
+            }
+            if (it >= 2 && !mbar_wait_backoff(&empty[b], (uint32_t)(((it - 2) >> 1) & 1), limit)) {
                 atomicExch(P.err, kDevTimeout);
                 // let this CTA's own copies in flight land before it leaves
                 for (int q = 0; q < 2; ++q)
@@ -566,16 +661,65 @@ __global__ void __launch_bounds__(Ws<TR>::kThreads, Ws<TR>::kMinBlocks)
                         mbar_wait_bounded(&full[q], (uint32_t)((issued[q] >> 1) & 1), kWaitLimitCycles);
                 return;
             }
-            const long long tile = it == 0 ? (long long)blockIdx.x : (long long)gridDim.x + atomicAdd(P.tile_ctr, 1);
-            if (tile >= P.n_tiles) {
-                tile_of[b] = -1;  // no more tiles: the consumers leave
+            long long q;
+            if (PERSIST)
+                q = atomicAdd(P.tile_ctr, 1);  // only running CTAs hold items
+            else
+                q = it == 0 ? (long long)blockIdx.x : (long long)gridDim.x + atomicAdd(P.tile_ctr, 1);
+            const long long k = PERSIST ? q / P.n_tiles : 0;
+            const long long tile = q - k * P.n_tiles;
+            bool ok = q < items;
+            if (ok && PERSIST && k > 0) {
+                // inputs of (k, tile): tiles tile - 1 .. tile + 1 of round k - 1
+                const int need = (int)(k * NW);
+                const long long jlo = tile > 0 ? tile - 1 : 0;
+                const long long jhi = tile + 1 < P.n_tiles ? tile + 1 : P.n_tiles - 1;
+                bool ready = true;
+                for (long long j = jlo; j <= jhi; ++j)
+                    ready = ready && ld_acquire(P.done + j) >= need;
+                if (!ready) {
+                    // before blocking: publish everything this CTA owes
+                    while (ok && sig < it) {
+                        ok = publish(sig, true);
+                        sig += ok ? 1 : 0;
+                    }
+                    const long long t0 = clock64();
+                    for (long long j = jlo; ok && j <= jhi; ++j) {
+                        while (ld_acquire(P.done + j) < need) {
+                            if (*(volatile int *)P.err != 0 || clock64() - t0 > limit) {
+                                ok = false;
+                                break;
+                            }
+                            __nanosleep(64);
+                        }
+                    }
+                    if (!ok) {
+                        atomicExch(P.err, kDevTimeout);
+                        failed = true;
+                    }
+                }
+                // the generic-proxy stores of those tiles, seen by this
+                // thread, before its TMA (async proxy) reads them
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
+            if (!ok) {
+                tile_of[b] = -1;  // no more items: the consumers leave
                 mbar_arrive(&full[b]);
+                // the copy of the previous item may still be landing (the one
+                // before it was read before empty[b] completed)
+                if (issued[b ^ 1] == it - 1)
+                    mbar_wait_bounded(&full[b ^ 1], (uint32_t)(((it - 1) >> 1) & 1), kWaitLimitCycles);
+                // what this CTA still owes (its consumers finish their items)
+                while (PERSIST && !failed && sig < it && publish(sig, true))
+                    ++sig;
                 return;
             }
-            tile_of[b] = tile;
+            tile_of[b] = q;
+            if (PERSIST)
+                sig_tile[it & 3] = (int)tile;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&full[b], kTileBytes);
-            tma_load_rows(tiles + b * kTileBytes, &tmap, &full[b], (int)(tile * ur - hr));
+            tma_load_rows(tiles + b * kTileBytes, (k & 1) ? &tmap1 : &tmap0, &full[b], (int)(tile * ur - hr));
             issued[b] = it;
         }
     }
@@ -594,9 +738,13 @@ __global__ void __launch_bounds__(Ws<TR>::kThreads, Ws<TR>::kMinBlocks)
                 atomicExch(P.err, kDevTimeout);
             return;
         }
-        const long long tile = tile_of[b];
-        if (tile < 0)
+        const long long q = tile_of[b];
+        if (q < 0)
             return;
+        // round and tile (both fit 32 bits: tiles < 2^31, rounds <= steps)
+        const int k = PERSIST ? (int)(q / P.n_tiles) : 0;
+        const int tile = (int)(q - (long long)k * P.n_tiles);
+        const BRound rd = PERSIST ? round_of(P, k) : launch_round(P);
         const unsigned char *cur = tiles + b * kTileBytes;
         Real v[K];
         {
@@ -615,7 +763,7 @@ __global__ void __launch_bounds__(Ws<TR>::kThreads, Ws<TR>::kMinBlocks)
         if (lane == 0)
             mbar_arrive(&empty[b]);  // this warp is done with the buffer
 
-        const long long grow = tile * ur - hr + my_row;
+        const long long grow = (long long)tile * ur - hr + my_row;
         const int pid = (grow >= 0 && grow < P.n_rows) ? __ldg(P.row_pid + grow) : -1;
         BatchDesc bd{};
         Span sp{K + 1, K + 1};
@@ -628,13 +776,13 @@ __global__ void __launch_bounds__(Ws<TR>::kThreads, Ws<TR>::kMinBlocks)
         const long long g0 = pid >= 0 ? grow * K - bd.off : 0;
         if (P.scaled) {
             if (edge_warp)
-                run_batch_scaled<true>(v, P, bd, pid, g0, x, sp);
+                run_batch_scaled<true>(v, P, rd, bd, pid, g0, x, sp);
             else
-                run_batch_scaled<false>(v, P, bd, pid, g0, x, sp);
+                run_batch_scaled<false>(v, P, rd, bd, pid, g0, x, sp);
         } else if (edge_warp) {
-            run_batch<true>(v, P, bd, x, sp);
+            run_batch<true>(v, P, rd, bd, x, sp);
         } else {
-            run_batch<false>(v, P, bd, x, sp);
+            run_batch<false>(v, P, rd, bd, x, sp);
         }
 
         if (writes) {
@@ -647,20 +795,20 @@ __global__ void __launch_bounds__(Ws<TR>::kThreads, Ws<TR>::kMinBlocks)
                 // only the points of the thread's problem
 #pragma unroll
                 for (int c = 0; c < CH; ++c) {
-                    Real *q = reinterpret_cast<Real *>(rp + ((c ^ (row_local & 7)) << 4));
+                    Real *qp = reinterpret_cast<Real *>(rp + ((c ^ (row_local & 7)) << 4));
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const int j = c * 4 + i;
                         if (pid >= 0 && j >= sp.jlo && j < sp.jhi)
-                            q[i] = v[j];
+                            qp[i] = v[j];
                     }
                 }
             }
         }
         __syncwarp();
         {
-            const long long grow0 = tile * ur + (long long)warp * out_rows;
-            unsigned char *out = static_cast<unsigned char *>(P.out);
+            const long long grow0 = (long long)tile * ur + (long long)warp * out_rows;
+            unsigned char *out = static_cast<unsigned char *>(PERSIST ? P.outs[k & 1] : P.out);
             for (int ch = lane; ch < out_rows * CH; ch += 32) {
                 const int lr = ch / CH, c = ch % CH;
                 const long long gr = grow0 + lr;
@@ -670,6 +818,8 @@ __global__ void __launch_bounds__(Ws<TR>::kThreads, Ws<TR>::kMinBlocks)
             }
         }
         __syncwarp();
+        if (PERSIST && lane == 0)
+            mbar_arrive(&stored[it & 3]);  // this warp's stores of the item (the producer publishes)
     }
 }
 
@@ -697,19 +847,34 @@ cudaError_t batch_attr_and_occupancy(int *blocks)
 template <int TR>
 cudaError_t ws_attr_and_occupancy(int *blocks)
 {
-    cudaError_t e = cudaFuncSetAttribute(tbb_ws_kernel<TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(tbb_ws_kernel<TR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Ws<TR>::smem_bytes());
     if (e != cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tbb_ws_kernel<TR>, Ws<TR>::kThreads,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tbb_ws_kernel<TR, false>, Ws<TR>::kThreads,
                                                          Ws<TR>::smem_bytes());
 }
 
 template <int TR>
-cudaError_t launch_ws(const void *tmap, const TbbParams &p, int grid, cudaStream_t s)
+cudaError_t ws_persist_occupancy(int *blocks)
 {
-    const CUtensorMap *m = static_cast<const CUtensorMap *>(tmap);
-    tbb_ws_kernel<TR><<<grid, Ws<TR>::kThreads, Ws<TR>::smem_bytes(), s>>>(*m, p);
+    cudaError_t e = cudaFuncSetAttribute(tbb_ws_kernel<TR, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Ws<TR>::smem_bytes());
+    if (e != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, tbb_ws_kernel<TR, true>, Ws<TR>::kThreads,
+                                                         Ws<TR>::smem_bytes());
+}
+
+template <int TR>
+cudaError_t launch_ws(const void *tmap, const void *tmap_other, const TbbParams &p, int grid, cudaStream_t s)
+{
+    const CUtensorMap *m0 = static_cast<const CUtensorMap *>(tmap);
+    const CUtensorMap *m1 = static_cast<const CUtensorMap *>(tmap_other ? tmap_other : tmap);
+    if (p.rounds > 1)
+        tbb_ws_kernel<TR, true><<<grid, Ws<TR>::kThreads, Ws<TR>::smem_bytes(), s>>>(*m0, *m1, p);
+    else
+        tbb_ws_kernel<TR, false><<<grid, Ws<TR>::kThreads, Ws<TR>::smem_bytes(), s>>>(*m0, *m1, p);
     return cudaGetLastError();
 }
 
@@ -878,10 +1043,19 @@ cudaError_t tbb_occupancy(int prec, int tile_rows, int *blocks)
                             : batch_attr_and_occupancy<float, true, 256>(blocks);
 }
 
-cudaError_t launch_tbb(int prec, int tile_rows, const void *tmap, const TbbParams &p, int grid, cudaStream_t s)
+cudaError_t tbb_persist_occupancy(int tile_rows, int *blocks)
+{
+    return tile_rows == 128 ? ws_persist_occupancy<128>(blocks) : ws_persist_occupancy<256>(blocks);
+}
+
+cudaError_t launch_tbb(int prec, int tile_rows, const void *tmap, const TbbParams &p, int grid, cudaStream_t s,
+                       const void *tmap_other)
 {
     if (prec == 1)
-        return tile_rows == 128 ? launch_ws<128>(tmap, p, grid, s) : launch_ws<256>(tmap, p, grid, s);
+        return tile_rows == 128 ? launch_ws<128>(tmap, tmap_other, p, grid, s)
+                                : launch_ws<256>(tmap, tmap_other, p, grid, s);
+    if (p.rounds > 1)
+        return cudaErrorInvalidValue;  // one launch per round for the other kernels
     if (prec == 0)
         return tile_rows == 128 ? launch_batch_one<double, false, 128>(tmap, p, grid, s)
                                 : launch_batch_one<double, false, 256>(tmap, p, grid, s);

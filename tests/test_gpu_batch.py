@@ -303,3 +303,54 @@ def test_tune_picks_a_geometry_on_the_callers_data():
         start = u[offs[i]:offs[i] + n[i]].astype(np.float32).astype(np.float64)
         want = oracle.run(start, r[i], bl[i], br[i], 60)
         assert rel(got[offs[i]:offs[i] + n[i]], want) <= tol(B.GE_F32, r[i]), i
+
+
+@pytest.mark.parametrize("tile_rows", [256, 128])
+@pytest.mark.parametrize("depth,steps", [(7, 301), (48, 2000), (96, 97)])
+def test_persistent_launch_gives_the_per_launch_bits(tile_rows, depth, steps):
+    """A plain FP32 run as one persistent launch (rounds of `depth` steps,
+    tiles of a round waiting on their neighbours of the round before) gives
+    the same bits as one launch per round, and matches the oracle."""
+    n, r, bl, br, offs, total, u = make_batch(MIXED * 3, seed=43 + depth, gap=32)
+    plan = B.ge_batch_create(n, r, bl, br, offs, total, B.GE_F32)
+    B.ge_batch_set_geometry(plan, tile_rows, 0)
+    B.ge_batch_set_depth(plan, depth)
+    outs = []
+    for persist in (0, 1):
+        B.ge_batch_set_persistent(plan, persist)
+        assert B.ge_batch_get_persistent(plan) == persist
+        x = torch.from_numpy(u).to(DEV, torch.float32)
+        B.ge_batch_run(plan, x, steps)
+        B.ge_batch_sync(plan)
+        outs.append(x.double().cpu().numpy())
+    B.ge_batch_destroy(plan)
+    assert np.array_equal(outs[0], outs[1])
+    got = outs[1]
+    for i in range(len(n)):
+        start = u[offs[i]:offs[i] + n[i]].astype(np.float32).astype(np.float64)
+        want = oracle.run(start, r[i], bl[i], br[i], steps)
+        assert rel(got[offs[i]:offs[i] + n[i]], want) <= tol(B.GE_F32, r[i]), i
+
+
+def test_persistent_launch_in_a_graph():
+    """Captured into a CUDA graph, a persistent run is its counter resets and
+    one launch; replays give the direct run's bits."""
+    n, r, bl, br, offs, total, u = make_batch(MIXED * 2, seed=44)
+    u0 = torch.from_numpy(u).to(DEV, torch.float32)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan = B.ge_batch_create(n, r, bl, br, offs, total, B.GE_F32, stream=s)
+        B.ge_batch_set_depth(plan, 32)
+        B.ge_batch_set_persistent(plan, 1)
+        a = u0.clone()
+        B.ge_batch_run(plan, a, 200)
+        x = u0.clone()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            x.copy_(u0)
+            B.ge_batch_run(plan, x, 200)
+        g.replay()
+        g.replay()
+    B.ge_batch_sync(plan)
+    B.ge_batch_destroy(plan)
+    assert torch.equal(a, x)
