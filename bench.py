@@ -790,6 +790,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-probe", action="store_true", help="skip the FMA throughput probe")
+    ap.add_argument("--probe-only", action="store_true",
+                    help="run only the FMA throughput probe sweep (FP64 and FP32) and print it")
     ap.add_argument("--only-surrogate", action="store_true", help="run only the surrogate workload")
     ap.add_argument("--sno-train-steps", type=int, default=3000)
     ap.add_argument("--no-sno-sweep", action="store_true", help="skip the surrogate's jump-length sweep")
@@ -827,6 +829,16 @@ def main():
         return 0
     if args.only_surrogate:
         print(json.dumps({"surrogate": measure_surrogate(B, torch, inputs, args.sno_train_steps)}), flush=True)
+        return 0
+    if args.probe_only:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        st = torch.cuda.Stream(device=dev)
+        res = {}
+        for name, pr in (("f64", B.GE_F64), ("f32", B.GE_F32)):
+            fma_s, cps, chains = fma_probe(B, torch, dev, st, pr, sms)
+            res[name] = {"fma_per_s": fma_s, "fma_per_clk_per_sm_at_max_clock": fma_s / (sms * 2070e6),
+                         "best_ctas_per_sm": cps, "best_chains": chains}
+        print(json.dumps({"alu_probe": res}), flush=True)
         return 0
     if args.only_sno_sweep:
         print(json.dumps({"surrogate_k_sweep": measure_surrogate_k_sweep(B, torch, inputs, args.sno_train_steps)}),
