@@ -183,7 +183,10 @@ def dist_setup(args):
     pg = None
     if world > 1:
         import torch.distributed as dist
-        backend = "gloo" if args.impl == "reference" else "nccl"
+        # GE_BENCH_DIST_BACKEND=gloo runs the multi-rank code paths with the
+        # ranks sharing fewer GPUs than ranks (a check of the host logic; their
+        # kernels never wait on one another, halos travel through the host)
+        backend = "gloo" if args.impl == "reference" else os.environ.get("GE_BENCH_DIST_BACKEND", "nccl")
         dist.init_process_group(backend=backend)
         pg = dist
     return world, rank, local, pg
@@ -820,6 +823,7 @@ def main():
     from paper_1310_3422_gb300 import inputs
 
     B.load()
+    local = local % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if args.only_batched:
