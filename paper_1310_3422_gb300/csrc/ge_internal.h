@@ -252,6 +252,9 @@ cudaError_t launch_sweep_tb_f32(const float *in, float *out, long long n, int pa
 // prec: 0 = FP64, 1 = FP32, 2 = FP32 compensated.  tmap: 128-byte-aligned
 // CUtensorMap (opaque here) describing the source buffer.
 cudaError_t launch_tb(int prec, const void *tmap, const TbParams &p, int grid, cudaStream_t s);
+// A launch of exactly one block step and nothing else (no entry, exit;
+// plain FP32): the streaming kernel, from buffer `in` to `out`.
+cudaError_t launch_tb_stream(int prec, const void *in, void *out, const TbParams &p, cudaStream_t s);
 // tile_rows: 256 or 128 (the tile geometry of the plan; the tensor map's box
 // must have as many rows).
 cudaError_t launch_tbb(int prec, int tile_rows, const void *tmap, const TbbParams &p, int grid, cudaStream_t s,

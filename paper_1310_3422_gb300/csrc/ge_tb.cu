@@ -348,6 +348,144 @@ __global__ void __launch_bounds__(Layout<Real, COMP>::NT, Layout<Real, COMP>::MI
     }
 }
 
+// One block step of a launch that does nothing else: no entry or exit
+// conversion, n_mid = 1 (the middle launches of the one-step-per-launch
+// path).  Such a launch moves 2 x 4 bytes per point for one multiply-add in
+// FP32, so it is an HBM stream: no tiles, shared memory or barriers.  (In
+// FP64 the same stream ran slower than the tiled kernel, 0.54 against 0.66
+// of the HBM roofline, so the FP64 one-step launches keep the TMA-fed tiled
+// kernel.  The FP64 kernels' profiles show DFMA issue waiting on the
+// tex_throttle queue, which the stream's global loads and stores also use.)
+// A warp takes 4 KB blocks; lane l holds the 16-byte chunks l, 32 + l, ...,
+// 224 + l of the block (every load and store of the warp is 512 contiguous
+// bytes).  A chunk starts on an even point, so grouping 0 pairs points inside
+// a chunk; under grouping 1 a chunk's first point pairs with the previous
+// chunk's last (the lane below, or lane 31 of the row before) and its last
+// with the next chunk's first, by shuffles, and a block's two outer
+// neighbours come from global memory.  Each chunk then takes exactly the
+// tiled kernel's stage (same arithmetic, same bits), the checked stage for a
+// chunk that holds a wall point, a singleton or a point outside the grid.
+constexpr int kStreamChunks = 8;  // 16-byte chunks per lane per block
+constexpr int kStreamThreads = 256;
+
+template <int Q, typename Real>
+__global__ void __launch_bounds__(kStreamThreads) onestep_stream_kernel(const Real *__restrict__ in,
+                                                                        Real *__restrict__ out,
+                                                                        const __grid_constant__ TbParams P)
+{
+    constexpr int E = 16 / (int)sizeof(Real);       // points per chunk
+    constexpr int BLK = 32 * kStreamChunks * E;     // points per warp block
+    const int lane = threadIdx.x & 31;
+    const long long total = P.n_rows * (kRowBytes / (long long)sizeof(Real));  // whole rows
+    const long long n_blocks = (total + BLK - 1) / BLK;
+    const long long warp0 = ((long long)blockIdx.x * kStreamThreads + threadIdx.x) >> 5;
+    const long long warps = ((long long)gridDim.x * kStreamThreads) >> 5;
+    const Real g = (Real)P.g, kap = (Real)P.kappa;
+    const StageC<Real> c{g, (Real)0, kap, (Real)0, (Real)0};
+    const bool rescale = P.rescale_every > 0 && P.rescale_phase == 1;
+    const Real rs = rescale ? pow2neg<Real>(P.rs_exp[0]) : (Real)1;
+    for (long long blk = warp0; blk < n_blocks; blk += warps) {
+        const long long base = blk * BLK;
+        Real v[kStreamChunks][E];
+#pragma unroll
+        for (int i = 0; i < kStreamChunks; ++i) {
+            const long long e0 = base + (long long)(i * 32 + lane) * E;
+            if (e0 < total) {
+                if constexpr (E == 2) {
+                    const double2 q = *reinterpret_cast<const double2 *>(in + e0);
+                    v[i][0] = q.x;
+                    v[i][1] = q.y;
+                } else {
+                    const float4 q = *reinterpret_cast<const float4 *>(in + e0);
+                    v[i][0] = q.x;
+                    v[i][1] = q.y;
+                    v[i][2] = q.z;
+                    v[i][3] = q.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < E; ++j)
+                    v[i][j] = (Real)0;
+            }
+        }
+        // outer neighbours of the block (grouping 1 only)
+        Real before = (Real)0, after = (Real)0;
+        if (Q == 1) {
+            if (lane == 0 && base > 0)
+                before = in[base - 1];
+            if (lane == 31 && base + BLK < total)
+                after = in[base + BLK];
+        }
+        Real nv[kStreamChunks][E];
+#pragma unroll
+        for (int i = 0; i < kStreamChunks; ++i) {
+            Real L = 0, R = 0;
+            if (Q == 1) {
+                L = __shfl_up_sync(0xffffffffu, v[i][E - 1], 1);
+                const Real wrapL = __shfl_sync(0xffffffffu, i > 0 ? v[i - 1][E - 1] : before, 31);
+                if (lane == 0)
+                    L = i > 0 ? wrapL : before;
+                R = __shfl_down_sync(0xffffffffu, v[i][0], 1);
+                const Real wrapR = __shfl_sync(0xffffffffu, i + 1 < kStreamChunks ? v[i + 1][0] : after, 0);
+                if (lane == 31)
+                    R = i + 1 < kStreamChunks ? wrapR : after;
+            }
+            const long long g0 = base + (long long)(i * 32 + lane) * E;
+#pragma unroll
+            for (int j = 0; j < E; ++j)
+                nv[i][j] = v[i][j];
+            if (g0 >= 1 && g0 + E <= P.n - 1) {
+                stage<Q, kMid, false>(nv[i], L, R, Span{-1, E + 1}, c);
+            } else {
+                // the wall terms of this step, scaled by sigma after it
+                // (double arithmetic only here: FP64 is slow on this GPU)
+                const double sig = P.sigma_in * P.onepg;
+                const StageC<Real> ce{g, (Real)0, kap, (Real)(sig * P.f_l), (Real)(sig * P.f_r)};
+                stage<Q, kMid, true>(nv[i], L, R, make_span<E>(g0, P.n), ce);
+            }
+            if (rescale) {
+#pragma unroll
+                for (int j = 0; j < E; ++j)
+                    nv[i][j] *= rs;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kStreamChunks; ++i) {
+            const long long e0 = base + (long long)(i * 32 + lane) * E;
+            if (e0 < total) {
+                if constexpr (E == 2)
+                    *reinterpret_cast<double2 *>(out + e0) = make_double2(nv[i][0], nv[i][1]);
+                else
+                    *reinterpret_cast<float4 *>(out + e0) = make_float4(nv[i][0], nv[i][1], nv[i][2], nv[i][3]);
+            }
+        }
+    }
+}
+
+template <typename Real>
+cudaError_t launch_stream(const void *in, void *out, const TbParams &p, cudaStream_t s)
+{
+    constexpr int E = 16 / (int)sizeof(Real);
+    constexpr long long BLK = 32LL * kStreamChunks * E;
+    const long long total = p.n_rows * (kRowBytes / (long long)sizeof(Real));
+    const long long n_blocks = (total + BLK - 1) / BLK;
+    const long long warps_per_cta = kStreamThreads / 32;
+    // one warp per block: the CTAs of a stream start as others finish, with no
+    // partial second wave of a capped grid
+    long long grid = (n_blocks + warps_per_cta - 1) / warps_per_cta;
+    if (grid > (1LL << 30))
+        grid = 1LL << 30;  // grid-stride beyond that
+    if (grid < 1)
+        grid = 1;
+    const Real *src = static_cast<const Real *>(in);
+    Real *dst = static_cast<Real *>(out);
+    if (p.p_first & 1)
+        onestep_stream_kernel<1, Real><<<(int)grid, kStreamThreads, 0, s>>>(src, dst, p);
+    else
+        onestep_stream_kernel<0, Real><<<(int)grid, kStreamThreads, 0, s>>>(src, dst, p);
+    return cudaGetLastError();
+}
+
 template <typename Real, bool COMP>
 cudaError_t launch_one(const void *tmap, const TbParams &p, int grid, cudaStream_t s)
 {
@@ -406,6 +544,13 @@ cudaError_t tb_occupancy(int prec, int *blocks)
     if (prec == 1)
         return set_attr_and_occupancy<float, false>(blocks);
     return set_attr_and_occupancy<float, true>(blocks);
+}
+
+cudaError_t launch_tb_stream(int prec, const void *in, void *out, const TbParams &p, cudaStream_t s)
+{
+    if (prec == 1)
+        return launch_stream<float>(in, out, p, s);
+    return cudaErrorInvalidValue;  // FP64 and compensated FP32 keep the tiled kernel
 }
 
 cudaError_t launch_tb(int prec, const void *tmap, const TbParams &p, int grid, cudaStream_t s)

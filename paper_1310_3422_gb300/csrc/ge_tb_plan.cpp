@@ -115,10 +115,16 @@ cudaError_t tb_run(const TbTarget &t, const TbParams &base, double growth_lo, bo
             grid = p.n_tiles;
         if (grid < 1)
             grid = 1;
-        // the launch's tile queue starts empty
-        cudaError_t e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int), s);
-        if (e == cudaSuccess)
-            e = df ? launch_tb_df(t.tmap[*cur], p, (int)grid, s) : launch_tb(prec, t.tmap[*cur], p, (int)grid, s);
+        cudaError_t e;
+        if (!df && prec == 1 && p.n_mid == 1 && !p.do_entry && !p.do_exit && p.stall == 0) {
+            // one FP32 block step and nothing else: an HBM stream, no tiles
+            e = launch_tb_stream(prec, t.buf[*cur], p.out, p, s);
+        } else {
+            // the launch's tile queue starts empty
+            e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int), s);
+            if (e == cudaSuccess)
+                e = df ? launch_tb_df(t.tmap[*cur], p, (int)grid, s) : launch_tb(prec, t.tmap[*cur], p, (int)grid, s);
+        }
         if (e != cudaSuccess)
             return e;
         *cur ^= 1;
