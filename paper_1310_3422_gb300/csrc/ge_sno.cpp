@@ -87,12 +87,17 @@ struct ge_sno {
     bool tc = true;                       // use it where the shape allows
     bool tc_ready = false;                // tensor maps encoded
     int num_sms = 0;
-    void *yt = nullptr;                   // [max_batch][C][2M] BF16
     void *wt = nullptr;                   // [L][C out][C in] BF16
     void *q1t = nullptr;                  // [H][C] BF16
+    void *wst = nullptr;                  // [L][M][2C out][2C in] BF16 (K-major spectral weights)
+    // the weight-derived operands above (and the rounded weights pw, pw16)
+    // no longer match the parameters: set when the parameters change
+    bool tc_stale = true;
     int *err = nullptr;                   // device error word of the tensor-core kernels
-    CUtensorMap tm_g, tm_yt, tm_wt, tm_q1t;
+    CUtensorMap tm_g, tm_y, tm_wt, tm_q1t, tm_f, tm_wst;
     std::vector<CUtensorMap> tm_v;        // one per activation buffer v[0..L]
+    std::vector<CUtensorMap> tm_vs;       // store maps of v[1..L] (index l: v[l + 1])
+    std::vector<CUtensorMap> tm_vh;       // one per spectrum buffer vh[0..L-1]
     std::vector<void *> allocs;
 };
 
@@ -210,8 +215,8 @@ bool tc_shape(const ge_sno *s)
 }
 bool tc_active(const ge_sno *s) { return s->tc && !s->split && tc_shape(s) && s->tc_ready; }
 
-// Inference with the tensor-core kernels for the fused layers and the
-// projection (the truncated DFT and the mode mixing keep the mma.sync GEMM).
+// Inference with the tensor-core kernels for the truncated DFT, the fused
+// layers and the projection (the mode mixing keeps the mma.sync GEMM).
 ge_status forward_tc(ge_sno *s, int B, const float *u0, const float *r, const float *bl, const float *br,
                      float *out);
 
@@ -310,14 +315,21 @@ ge_status forward_tc(ge_sno *s, int B, const float *u0, const float *r, const fl
     const long long R = (long long)B * n;
     cudaStream_t st = s->stream;
     const float *P = s->pw;
-    SNO_TRY(ge::sno_round_bf16(s->params, s->pw, s->pw16, s->n_params, st));
-    // K-major copies of the B operands: W^T per layer, Q1^T
-    for (int l = 0; l < s->L; ++l)
-        SNO_TRY(ge::sno_transpose_rows(at(s->pw16, s->lay[l].w, true), at(s->wt, (long long)l * C * C, true), 1, C,
-                                       C, st));
-    SNO_TRY(ge::sno_transpose_rows(at(s->pw16, s->off_q1, true), s->q1t, 1, C, H, st));
+    if (s->tc_stale) {
+        // operands derived from the weights, once per parameter change: the
+        // rounded weights, the K-major copies W^T (per layer) and Q1^T, and
+        // the K-major spectral weights Wspec_m^T
+        SNO_TRY(ge::sno_round_bf16(s->params, s->pw, s->pw16, s->n_params, st));
+        for (int l = 0; l < s->L; ++l)
+            SNO_TRY(ge::sno_transpose_rows(at(s->pw16, s->lay[l].w, true), at(s->wt, (long long)l * C * C, true), 1,
+                                           C, C, st));
+        SNO_TRY(ge::sno_transpose_rows(at(s->pw16, s->off_q1, true), s->q1t, 1, C, H, st));
+        for (int l = 0; l < s->L; ++l)
+            SNO_TRY(ge::sno_spec_assemble(P + s->lay[l].rr, P + s->lay[l].ri,
+                                          at(s->wst, (long long)l * M * 4 * C * C, true), M, C, 1, st, true));
+        s->tc_stale = false;
+    }
     SNO_TRY(ge::sno_lift(u0, r, bl, br, weight(s, s->off_w0), P + s->off_b0, s->v[0], B, n, C, 1, st));
-    ge::GemmArgs g;
     ge::SnoTcArgs a{};
     a.n_tiles = R / 128;
     a.tiles_per_problem = n / 128;
@@ -325,25 +337,17 @@ ge_status forward_tc(ge_sno *s, int B, const float *u0, const float *r, const fl
     a.limit = ge::kWaitLimitCycles;
     for (int l = 0; l < s->L; ++l) {
         const LayerOff &o = s->lay[l];
-        void *ws = at(s->wspec, (long long)l * M * 4 * C * C, true);
-        SNO_TRY(ge::sno_spec_assemble(P + o.rr, P + o.ri, ws, M, C, 1, st));
-        g = gemm(s->F16, n, 1, s->v[l], C, 1, s->vh[l], C, 2 * M, C, n);
-        g.sA = 0;
-        g.sB = (long long)n * C;
-        g.sC = 2LL * M * C;
-        SNO_TRY(ge::sno_gemm(act_fmt(g, true), B, false, st));
-        g = gemm(s->vh[l], 2LL * M * C, 1, ws, 2 * C, 1, s->y, 2LL * M * C, B, 2 * C, 2 * C);
-        g.sA = 2 * C;
-        g.sB = 4LL * C * C;
-        g.sC = 2 * C;
-        SNO_TRY(ge::sno_gemm(act_fmt(g, true), M, false, st));
-        // y [B][2M][C] -> y^T [B][C][2M] (K-major B operand of G y)
-        SNO_TRY(ge::sno_transpose_rows(s->y, s->yt, B, 2 * M, C, st));
+        // truncated DFT: vh[b] = F v[b]
+        a.out = s->vh[l];
+        SNO_TRY(ge::sno_tc_dft(&s->tm_f, &s->tm_v[l], a, s->num_sms, st));
+        // per-mode complex mixing: y[b, m] = vh[b, m] Wspec_m
+        const ge::SnoTcMixArgs x{B, l * M * 2 * C, 2LL * M * C, s->y, s->err, ge::kWaitLimitCycles};
+        SNO_TRY(ge::sno_tc_mix(&s->tm_vh[l], &s->tm_wst, x, M, st));
         a.b2_row = l * C;
         a.gelu = l < s->L - 1 ? 1 : 0;
         a.bias = P + o.b;
         a.out = s->v[l + 1];
-        const ge::SnoTcMaps m{&s->tm_g, &s->tm_yt, &s->tm_v[l], &s->tm_wt};
+        const ge::SnoTcMaps m{&s->tm_g, &s->tm_y, &s->tm_v[l], &s->tm_wt, &s->tm_vs[l]};
         SNO_TRY(ge::sno_tc_layer(m, a, s->num_sms, st));
     }
     a.b2_row = 0;
@@ -353,7 +357,7 @@ ge_status forward_tc(ge_sno *s, int B, const float *u0, const float *r, const fl
     a.q2b = P + s->off_qb2;
     a.u0 = u0;
     a.out = out;
-    const ge::SnoTcMaps m{nullptr, nullptr, &s->tm_v[s->L], &s->tm_q1t};
+    const ge::SnoTcMaps m{nullptr, nullptr, &s->tm_v[s->L], &s->tm_q1t, nullptr};
     SNO_TRY(ge::sno_tc_projection(m, a, s->num_sms, st));
     return GE_OK;
 }
@@ -567,9 +571,9 @@ ge_status ge_sno_create(ge_sno **out, int32_t n, int32_t width, int32_t modes, i
     e = e ? e : alloc(&s->loss, max_batch);
     e = e ? e : alloc(&s->dA, R * (C > H ? C : H));
     e = e ? e : alloc(&s->dB, R * (C > H ? C : H));
-    e = e ? e : alloc_bytes(&s->yt, 2LL * max_batch * 2 * M * C);
     e = e ? e : alloc_bytes(&s->wt, 2LL * layers * C * C);
     e = e ? e : alloc_bytes(&s->q1t, 2LL * H * C);
+    e = e ? e : alloc_bytes(&s->wst, 2LL * layers * M * 4 * C * C);
     e = e ? e : alloc_bytes(reinterpret_cast<void **>(&s->err), 256);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(s->err, 0, 256, s->stream);
@@ -585,12 +589,20 @@ ge_status ge_sno_create(ge_sno **out, int32_t n, int32_t width, int32_t modes, i
     if (tc_shape(s)) {
         // tensor maps of the tensor-core path (BF16 views of the buffers)
         bool ok = bf16_map(&s->tm_g, s->G16, n, 2 * modes, 2 * modes, 128) &&
-                  bf16_map(&s->tm_yt, s->yt, (long long)max_batch * C, 2 * modes, 2 * modes, 64) &&
+                  bf16_map(&s->tm_f, s->F16, 2 * modes, n, 64, 2 * modes) &&
+                  bf16_map(&s->tm_y, s->y, (long long)max_batch * 2 * modes, width, width, 2 * modes) &&
                   bf16_map(&s->tm_wt, s->wt, (long long)layers * C, width, width, 64) &&
                   bf16_map(&s->tm_q1t, s->q1t, hidden, width, width, 128);
+        ok = ok && bf16_map(&s->tm_wst, s->wst, (long long)layers * modes * 2 * width, 2 * width, 64, 128);
         s->tm_v.resize(layers + 1);
         for (int l = 0; l <= layers && ok; ++l)
             ok = bf16_map(&s->tm_v[l], s->v[l], R, width, width, 128);
+        s->tm_vs.resize(layers);
+        for (int l = 0; l < layers && ok; ++l)
+            ok = bf16_map(&s->tm_vs[l], s->v[l + 1], R, width, 32, 32);
+        s->tm_vh.resize(layers);
+        for (int l = 0; l < layers && ok; ++l)
+            ok = bf16_map(&s->tm_vh[l], s->vh[l], max_batch, 2 * modes * width, 64, 128);
         s->tc_ready = ok;
     }
     // DFT bases: F[2m][j] = cos(2 pi m j / n), F[2m+1][j] = -sin(...);
@@ -672,6 +684,7 @@ ge_status ge_sno_set_params(ge_sno *s, const float *src_dev)
 {
     if (!s || !src_dev)
         return sfail(GE_EINVAL, "ge_sno_set_params: NULL argument");
+    s->tc_stale = true;
     cudaError_t e = cudaMemcpyAsync(s->params, src_dev, sizeof(float) * s->n_params, cudaMemcpyDeviceToDevice, s->stream);
     return e == cudaSuccess ? GE_OK : scuda(e, "ge_sno_set_params");
 }
@@ -793,6 +806,7 @@ ge_status ge_sno_adam_step(ge_sno *s, float lr)
     if (!s || !(lr >= 0.0f))
         return sfail(GE_EINVAL, "ge_sno_adam_step: NULL model or bad learning rate");
     s->adam_t += 1;
+    s->tc_stale = true;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.0f - (float)std::pow(b1, (double)s->adam_t), c2 = 1.0f - (float)std::pow(b2, (double)s->adam_t);
     cudaError_t e = ge::sno_adam(s->params, s->grads, s->adam_m, s->adam_v, s->n_params, lr, b1, b2, 1e-8f, c1, c2,

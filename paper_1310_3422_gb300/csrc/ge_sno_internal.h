@@ -62,14 +62,16 @@ cudaError_t sno_gemm(const GemmArgs &g, int batch, bool split, cudaStream_t s);
 // Tensor-core (tcgen05) inference GEMMs of ge_sno_tc.cu, over 128-row tiles
 // of the activation rows (rows = batch * n, n a multiple of 128, C = 64
 // channels, 2M = 32 spectral rows, H = 128 hidden columns).  Tensor maps
-// (CUtensorMap, 64-byte aligned, opaque here), all BF16 and K-major:
-//   layer:      a1 = G [n][2M] (box 32 x 128, 64-byte swizzle), b1 = y^T
-//               [batch * C][2M] (box 32 x 64, 64-byte swizzle), a2 = v
-//               [rows][C] (box 64 x 128, 128-byte swizzle), b2 = W^T of all
-//               layers [L * C][C] (box 64 x 64, 128-byte swizzle);
+// (CUtensorMap, 64-byte aligned, opaque here), all BF16:
+//   layer:      a1 = G [n][2M] (box 32 x 128, 64-byte swizzle), b1 = y
+//               [batch * 2M][C] (box 64 x 32, 128-byte swizzle; read
+//               MN-major), a2 = v [rows][C] (box 64 x 128, 128-byte swizzle),
+//               b2 = W^T of all layers [L * C][C] (box 64 x 64, 128-byte
+//               swizzle);
 //   projection: a2 = v as above, b2 = Q1^T [H][C] (box 64 x 128).
 struct SnoTcMaps {
     const void *a1, *b1, *a2, *b2;
+    const void *out;  // layer: store map of the next activation [rows][C] (box 32 x 32, 64-byte swizzle)
 };
 struct SnoTcArgs {
     long long n_tiles;      // rows / 128
@@ -86,11 +88,30 @@ struct SnoTcArgs {
 };
 cudaError_t sno_tc_layer(const SnoTcMaps &m, const SnoTcArgs &a, int sms, cudaStream_t s);
 cudaError_t sno_tc_projection(const SnoTcMaps &m, const SnoTcArgs &a, int sms, cudaStream_t s);
-// yt[b][c][k] = y[b][k][c] for BF16 [batch][k_rows][c_cols] blocks.
+// Truncated DFT vh[b] = F v[b] on the tensor cores (2M = 32, C = 64; map_f:
+// F [2M][n] BF16, box 64 x 32, 128-byte swizzle; map_v: the activation map of
+// the layer kernel); writes a.out = vh, BF16 [batch][2M][C].
+cudaError_t sno_tc_dft(const void *map_f, const void *map_v, const SnoTcArgs &a, int sms, cudaStream_t s);
+// Mode mixing y[b, m] = vh[b, m] Wspec_m on the tensor cores (2C = 128):
+// map_vh over vh [batch rows][2M * 2C] (box 64 x 128, 128-byte swizzle),
+// map_wst over the K-major spectral weights Wspec_m^T of all layers
+// [L * M * 2C][2C] (box 64 x 128); grid = (ceil(batch / 128), modes).
+struct SnoTcMixArgs {
+    int batch;           // problems (rows of vh and y)
+    int b_row0;          // first row of this layer's block of map_wst (l * M * 2C)
+    long long row_elems; // elements of one problem's spectrum (2M * C)
+    void *y;             // out: BF16 [batch][row_elems]
+    int *err;            // device error word
+    long long limit;     // wait limit in SM cycles
+};
+cudaError_t sno_tc_mix(const void *map_vh, const void *map_wst, const SnoTcMixArgs &a, int modes, cudaStream_t s);
+// yt[b][c][k] = y[b][k][c] for BF16 [batch][k_rows][c_cols] blocks (the
+// K-major copies W^T and Q1^T).
 cudaError_t sno_transpose_rows(const void *y, void *yt, long long batch, int k_rows, int c_cols, cudaStream_t s);
 cudaError_t sno_features(const float *u0, const float *r, const float *bl, const float *br, void *f, int batch,
                          int n, int bf16, cudaStream_t s);
-cudaError_t sno_spec_assemble(const float *rr, const float *ri, void *w, int modes, int c, int bf16, cudaStream_t s);
+cudaError_t sno_spec_assemble(const float *rr, const float *ri, void *w, int modes, int c, int bf16, cudaStream_t s,
+                              bool k_major = false);
 cudaError_t sno_spec_reduce(const float *dw, float *drr, float *dri, int modes, int c, cudaStream_t s);
 cudaError_t sno_colsum(const void *x, float *out, long long rows, int cols, int bf16, cudaStream_t s);
 cudaError_t sno_rel_l2(const float *pred, const float *target, void *dpred, float *loss, int n, int batch, int bf16,

@@ -615,8 +615,10 @@ __global__ void features_kernel(const float *__restrict__ u0, const float *__res
 // vector (re, im): [[Rr^T, Ri^T], [-Ri^T, Rr^T]] with R = Rr + i Ri (C x C,
 // out x in).  Layout of rr/ri: [m][out][in]; of w: [m][2C][2C].
 __global__ void spec_assemble_kernel(const float *__restrict__ rr, const float *__restrict__ ri,
-                                     void *__restrict__ w, int modes, int c, int bf16)
+                                     void *__restrict__ w, int modes, int c, int bf16, int k_major)
 {
+    // k_major: store each mode's matrix transposed, [2C out][2C in] (the
+    // K-major B operand of the tensor-core mixing)
     const long long total = (long long)modes * 2 * c * 2 * c;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         const int m = (int)(e / (4LL * c * c));
@@ -634,10 +636,11 @@ __global__ void spec_assemble_kernel(const float *__restrict__ rr, const float *
             v = -ri[ro];
         else
             v = rr[ro];
+        const long long o = k_major ? (long long)m * 4 * c * c + (long long)col * 2 * c + row : e;
         if (bf16)
-            static_cast<__nv_bfloat16 *>(w)[e] = __float2bfloat16_rn(v);
+            static_cast<__nv_bfloat16 *>(w)[o] = __float2bfloat16_rn(v);
         else
-            static_cast<float *>(w)[e] = v;
+            static_cast<float *>(w)[o] = v;
     }
 }
 
@@ -754,8 +757,9 @@ __global__ void lift_kernel(const float *__restrict__ u0, const float *__restric
                             const float *__restrict__ br, const T *__restrict__ w0, const float *__restrict__ b0,
                             T *__restrict__ v0, int batch, int n, int c, int bf16)
 {
-    // I: index type (32-bit when every index fits: 64-bit divisions cost more
-    // than the rest of the work)
+    // I: index type of the point and work counters (32-bit when they fit:
+    // 64-bit divisions cost more than the rest of the work); the activation
+    // index i * c is formed in 64 bits
     // the lift's weights and bias, once per CTA (c <= kLiftMaxC; else from global)
     __shared__ float sw[4 * kLiftMaxC], sb[kLiftMaxC];
     const bool staged = c <= kLiftMaxC;
@@ -795,13 +799,96 @@ __global__ void lift_kernel(const float *__restrict__ u0, const float *__restric
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 h[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-            *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(v0) + i * c + c0) =
+            *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(v0) + (long long)i * c + c0) =
                 *reinterpret_cast<const uint4 *>(h);
         } else {
 #pragma unroll
             for (int q = 0; q < 8; ++q)
                 if (c0 + q < c)
-                    v0[i * c + c0 + q] = (T)v[q];
+                    v0[(long long)i * c + c0 + q] = (T)v[q];
+        }
+    }
+}
+
+// The same lift with a warp per 32 consecutive points, when the number of
+// channel groups cg divides 32: lane l forms the features of point l once
+// (one division by n, the BF16 roundings), then cg rounds each hand 32 / cg
+// points' features to the lanes by shuffles, lane l computing channel group
+// l % cg of point l / cg of the round.  Each lane's channel group is fixed,
+// so its 8 channels' weights live in registers.  The per-point scalar work
+// is done once per point instead of once per channel group, which leaves
+// the kernel bound by its writes.  Same products in the same order as
+// lift_kernel, so the two give the same bits.
+template <typename T, typename I>
+__global__ void __launch_bounds__(256) lift_fixed_kernel(const float *__restrict__ u0, const float *__restrict__ r,
+                                                         const float *__restrict__ bl, const float *__restrict__ br,
+                                                         const T *__restrict__ w0, const float *__restrict__ b0,
+                                                         T *__restrict__ v0, int batch, int n, int c, int bf16)
+{
+    const int cg = (c + 7) / 8;  // lanes per point
+    const int per_round = 32 / cg;
+    const int lane = threadIdx.x & 31;
+    const int c0 = (lane % cg) * 8;
+    float w[4][8], bias[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int ch = c0 + q < c ? c0 + q : c - 1;
+        bias[q] = b0[ch];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            w[k][q] = (float)w0[k * c + ch];
+    }
+    const I points = (I)batch * n;
+    const I warp0 = ((I)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const I warps = (I)gridDim.x * (blockDim.x / 32);
+    for (I p0 = warp0 * 32; p0 < points; p0 += warps * 32) {
+        // the features of point p0 + lane
+        const I ip = p0 + lane;
+        float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (ip < points) {
+            const int b = (int)(ip / n), j = (int)(ip - (I)b * n);
+            const float x = (float)(j + 1) / (float)(n + 1);
+            g[0] = u0[ip];
+            g[1] = x;
+            g[2] = r[b];
+            g[3] = bl[b] + (br[b] - bl[b]) * x;
+            if (bf16) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    g[k] = __bfloat162float(__float2bfloat16_rn(g[k]));
+            }
+        }
+        for (int rd = 0; rd < cg; ++rd) {
+            const int src = rd * per_round + lane / cg;
+            float f[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                f[k] = __shfl_sync(0xffffffffu, g[k], src);
+            const I i = p0 + src;
+            if (i >= points)
+                continue;
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float a = bias[q];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    a = fmaf(f[k], w[k][q], a);
+                v[q] = a;
+            }
+            if (bf16 && c % 8 == 0) {
+                __nv_bfloat162 h[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    h[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+                *reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(v0) + (long long)i * c + c0) =
+                    *reinterpret_cast<const uint4 *>(h);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (c0 + q < c)
+                        v0[(long long)i * c + c0 + q] = (T)v[q];
+            }
         }
     }
 }
@@ -972,9 +1059,10 @@ cudaError_t sno_features(const float *u0, const float *r, const float *bl, const
     return cudaGetLastError();
 }
 
-cudaError_t sno_spec_assemble(const float *rr, const float *ri, void *w, int modes, int c, int bf16, cudaStream_t s)
+cudaError_t sno_spec_assemble(const float *rr, const float *ri, void *w, int modes, int c, int bf16, cudaStream_t s,
+                              bool k_major)
 {
-    spec_assemble_kernel<<<grid_for(4LL * modes * c * c), 256, 0, s>>>(rr, ri, w, modes, c, bf16);
+    spec_assemble_kernel<<<grid_for(4LL * modes * c * c), 256, 0, s>>>(rr, ri, w, modes, c, bf16, k_major ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1008,7 +1096,42 @@ cudaError_t sno_lift(const float *u0, const float *r, const float *bl, const flo
                      const float *b0, void *v0, int batch, int n, int c, int bf16, cudaStream_t s)
 {
     const long long total = (long long)batch * n * ((c + 7) / 8);
-    {
+    if (32 % ((c + 7) / 8) == 0) {
+        // 32-bit indices when the loop's point counter (up to the points plus
+        // one grid stride of 32 points a warp) cannot overflow them
+        const bool small = (long long)batch * n < (1LL << 31) - 2LL * 32 * 8 * 4096;
+        // a few resident blocks per SM, each warp looping over many points
+        // (the weights are loaded once per thread)
+        static int sms = 0;
+        if (sms == 0) {
+            int dev = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e == cudaSuccess)
+                e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess)
+                return e;
+        }
+        long long blocks = ((long long)batch * n + 255) / 256;
+        if (blocks > 4LL * sms)
+            blocks = 4LL * sms;
+        if (blocks > 4096)
+            blocks = 4096;
+        const int grid = (int)(blocks < 1 ? 1 : blocks);
+        if (bf16 && small)
+            lift_fixed_kernel<__nv_bfloat16, int><<<grid, 256, 0, s>>>(
+                u0, r, bl, br, static_cast<const __nv_bfloat16 *>(w0), b0, static_cast<__nv_bfloat16 *>(v0), batch, n,
+                c, 1);
+        else if (bf16)
+            lift_fixed_kernel<__nv_bfloat16, long long><<<grid, 256, 0, s>>>(
+                u0, r, bl, br, static_cast<const __nv_bfloat16 *>(w0), b0, static_cast<__nv_bfloat16 *>(v0), batch, n,
+                c, 1);
+        else if (small)
+            lift_fixed_kernel<float, int><<<grid, 256, 0, s>>>(u0, r, bl, br, static_cast<const float *>(w0),
+                                                                          b0, static_cast<float *>(v0), batch, n, c, 0);
+        else
+            lift_fixed_kernel<float, long long><<<grid, 256, 0, s>>>(
+                u0, r, bl, br, static_cast<const float *>(w0), b0, static_cast<float *>(v0), batch, n, c, 0);
+    } else {
         // 32-bit indices when the grid-stride loop cannot overflow them
         const bool small = total < (1LL << 31) - 2LL * 256 * 4096;
         if (bf16 && small)

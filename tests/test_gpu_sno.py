@@ -299,3 +299,42 @@ def test_tensor_core_path_matches_the_mma_path(batch):
         want = S.predict(oracle_params(m), FULL, u0, r, bl, br)
         assert np.all(rel_rows(a_tc, want) <= 3e-2)
     B.ge_sno_destroy(m)
+
+
+def test_tensor_core_path_follows_parameter_changes():
+    """The tcgen05 path keeps the operands it derives from the weights (BF16
+    rounding, K-major copies, K-major spectral weights) from one call to the
+    next.  After ge_sno_set_params, and after a training step, its output is
+    bit-for-bit that of a second model given the same parameters (same
+    kernels, same inputs), and differs from the output before the change."""
+    batch = 4
+    m = make_model(FULL, batch, seed=3, split=0)
+    ref = make_model(FULL, batch, seed=9, split=0)
+    u0, r, bl, br = problem_batch(FULL, batch, 23)
+    args = dev(u0, r, bl, br)
+
+    def run(model):
+        out = torch.empty(batch, FULL.n, dtype=torch.float32, device=DEV)
+        B.ge_sno_forward(model, batch, *args, out)
+        B.ge_sno_sync(model)
+        return out.cpu().numpy()
+
+    def same_as_fresh(model):
+        p = torch.tensor(get_params(model), device=DEV)
+        B.ge_sno_set_params(ref, p)
+        return np.array_equal(run(model), run(ref))
+
+    before = run(m)
+    assert same_as_fresh(m)
+    p = torch.tensor(get_params(m), device=DEV)
+    B.ge_sno_set_params(m, p * 0.75)
+    after_set = run(m)
+    assert not np.array_equal(after_set, before)
+    assert same_as_fresh(m)
+    target = torch.tensor(u0, device=DEV)
+    B.ge_sno_train_step(m, batch, *args, target, 1e-3)
+    after_step = run(m)
+    assert not np.array_equal(after_step, after_set)
+    assert same_as_fresh(m)
+    B.ge_sno_destroy(m)
+    B.ge_sno_destroy(ref)
