@@ -841,23 +841,38 @@ __global__ void __launch_bounds__(256) lift_fixed_kernel(const float *__restrict
     const I points = (I)batch * n;
     const I warp0 = ((I)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const I warps = (I)gridDim.x * (blockDim.x / 32);
+    // the loads of point p0 + lane of the next pass are issued before this
+    // pass's stores, so their latency hides behind them
+    float nu = 0.0f, nr = 0.0f, nl = 0.0f, nrt = 0.0f;
+    int nj = 0;
+    auto fetch = [&](I p) {
+        const I ip = p + lane;
+        if (ip < points) {
+            const int b = (int)(ip / n);
+            nj = (int)(ip - (I)b * n);
+            nu = u0[ip];
+            nr = r[b];
+            nl = bl[b];
+            nrt = br[b];
+        }
+    };
+    fetch(warp0 * 32);
     for (I p0 = warp0 * 32; p0 < points; p0 += warps * 32) {
         // the features of point p0 + lane
-        const I ip = p0 + lane;
         float g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (ip < points) {
-            const int b = (int)(ip / n), j = (int)(ip - (I)b * n);
-            const float x = (float)(j + 1) / (float)(n + 1);
-            g[0] = u0[ip];
+        if (p0 + lane < points) {
+            const float x = (float)(nj + 1) / (float)(n + 1);
+            g[0] = nu;
             g[1] = x;
-            g[2] = r[b];
-            g[3] = bl[b] + (br[b] - bl[b]) * x;
+            g[2] = nr;
+            g[3] = nl + (nrt - nl) * x;
             if (bf16) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     g[k] = __bfloat162float(__float2bfloat16_rn(g[k]));
             }
         }
+        fetch(p0 + warps * 32);
         for (int rd = 0; rd < cg; ++rd) {
             const int src = rd * per_round + lane / cg;
             float f[4];
@@ -1100,20 +1115,24 @@ cudaError_t sno_lift(const float *u0, const float *r, const float *bl, const flo
         // 32-bit indices when the loop's point counter (up to the points plus
         // one grid stride of 32 points a warp) cannot overflow them
         const bool small = (long long)batch * n < (1LL << 31) - 2LL * 32 * 8 * 4096;
-        // a few resident blocks per SM, each warp looping over many points
+        // one wave of resident blocks, each warp looping over many points
         // (the weights are loaded once per thread)
-        static int sms = 0;
-        if (sms == 0) {
-            int dev = 0;
+        static int resident = 0;
+        if (resident == 0) {
+            int dev = 0, sms = 0, per_sm = 0;
             cudaError_t e = cudaGetDevice(&dev);
             if (e == cudaSuccess)
                 e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lift_fixed_kernel<__nv_bfloat16, int>, 256,
+                                                                  0);
             if (e != cudaSuccess)
                 return e;
+            resident = sms * (per_sm < 1 ? 1 : per_sm);
         }
         long long blocks = ((long long)batch * n + 255) / 256;
-        if (blocks > 4LL * sms)
-            blocks = 4LL * sms;
+        if (blocks > resident)
+            blocks = resident;
         if (blocks > 4096)
             blocks = 4096;
         const int grid = (int)(blocks < 1 ? 1 : blocks);
