@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cstdint>
 
+#include "ge_f32x2.cuh"
 #include "ge_sno_internal.h"
 
 namespace ge {
@@ -815,10 +816,10 @@ __global__ void lift_kernel(const float *__restrict__ u0, const float *__restric
 // (one division by n, the BF16 roundings), then cg rounds each hand 32 / cg
 // points' features to the lanes by shuffles, lane l computing channel group
 // l % cg of point l / cg of the round.  Each lane's channel group is fixed,
-// so its 8 channels' weights live in registers.  The per-point scalar work
-// is done once per point instead of once per channel group, which leaves
-// the kernel bound by its writes.  Same products in the same order as
-// lift_kernel, so the two give the same bits.
+// so its 8 channels' weights live in registers, as channel pairs for packed
+// FMAs.  The per-point scalar work is done once per point instead of once
+// per channel group.  Same fused products in the same order as lift_kernel,
+// so the two give the same bits.
 template <typename T, typename I>
 __global__ void __launch_bounds__(256) lift_fixed_kernel(const float *__restrict__ u0, const float *__restrict__ r,
                                                          const float *__restrict__ bl, const float *__restrict__ br,
@@ -829,14 +830,15 @@ __global__ void __launch_bounds__(256) lift_fixed_kernel(const float *__restrict
     const int per_round = 32 / cg;
     const int lane = threadIdx.x & 31;
     const int c0 = (lane % cg) * 8;
-    float w[4][8], bias[8];
+    // the weights and biases of channel pairs (q, q + 1), for packed FMAs
+    uint64_t w2[4][4], bias2[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int ch = c0 + q < c ? c0 + q : c - 1;
-        bias[q] = b0[ch];
+    for (int q = 0; q < 8; q += 2) {
+        const int ch0 = c0 + q < c ? c0 + q : c - 1, ch1 = c0 + q + 1 < c ? c0 + q + 1 : c - 1;
+        bias2[q / 2] = f2(b0[ch0], b0[ch1]);
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            w[k][q] = (float)w0[k * c + ch];
+            w2[k][q / 2] = f2((float)w0[k * c + ch0], (float)w0[k * c + ch1]);
     }
     const I points = (I)batch * n;
     const I warp0 = ((I)blockIdx.x * blockDim.x + threadIdx.x) / 32;
@@ -875,21 +877,25 @@ __global__ void __launch_bounds__(256) lift_fixed_kernel(const float *__restrict
         fetch(p0 + warps * 32);
         for (int rd = 0; rd < cg; ++rd) {
             const int src = rd * per_round + lane / cg;
-            float f[4];
+            uint64_t f[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                f[k] = __shfl_sync(0xffffffffu, g[k], src);
+            for (int k = 0; k < 4; ++k) {
+                const float fk = __shfl_sync(0xffffffffu, g[k], src);
+                f[k] = f2(fk, fk);
+            }
             const I i = p0 + src;
             if (i >= points)
                 continue;
             float v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float a = bias[q];
+            for (int q = 0; q < 4; ++q) {
+                uint64_t a = bias2[q];
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    a = fmaf(f[k], w[k][q], a);
-                v[q] = a;
+                    a = f2_fma(f[k], w2[k][q], a);
+                const float2 aq = f2_split(a);
+                v[2 * q] = aq.x;
+                v[2 * q + 1] = aq.y;
             }
             if (bf16 && c % 8 == 0) {
                 __nv_bfloat162 h[4];

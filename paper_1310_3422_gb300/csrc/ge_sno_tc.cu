@@ -47,6 +47,7 @@
 
 #include <cstdint>
 
+#include "ge_f32x2.cuh"
 #include "ge_internal.h"
 #include "ge_sno_internal.h"
 
@@ -228,39 +229,6 @@ __device__ __forceinline__ float gelu_hw(float x)
     float t;
     asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(k0 * (x + k1 * x * x * x)));
     return 0.5f * x * (1.0f + t);
-}
-
-// Packed FP32 pairs (.f32x2: two lanes of FP32 arithmetic per instruction,
-// each rounded as the scalar operation would be).
-__device__ __forceinline__ uint64_t f2(float a, float b)
-{
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float2 f2_split(uint64_t v)
-{
-    float2 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-    return r;
-}
-__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
-{
-    uint64_t r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b)
-{
-    uint64_t r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
-{
-    uint64_t r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
@@ -473,29 +441,38 @@ __global__ void __launch_bounds__(kTcThreads) sno_tc_kernel(const __grid_constan
             } else {
                 // sum_h GELU(x_h) Q2_h with x_h = acc_h + q1_h, on column pairs
                 // in packed FP32: GELU(x) Q2 = (x + x tanh(a)) (Q2 / 2) with
-                // a = x (k0 + k0 k1 x^2); the even and the odd columns keep
-                // their own partial sums, added at the end (a fixed order)
+                // a = x (k0 + k0 k1 x^2).  Pair p of the row goes to partial
+                // sum p % 4 (four short dependency chains); the partial sums
+                // and their two lanes are added at the end in a fixed order.
+                // TMEM is read 64 columns at a time (two loads, one wait).
                 const uint64_t c_lo = f2(kGeluK0, kGeluK0), c_hi = f2(kGeluK0K1, kGeluK0K1);
-                uint64_t acc2 = f2(0.0f, 0.0f);
+                uint64_t part[4];
 #pragma unroll
-                for (int h = 0; h < N / 32; ++h) {
-                    uint32_t r[32];
-                    tmem_ld32(taddr + 32 * h, r);
+                for (int k = 0; k < 4; ++k)
+                    part[k] = f2(0.0f, 0.0f);
+#pragma unroll
+                for (int h = 0; h < N / 64; ++h) {
+                    uint32_t r[2][32];
+                    tmem_ld32(taddr + 64 * h, r[0]);
+                    tmem_ld32(taddr + 64 * h + 32, r[1]);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int c = 0; c < 32; c += 2) {
-                        const float2 bq = *reinterpret_cast<const float2 *>(&s_bias[32 * h + c]);
-                        const float2 wq = *reinterpret_cast<const float2 *>(&s_q2[32 * h + c]);
-                        const uint64_t x = f2_add(f2(__uint_as_float(r[c]), __uint_as_float(r[c + 1])), f2(bq.x, bq.y));
+                    for (int c = 0; c < 64; c += 2) {
+                        const int col = 64 * h + c;
+                        const float2 bq = *reinterpret_cast<const float2 *>(&s_bias[col]);
+                        const float2 wq = *reinterpret_cast<const float2 *>(&s_q2[col]);
+                        const uint32_t *rr = r[c >> 5];
+                        const uint64_t x =
+                            f2_add(f2(__uint_as_float(rr[c & 31]), __uint_as_float(rr[(c & 31) + 1])), f2(bq.x, bq.y));
                         const uint64_t a = f2_mul(x, f2_fma(f2_mul(x, x), c_hi, c_lo));
                         const float2 af = f2_split(a);
                         float t0, t1;
                         asm("tanh.approx.f32 %0, %1;" : "=f"(t0) : "f"(af.x));
                         asm("tanh.approx.f32 %0, %1;" : "=f"(t1) : "f"(af.y));
-                        acc2 = f2_fma(f2_fma(x, f2(t0, t1), x), f2(wq.x, wq.y), acc2);
+                        part[(c >> 1) & 3] = f2_fma(f2_fma(x, f2(t0, t1), x), f2(wq.x, wq.y), part[(c >> 1) & 3]);
                     }
                 }
-                const float2 accf = f2_split(acc2);
+                const float2 accf = f2_split(f2_add(f2_add(part[0], part[1]), f2_add(part[2], part[3])));
                 const float sum = accf.x + accf.y;
                 tc_fence_before();
                 __syncwarp();
