@@ -101,6 +101,52 @@ __device__ __forceinline__ void run_scaled(Real (&v)[K], const TbParams &P, Exch
     const Real g = (Real)P.g, kap = (Real)P.kappa;
     double sig = P.sigma_in;  // used on the checked path only
     int until = P.rescale_phase, ev = 0, m = 0;
+    if constexpr (!EDGE && sizeof(Real) == 4 && K % 4 == 0) {
+        // interior FP32 tiles: the same steps and rescalings on register
+        // pairs (packed FMAs; the same bits)
+        constexpr int H = K / 2;
+        uint64_t pr[H];
+        to_pairs(v, pr);
+        const uint64_t g2 = f2((float)g, (float)g);
+        auto pair_step = [&](int q) {
+            if (q == 1) {
+                exchange_ends(f2_split(pr[0]).x, f2_split(pr[H - 1]).y, L, R, x);
+                pair_mid<1>(pr, L, R, g2);
+            } else {
+                pair_mid<0>(pr, L, R, g2);
+            }
+        };
+        while (m < P.n_mid) {
+            int count = P.n_mid - m;
+            if (until > 0 && until < count)
+                count = until;
+            int mm = m;
+            const int end = m + count;
+            if (mm < end && ((P.p_first + mm) & 1)) {
+                pair_step(1);
+                ++mm;
+            }
+            for (; mm + 1 < end; mm += 2) {
+                pair_step(0);
+                pair_step(1);
+            }
+            if (mm < end)
+                pair_step(0);
+            m += count;
+            if (until > 0) {
+                until -= count;
+                if (until == 0) {
+                    until = P.rescale_every;
+                    const float sc = pow2neg<float>(P.rs_exp[ev++]);
+                    const uint64_t s2 = f2(sc, sc);
+#pragma unroll
+                    for (int j = 0; j < H; ++j)
+                        pr[j] = f2_mul(pr[j], s2);
+                }
+            }
+        }
+        from_pairs(pr, v);
+    } else {
     while (m < P.n_mid) {
         int count = P.n_mid - m;
         if (until > 0 && until < count)
@@ -117,6 +163,7 @@ __device__ __forceinline__ void run_scaled(Real (&v)[K], const TbParams &P, Exch
                     sig *= pow2neg<double>(e);
             }
         }
+    }
     }
     if (P.do_exit) {
         // x1, x2, xs arrive divided by the final scale

@@ -8,6 +8,7 @@
 #include <cuda.h>
 #include <cstdint>
 
+#include "ge_f32x2.cuh"
 #include "ge_internal.h"
 
 namespace ge {
@@ -212,17 +213,17 @@ struct Exch {
 };
 
 // L = left thread's last value, R = right thread's first value (parity-1
-// groups cross thread boundaries).
-template <typename Real, int K, int NW, bool WT>
-__device__ __forceinline__ void exchange(const Real (&v)[K], Real &L, Real &R, Exch<Real, NW, WT> &x)
+// groups cross thread boundaries), from the thread's first and last values.
+template <typename Real, int NW, bool WT>
+__device__ __forceinline__ void exchange_ends(Real first, Real last, Real &L, Real &R, Exch<Real, NW, WT> &x)
 {
-    L = __shfl_up_sync(0xffffffffu, v[K - 1], 1);
-    R = __shfl_down_sync(0xffffffffu, v[0], 1);
+    L = __shfl_up_sync(0xffffffffu, last, 1);
+    R = __shfl_down_sync(0xffffffffu, first, 1);
     if constexpr (!WT) {
         if (x.lane == 0)
-            x.slot[x.eb][x.warp][0] = v[0];
+            x.slot[x.eb][x.warp][0] = first;
         if (x.lane == 31)
-            x.slot[x.eb][x.warp][1] = v[K - 1];
+            x.slot[x.eb][x.warp][1] = last;
         __syncthreads();
         if (x.lane == 0 && x.warp > 0)
             L = x.slot[x.eb][x.warp - 1][1];
@@ -230,6 +231,12 @@ __device__ __forceinline__ void exchange(const Real (&v)[K], Real &L, Real &R, E
             R = x.slot[x.eb][x.warp + 1][0];
         x.eb ^= 1;
     }
+}
+
+template <typename Real, int K, int NW, bool WT>
+__device__ __forceinline__ void exchange(const Real (&v)[K], Real &L, Real &R, Exch<Real, NW, WT> &x)
+{
+    exchange_ends(v[0], v[K - 1], L, R, x);
 }
 
 enum StageKind { kEntry = 0, kMid = 1, kExit = 2, kMidN = 3 };
@@ -288,6 +295,53 @@ __device__ __forceinline__ void stage(Real (&v)[K], Real L, Real R, Span sp, con
 #pragma unroll
     for (int j = 0; j < K; ++j)
         v[j] = nv[j];
+}
+
+// Paired FP32 block steps for threads whose points and partners all lie
+// inside one problem (no singletons, no walls): register j and register
+// j + K/2 share one 64-bit register, a pair, and one fma.rn.f32x2 advances
+// both points (two FP32 FMAs, each rounded as fmaf: the scalar step's bits
+// with half the issue slots).  With K/2 even both halves of a pair have the
+// same grouping parity, so a pair's partner is the neighbouring pair, except
+// at the ends under grouping 1: pair 0 takes (L, v[K/2 - 1]) and pair
+// K/2 - 1 takes (v[K/2], R).
+template <int K>
+__device__ __forceinline__ void to_pairs(const float (&v)[K], uint64_t (&p)[K / 2])
+{
+#pragma unroll
+    for (int j = 0; j < K / 2; ++j)
+        p[j] = f2(v[j], v[j + K / 2]);
+}
+
+template <int K>
+__device__ __forceinline__ void from_pairs(const uint64_t (&p)[K / 2], float (&v)[K])
+{
+#pragma unroll
+    for (int j = 0; j < K / 2; ++j) {
+        const float2 t = f2_split(p[j]);
+        v[j] = t.x;
+        v[j + K / 2] = t.y;
+    }
+}
+
+// x <- x + g x_partner on the pairs (g2 = (g, g)): the scaled mid stage.
+template <int Q, int H>
+__device__ __forceinline__ void pair_mid(uint64_t (&p)[H], float L, float R, uint64_t g2)
+{
+    static_assert(H % 2 == 0, "paired steps need an even number of pairs");
+    uint64_t np[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        uint64_t q;
+        if (((j + Q) & 1) == 0)
+            q = (j + 1 < H) ? p[j + 1] : f2(f2_split(p[0]).y, R);
+        else
+            q = (j >= 1) ? p[j - 1] : f2(L, f2_split(p[H - 1]).x);
+        np[j] = f2_fma(g2, q, p[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < H; ++j)
+        p[j] = np[j];
 }
 
 // Exact 2^-e (0 <= e <= 1022 for double, 0 <= e <= 126 for float).

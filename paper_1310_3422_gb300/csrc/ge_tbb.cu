@@ -323,6 +323,42 @@ __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &
     }
     const StageC<Real> cm{(Real)bd.g, (Real)0, (Real)bd.kap_s, (Real)0, (Real)0};
     const BatchFix fx = batch_fix<K>(pid, sp);
+    if constexpr (!EDGE && sizeof(Real) == 4 && K % 4 == 0) {
+        // interior FP32 warps: the same steps and rescalings on register
+        // pairs (packed FMAs; the same bits)
+        constexpr int H = K / 2;
+        uint64_t pr[H];
+        to_pairs(v, pr);
+        const uint64_t g2 = f2((float)cm.a, (float)cm.a);
+        int m = 0, q = 0;
+        while (m < rd.n_mid) {
+            const int cnt = (rd.n_mid - m < P.R) ? rd.n_mid - m : P.R;
+            int i = 0;
+            if (((rd.p_first + m) & 1) == 1) {
+                exchange_ends(f2_split(pr[0]).x, f2_split(pr[H - 1]).y, L, R, x);
+                pair_mid<1>(pr, L, R, g2);
+                i = 1;
+            }
+            for (; i + 1 < cnt; i += 2) {
+                pair_mid<0>(pr, L, R, g2);
+                exchange_ends(f2_split(pr[0]).x, f2_split(pr[H - 1]).y, L, R, x);
+                pair_mid<1>(pr, L, R, g2);
+            }
+            if (i < cnt)
+                pair_mid<0>(pr, L, R, g2);
+            m += cnt;
+            if (cnt == P.R) {
+                const int e = pid >= 0 ? P.exps[(long long)pid * P.Q + q] : 0;
+                const float sc = pow2neg<float>(e);
+                const uint64_t s2 = f2(sc, sc);
+#pragma unroll
+                for (int j = 0; j < H; ++j)
+                    pr[j] = f2_mul(pr[j], s2);
+            }
+            ++q;
+        }
+        from_pairs(pr, v);
+    } else {
     int m = 0, q = 0;
     while (m < rd.n_mid) {
         const int cnt = (rd.n_mid - m < P.R) ? rd.n_mid - m : P.R;
@@ -347,6 +383,7 @@ __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &
             scale_pow2<!EDGE>(v, e, pid >= 0 ? sp.jlo : 0, pid >= 0 ? sp.jhi : 0);
         }
         ++q;
+    }
     }
     if (pid >= 0) {
         Real fh, fl;
