@@ -190,6 +190,10 @@ __device__ __forceinline__ void run_comp(float (&v)[K], const TbParams &P, Exch<
             stage<0, kEntry, EDGE>(v, L, R, sp, c);
         }
     }
+    if constexpr (!EDGE && K % 4 == 0) {
+        // interior tiles: the same steps on register pairs (the same bits)
+        comp_steps_pairs(v, P.p_first, P.n_mid, (float)P.d, x);
+    } else {
     float lo[K];
 #pragma unroll
     for (int j = 0; j < K; ++j)
@@ -211,6 +215,7 @@ __device__ __forceinline__ void run_comp(float (&v)[K], const TbParams &P, Exch<
 #pragma unroll
     for (int j = 0; j < K; ++j)
         v[j] += lo[j];
+    }
     if (P.do_exit) {
         const StageC<float> c{(float)P.x1, (float)P.x2, (float)P.xs, 0.0f, 0.0f};
         if (((P.p_first + P.n_mid) & 1) == 1) {

@@ -485,5 +485,88 @@ __device__ __forceinline__ void mid_comp(float (&v)[K], float (&lo)[K], const Tb
     }
 }
 
+// Compensated block steps on register pairs (threads whose points and
+// partners all lie inside one problem): the same deltas and Kahan sums as
+// mid_comp, two points per packed instruction, the same bits.  A group's
+// second member takes its update -t as lo - t (the number the scalar sum
+// (-t) + lo gives).  Under grouping 1 the end pairs take their partners
+// across the halves: pair 0 = (v[0], v[K/2]) pairs with (L, v[K/2 - 1]),
+// pair K/2 - 1 = (v[K/2 - 1], v[K - 1]) with (v[K/2], R); the group
+// (K/2 - 1, K/2) so gets d (v[K/2] - v[K/2 - 1]) on one side and its exact
+// negative on the other, as in the scalar step.
+__device__ __forceinline__ void kahan2(uint64_t &hi, uint64_t &lo, uint64_t delta)
+{
+    const uint64_t y = f2_add(delta, lo);
+    const uint64_t s = f2_add(hi, y);
+    lo = f2_sub(y, f2_sub(s, hi));
+    hi = s;
+}
+__device__ __forceinline__ void kahan2_neg(uint64_t &hi, uint64_t &lo, uint64_t t)
+{
+    const uint64_t y = f2_sub(lo, t);
+    const uint64_t s = f2_add(hi, y);
+    lo = f2_sub(y, f2_sub(s, hi));
+    hi = s;
+}
+
+template <int Q, int H, int NW, bool WT>
+__device__ __forceinline__ void pair_mid_comp(uint64_t (&p)[H], uint64_t (&lo)[H], uint64_t d2, uint64_t nz,
+                                              Exch<float, NW, WT> &x)
+{
+    static_assert(H % 2 == 0, "paired steps need an even number of pairs");
+    if (Q == 0) {
+#pragma unroll
+        for (int j = 0; j < H; j += 2) {
+            const uint64_t t = f2_mul_alone(d2, f2_sub(p[j + 1], p[j]), nz);
+            kahan2(p[j], lo[j], t);
+            kahan2_neg(p[j + 1], lo[j + 1], t);
+        }
+    } else {
+        const float2 a = f2_split(p[0]), b = f2_split(p[H - 1]);
+        float L = 0.0f, R = 0.0f;
+        exchange_ends(a.x, b.y, L, R, x);
+        const uint64_t t0 = f2_mul_alone(d2, f2_sub(f2(L, b.x), p[0]), nz);
+        const uint64_t tk = f2_mul_alone(d2, f2_sub(f2(a.y, R), p[H - 1]), nz);
+#pragma unroll
+        for (int j = 1; j + 1 < H; j += 2) {
+            const uint64_t t = f2_mul_alone(d2, f2_sub(p[j + 1], p[j]), nz);
+            kahan2(p[j], lo[j], t);
+            kahan2_neg(p[j + 1], lo[j + 1], t);
+        }
+        kahan2(p[0], lo[0], t0);
+        kahan2(p[H - 1], lo[H - 1], tk);
+    }
+}
+
+// n_mid compensated block steps from grouping parity p_first, the
+// compensation word folded in at the end (v += lo), on pairs.
+template <int K, int NW, bool WT>
+__device__ __forceinline__ void comp_steps_pairs(float (&v)[K], int p_first, int n_mid, float d,
+                                                 Exch<float, NW, WT> &x)
+{
+    constexpr int H = K / 2;
+    uint64_t p[H], lo[H];
+    to_pairs(v, p);
+#pragma unroll
+    for (int j = 0; j < H; ++j)
+        lo[j] = f2(0.0f, 0.0f);
+    const uint64_t d2 = f2(d, d), nz = f2_neg_zero(d);  // d = 2r / (1 + 2r) >= 0
+    int m = 0;
+    if (n_mid > 0 && (p_first & 1)) {
+        pair_mid_comp<1>(p, lo, d2, nz, x);
+        m = 1;
+    }
+    for (; m + 1 < n_mid; m += 2) {
+        pair_mid_comp<0>(p, lo, d2, nz, x);
+        pair_mid_comp<1>(p, lo, d2, nz, x);
+    }
+    if (m < n_mid)
+        pair_mid_comp<0>(p, lo, d2, nz, x);
+#pragma unroll
+    for (int j = 0; j < H; ++j)
+        p[j] = f2_add(p[j], lo[j]);
+    from_pairs(p, v);
+}
+
 }  // namespace
 }  // namespace ge

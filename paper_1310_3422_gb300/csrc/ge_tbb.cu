@@ -256,6 +256,10 @@ __device__ __forceinline__ void run_batch_comp(float (&v)[K], const TbbParams &P
             stage<0, kEntry, EDGE>(v, L, R, sp, c);
         }
     }
+    if constexpr (!EDGE && K % 4 == 0) {
+        // interior warps: the same steps on register pairs (the same bits)
+        comp_steps_pairs(v, P.p_first, P.n_mid, (float)bd.d, x);
+    } else {
     float lo[K];
 #pragma unroll
     for (int j = 0; j < K; ++j)
@@ -279,6 +283,7 @@ __device__ __forceinline__ void run_batch_comp(float (&v)[K], const TbbParams &P
 #pragma unroll
     for (int j = 0; j < K; ++j)
         v[j] += lo[j];
+    }
     if (P.do_exit) {
         const StageC<float> c{(float)bd.x1, (float)bd.x2, (float)bd.xs, 0.0f, 0.0f};
         if (((P.p_first + P.n_mid) & 1) == 1) {
