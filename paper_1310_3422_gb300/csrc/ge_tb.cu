@@ -48,7 +48,7 @@ namespace {
 // double, with the same recurrence the host runs (see TbParams).
 template <int Q, bool EDGE, typename Real, int K, int NW, bool WT>
 __device__ __forceinline__ void mid_scaled(Real (&v)[K], double &sig, const TbParams &P, Exch<Real, NW, WT> &x,
-                                           Span sp, Real g, Real kap)
+                                           Span sp, Real g, Real kap, const EmuG &eg)
 {
     Real L = 0, R = 0;
     if (Q == 1)
@@ -59,6 +59,12 @@ __device__ __forceinline__ void mid_scaled(Real (&v)[K], double &sig, const TbPa
         c.fl = (Real)(sig * P.f_l);
         c.fr = (Real)(sig * P.f_r);
     }
+    if constexpr (!EDGE && sizeof(Real) == 8 && GE_EMU_F64 > 0 && K % GE_EMU_F64 == 0) {
+        if (emu_g_usable(eg)) {
+            stage_mid_hybrid<Q, GE_EMU_F64>(v, L, R, g, eg);
+            return;
+        }
+    }
     stage<Q, kMid, EDGE>(v, L, R, sp, c);
 }
 
@@ -67,20 +73,20 @@ __device__ __forceinline__ void mid_scaled(Real (&v)[K], double &sig, const TbPa
 // trailing step.  No rescaling inside.
 template <bool EDGE, typename Real, int K, int NW, bool WT>
 __device__ __forceinline__ void mid_run(Real (&v)[K], int m0, int count, double &sig, const TbParams &P,
-                                        Exch<Real, NW, WT> &x, Span sp, Real g, Real kap)
+                                        Exch<Real, NW, WT> &x, Span sp, Real g, Real kap, const EmuG &eg)
 {
     int m = m0;
     const int end = m0 + count;
     if (m < end && ((P.p_first + m) & 1)) {
-        mid_scaled<1, EDGE>(v, sig, P, x, sp, g, kap);
+        mid_scaled<1, EDGE>(v, sig, P, x, sp, g, kap, eg);
         ++m;
     }
     for (; m + 1 < end; m += 2) {
-        mid_scaled<0, EDGE>(v, sig, P, x, sp, g, kap);
-        mid_scaled<1, EDGE>(v, sig, P, x, sp, g, kap);
+        mid_scaled<0, EDGE>(v, sig, P, x, sp, g, kap, eg);
+        mid_scaled<1, EDGE>(v, sig, P, x, sp, g, kap, eg);
     }
     if (m < end)
-        mid_scaled<0, EDGE>(v, sig, P, x, sp, g, kap);
+        mid_scaled<0, EDGE>(v, sig, P, x, sp, g, kap, eg);
 }
 
 // Entry, the launch's block steps (in runs between rescalings) and exit on
@@ -99,6 +105,7 @@ __device__ __forceinline__ void run_scaled(Real (&v)[K], const TbParams &P, Exch
         }
     }
     const Real g = (Real)P.g, kap = (Real)P.kappa;
+    const EmuG eg = emu_g(P.g);  // FP64: the integer-pipe share of the updates
     double sig = P.sigma_in;  // used on the checked path only
     int until = P.rescale_phase, ev = 0, m = 0;
     if constexpr (!EDGE && sizeof(Real) == 4 && K % 4 == 0) {
@@ -151,7 +158,7 @@ __device__ __forceinline__ void run_scaled(Real (&v)[K], const TbParams &P, Exch
         int count = P.n_mid - m;
         if (until > 0 && until < count)
             count = until;
-        mid_run<EDGE>(v, m, count, sig, P, x, sp, g, kap);
+        mid_run<EDGE>(v, m, count, sig, P, x, sp, g, kap, eg);
         m += count;
         if (until > 0) {
             until -= count;

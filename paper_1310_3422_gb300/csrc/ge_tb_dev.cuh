@@ -8,6 +8,7 @@
 #include <cuda.h>
 #include <cstdint>
 
+#include "ge_dfma_emu.cuh"
 #include "ge_f32x2.cuh"
 #include "ge_internal.h"
 
@@ -342,6 +343,52 @@ __device__ __forceinline__ void pair_mid(uint64_t (&p)[H], float L, float R, uin
 #pragma unroll
     for (int j = 0; j < H; ++j)
         p[j] = np[j];
+}
+
+// FP64 registers per thread whose scaled update runs on the integer pipes
+// (emu_fma) instead of the FP64 unit, in the interior warps' block steps.
+#ifndef GE_EMU_F64
+#define GE_EMU_F64 4
+#endif
+
+// Register j is one of the E emulated ones of K: spread evenly (the last of
+// every K / E).
+template <int K, int E>
+__device__ __forceinline__ constexpr bool emu_reg(int j)
+{
+    return E > 0 && (j % (K / E)) == (K / E) - 1;
+}
+
+// The scaled mid stage x <- x + g x_partner in FP64 on a warp whose points
+// and partners all lie inside the grid, E registers per thread on the
+// integer pipes.  If any lane's emulated update leaves the fast path, the
+// warp recomputes its emulated registers on the FP64 unit, so the result is
+// always the FP64 unit's fma, bit for bit.
+template <int Q, int E, int K>
+__device__ __forceinline__ void stage_mid_hybrid(double (&v)[K], double L, double R, double g, const EmuG &eg)
+{
+    double nv[K];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const double p = pval<Q>(v, j, L, R);
+        if (emu_reg<K, E>(j)) {
+            bool o;
+            nv[j] = emu_fma(eg, p, v[j], o);
+            ok = ok && o;
+        } else {
+            nv[j] = fma(g, p, v[j]);
+        }
+    }
+    if (!__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (emu_reg<K, E>(j))
+                nv[j] = fma(g, pval<Q>(v, j, L, R), v[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        v[j] = nv[j];
 }
 
 // Exact 2^-e (0 <= e <= 1022 for double, 0 <= e <= 126 for float).
