@@ -972,17 +972,29 @@ def main():
                     "kernel": kname}
     elif args.kernel == "temporal":
         updates_per_launch = N_POINTS * (GE_STEPS / n_launch)
-        achieved = flops_per_update * updates_per_launch / (launch_ms / 1e3)
+        # FP64: a build-fixed share of the interior updates runs as exact FP64
+        # multiply-adds on the integer pipes; the FP64 unit does the rest
+        int_share = B.ge_fp64_int_share() if prec == B.GE_F64 else 0.0
+        unit_flops_per_update = flops_per_update * (1.0 - int_share)
+        achieved = unit_flops_per_update * updates_per_launch / (launch_ms / 1e3)
         kname = "tb_kernel<%s>" % ("double" if prec == B.GE_F64 else "float")
         traffic = measured_traffic(kname) if (prec == B.GE_F64 and depth == 48) else None
+        if prec == B.GE_F32_COMP:
+            work = "normalised block map + Kahan sum"
+        elif int_share > 0:
+            work = ("one multiply-add per point and step (right-hand-side form); %.0f %% of the interior updates "
+                    "as exact FP64 multiply-adds on the integer pipes, the rest on the FP64 unit (achieved and "
+                    "frac count the FP64 unit's share)" % (100 * int_share))
+        else:
+            work = "one multiply-add per point and step (right-hand-side form)"
         roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
                     "unit": "TFLOP/s", "frac": achieved / alu_peak,
                     "traffic": traffic, "algorithmic_bytes_per_launch": 2 * bytes_per_update * N_POINTS,
                     "kernel": kname,
                     # achieved = executed_flops_per_update x updates_per_launch / launch_ms
-                    "executed_flops_per_update": flops_per_update,
-                    "executed_work": ("one multiply-add per point and step (right-hand-side form)"
-                                      if prec != B.GE_F32_COMP else "normalised block map + Kahan sum"),
+                    "executed_flops_per_update": unit_flops_per_update,
+                    "executed_work": work,
+                    "int_pipe_share": int_share,
                     "updates_per_launch": updates_per_launch, "launch_ms": launch_ms,
                     # peak = 2 flops x FMA/clk/SM x SMs x max SM clock
                     "peak_source": "derived: 2 flops x %g FMA/clk/SM x %d SMs (device attribute) x %.0f MHz "
@@ -993,6 +1005,11 @@ def main():
         if probe is not None:
             roofline["peak_probe"] = probe["flops_per_s"] / 1e12
             roofline["frac_of_probe"] = achieved / probe["flops_per_s"]
+            if int_share > 0:
+                # every update's multiply-add against the FP64 unit's measured
+                # ceiling: above 1 is what the integer pipes add
+                roofline["all_updates_frac_of_probe"] = (flops_per_update * updates_per_launch
+                                                         / (launch_ms / 1e3) / probe["flops_per_s"])
     else:
         # one step per launch: report the roofline that binds (HBM bytes or
         # the ALU), with the other fraction beside it

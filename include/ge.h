@@ -347,6 +347,17 @@ ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double beta_r, ge
                            int32_t depth, int64_t steps, const void *u0_dev, void *u_out_dev,
                            void *stream);
 
+/* Build information: the fraction of the FP64 tiled kernel's interior
+ * updates (GE_KERNEL_TEMPORAL, GE_F64, threads whose points and partners
+ * all lie inside the grid) computed as exact FP64 multiply-adds on the
+ * integer pipes instead of the FP64 unit (the scaled block step of Sec. 2,
+ * x <- x + 2r x_partner; same bits either way).  A warp whose emulated
+ * updates leave the integer fast path in a step (zeros, subnormals, far-apart
+ * magnitudes) recomputes them on the FP64 unit, so the realised share can
+ * be lower.  *share (host) receives the build's share, 0 when disabled.
+ * Errors: GE_EINVAL (NULL share). */
+ge_status ge_fp64_int_share(double *share);
+
 /* Diagnostic: register-only fused multiply-add throughput probe, the
  * measured ALU ceiling the tiled kernels are read against (the paper has no
  * counterpart).  Launches `blocks` CTAs of 256 threads on `stream`; every

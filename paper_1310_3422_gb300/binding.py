@@ -31,7 +31,7 @@ EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", 
            "ge_batch_sync",
            "ge_batch_destroy",
            "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error", "ge_debug_stall",
-           "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune", "ge_probe_fma",
+           "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune", "ge_probe_fma", "ge_fp64_int_share",
            "ge_sno_create", "ge_sno_num_params", "ge_sno_get_params", "ge_sno_set_params",
            "ge_sno_set_precision", "ge_sno_set_tensor_cores", "ge_sno_get_tensor_cores", "ge_sno_sync", "ge_sno_forward", "ge_sno_loss_grad", "ge_sno_adam_step",
            "ge_sno_train_step", "ge_sno_rows_nonfinite", "ge_sno_rows_gather", "ge_sno_rows_scatter",
@@ -122,6 +122,8 @@ def load(path: str | None = None):
         lib.ge_solve_noalloc.restype = ctypes.c_int
         lib.ge_probe_fma.argtypes = [_I32, _I32, _I32, _I64, _VP, _VP]
         lib.ge_probe_fma.restype = ctypes.c_int
+        lib.ge_fp64_int_share.argtypes = [ctypes.POINTER(ctypes.c_double)]
+        lib.ge_fp64_int_share.restype = ctypes.c_int
         lib.ge_sno_create.argtypes = [ctypes.POINTER(_VP), _I32, _I32, _I32, _I32, _I32, _I32, ctypes.c_uint64, _VP]
         lib.ge_sno_create.restype = ctypes.c_int
         lib.ge_sno_set_tensor_cores.argtypes = [_VP, _I32]
@@ -459,6 +461,13 @@ def ge_solve_noalloc(n: int, r: float, beta_l: float, beta_r: float, prec: int, 
 
 
 PROBE_THREADS = 256
+
+
+def ge_fp64_int_share() -> float:
+    """Share of the FP64 tiled kernel's interior updates done on the integer pipes."""
+    v = ctypes.c_double()
+    _check(load().ge_fp64_int_share(ctypes.byref(v)), "ge_fp64_int_share")
+    return float(v.value)
 
 
 def ge_probe_fma(prec: int, blocks: int, chains: int, iters: int, sink, stream=None) -> int:

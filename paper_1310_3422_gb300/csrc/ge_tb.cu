@@ -38,6 +38,7 @@
 // Compensated FP32 (GE_F32_COMP): the block map is applied in normalised
 // form x <- x + d (x_partner - x), d = 2r/(1+2r), and each point's updates
 // are Kahan-summed into (hi, lo); lo lives in registers for the launch.
+#include "ge.h"
 #include "ge_tb_dev.cuh"
 
 namespace ge {
@@ -622,3 +623,14 @@ cudaError_t launch_tb(int prec, const void *tmap, const TbParams &p, int grid, c
 }
 
 }  // namespace ge
+
+extern "C" ge_status ge_fp64_int_share(double *share)
+{
+    if (!share) {
+        ge::set_last_error("ge_fp64_int_share: NULL share");
+        return GE_EINVAL;
+    }
+    constexpr int K = ge::Layout<double, false>::KT;  // FP64 values per thread
+    *share = (GE_EMU_F64 > 0 && K % GE_EMU_F64 == 0) ? (double)GE_EMU_F64 / K : 0.0;
+    return GE_OK;
+}

@@ -142,3 +142,12 @@ def test_sno_calls_on_null_model(lib):
 def test_debug_stall_checks_its_arguments(lib):
     assert lib.ge_debug_stall(None, 0) == B.GE_EINVAL
     assert lib.ge_batch_debug_stall(None, 0) == B.GE_EINVAL
+
+
+def test_fp64_int_share_is_a_fraction(lib):
+    """The share of the FP64 tiled kernel's interior updates on the integer
+    pipes: a build constant in [0, 1) (4 of a thread's 16 values by default)."""
+    share = B.ge_fp64_int_share()
+    assert 0.0 <= share < 1.0
+    assert share in (0.0, 1 / 16, 2 / 16, 4 / 16, 8 / 16)
+    assert lib.ge_fp64_int_share(None) == B.GE_EINVAL
