@@ -358,6 +358,17 @@ ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double beta_r, ge
  * Errors: GE_EINVAL (NULL share). */
 ge_status ge_fp64_int_share(double *share);
 
+/* Diagnostic: checks the integer-pipe FP64 multiply-add of the FP64 tiled
+ * kernel (the scaled block step x + g p, Sec. 2) against the FP64 unit's fma
+ * on n inputs p_dev[i], x_dev[i] (device, caller-owned, n doubles each).
+ * counts_dev (device, 3 uint64, overwritten): [0] inputs where the integer
+ * form reported its fast path but gave other bits than the FP64 unit (0 in
+ * a correct build), [1] inputs its general fast path took, [2] inputs its
+ * addition-only form took.  Asynchronous on `stream`.  Errors: GE_EINVAL
+ * (NULL buffer, n < 0), GE_ECUDA. */
+ge_status ge_emu_fma_check(double g, const double *p_dev, const double *x_dev, int64_t n, uint64_t *counts_dev,
+                           void *stream);
+
 /* Diagnostic: register-only fused multiply-add throughput probe, the
  * measured ALU ceiling the tiled kernels are read against (the paper has no
  * counterpart).  Launches `blocks` CTAs of 256 threads on `stream`; every

@@ -32,6 +32,7 @@ EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", 
            "ge_batch_destroy",
            "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error", "ge_debug_stall",
            "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune", "ge_probe_fma", "ge_fp64_int_share",
+           "ge_emu_fma_check",
            "ge_sno_create", "ge_sno_num_params", "ge_sno_get_params", "ge_sno_set_params",
            "ge_sno_set_precision", "ge_sno_set_tensor_cores", "ge_sno_get_tensor_cores", "ge_sno_sync", "ge_sno_forward", "ge_sno_loss_grad", "ge_sno_adam_step",
            "ge_sno_train_step", "ge_sno_rows_nonfinite", "ge_sno_rows_gather", "ge_sno_rows_scatter",
@@ -124,6 +125,8 @@ def load(path: str | None = None):
         lib.ge_probe_fma.restype = ctypes.c_int
         lib.ge_fp64_int_share.argtypes = [ctypes.POINTER(ctypes.c_double)]
         lib.ge_fp64_int_share.restype = ctypes.c_int
+        lib.ge_emu_fma_check.argtypes = [ctypes.c_double, _VP, _VP, _I64, _VP, _VP]
+        lib.ge_emu_fma_check.restype = ctypes.c_int
         lib.ge_sno_create.argtypes = [ctypes.POINTER(_VP), _I32, _I32, _I32, _I32, _I32, _I32, ctypes.c_uint64, _VP]
         lib.ge_sno_create.restype = ctypes.c_int
         lib.ge_sno_set_tensor_cores.argtypes = [_VP, _I32]
@@ -468,6 +471,16 @@ def ge_fp64_int_share() -> float:
     v = ctypes.c_double()
     _check(load().ge_fp64_int_share(ctypes.byref(v)), "ge_fp64_int_share")
     return float(v.value)
+
+
+def ge_emu_fma_check(g: float, p, x, counts, stream=None):
+    """Integer-pipe FP64 multiply-add against the FP64 unit on p, x (device
+    float64 tensors of equal length); counts: device int64 tensor of 3."""
+    n = p.numel()
+    if x.numel() != n or counts.numel() < 3:
+        raise ValueError("p and x must have equal length; counts needs 3 elements")
+    _check(load().ge_emu_fma_check(float(g), _dptr(p), _dptr(x), int(n), _dptr(counts), _stream_handle(stream)),
+           "ge_emu_fma_check")
 
 
 def ge_probe_fma(prec: int, blocks: int, chains: int, iters: int, sink, stream=None) -> int:

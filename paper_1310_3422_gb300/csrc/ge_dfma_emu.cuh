@@ -48,6 +48,9 @@ __device__ __forceinline__ EmuG emu_g(double g)
 // g must be normal and nonzero for the fast path.
 __device__ __forceinline__ bool emu_g_usable(const EmuG &g) { return (unsigned)(g.eb - 1) < 0x7feu; }
 
+// SUB = false: the caller has checked that the product and x have the same
+// sign (an addition), which drops the two's-complement negations.
+template <bool SUB = true>
 __device__ __forceinline__ double emu_fma(const EmuG &g, double p, double x, bool &ok)
 {
     const uint32_t Ph = (uint32_t)__double2hiint(p), Pl = (uint32_t)__double2loint(p);
@@ -71,37 +74,46 @@ __device__ __forceinline__ double emu_fma(const EmuG &g, double p, double x, boo
     uint32_t x2 = q == 0 ? v2 : (q == 1 ? v1 : v0);
     uint32_t x3 = q == 0 ? 0u : (q == 1 ? v2 : v1);
     // R = M + X, or M - X when the signs differ (two's complement), then |R|
-    const uint32_t sprod = (Ph >> 31) ^ g.s, sub = sprod ^ (Xh >> 31);
-    const uint32_t inv = 0u - sub;
-    x0 ^= inv;
-    x1 ^= inv;
-    x2 ^= inv;
-    x3 ^= inv;
-    uint32_t r0, r1, r2, r3;
-    asm("add.cc.u32 %0, %4, %8;\n\t"
-        "addc.cc.u32 %1, %5, %9;\n\t"
-        "addc.cc.u32 %2, %6, %10;\n\t"
-        "addc.u32 %3, %7, %11;"
-        : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-        : "r"(m0), "r"(m1), "r"(m2), "r"(m3), "r"(x0), "r"(x1), "r"(x2), "r"(x3));
-    asm("add.cc.u32 %0, %0, %4;\n\t"
-        "addc.cc.u32 %1, %1, 0;\n\t"
-        "addc.cc.u32 %2, %2, 0;\n\t"
-        "addc.u32 %3, %3, 0;"
-        : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
-        : "r"(sub));
-    const uint32_t neg = 0u - (r3 >> 31);
-    r0 ^= neg;
-    r1 ^= neg;
-    r2 ^= neg;
-    r3 ^= neg;
-    asm("add.cc.u32 %0, %0, %4;\n\t"
-        "addc.cc.u32 %1, %1, 0;\n\t"
-        "addc.cc.u32 %2, %2, 0;\n\t"
-        "addc.u32 %3, %3, 0;"
-        : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
-        : "r"(neg & 1u));
-    const uint32_t s = sprod ^ (neg & 1u);
+    const uint32_t sprod = (Ph >> 31) ^ g.s;
+    uint32_t r0, r1, r2, r3, s = sprod;
+    if constexpr (SUB) {
+        const uint32_t sub = sprod ^ (Xh >> 31), inv = 0u - sub;
+        x0 ^= inv;
+        x1 ^= inv;
+        x2 ^= inv;
+        x3 ^= inv;
+        asm("add.cc.u32 %0, %4, %8;\n\t"
+            "addc.cc.u32 %1, %5, %9;\n\t"
+            "addc.cc.u32 %2, %6, %10;\n\t"
+            "addc.u32 %3, %7, %11;"
+            : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+            : "r"(m0), "r"(m1), "r"(m2), "r"(m3), "r"(x0), "r"(x1), "r"(x2), "r"(x3));
+        asm("add.cc.u32 %0, %0, %4;\n\t"
+            "addc.cc.u32 %1, %1, 0;\n\t"
+            "addc.cc.u32 %2, %2, 0;\n\t"
+            "addc.u32 %3, %3, 0;"
+            : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
+            : "r"(sub));
+        const uint32_t neg = 0u - (r3 >> 31);
+        r0 ^= neg;
+        r1 ^= neg;
+        r2 ^= neg;
+        r3 ^= neg;
+        asm("add.cc.u32 %0, %0, %4;\n\t"
+            "addc.cc.u32 %1, %1, 0;\n\t"
+            "addc.cc.u32 %2, %2, 0;\n\t"
+            "addc.u32 %3, %3, 0;"
+            : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
+            : "r"(neg & 1u));
+        s ^= neg & 1u;
+    } else {
+        asm("add.cc.u32 %0, %4, %8;\n\t"
+            "addc.cc.u32 %1, %5, %9;\n\t"
+            "addc.cc.u32 %2, %6, %10;\n\t"
+            "addc.u32 %3, %7, %11;"
+            : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+            : "r"(m0), "r"(m1), "r"(m2), "r"(m3), "r"(x0), "r"(x1), "r"(x2), "r"(x3));
+    }
     ok = ok & (r3 != 0u);
     const int L = 127 - __clz((int)r3);  // the leading bit, 96 .. 126
     // significand = bits L-52 .. L, from the window (r3:r2:r1) >> (L - 84)

@@ -14,6 +14,7 @@
 #include <cstdint>
 
 #include "ge.h"
+#include "ge_dfma_emu.cuh"
 #include "ge_internal.h"
 
 namespace {
@@ -50,7 +51,62 @@ void launch_probe(int chains, int blocks, long long iters, Real a, Real b, Real 
     }
 }
 
+// The integer-pipe FMA against the FP64 unit's on every input: counts[0] =
+// inputs where a fast path reported ok but gave other bits than the FP64
+// unit's fma (must stay 0), counts[1] = inputs the general fast path took,
+// counts[2] = inputs the addition-only fast path took (same-sign inputs).
+__global__ void emu_check_kernel(double g, const double *__restrict__ p, const double *__restrict__ x, long long n,
+                                 unsigned long long *counts)
+{
+    const ge::EmuG eg = ge::emu_g(g);
+    const bool usable = ge::emu_g_usable(eg);
+    unsigned long long bad = 0, fast = 0, fast_add = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double want = __fma_rn(g, p[i], x[i]);
+        bool ok;
+        const double e = ge::emu_fma<true>(eg, p[i], x[i], ok);
+        if (ok && usable) {
+            ++fast;
+            bad += __double_as_longlong(e) != __double_as_longlong(want);
+        }
+        const unsigned same = ((unsigned)__double2hiint(p[i]) ^ (unsigned)__double2hiint(x[i]) ^
+                               ((unsigned)eg.s << 31)) >> 31;
+        if (same == 0u) {
+            const double e2 = ge::emu_fma<false>(eg, p[i], x[i], ok);
+            if (ok && usable) {
+                ++fast_add;
+                bad += __double_as_longlong(e2) != __double_as_longlong(want);
+            }
+        }
+    }
+    atomicAdd(counts, bad);
+    atomicAdd(counts + 1, fast);
+    atomicAdd(counts + 2, fast_add);
+}
+
 }  // namespace
+
+extern "C" ge_status ge_emu_fma_check(double g, const double *p_dev, const double *x_dev, int64_t n,
+                                      uint64_t *counts_dev, void *stream)
+{
+    if (!p_dev || !x_dev || !counts_dev || n < 0) {
+        ge::set_last_error("ge_emu_fma_check: NULL buffer or n < 0");
+        return GE_EINVAL;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(counts_dev, 0, 3 * sizeof(uint64_t), s);
+    if (e == cudaSuccess && n > 0) {
+        const long long blocks = (n + kThreads - 1) / kThreads;
+        emu_check_kernel<<<(int)(blocks < 4096 ? blocks : 4096), kThreads, 0, s>>>(
+            g, p_dev, x_dev, n, reinterpret_cast<unsigned long long *>(counts_dev));
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        ge::set_last_error(cudaGetErrorString(e));
+        return GE_ECUDA;
+    }
+    return GE_OK;
+}
 
 extern "C" ge_status ge_probe_fma(int32_t prec, int32_t blocks, int32_t chains, int64_t iters, void *sink_dev,
                                   void *stream)

@@ -369,15 +369,37 @@ __device__ __forceinline__ void stage_mid_hybrid(double (&v)[K], double L, doubl
 {
     double nv[K];
     bool ok = true;
+    // the cheaper form when every lane's emulated updates are additions (the
+    // product and x of the same sign: a smooth field of one sign)
+    uint32_t anysub = 0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const double p = pval<Q>(v, j, L, R);
-        if (emu_reg<K, E>(j)) {
-            bool o;
-            nv[j] = emu_fma(eg, p, v[j], o);
-            ok = ok && o;
-        } else {
-            nv[j] = fma(g, p, v[j]);
+    for (int j = 0; j < K; ++j)
+        if (emu_reg<K, E>(j))
+            anysub |= ((((uint32_t)__double2hiint(pval<Q>(v, j, L, R)) ^ (uint32_t)__double2hiint(v[j])) >> 31) ^
+                       eg.s);
+    if (__any_sync(0xffffffffu, anysub != 0u)) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const double p = pval<Q>(v, j, L, R);
+            if (emu_reg<K, E>(j)) {
+                bool o;
+                nv[j] = emu_fma<true>(eg, p, v[j], o);
+                ok = ok && o;
+            } else {
+                nv[j] = fma(g, p, v[j]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const double p = pval<Q>(v, j, L, R);
+            if (emu_reg<K, E>(j)) {
+                bool o;
+                nv[j] = emu_fma<false>(eg, p, v[j], o);
+                ok = ok && o;
+            } else {
+                nv[j] = fma(g, p, v[j]);
+            }
         }
     }
     if (!__all_sync(0xffffffffu, ok)) {
