@@ -60,7 +60,7 @@ __device__ __forceinline__ void mid_scaled(Real (&v)[K], double &sig, const TbPa
         c.fl = (Real)(sig * P.f_l);
         c.fr = (Real)(sig * P.f_r);
     }
-    if constexpr (!EDGE && sizeof(Real) == 8 && GE_EMU_F64 > 0 && K % GE_EMU_F64 == 0) {
+    if constexpr (!EDGE && sizeof(Real) == 8 && GE_EMU_F64 > 0 && GE_EMU_F64 < K) {
         if (emu_g_usable(eg)) {
             stage_mid_hybrid<Q, GE_EMU_F64>(v, L, R, g, eg);
             return;
@@ -631,6 +631,6 @@ extern "C" ge_status ge_fp64_int_share(double *share)
         return GE_EINVAL;
     }
     constexpr int K = ge::Layout<double, false>::KT;  // FP64 values per thread
-    *share = (GE_EMU_F64 > 0 && K % GE_EMU_F64 == 0) ? (double)GE_EMU_F64 / K : 0.0;
+    *share = (GE_EMU_F64 > 0 && GE_EMU_F64 < K) ? (double)GE_EMU_F64 / K : 0.0;
     return GE_OK;
 }

@@ -351,12 +351,12 @@ __device__ __forceinline__ void pair_mid(uint64_t (&p)[H], float L, float R, uin
 #define GE_EMU_F64 4
 #endif
 
-// Register j is one of the E emulated ones of K: spread evenly (the last of
-// every K / E).
+// Register j is one of the E emulated ones of K, spread evenly: j is taken
+// where floor(j E / K) steps up (E = K / 4: registers 3, 7, 11, 15 of 16).
 template <int K, int E>
 __device__ __forceinline__ constexpr bool emu_reg(int j)
 {
-    return E > 0 && (j % (K / E)) == (K / E) - 1;
+    return E > 0 && ((j + 1) * E) / K > (j * E) / K;
 }
 
 // The scaled mid stage x <- x + g x_partner in FP64 on a warp whose points
