@@ -48,9 +48,6 @@ __device__ __forceinline__ EmuG emu_g(double g)
 // g must be normal and nonzero for the fast path.
 __device__ __forceinline__ bool emu_g_usable(const EmuG &g) { return (unsigned)(g.eb - 1) < 0x7feu; }
 
-// SUB = false: the caller has checked that the product and x have the same
-// sign (an addition), which drops the two's-complement negations.
-template <bool SUB = true>
 __device__ __forceinline__ double emu_fma(const EmuG &g, double p, double x, bool &ok)
 {
     const uint32_t Ph = (uint32_t)__double2hiint(p), Pl = (uint32_t)__double2loint(p);
@@ -74,46 +71,36 @@ __device__ __forceinline__ double emu_fma(const EmuG &g, double p, double x, boo
     uint32_t x2 = q == 0 ? v2 : (q == 1 ? v1 : v0);
     uint32_t x3 = q == 0 ? 0u : (q == 1 ? v2 : v1);
     // R = M + X, or M - X when the signs differ (two's complement), then |R|
-    const uint32_t sprod = (Ph >> 31) ^ g.s;
-    uint32_t r0, r1, r2, r3, s = sprod;
-    if constexpr (SUB) {
-        const uint32_t sub = sprod ^ (Xh >> 31), inv = 0u - sub;
-        x0 ^= inv;
-        x1 ^= inv;
-        x2 ^= inv;
-        x3 ^= inv;
-        asm("add.cc.u32 %0, %4, %8;\n\t"
-            "addc.cc.u32 %1, %5, %9;\n\t"
-            "addc.cc.u32 %2, %6, %10;\n\t"
-            "addc.u32 %3, %7, %11;"
-            : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-            : "r"(m0), "r"(m1), "r"(m2), "r"(m3), "r"(x0), "r"(x1), "r"(x2), "r"(x3));
-        asm("add.cc.u32 %0, %0, %4;\n\t"
-            "addc.cc.u32 %1, %1, 0;\n\t"
-            "addc.cc.u32 %2, %2, 0;\n\t"
-            "addc.u32 %3, %3, 0;"
-            : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
-            : "r"(sub));
-        const uint32_t neg = 0u - (r3 >> 31);
-        r0 ^= neg;
-        r1 ^= neg;
-        r2 ^= neg;
-        r3 ^= neg;
-        asm("add.cc.u32 %0, %0, %4;\n\t"
-            "addc.cc.u32 %1, %1, 0;\n\t"
-            "addc.cc.u32 %2, %2, 0;\n\t"
-            "addc.u32 %3, %3, 0;"
-            : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
-            : "r"(neg & 1u));
-        s ^= neg & 1u;
-    } else {
-        asm("add.cc.u32 %0, %4, %8;\n\t"
-            "addc.cc.u32 %1, %5, %9;\n\t"
-            "addc.cc.u32 %2, %6, %10;\n\t"
-            "addc.u32 %3, %7, %11;"
-            : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-            : "r"(m0), "r"(m1), "r"(m2), "r"(m3), "r"(x0), "r"(x1), "r"(x2), "r"(x3));
-    }
+    const uint32_t sprod = (Ph >> 31) ^ g.s, sub = sprod ^ (Xh >> 31), inv = 0u - sub;
+    x0 ^= inv;
+    x1 ^= inv;
+    x2 ^= inv;
+    x3 ^= inv;
+    uint32_t r0, r1, r2, r3;
+    asm("add.cc.u32 %0, %4, %8;\n\t"
+        "addc.cc.u32 %1, %5, %9;\n\t"
+        "addc.cc.u32 %2, %6, %10;\n\t"
+        "addc.u32 %3, %7, %11;"
+        : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+        : "r"(m0), "r"(m1), "r"(m2), "r"(m3), "r"(x0), "r"(x1), "r"(x2), "r"(x3));
+    asm("add.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, 0;\n\t"
+        "addc.cc.u32 %2, %2, 0;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
+        : "r"(sub));
+    const uint32_t neg = 0u - (r3 >> 31);
+    r0 ^= neg;
+    r1 ^= neg;
+    r2 ^= neg;
+    r3 ^= neg;
+    asm("add.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, 0;\n\t"
+        "addc.cc.u32 %2, %2, 0;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3)
+        : "r"(neg & 1u));
+    const uint32_t s = sprod ^ (neg & 1u);
     ok = ok & (r3 != 0u);
     const int L = 127 - __clz((int)r3);  // the leading bit, 96 .. 126
     // significand = bits L-52 .. L, from the window (r3:r2:r1) >> (L - 84)
@@ -144,6 +131,51 @@ __device__ __forceinline__ double emu_fma(const EmuG &g, double p, double x, boo
     const int eb = g.eb + ep + L - 1127 + (int)carry;
     mant = carry ? (mant >> 1) : mant;
     ok = ok & ((unsigned)(eb - 1) < 0x7feu);
+    const uint32_t hi = (s << 31) | ((uint32_t)eb << 20) | ((uint32_t)(mant >> 32) & 0xfffffu);
+    return __hiloint2double((int)hi, (int)(uint32_t)mant);
+}
+
+// The addition-only form for the common case, narrower still: the product
+// and x of the same sign (the caller checked) and x's lowest bit 32 .. 62
+// positions above the product's (x between about 2^-21 and 2^9 of g p, where
+// a smooth field and its scaled neighbour sit).  Then x's significand fills
+// limbs 1 .. 3 with one shift amount and no selects, limb 0 of the sum is the
+// product's, the leading bit lies in 104 .. 115, so the significand window and
+// the rounding bit need no branch.  ok = false outside that range.
+__device__ __forceinline__ double emu_fma_add(const EmuG &g, double p, double x, bool &ok)
+{
+    const uint32_t Ph = (uint32_t)__double2hiint(p), Pl = (uint32_t)__double2loint(p);
+    const uint32_t Xh = (uint32_t)__double2hiint(x), Xl = (uint32_t)__double2loint(x);
+    const int ep = (int)((Ph >> 20) & 0x7ff), ex = (int)((Xh >> 20) & 0x7ff);
+    const uint32_t ph = (Ph & 0xfffffu) | 0x100000u, xh = (Xh & 0xfffffu) | 0x100000u;
+    const uint64_t t = (uint64_t)g.gl * Pl;
+    const uint64_t t2 = (uint64_t)g.gh * Pl + (t >> 32);
+    const uint64_t t3 = (uint64_t)g.gl * ph + (uint32_t)t2;
+    const uint64_t t4 = (uint64_t)g.gh * ph + (t2 >> 32) + (t3 >> 32);
+    const uint32_t r0 = (uint32_t)t, m1 = (uint32_t)t3, m2 = (uint32_t)t4, m3 = (uint32_t)(t4 >> 32);
+    const int D = ex - g.eb - ep + 1075;
+    ok = ((unsigned)(ep - 1) < 0x7feu) & ((unsigned)(ex - 1) < 0x7feu) & ((unsigned)(D - 32) <= 30u);
+    const uint32_t b = (uint32_t)(D - 32) & 31u;
+    // x's significand << D: limbs 1, 2, 3 (limb 0 is zero)
+    const uint32_t x1 = Xl << b, x2 = __funnelshift_l(Xl, xh, b), x3 = __funnelshift_l(xh, 0u, b);
+    uint32_t r1, r2, r3;
+    asm("add.cc.u32 %0, %3, %6;\n\t"
+        "addc.cc.u32 %1, %4, %7;\n\t"
+        "addc.u32 %2, %5, %8;"
+        : "=r"(r1), "=r"(r2), "=r"(r3)
+        : "r"(m1), "r"(m2), "r"(m3), "r"(x1), "r"(x2), "r"(x3));
+    const int L = 127 - __clz((int)r3);  // 104 .. 115 in range
+    const uint32_t sh = (uint32_t)(L - 84) & 31u;
+    const uint32_t mlo = __funnelshift_r(r1, r2, sh), mhi = __funnelshift_r(r2, r3, sh);
+    const uint32_t k = (uint32_t)(L - 85) & 31u;  // the rounding bit L - 53 sits in limb 1
+    const uint32_t guard = (r1 >> k) & 1u, sticky = r0 | (r1 & ((1u << k) - 1u));
+    const uint32_t up = guard & ((sticky != 0u) | (mlo & 1u));
+    uint64_t mant = ((uint64_t)mhi << 32 | mlo) + up;
+    const uint32_t carry = (uint32_t)(mant >> 53);
+    const int eb = g.eb + ep + L - 1127 + (int)carry;
+    mant = carry ? (mant >> 1) : mant;
+    ok = ok & ((unsigned)(eb - 1) < 0x7feu);
+    const uint32_t s = (Ph >> 31) ^ g.s;
     const uint32_t hi = (s << 31) | ((uint32_t)eb << 20) | ((uint32_t)(mant >> 32) & 0xfffffu);
     return __hiloint2double((int)hi, (int)(uint32_t)mant);
 }

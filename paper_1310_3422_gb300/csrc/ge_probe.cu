@@ -64,7 +64,7 @@ __global__ void emu_check_kernel(double g, const double *__restrict__ p, const d
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const double want = __fma_rn(g, p[i], x[i]);
         bool ok;
-        const double e = ge::emu_fma<true>(eg, p[i], x[i], ok);
+        const double e = ge::emu_fma(eg, p[i], x[i], ok);
         if (ok && usable) {
             ++fast;
             bad += __double_as_longlong(e) != __double_as_longlong(want);
@@ -72,7 +72,7 @@ __global__ void emu_check_kernel(double g, const double *__restrict__ p, const d
         const unsigned same = ((unsigned)__double2hiint(p[i]) ^ (unsigned)__double2hiint(x[i]) ^
                                ((unsigned)eg.s << 31)) >> 31;
         if (same == 0u) {
-            const double e2 = ge::emu_fma<false>(eg, p[i], x[i], ok);
+            const double e2 = ge::emu_fma_add(eg, p[i], x[i], ok);
             if (ok && usable) {
                 ++fast_add;
                 bad += __double_as_longlong(e2) != __double_as_longlong(want);

@@ -369,8 +369,9 @@ __device__ __forceinline__ void stage_mid_hybrid(double (&v)[K], double L, doubl
 {
     double nv[K];
     bool ok = true;
-    // the cheaper form when every lane's emulated updates are additions (the
-    // product and x of the same sign: a smooth field of one sign)
+    // the cheaper, narrower form when every lane's emulated updates are
+    // additions (the product and x of the same sign: a smooth field of one
+    // sign)
     uint32_t anysub = 0;
 #pragma unroll
     for (int j = 0; j < K; ++j)
@@ -383,7 +384,7 @@ __device__ __forceinline__ void stage_mid_hybrid(double (&v)[K], double L, doubl
             const double p = pval<Q>(v, j, L, R);
             if (emu_reg<K, E>(j)) {
                 bool o;
-                nv[j] = emu_fma<true>(eg, p, v[j], o);
+                nv[j] = emu_fma(eg, p, v[j], o);
                 ok = ok && o;
             } else {
                 nv[j] = fma(g, p, v[j]);
@@ -395,7 +396,7 @@ __device__ __forceinline__ void stage_mid_hybrid(double (&v)[K], double L, doubl
             const double p = pval<Q>(v, j, L, R);
             if (emu_reg<K, E>(j)) {
                 bool o;
-                nv[j] = emu_fma<false>(eg, p, v[j], o);
+                nv[j] = emu_fma_add(eg, p, v[j], o);
                 ok = ok && o;
             } else {
                 nv[j] = fma(g, p, v[j]);
