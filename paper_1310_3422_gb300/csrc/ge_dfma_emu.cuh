@@ -23,7 +23,8 @@
 //     positive;
 //   - the top 53 bits below the leading one, rounded to nearest-even from the
 //     next bit and the OR of all bits below it;
-//   - the exponent from the product's and the leading bit's positions.
+//   - the exponent from the product's and the leading bit's positions, packed
+//     so that a carry out of the rounding moves into the exponent field.
 // Anything else (zeros, subnormals, infinities, NaNs, far-apart magnitudes,
 // results that cancel below bit 96 or leave the normal range) clears ok.
 #pragma once
@@ -47,6 +48,24 @@ __device__ __forceinline__ EmuG emu_g(double g)
 
 // g must be normal and nonzero for the fast path.
 __device__ __forceinline__ bool emu_g_usable(const EmuG &g) { return (unsigned)(g.eb - 1) < 0x7feu; }
+
+// The result's bits from its sign s, the biased exponent eb of its leading
+// bit, the 53-bit significand (mhi:mlo, leading 1 at bit 52) and the
+// rounding increment up.  The exponent field goes in as eb - 1 and the
+// significand's leading 1 adds the missing one; a carry out of the rounded
+// significand (all ones + 1 = 2^53) moves into the exponent field by itself
+// and leaves a zero fraction, so rounding needs no separate renormalisation.
+// ok stays set for eb in [1, 2045] (normal even after such a carry).
+__device__ __forceinline__ double emu_pack(uint32_t s, int eb, uint32_t mhi, uint32_t mlo, uint32_t up, bool &ok)
+{
+    ok = ok & ((unsigned)(eb - 1) < 0x7fdu);
+    uint32_t lo, hi;
+    asm("add.cc.u32 %0, %2, %3;\n\t"
+        "addc.u32 %1, %4, %5;"
+        : "=r"(lo), "=r"(hi)
+        : "r"(mlo), "r"(up), "r"(mhi), "r"((s << 31) + ((uint32_t)(eb - 1) << 20)));
+    return __hiloint2double((int)hi, (int)lo);
+}
 
 __device__ __forceinline__ double emu_fma(const EmuG &g, double p, double x, bool &ok)
 {
@@ -126,13 +145,7 @@ __device__ __forceinline__ double emu_fma(const EmuG &g, double p, double x, boo
         sticky = r0 | r1 | (r2 & ((1u << k) - 1u));
     }
     const uint32_t up = guard & ((sticky != 0u) | (mlo & 1u));
-    uint64_t mant = ((uint64_t)mhi << 32 | mlo) + up;
-    const uint32_t carry = (uint32_t)(mant >> 53);  // rounded up to 2^53
-    const int eb = g.eb + ep + L - 1127 + (int)carry;
-    mant = carry ? (mant >> 1) : mant;
-    ok = ok & ((unsigned)(eb - 1) < 0x7feu);
-    const uint32_t hi = (s << 31) | ((uint32_t)eb << 20) | ((uint32_t)(mant >> 32) & 0xfffffu);
-    return __hiloint2double((int)hi, (int)(uint32_t)mant);
+    return emu_pack(s, g.eb + ep + L - 1127, mhi, mlo, up, ok);
 }
 
 // The addition-only form for the common case, narrower still: the product
@@ -170,14 +183,7 @@ __device__ __forceinline__ double emu_fma_add(const EmuG &g, double p, double x,
     const uint32_t k = (uint32_t)(L - 85) & 31u;  // the rounding bit L - 53 sits in limb 1
     const uint32_t guard = (r1 >> k) & 1u, sticky = r0 | (r1 & ((1u << k) - 1u));
     const uint32_t up = guard & ((sticky != 0u) | (mlo & 1u));
-    uint64_t mant = ((uint64_t)mhi << 32 | mlo) + up;
-    const uint32_t carry = (uint32_t)(mant >> 53);
-    const int eb = g.eb + ep + L - 1127 + (int)carry;
-    mant = carry ? (mant >> 1) : mant;
-    ok = ok & ((unsigned)(eb - 1) < 0x7feu);
-    const uint32_t s = (Ph >> 31) ^ g.s;
-    const uint32_t hi = (s << 31) | ((uint32_t)eb << 20) | ((uint32_t)(mant >> 32) & 0xfffffu);
-    return __hiloint2double((int)hi, (int)(uint32_t)mant);
+    return emu_pack((Ph >> 31) ^ g.s, g.eb + ep + L - 1127, mhi, mlo, up, ok);
 }
 
 }  // namespace ge
