@@ -348,11 +348,11 @@ __device__ __forceinline__ void pair_mid(uint64_t (&p)[H], float L, float R, uin
 // FP64 registers per thread whose scaled update runs on the integer pipes
 // (emu_fma) instead of the FP64 unit, in the interior warps' block steps.
 #ifndef GE_EMU_F64
-#define GE_EMU_F64 6
+#define GE_EMU_F64 7
 #endif
 
 // Register j is one of the E emulated ones of K, spread evenly: j is taken
-// where floor(j E / K) steps up (E = 6 of K = 16: registers 2, 5, 7, 10, 13, 15).
+// where floor(j E / K) steps up (E = 7 of K = 16: registers 2, 4, 6, 9, 11, 13, 15).
 template <int K, int E>
 __device__ __forceinline__ constexpr bool emu_reg(int j)
 {

@@ -146,7 +146,7 @@ def test_debug_stall_checks_its_arguments(lib):
 
 def test_fp64_int_share_is_a_fraction(lib):
     """The share of the FP64 tiled kernel's interior updates on the integer
-    pipes: a build constant in [0, 1) (6 of a thread's 16 values by default)."""
+    pipes: a build constant in [0, 1) (7 of a thread's 16 values by default)."""
     share = B.ge_fp64_int_share()
     assert 0.0 <= share < 1.0
     assert share * 16 == round(share * 16)
