@@ -346,7 +346,8 @@ __device__ __forceinline__ void pair_mid(uint64_t (&p)[H], float L, float R, uin
 }
 
 // FP64 registers per thread whose scaled update runs on the integer pipes
-// (emu_fma) instead of the FP64 unit, in the interior warps' block steps.
+// (emu_fma) instead of the FP64 unit, in the interior warps' block steps of
+// the tiled and the batched FP64 kernels.
 #ifndef GE_EMU_F64
 #define GE_EMU_F64 7
 #endif
@@ -361,14 +362,15 @@ __device__ __forceinline__ constexpr bool emu_reg(int j)
 
 // The scaled mid stage x <- x + g x_partner in FP64 on a warp whose points
 // and partners all lie inside the grid, E registers per thread on the
-// integer pipes.  If any lane's emulated update leaves the fast path, the
-// warp recomputes its emulated registers on the FP64 unit, so the result is
-// always the FP64 unit's fma, bit for bit.
+// integer pipes.  If any lane's emulated update leaves the fast path (or a
+// lane passes usable = false), the warp recomputes its emulated registers on
+// the FP64 unit, so the result is always the FP64 unit's fma, bit for bit.
 template <int Q, int E, int K>
-__device__ __forceinline__ void stage_mid_hybrid(double (&v)[K], double L, double R, double g, const EmuG &eg)
+__device__ __forceinline__ void stage_mid_hybrid(double (&v)[K], double L, double R, double g, const EmuG &eg,
+                                                 bool usable = true)
 {
     double nv[K];
-    bool ok = true;
+    bool ok = usable;
     // the cheaper, narrower form when every lane's emulated updates are
     // additions (the product and x of the same sign: a smooth field of one
     // sign)

@@ -153,12 +153,18 @@ __device__ __forceinline__ void batch_mid_fixed(Real (&v)[K], Real L, Real R, co
 // on warps that hold boundaries.
 template <int Q, bool EDGE, typename Real, int K>
 __device__ __forceinline__ void batch_mid(Real (&v)[K], Real L, Real R, Span sp, const BatchFix &f,
-                                          const StageC<Real> &cm)
+                                          const StageC<Real> &cm, const EmuG &eg)
 {
-    if constexpr (EDGE)
+    if constexpr (EDGE) {
         batch_mid_fixed<Q>(v, L, R, f, cm.a, cm.s);
-    else
+    } else if constexpr (sizeof(Real) == 8 && GE_EMU_F64 > 0 && GE_EMU_F64 < K) {
+        // FP64 interior warps: GE_EMU_F64 of each thread's updates on the
+        // integer pipes (the FP64 unit's bits; the warp falls back if any lane
+        // cannot, or if the problem's g is not a normal number)
+        stage_mid_hybrid<Q, GE_EMU_F64>(v, L, R, cm.a, eg, emu_g_usable(eg));
+    } else {
         stage<Q, kMid, false>(v, L, R, sp, cm);
+    }
 }
 
 // Compensated block step on a warp that holds problem boundaries (the
@@ -328,6 +334,9 @@ __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &
     }
     const StageC<Real> cm{(Real)bd.g, (Real)0, (Real)bd.kap_s, (Real)0, (Real)0};
     const BatchFix fx = batch_fix<K>(pid, sp);
+    // an interior (non-edge) warp holds rows of one problem only: lane 0's g
+    // is the warp's (the edge path does not use it)
+    const EmuG eg = emu_g(__shfl_sync(0xffffffffu, bd.g, 0));
     if constexpr (!EDGE && sizeof(Real) == 4 && K % 4 == 0) {
         // interior FP32 warps: the same steps and rescalings on register
         // pairs (packed FMAs; the same bits)
@@ -370,16 +379,16 @@ __device__ __forceinline__ void run_batch_scaled(Real (&v)[K], const TbbParams &
         int i = 0;
         if (((rd.p_first + m) & 1) == 1) {
             exchange(v, L, R, x);
-            batch_mid<1, EDGE>(v, L, R, sp, fx, cm);
+            batch_mid<1, EDGE>(v, L, R, sp, fx, cm, eg);
             i = 1;
         }
         for (; i + 1 < cnt; i += 2) {
-            batch_mid<0, EDGE>(v, L, R, sp, fx, cm);
+            batch_mid<0, EDGE>(v, L, R, sp, fx, cm, eg);
             exchange(v, L, R, x);
-            batch_mid<1, EDGE>(v, L, R, sp, fx, cm);
+            batch_mid<1, EDGE>(v, L, R, sp, fx, cm, eg);
         }
         if (i < cnt)
-            batch_mid<0, EDGE>(v, L, R, sp, fx, cm);
+            batch_mid<0, EDGE>(v, L, R, sp, fx, cm, eg);
         m += cnt;
         if (cnt == P.R) {
             // every lane takes part (the FP64 form decides warp-wide); a lane
