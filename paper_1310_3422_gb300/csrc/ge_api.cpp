@@ -231,7 +231,7 @@ ge_status run_tiled(ge_ctx *c, int64_t steps, int depth, bool df = false)
     t.n = c->n;
     t.n_rows = c->n_rows;
     t.err = c->err_dev;
-    t.tile_ctr = c->err_dev + 48;
+    t.tile_ctr = c->err_dev + 48;  // two tile-queue words (48, 49)
     t.grid_cap = (long long)c->num_sms * (df ? c->tb_df_blocks_per_sm : c->tb_blocks_per_sm);
     const cudaError_t e = ge::tb_run(t, base, growth_lo, df, prec, &c->cur, c->step, steps, depth, c->stream);
     if (e == cudaErrorInvalidValue)

@@ -100,8 +100,11 @@ struct TbParams {
     int df_out;           // write doubles, else (hi, lo) float pairs
     int df_gl;            // the pair of g = 2r has a nonzero low part
     const int *df_code;   // prescale exponent word written by df_prescale
-    int *tile_ctr;        // dynamic tile queue: zeroed before the launch; CTA b takes
+    int *tile_ctr;        // dynamic tile queue: zero at the launch's start; CTA b takes
                           // queue position b first, then gridDim.x + atomicAdd(tile_ctr, 1)
+    int *tile_ctr_next;   // the next launch's queue word, zeroed by this launch (CTA 0);
+                          // the launches of a stream alternate between two words, so no
+                          // memset runs between them
     float dfc[7][2];      // (hi, lo) of g, kappa, r, 1 - r, x1, x2, xs
 };
 
@@ -296,7 +299,7 @@ struct TbTarget {
     void *buf[2];
     long long n, n_rows;
     int *err;
-    int *tile_ctr;
+    int *tile_ctr;        // two tile-queue words (alternating launches)
     long long grid_cap;   // SMs x co-resident CTAs per SM
 };
 // Issue the launches of `steps` steps from global step `step0`, `depth` steps

@@ -195,7 +195,7 @@ extern "C" ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double
         t.n = n;
         t.n_rows = n_rows;
         t.err = err;
-        t.tile_ctr = err + 48;  // the launch's tile queue, zeroed before each launch
+        t.tile_ctr = err + 48;  // the launches' two tile-queue words (48, 49)
         t.grid_cap = (long long)sms * bps;
         e = ge::tb_run(t, base_p, growth_lo, false, pidx, &cur, 0, steps, d, s);
         if (e == cudaErrorInvalidValue)

@@ -313,6 +313,9 @@ __global__ void __launch_bounds__(Layout<Real, COMP>::NT, Layout<Real, COMP>::MI
         mbar_init(&mbar[1], 1);
         mbar_init(&mbar[2], 1);
         fence_mbar_init();
+        // the next launch's tile queue starts empty (it runs after this one)
+        if (blockIdx.x == 0 && P.tile_ctr_next)
+            *P.tile_ctr_next = 0;
     }
     __syncthreads();
 

@@ -66,6 +66,14 @@ cudaError_t tb_run(const TbTarget &t, const TbParams &base, double growth_lo, bo
     double sigma = 1.0, sigma_lo = 0.0;  // double-double scale
     int until = every;
     long long n0 = 0;
+    // the tiled launches' queue words: both zero now; each launch zeroes the
+    // one the next launch uses
+    int k_tiled = 0;
+    if (steps > 0) {
+        const cudaError_t e = cudaMemsetAsync(t.tile_ctr, 0, 2 * sizeof(int), s);
+        if (e != cudaSuccess)
+            return e;
+    }
     while (n0 < steps) {
         const long long L = (steps - n0 < depth) ? steps - n0 : depth;
         TbParams p = base;
@@ -109,7 +117,8 @@ cudaError_t tb_run(const TbTarget &t, const TbParams &base, double growth_lo, bo
         p.n_tiles = (t.n + p.U - 1) / p.U;
         p.out = t.buf[*cur ^ 1];
         p.err = t.err;
-        p.tile_ctr = t.tile_ctr;
+        p.tile_ctr = t.tile_ctr + (k_tiled & 1);
+        p.tile_ctr_next = t.tile_ctr + ((k_tiled + 1) & 1);
         long long grid = t.grid_cap;
         if (grid > p.n_tiles)
             grid = p.n_tiles;
@@ -120,10 +129,8 @@ cudaError_t tb_run(const TbTarget &t, const TbParams &base, double growth_lo, bo
             // one FP32 block step and nothing else: an HBM stream, no tiles
             e = launch_tb_stream(prec, t.buf[*cur], p.out, p, s);
         } else {
-            // the launch's tile queue starts empty
-            e = cudaMemsetAsync(p.tile_ctr, 0, sizeof(int), s);
-            if (e == cudaSuccess)
-                e = df ? launch_tb_df(t.tmap[*cur], p, (int)grid, s) : launch_tb(prec, t.tmap[*cur], p, (int)grid, s);
+            e = df ? launch_tb_df(t.tmap[*cur], p, (int)grid, s) : launch_tb(prec, t.tmap[*cur], p, (int)grid, s);
+            ++k_tiled;
         }
         if (e != cudaSuccess)
             return e;
