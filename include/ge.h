@@ -347,6 +347,14 @@ ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double beta_r, ge
                            int32_t depth, int64_t steps, const void *u0_dev, void *u_out_dev,
                            void *stream);
 
+/* Whether the FP64 tiled kernel of this context computes part of its
+ * interior updates as exact FP64 multiply-adds on the integer pipes (on = 1,
+ * the default; see ge_fp64_int_share) or all of them on the FP64 unit
+ * (on = 0).  The results are the same bits either way; the switch exists to
+ * compare the two.  Affects later GE_KERNEL_TEMPORAL / ONESTEP steps of
+ * GE_F64 contexts.  Errors: GE_EINVAL (NULL ctx, on not 0 or 1). */
+ge_status ge_set_int_pipes(ge_ctx *ctx, int32_t on);
+
 /* Build information: the fraction of the FP64 tiled kernel's interior
  * updates (GE_KERNEL_TEMPORAL, GE_F64, threads whose points and partners
  * all lie inside the grid) computed as exact FP64 multiply-adds on the

@@ -31,7 +31,7 @@ EXPORTS = ("ge_create", "ge_set_kernel", "ge_set_subdomain_width", "ge_step_n", 
            "ge_batch_sync",
            "ge_batch_destroy",
            "ge_solve_batch", "ge_solve_noalloc", "ge_status_str", "ge_last_error", "ge_debug_stall",
-           "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune", "ge_probe_fma", "ge_fp64_int_share",
+           "ge_batch_debug_stall", "ge_batch_check", "ge_get_kernel", "ge_tune", "ge_probe_fma", "ge_fp64_int_share", "ge_set_int_pipes",
            "ge_emu_fma_check",
            "ge_sno_create", "ge_sno_num_params", "ge_sno_get_params", "ge_sno_set_params",
            "ge_sno_set_precision", "ge_sno_set_tensor_cores", "ge_sno_get_tensor_cores", "ge_sno_sync", "ge_sno_forward", "ge_sno_loss_grad", "ge_sno_adam_step",
@@ -123,6 +123,8 @@ def load(path: str | None = None):
         lib.ge_solve_noalloc.restype = ctypes.c_int
         lib.ge_probe_fma.argtypes = [_I32, _I32, _I32, _I64, _VP, _VP]
         lib.ge_probe_fma.restype = ctypes.c_int
+        lib.ge_set_int_pipes.argtypes = [_VP, _I32]
+        lib.ge_set_int_pipes.restype = ctypes.c_int
         lib.ge_fp64_int_share.argtypes = [ctypes.POINTER(ctypes.c_double)]
         lib.ge_fp64_int_share.restype = ctypes.c_int
         lib.ge_emu_fma_check.argtypes = [ctypes.c_double, _VP, _VP, _I64, _VP, _VP]
@@ -464,6 +466,10 @@ def ge_solve_noalloc(n: int, r: float, beta_l: float, beta_r: float, prec: int, 
 
 
 PROBE_THREADS = 256
+
+
+def ge_set_int_pipes(ctx: Ctx, on: int):
+    _check(load().ge_set_int_pipes(ctx.handle, int(on)), "ge_set_int_pipes")
 
 
 def ge_fp64_int_share() -> float:

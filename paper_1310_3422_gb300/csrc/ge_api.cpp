@@ -435,6 +435,14 @@ ge_status ge_set_kernel(ge_ctx *c, ge_kernel kernel, int32_t depth)
     return GE_OK;
 }
 
+ge_status ge_set_int_pipes(ge_ctx *c, int32_t on)
+{
+    if (!c || (on != 0 && on != 1))
+        return fail(GE_EINVAL, "ge_set_int_pipes: NULL ctx or on not 0/1");
+    c->tb.emu = on;
+    return GE_OK;
+}
+
 ge_status ge_get_kernel(const ge_ctx *c, ge_kernel *kernel, int32_t *depth)
 {
     if (!c || !kernel || !depth)

@@ -102,6 +102,8 @@ struct TbParams {
     const int *df_code;   // prescale exponent word written by df_prescale
     int *tile_ctr;        // dynamic tile queue: zero at the launch's start; CTA b takes
                           // queue position b first, then gridDim.x + atomicAdd(tile_ctr, 1)
+    int emu;              // FP64: part of the interior updates on the integer pipes (1) or
+                          // every update on the FP64 unit (0); the same bits either way
     int *tile_ctr_next;   // the next launch's queue word, zeroed by this launch (CTA 0);
                           // the launches of a stream alternate between two words, so no
                           // memset runs between them

@@ -61,7 +61,7 @@ __device__ __forceinline__ void mid_scaled(Real (&v)[K], double &sig, const TbPa
         c.fr = (Real)(sig * P.f_r);
     }
     if constexpr (!EDGE && sizeof(Real) == 8 && GE_EMU_F64 > 0 && GE_EMU_F64 < K) {
-        if (emu_g_usable(eg)) {
+        if (P.emu && emu_g_usable(eg)) {
             stage_mid_hybrid<Q, GE_EMU_F64>(v, L, R, g, eg);
             return;
         }

@@ -22,6 +22,7 @@ void tb_fill_base(double r, double beta_l, double beta_r, int prec, TbParams *ou
     // exactly), so no systematic scale error builds up over many steps.
     scaled_growth(r, prec == 1, &p.onepg, growth_lo);
     p.stall = 0;
+    p.emu = 1;
     p.r = r;
     p.omr = 1.0 - r;
     p.d = 2.0 * r / det;

@@ -94,3 +94,56 @@ def test_results_near_the_range_limits():
 
 def test_share_is_reported():
     assert 0.0 <= B.ge_fp64_int_share() < 1.0
+
+
+def _solve(u0, r, bl, br, steps, on, kernel, depth):
+    n = len(u0)
+    ctx = B.ge_create(n, r, bl, br, B.GE_F64, torch.tensor(u0, device=DEV))
+    B.ge_set_kernel(ctx, kernel, depth)
+    B.ge_set_int_pipes(ctx, on)
+    B.ge_step_n(ctx, steps)
+    out = torch.empty(n, dtype=torch.float64, device=DEV)
+    B.ge_read_state(ctx, out)
+    torch.cuda.synchronize()
+    B.ge_destroy(ctx)
+    return out.cpu().numpy()
+
+
+def _initial(kind, n, seed):
+    rng = np.random.default_rng(seed)
+    x = np.arange(1, n + 1) / (n + 1)
+    if kind == "smooth":
+        return np.sin(np.pi * x) + 0.3 * np.sin(7 * np.pi * x)
+    if kind == "signs":  # a sign change between most neighbours
+        return rng.standard_normal(n)
+    if kind == "zeros":  # exact zeros in blocks, isolated spikes
+        u = np.sin(np.pi * x)
+        u[(np.arange(n) // 5000) % 3 == 1] = 0.0
+        u[rng.integers(0, n, 50)] = 1e6
+        return u
+    # magnitudes over 400 decades, so the integer form's window is often left
+    return rng.standard_normal(n) * 10.0 ** rng.uniform(-200, 200, n)
+
+
+@pytest.mark.parametrize("kind", ["smooth", "signs", "zeros", "range"])
+@pytest.mark.parametrize("r", [0.3, 2.0, 3.7])
+@pytest.mark.parametrize("kernel,depth", [(B.GE_KERNEL_TEMPORAL, 48), (B.GE_KERNEL_TEMPORAL, 7),
+                                          (B.GE_KERNEL_ONESTEP, 0)])
+def test_kernel_bits_do_not_depend_on_the_integer_pipes(kind, r, kernel, depth):
+    """The FP64 tiled kernel with part of its updates on the integer pipes
+    and with every update on the FP64 unit: the same bits on every point,
+    whatever the data do to the integer form's fast path (fallbacks for
+    zeros, sign changes, magnitude gaps).  300,000 points span many tiles;
+    301 steps span entry, middle and exit launches and rescalings."""
+    u0 = _initial(kind, 300_000, seed=int(r * 10) + len(kind))
+    steps = 301 if kernel == B.GE_KERNEL_TEMPORAL else 41
+    on = _solve(u0, r, 0.25, -0.5, steps, 1, kernel, depth)
+    off = _solve(u0, r, 0.25, -0.5, steps, 0, kernel, depth)
+    assert np.array_equal(on.view(np.uint64), off.view(np.uint64))
+
+
+def test_int_pipes_switch_rejects_bad_values():
+    ctx = B.ge_create(64, 1.0, 0.0, 0.0, B.GE_F64)
+    with pytest.raises(B.GeError):
+        B.ge_set_int_pipes(ctx, 2)
+    B.ge_destroy(ctx)
