@@ -151,3 +151,8 @@ def test_fp64_int_share_is_a_fraction(lib):
     assert 0.0 <= share < 1.0
     assert share * 16 == round(share * 16)
     assert lib.ge_fp64_int_share(None) == B.GE_EINVAL
+
+
+def test_int_pipes_switch_checks_its_arguments(lib):
+    assert lib.ge_set_int_pipes(None, 1) == B.GE_EINVAL
+    assert lib.ge_emu_fma_check(1.0, None, None, 0, None, None) == B.GE_EINVAL
