@@ -373,14 +373,13 @@ __device__ __forceinline__ void stage_mid_hybrid(double (&v)[K], double L, doubl
     bool ok = usable;
     // the cheaper, narrower form when every lane's emulated updates are
     // additions (the product and x of the same sign: a smooth field of one
-    // sign)
-    uint32_t anysub = 0;
+    // sign); taken for g > 0 only, where that is sign(x_partner) == sign(x)
+    uint32_t diff = eg.s << 31;
 #pragma unroll
     for (int j = 0; j < K; ++j)
         if (emu_reg<K, E>(j))
-            anysub |= ((((uint32_t)__double2hiint(pval<Q>(v, j, L, R)) ^ (uint32_t)__double2hiint(v[j])) >> 31) ^
-                       eg.s);
-    if (__any_sync(0xffffffffu, anysub != 0u)) {
+            diff |= (uint32_t)__double2hiint(pval<Q>(v, j, L, R)) ^ (uint32_t)__double2hiint(v[j]);
+    if (__any_sync(0xffffffffu, (diff >> 31) != 0u)) {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const double p = pval<Q>(v, j, L, R);
