@@ -356,10 +356,11 @@ ge_status ge_solve_noalloc(int64_t n, double r, double beta_l, double beta_r, ge
 ge_status ge_set_int_pipes(ge_ctx *ctx, int32_t on);
 
 /* Build information: the fraction of the FP64 tiled kernel's interior
- * updates (GE_KERNEL_TEMPORAL, GE_F64, threads whose points and partners
- * all lie inside the grid) computed as exact FP64 multiply-adds on the
- * integer pipes instead of the FP64 unit (the scaled block step of Sec. 2,
- * x <- x + 2r x_partner; same bits either way).  A warp whose emulated
+ * updates (GE_KERNEL_TEMPORAL and ONESTEP, GE_F64, threads whose points and
+ * partners all lie inside the grid; the batched FP64 kernel of ge_batch_*
+ * takes the same share in its interior warps) computed as exact FP64
+ * multiply-adds on the integer pipes instead of the FP64 unit (the scaled
+ * block step of Sec. 2, x <- x + 2r x_partner; same bits either way).  A warp whose emulated
  * updates leave the integer fast path in a step (zeros, subnormals, far-apart
  * magnitudes) recomputes them on the FP64 unit, so the realised share can
  * be lower.  *share (host) receives the build's share, 0 when disabled.
